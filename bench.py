@@ -1,0 +1,422 @@
+"""Benchmark: QFactor gate-updates/s at 12 qubits on one GB300.
+
+Workload: 12-qubit linear brickwork of 12 layers (66 general U(4) gates),
+target reachable from seeded Haar-random gates, 8 seeded Haar starts, circuit
+tensors in complex64 (4x4 updates in FP64).  One step = one TwoSidedSweep of
+all 8 starts = 8 x 132 = 1056 gate updates; the tensors are rebuilt from the
+target every 40 sweeps as in Qfactor.  The 8 tensors hold 1.07 GB, far more
+than L2, so no L2 flush is needed between steps.
+
+Prints one JSON line (see the repository's benchmark contract).  With
+``--impl reference`` it times the FP64 CPU oracle instead, on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import qf_inputs as qi  # noqa: E402
+
+N_QUBITS = 12
+LAYERS = 12
+STARTS = 8
+SEED = 2024
+METRIC = "gate-updates/s at 12 qubits (% HBM roofline)"
+UNIT = "gate-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--starts", type=int, default=STARTS)
+    ap.add_argument("--qubits", type=int, default=N_QUBITS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="timed CPU work of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def workload(n, starts):
+    locs = qi.brickwork_locations(n, LAYERS)
+    inst = qi.make_problem(n, locs, starts, seed=SEED)
+    return inst
+
+
+def config_dict(args, inst):
+    prec = "complex64 tensor, FP64 4x4 update" if args.precision == "c64" else "complex128 tensor, FP64"
+    return {
+        "workload": f"{inst.n}-qubit linear brickwork, {LAYERS} layers ({inst.p} U(4) gates), "
+                    f"{inst.n_starts} starts per GPU, reachable Haar target, {prec}",
+        "n_qubits": inst.n,
+        "n_gates": inst.p,
+        "starts_per_gpu": inst.n_starts,
+        "precision": args.precision,
+        "updates_per_step_per_gpu": inst.n_starts * 2 * inst.p,
+        "step": "one TwoSidedSweep of every start (rebuild every 40 sweeps)",
+        "l2": "no flush: the circuit tensors (%.2f GB) exceed L2" % (
+            inst.n_starts * 4**inst.n * (8 if args.precision == "c64" else 16) / 1e9),
+        "parallelism": "replicas (independent starts per GPU)",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        try:
+            sm = [float(r[1]) for r in rows]
+            smax = max(float(r[2]) for r in rows)
+        except ValueError:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("[N/A]", ""))
+                if any(r[3] not in ("[N/A]", "") for r in rows) else None}
+
+
+# ------------------------------------------------------------------ helpers
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(precision, starts, n):
+    """DRAM bytes per pass launch from a committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "pass_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_2306_08152_gb300", "csrc", "qf_kernels.cu")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()
+    if d.get("kernel_sha256") != h:
+        return None
+    key = f"{precision}"
+    entry = d.get("per_launch", {}).get(key)
+    if not entry:
+        return None
+    # scale a capture of a smaller case by the entries processed
+    scale = (starts * 4**n) / float(entry["entries"])
+    return entry["dram_bytes"] * scale
+
+
+def oracle_sample(inst, seconds, max_updates=None):
+    """Time the oracle's gate updates (Alg. 1 TwoSidedSweep backward steps)
+    on start 0 of the workload.  Setup (the target and the initial circuit
+    tensor, built by the oracle) is untimed."""
+    import oracle as orc
+
+    n, locs = inst.n, inst.locs
+    V = orc.circuit_unitary(inst.target_gates, locs, n)
+    T = orc.init_circuit_tensor(V, inst.starts[0], locs, n)
+    gates = inst.starts[0].copy()
+    p = len(locs)
+    done = 0
+    w0 = time.perf_counter()
+    c0 = time.process_time()
+    k = p - 1
+    while True:
+        a, b = int(locs[k][0]), int(locs[k][1])
+        T = orc.apply_right(T, gates[k].conj().T, a, b, n)
+        E = orc.calc_env_mat(T, a, b, n)
+        u, _ = orc.optimize_gate(E)
+        gates[k] = u
+        T = orc.apply_left(T, u, a, b, n)
+        done += 1
+        k = (k - 1) % p
+        el = time.perf_counter() - w0
+        if el >= seconds or (max_updates and done >= max_updates):
+            break
+    wall = time.perf_counter() - w0
+    cpu = time.process_time() - c0
+    return done, wall, cpu
+
+
+# ------------------------------------------------------------------ reference arm
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    inst = workload(args.qubits, 1)
+    import oracle as orc  # noqa: F401
+
+    # warm-up samples of one update each, then K timed samples of 2 updates
+    for _ in range(args.warmup):
+        oracle_sample_cached(inst, 1)
+    total_updates = 0
+    total_wall = 0.0
+    total_cpu = 0.0
+    for _ in range(args.steps):
+        d, w, c = oracle_sample_cached(inst, 2)
+        total_updates += d
+        total_wall += w
+        total_cpu += c
+    value = total_updates / total_wall
+    cores = round(total_cpu / total_wall, 2)
+    cfg = config_dict(args, inst)
+    cfg["starts_per_gpu"] = 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{total_updates} gate updates (ApplyRight, CalcEnvMat, "
+                                   f"OptimizeGate, ApplyLeft) of the FP64 NumPy oracle on one "
+                                   f"start, {inst.n} qubits; 2 updates per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+_ORACLE_STATE = {}
+
+
+def oracle_sample_cached(inst, updates):
+    """Like oracle_sample, but keeps the oracle's tensor between calls so
+    that each reference step times only its own updates."""
+    import oracle as orc
+
+    st = _ORACLE_STATE.get(id(inst))
+    n, locs = inst.n, inst.locs
+    if st is None:
+        V = orc.circuit_unitary(inst.target_gates, locs, n)
+        T = orc.init_circuit_tensor(V, inst.starts[0], locs, n)
+        st = {"T": T, "gates": inst.starts[0].copy(), "k": len(locs) - 1}
+        _ORACLE_STATE[id(inst)] = st
+    w0 = time.perf_counter()
+    c0 = time.process_time()
+    for _ in range(updates):
+        k = st["k"]
+        a, b = int(locs[k][0]), int(locs[k][1])
+        T = orc.apply_right(st["T"], st["gates"][k].conj().T, a, b, n)
+        E = orc.calc_env_mat(T, a, b, n)
+        u, _ = orc.optimize_gate(E)
+        st["gates"][k] = u
+        st["T"] = orc.apply_left(T, u, a, b, n)
+        st["k"] = (k - 1) % len(locs)
+    return updates, time.perf_counter() - w0, time.process_time() - c0
+
+
+# ------------------------------------------------------------------ our arm
+
+
+def run_ours(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2306_08152_gb300 as qf
+
+    qf._native.load()
+    inst = workload(args.qubits, args.starts)
+    n, locs = inst.n, inst.locs
+    # replicas: rank r runs its own seeded starts (seed offset by rank)
+    if rank > 0:
+        inst = qi.make_problem(n, locs, args.starts, seed=SEED + 1000 * rank)
+    prec = qf.QF_C64 if args.precision == "c64" else qf.QF_C128
+    stream = torch.cuda.current_stream(dev)
+    V = qf.circuit_unitary(n, locs, torch.from_numpy(inst.target_gates), device=dev)
+    starts = torch.from_numpy(inst.starts).to(dev)
+    plan = qf.Plan(n, locs, inst.n_starts, prec)
+    plan.load(V, starts, stream=stream)
+    for _ in range(args.warmup):
+        plan.sweep(1, reset_iter=40)
+    plan.costs()
+    plan.pass_stats()  # reset counters
+    plan.enable_pass_timing(True)
+
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.sweep(1, reset_iter=40)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    pass_ms, pass_launches, all_launches = plan.pass_stats()
+    plan.enable_pass_timing(False)
+    if plan.status() != 0:
+        raise RuntimeError("device status reports a non-finite update")
+    costs = plan.costs()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    updates_per_step = inst.n_starts * 2 * inst.p * world
+    value = updates_per_step * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel (the fused pass)
+    eb = 8 if args.precision == "c64" else 16
+    alg_bytes = inst.n_starts * 4**n * 2 * eb  # one read + one write of every tensor
+    avg_pass_s = (pass_ms / 1e3) / max(pass_launches, 1)
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / avg_pass_s / 1e9
+    traffic = kernel_traffic(args.precision, inst.n_starts, n)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "pass_kernel (fused B <- L B R over every 4x4 block)",
+                "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_pass_s * 1e3,
+                "pass_share_of_step": (pass_ms / ms) if ms > 0 else None}
+    if args.precision == "c128":
+        fp64_peak = 1250.0  # GFLOP/s nominal FP64 (no measured FP64 peak on this machine)
+        flops = inst.n_starts * 4**n * 64
+        roofline_fp64 = flops / avg_pass_s / 1e9
+        roofline = {"bound": "alu", "achieved": roofline_fp64, "peak": fp64_peak, "unit": "GFLOP/s",
+                    "frac": roofline_fp64 / fp64_peak, "traffic": traffic,
+                    "kernel": roofline["kernel"],
+                    "peak_source": "nominal FP64 1.25 TFLOP/s (64 FP64 flops per entry)",
+                    "hbm_gbs": achieved, "hbm_frac": achieved / peak, "avg_launch_ms": avg_pass_s * 1e3}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        V_h = V.cpu().pin_memory()
+        starts_h = starts.cpu().pin_memory()
+        opts = qf.Options(dist_tol=0.0, max_sweeps=1,
+                          precision=qf.QF_C64 if args.precision == "c64" else qf.QF_C128)
+        e2e_steps = max(1, min(args.steps, 10))
+        qf.instantiate_ex(V_h, locs, starts_h, options=opts, stream=stream)  # warm-up
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            r = qf.instantiate_ex(V_h, locs, starts_h, options=opts, stream=stream)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        h2d = V_h.numel() * 16 + starts_h.numel() * 16 + locs.size * 4
+        d2h = starts_h.numel() * 16 + inst.n_starts * 8
+        e2e = {"value": updates_per_step * e2e_steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": e2e_steps,
+               "call": "qf_instantiate_ex(host target, host starts, max_sweeps=1): "
+                       "allocation, H2D, InitCircuitTensor, one sweep, D2H"}
+        del r
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        done, wall, cput = oracle_sample(inst, args.cpu_seconds)
+        cpu = {"value": done / wall, "unit": UNIT, "cores": round(cput / wall, 2), "kind": "oracle",
+               "sample": f"{done} gate updates (ApplyRight, CalcEnvMat, OptimizeGate, ApplyLeft) "
+                         f"of the FP64 NumPy oracle on start 0 of the same {n}-qubit workload, "
+                         f"{wall:.1f} s wall; cores = CPU time / wall time"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64" if args.precision == "c64" else "c128",
+            "data": "synthetic", "config": config_dict(args, inst),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(all_launches), "clocks": clock_info,
+            "final_costs": [float(c) for c in costs],
+        }
+        print(json.dumps(line))
+    plan.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,281 @@
+/*
+ * qfactor.h -- C ABI of the GB300 QFactor instantiation engine.
+ *
+ * QFactor (Kukliansky, Younis, Cincio, Iancu, arXiv 2306.08152) fits the
+ * gates of a circuit of general two-qubit unitaries to a target unitary V by
+ * sweeping over one 2^n x 2^n complex circuit tensor T (Sec. III, Alg. 1).
+ * Every step of the sweep runs in hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions (shared with the test oracle):
+ *   - N = 2^n.  Qubit 0 is the most significant bit of a basis index.
+ *   - A gate is 16 qf_c128 values, a 4x4 matrix in row-major order.  A gate on
+ *     location (a, b) acts on the local index 2*bit(a) + bit(b), tensored with
+ *     the identity on every other qubit; (b, a) is SWAP u SWAP on (a, b).
+ *   - Gate lists are in product order: C = G_0 G_1 ... G_{p-1}, where list
+ *     index 0 is the paper's u_1 (Sec. III: U = u_1 ... u_p).
+ *   - Matrices (targets, circuit tensors) are row-major, entry (r, c) at
+ *     r*N + c, interleaved complex (re, im).
+ *   - Circuit tensors hold T = V^dagger C after initialisation (Alg. 1,
+ *     InitCircuitTensor).  In precision QF_C128 an entry is a qf_c128
+ *     (16 bytes); in QF_C64 it is a qf_c64 (8 bytes).  Several starts are
+ *     stored back to back: start s begins at entry s*N*N.
+ *   - The environment of gate k is E_k = Tr_{other qubits}(G_{k+1}...G_{p-1}
+ *     V^dagger G_0...G_{k-1}), so Tr(V^dagger C) = Tr(E_k u_k) (Sec. III,
+ *     environment matrix, Fig. 3).  dTr(V^dagger C)/d(u_k)_{ij} = (E_k)_{ji}.
+ *   - Cost: 1 - |Tr(V^dagger C)| / N (Sec. II, Delta).
+ *
+ * Memory: "device" arguments are CUDA device pointers in the current
+ * context; "host-or-device" arguments may be either (the library inspects the
+ * pointer and copies host data itself).  The caller owns every argument
+ * array.  The library allocates its own workspace (circuit tensors) with
+ * cudaMalloc and frees it before a call returns, except inside a qf_plan,
+ * which owns its workspace until qf_plan_destroy.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls that return host values synchronise that stream; the
+ * others only enqueue work.
+ *
+ * Errors: every call returns QF_OK (0) or a negative QF_E* code, and
+ * qf_last_error() returns a message for the calling thread's last failure.
+ * Output arrays are unspecified after a failure.
+ */
+#ifndef QFACTOR_H
+#define QFACTOR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } qf_c128;   /* same layout as cuDoubleComplex */
+typedef struct { float re, im; } qf_c64;     /* same layout as cuFloatComplex  */
+typedef struct { int32_t a, b; } qf_loc;     /* gate location: qubits a != b  */
+
+/* Return codes. */
+#define QF_OK            0
+#define QF_EINVAL       -1   /* bad size, location, NULL pointer or option   */
+#define QF_ENOMEM       -2   /* device allocation failed                     */
+#define QF_ECUDA        -3   /* a CUDA runtime call failed                   */
+#define QF_ENONFINITE   -4   /* NaN/Inf in an input or in an environment     */
+
+/* Circuit-tensor precision. */
+#define QF_C128          0   /* complex128 tensor, FP64 arithmetic throughout */
+#define QF_C64           1   /* complex64 tensor, FP32 gate application; the
+                                partial trace accumulates and the 4x4 update
+                                runs in FP64 */
+#define QF_C64_REFINE64  2   /* bulk sweeps in QF_C64, then the tensor is
+                                rebuilt in QF_C128 for the final sweeps    */
+
+/* Termination reasons. */
+#define QF_STOP_CONVERGED   1   /* some start reached dist_tol               */
+#define QF_STOP_PLATEAU     2   /* every start met a plateau test            */
+#define QF_STOP_MAX_SWEEPS  3
+
+/* Supported sizes. */
+#define QF_MIN_QUBITS 2
+#define QF_MAX_QUBITS 14
+
+/*
+ * Hyperparameters of Sec. III-A2.  qf_options_default() fills: dist_tol 1e-10,
+ * max_sweeps 500, min_sweeps 0, reset_iter 40, diff_tol_a 0, diff_tol_r 0,
+ * long_diff_count 0, long_diff_r 0.1, beta 0, precision QF_C128,
+ * switch_tol 1e-6, max_c64_sweeps 1000.
+ *   dist_tol      stop once a start's cost is <= dist_tol.
+ *   max_sweeps    upper bound on two-sided sweeps (all phases together).
+ *   min_sweeps    no stopping test before this many sweeps.
+ *   reset_iter    rebuild every tensor from V and the gates after every
+ *                 reset_iter sweeps (0 = never).
+ *   diff_tol_a/r  short plateau: a start plateaus when
+ *                 c_{i-1} - c_i <= diff_tol_a + diff_tol_r * c_i
+ *                 (off when both are 0).
+ *   long_diff_count/_r  long plateau: c_{i-L} - c_i < long_diff_r * c_{i-L},
+ *                 L = long_diff_count (off when 0).
+ *   beta          the update takes the SVD of (1-beta) E + beta u^dagger.
+ *   precision     QF_C128, QF_C64 or QF_C64_REFINE64.
+ *   switch_tol    QF_C64_REFINE64: leave the c64 phase once the best cost is
+ *                 <= switch_tol, or once a c64 sweep lowers no start's cost
+ *                 by more than 1e-3 of its value, or after max_c64_sweeps.
+ */
+typedef struct {
+    double dist_tol;
+    int32_t max_sweeps;
+    int32_t min_sweeps;
+    int32_t reset_iter;
+    int32_t long_diff_count;
+    double diff_tol_a;
+    double diff_tol_r;
+    double long_diff_r;
+    double beta;
+    int32_t precision;
+    int32_t max_c64_sweeps;
+    double switch_tol;
+} qf_options;
+
+/* Result summary of an instantiation. */
+typedef struct {
+    int32_t best_start;   /* start with the lowest final cost               */
+    int32_t sweeps;       /* sweeps run (all phases)                        */
+    int32_t c64_sweeps;   /* of which in complex64                          */
+    int32_t reason;       /* QF_STOP_*                                      */
+    double best_cost;     /* cost of best_start, from an FP64 trace          */
+} qf_result;
+
+/* Message for the calling thread's last error ("" if none). */
+const char* qf_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int qf_version(void);
+
+/* Fill *opts with the defaults listed above.  Returns QF_EINVAL on NULL. */
+int qf_options_default(qf_options* opts);
+
+/*
+ * qf_instantiate -- Qfactor of Alg. 1 for one start, in QF_C128.
+ *   target         host-or-device, N x N unitary V.
+ *   n_qubits       2 .. QF_MAX_QUBITS.
+ *   n_gates        p >= 1.
+ *   locations      host-or-device, p locations.
+ *   initial_gates  host-or-device, p x 16.
+ *   tol            dist_tol; max_sweeps >= 1.
+ *   out_gates      host-or-device, p x 16 (may alias initial_gates).
+ *   out_cost       host, final cost (FP64 trace of the tensor).
+ *   out_sweeps     host, sweeps run; may be NULL.
+ * Synchronises `stream`.
+ */
+int qf_instantiate(const qf_c128* target, int n_qubits, int n_gates,
+                   const qf_loc* locations, const qf_c128* initial_gates,
+                   double tol, int max_sweeps, qf_c128* out_gates,
+                   double* out_cost, int* out_sweeps, void* stream);
+
+/*
+ * qf_instantiate_ex -- lock-step multistart Qfactor with all options.
+ * All starts sweep together (Sec. IV-A): the run stops after the first sweep
+ * in which any start reaches dist_tol, once every start has met a plateau
+ * test (the mark is kept once set), or at max_sweeps.
+ *   initial_gates  host-or-device, n_starts x p x 16.
+ *   opts           host; NULL = defaults.
+ *   out_gates      host-or-device, n_starts x p x 16.
+ *   out_costs      host, n_starts final costs; may be NULL.
+ *   out_result     host, summary; may be NULL.
+ * Synchronises `stream`.
+ */
+int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
+                      const qf_loc* locations, int n_starts,
+                      const qf_c128* initial_gates, const qf_options* opts,
+                      qf_c128* out_gates, double* out_costs,
+                      qf_result* out_result, void* stream);
+
+/*
+ * qf_cost_and_env -- cost and every environment matrix of n_sets gate sets
+ * (the adjoint walk: the tensor is built once, then each gate is moved from
+ * the right of the tensor to its left with one pass, and its environment is
+ * read on the way; O(4^n) memory for any p).
+ *   gates      host-or-device, n_sets x p x 16.
+ *   out_cost   host, n_sets costs; may be NULL.
+ *   out_env    host-or-device, n_sets x p x 16: E_k of each set (FP64).
+ *   out_trace  host, n_sets values Tr(V^dagger C); may be NULL.
+ * Synchronises `stream`.
+ */
+int qf_cost_and_env(const qf_c128* target, int n_qubits, int n_gates,
+                    const qf_loc* locations, int n_sets,
+                    const qf_c128* gates, double* out_cost, qf_c128* out_env,
+                    qf_c128* out_trace, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Resident plan: device-resident tensors, target and gates for repeated
+ * sweeps (the form the benchmark times).
+ * ---------------------------------------------------------------------- */
+typedef struct qf_plan qf_plan;
+
+/* Allocate a plan for n_starts circuits of the given structure.  precision
+ * is QF_C128 or QF_C64.  locations: host-or-device.  Allocates
+ * n_starts*N*N tensor entries plus the target and gates on the current
+ * device. */
+int qf_plan_create(int n_qubits, int n_gates, const qf_loc* locations,
+                   int n_starts, int precision, qf_plan** out_plan);
+int qf_plan_destroy(qf_plan* plan);
+
+/* Copy the target (host-or-device, N x N) and gates (host-or-device,
+ * n_starts x p x 16) into the plan and build every tensor (InitCircuitTensor).
+ * Enqueued on `stream`; the plan records `stream` for its later calls. */
+int qf_plan_load(qf_plan* plan, const qf_c128* target, const qf_c128* gates,
+                 void* stream);
+
+/* Run n_sweeps two-sided sweeps on every start; the tensors are rebuilt after
+ * every reset_iter-th sweep counted since qf_plan_load (reset_iter <= 0:
+ * never).  Enqueue only. */
+int qf_plan_sweep(qf_plan* plan, int n_sweeps, int reset_iter, double beta);
+
+/* Rebuild every tensor from the target and the current gates, in
+ * `precision` (QF_C128 or QF_C64; switching precision re-types the tensors). */
+int qf_plan_rebuild(qf_plan* plan, int precision);
+
+/* FP64 trace of every tensor -> host out_costs[s] = 1 - |Tr T_s|/N and, if
+ * out_trace != NULL, Tr T_s.  Synchronises. */
+int qf_plan_costs(qf_plan* plan, double* out_costs, qf_c128* out_trace);
+
+/* Copy the current gates (n_starts x p x 16) to host-or-device `out`.
+ * Synchronises. */
+int qf_plan_get_gates(qf_plan* plan, qf_c128* out);
+
+/* Kernel timing of the gate-application pass: when enabled, every pass
+ * launch is bracketed by CUDA events on the plan's stream; qf_plan_pass_stats
+ * synchronises and returns the summed pass time (ms), the pass-launch count
+ * and the count of all kernel launches since the last reset, then resets. */
+int qf_plan_enable_pass_timing(qf_plan* plan, int enable);
+int qf_plan_pass_stats(qf_plan* plan, double* pass_ms, int64_t* pass_launches,
+                       int64_t* all_launches);
+
+/* Current device status word of the plan (0 = clean; QF_ENONFINITE if an
+ * update met a non-finite environment).  Synchronises. */
+int qf_plan_status(qf_plan* plan);
+
+/* ------------------------------------------------------------------------
+ * Single steps of the sweep (Alg. 1), on device arrays, enqueue only.
+ * ---------------------------------------------------------------------- */
+
+/* Step a1, InitCircuitTensor (Alg. 1): T_s <- V^dagger, then
+ * T_s <- T_s (u_{s,k} on loc_k) for k = 0..p-1.
+ *   target  device N x N (qf_c128);  locations host or device;
+ *   gates   device n_starts x p x 16; T device n_starts x N x N of the
+ *   given precision (QF_C128 | QF_C64). */
+int qf_init_tensor(const qf_c128* target, int n_qubits, int n_gates,
+                   const qf_loc* locations, int n_starts, const qf_c128* gates,
+                   void* T, int precision, void* stream);
+
+/* Steps a2+a5 fused (Alg. 1 ApplyRight/ApplyLeft on one location):
+ * T_s <- (L_s on (a,b)) T_s (R_s on (a,b)) in one read and one write of T.
+ * L, R: device n_starts x 16 (FP64; cast to the tensor's precision), either
+ * may be NULL for the identity. */
+int qf_apply_pair(void* T, int n_qubits, int n_starts, int a, int b,
+                  const qf_c128* L, const qf_c128* R, int precision,
+                  void* stream);
+
+/* Step a3, CalcEnvMat (Alg. 1): P_s = partial trace of T_s over every qubit
+ * except (a, b), accumulated in FP64.  P: device n_starts x 16. */
+int qf_partial_trace(const void* T, int n_qubits, int n_starts, int a, int b,
+                     qf_c128* P, int precision, void* stream);
+
+/* Step a4, OptimizeGate (Sec. III-A1, Eq. opt_u): for each of `count`
+ * matrices E_i, with A_i = (1-beta) E_i + beta u_old_i^dagger = X D Y^dagger,
+ * u_out_i = Y X^dagger and sigma_out_i = sum(D).  All device arrays; u_old may
+ * be NULL when beta == 0; sigma_out may be NULL. FP64. */
+int qf_optimize_gates(const qf_c128* E, const qf_c128* u_old, double beta,
+                      int count, qf_c128* u_out, double* sigma_out,
+                      void* stream);
+
+/* Step a6: tr_out_s = Tr T_s (FP64 accumulation).  tr_out: device n_starts. */
+int qf_trace(const void* T, int n_qubits, int n_starts, qf_c128* tr_out,
+             int precision, void* stream);
+
+/* C = G_0 G_1 ... G_{p-1} (InitCircuitTensor with the identity target), FP64.
+ *   locations host or device; gates device p x 16; C_out device N x N. */
+int qf_circuit_unitary(int n_qubits, int n_gates, const qf_loc* locations,
+                       const qf_c128* gates, qf_c128* C_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QFACTOR_H */

@@ -1,0 +1,130 @@
+"""ctypes declarations of the C ABI in include/qfactor.h.
+
+The shared library libqfactor.so is built in-tree (``_build.build()``).  If
+it is missing, loading fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+from . import _build
+
+QF_OK = 0
+QF_EINVAL = -1
+QF_ENOMEM = -2
+QF_ECUDA = -3
+QF_ENONFINITE = -4
+
+QF_C128 = 0
+QF_C64 = 1
+QF_C64_REFINE64 = 2
+
+QF_STOP_CONVERGED = 1
+QF_STOP_PLATEAU = 2
+QF_STOP_MAX_SWEEPS = 3
+
+REASONS = {QF_STOP_CONVERGED: "converged", QF_STOP_PLATEAU: "plateau",
+           QF_STOP_MAX_SWEEPS: "max_sweeps"}
+
+
+class qf_options(ct.Structure):
+    _fields_ = [
+        ("dist_tol", ct.c_double),
+        ("max_sweeps", ct.c_int32),
+        ("min_sweeps", ct.c_int32),
+        ("reset_iter", ct.c_int32),
+        ("long_diff_count", ct.c_int32),
+        ("diff_tol_a", ct.c_double),
+        ("diff_tol_r", ct.c_double),
+        ("long_diff_r", ct.c_double),
+        ("beta", ct.c_double),
+        ("precision", ct.c_int32),
+        ("max_c64_sweeps", ct.c_int32),
+        ("switch_tol", ct.c_double),
+    ]
+
+
+class qf_result(ct.Structure):
+    _fields_ = [
+        ("best_start", ct.c_int32),
+        ("sweeps", ct.c_int32),
+        ("c64_sweeps", ct.c_int32),
+        ("reason", ct.c_int32),
+        ("best_cost", ct.c_double),
+    ]
+
+
+P = ct.c_void_p
+I = ct.c_int
+D = ct.c_double
+DP = ct.POINTER(ct.c_double)
+I64P = ct.POINTER(ct.c_int64)
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "qf_last_error": (ct.c_char_p, []),
+    "qf_version": (I, []),
+    "qf_options_default": (I, [ct.POINTER(qf_options)]),
+    "qf_instantiate": (I, [P, I, I, P, P, D, I, P, DP, ct.POINTER(I), P]),
+    "qf_instantiate_ex": (I, [P, I, I, P, I, P, ct.POINTER(qf_options), P, DP,
+                              ct.POINTER(qf_result), P]),
+    "qf_cost_and_env": (I, [P, I, I, P, I, P, DP, P, P, P]),
+    "qf_plan_create": (I, [I, I, P, I, I, ct.POINTER(P)]),
+    "qf_plan_destroy": (I, [P]),
+    "qf_plan_load": (I, [P, P, P, P]),
+    "qf_plan_sweep": (I, [P, I, I, D]),
+    "qf_plan_rebuild": (I, [P, I]),
+    "qf_plan_costs": (I, [P, DP, P]),
+    "qf_plan_get_gates": (I, [P, P]),
+    "qf_plan_enable_pass_timing": (I, [P, I]),
+    "qf_plan_pass_stats": (I, [P, DP, I64P, I64P]),
+    "qf_plan_status": (I, [P]),
+    "qf_init_tensor": (I, [P, I, I, P, I, P, P, I, P]),
+    "qf_apply_pair": (I, [P, I, I, I, I, P, P, I, P]),
+    "qf_partial_trace": (I, [P, I, I, I, I, P, I, P]),
+    "qf_optimize_gates": (I, [P, P, D, I, P, P, P]),
+    "qf_trace": (I, [P, I, I, P, I, P]),
+    "qf_circuit_unitary": (I, [I, I, P, P, P, P]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = False):
+    """Load libqfactor.so (optionally building it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(
+                f"QFactor CUDA library not found at {path}; build it with "
+                "paper_2306_08152_gb300._build.build() (there is no CPU fallback)")
+    lib = ct.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class QFactorError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"QFactor error {code}: {msg}")
+        self.code = code
+
+
+def check(rc: int):
+    if rc != QF_OK:
+        msg = load().qf_last_error()
+        raise QFactorError(rc, msg.decode() if msg else "")
+    return rc

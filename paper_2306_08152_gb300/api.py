@@ -1,0 +1,292 @@
+"""Python binding of the QFactor C ABI (argument marshalling only).
+
+Tensors are PyTorch tensors: targets complex128 (N, N), gates complex128
+(..., 4, 4) in the list order C = G_0 ... G_{p-1}, locations int32 (p, 2).
+Host (CPU) tensors are accepted where the C ABI accepts host-or-device
+arrays; the single-step functions need CUDA tensors.  Every computation runs
+in libqfactor.so on the GPU.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+
+import numpy as np
+import torch
+
+from . import _native as nat
+from ._native import check
+
+__all__ = [
+    "QF_C128", "QF_C64", "QF_C64_REFINE64", "Options", "instantiate",
+    "instantiate_ex", "cost_and_env", "Plan", "init_tensor", "apply_pair",
+    "partial_trace", "optimize_gates", "trace", "circuit_unitary",
+]
+
+QF_C128 = nat.QF_C128
+QF_C64 = nat.QF_C64
+QF_C64_REFINE64 = nat.QF_C64_REFINE64
+
+
+def _lib():
+    return nat.load()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        if torch.cuda.is_available():
+            return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ct.c_void_p(0)
+    if isinstance(stream, torch.cuda.Stream):
+        return ct.c_void_p(stream.cuda_stream)
+    return ct.c_void_p(int(stream))
+
+
+def _c128(t, name):
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t, dtype=np.complex128))
+    if t.dtype != torch.complex128:
+        raise TypeError(f"{name} must be complex128, got {t.dtype}")
+    return t.contiguous()
+
+
+def _locs(locations):
+    if isinstance(locations, torch.Tensor):
+        t = locations.to(torch.int32).contiguous()
+    else:
+        t = torch.as_tensor(np.ascontiguousarray(np.asarray(locations, dtype=np.int32)))
+    if t.dim() != 2 or t.shape[1] != 2:
+        raise ValueError("locations must have shape (p, 2)")
+    return t
+
+
+def _ptr(t):
+    return ct.c_void_p(t.data_ptr())
+
+
+def _nqubits(target):
+    N = target.shape[-1]
+    n = int(N).bit_length() - 1
+    if target.dim() != 2 or target.shape[0] != N or (1 << n) != N:
+        raise ValueError("target must be a 2^n x 2^n matrix")
+    return n
+
+
+class Options:
+    """Hyperparameters of Sec. III-A2 (see qf_options in qfactor.h)."""
+
+    def __init__(self, **kw):
+        o = nat.qf_options()
+        check(_lib().qf_options_default(ct.byref(o)))
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise AttributeError(f"unknown option {k}")
+            setattr(o, k, v)
+        self.c = o
+
+    def __getattr__(self, k):
+        return getattr(self.__dict__["c"], k)
+
+
+def instantiate(target, locations, initial_gates, tol=1e-10, max_sweeps=500, stream=None):
+    """One-start Qfactor (qf_instantiate).  Returns (gates, cost, sweeps);
+    gates live where ``initial_gates`` lives."""
+    target = _c128(target, "target")
+    gates = _c128(initial_gates, "initial_gates")
+    locs = _locs(locations)
+    n = _nqubits(target)
+    out = torch.empty_like(gates)
+    cost = ct.c_double()
+    sweeps = ct.c_int()
+    check(_lib().qf_instantiate(_ptr(target), n, locs.shape[0], _ptr(locs), _ptr(gates),
+                                float(tol), int(max_sweeps), _ptr(out), ct.byref(cost),
+                                ct.byref(sweeps), _stream_handle(stream)))
+    return out, cost.value, sweeps.value
+
+
+def instantiate_ex(target, locations, starts, options=None, stream=None, **kw):
+    """Lock-step multistart Qfactor (qf_instantiate_ex).  ``starts`` has
+    shape (S, p, 4, 4).  Returns a dict with gates, costs, best, sweeps,
+    c64_sweeps, reason and best_cost."""
+    target = _c128(target, "target")
+    starts = _c128(starts, "starts")
+    locs = _locs(locations)
+    n = _nqubits(target)
+    S, p = starts.shape[0], starts.shape[1]
+    if p != locs.shape[0]:
+        raise ValueError("starts and locations disagree on the gate count")
+    opts = options if options is not None else Options(**kw)
+    out = torch.empty_like(starts)
+    costs = (ct.c_double * S)()
+    res = nat.qf_result()
+    check(_lib().qf_instantiate_ex(_ptr(target), n, p, _ptr(locs), S, _ptr(starts),
+                                   ct.byref(opts.c), _ptr(out), costs, ct.byref(res),
+                                   _stream_handle(stream)))
+    return {"gates": out, "costs": np.array(costs[:]), "best": res.best_start,
+            "sweeps": res.sweeps, "c64_sweeps": res.c64_sweeps,
+            "reason": nat.REASONS.get(res.reason, str(res.reason)), "best_cost": res.best_cost}
+
+
+def cost_and_env(target, locations, gates, stream=None):
+    """Costs, environments and traces of gate sets (qf_cost_and_env).
+    ``gates`` has shape (S, p, 4, 4) or (p, 4, 4).  Returns (costs (S,),
+    envs like gates, traces (S,) complex)."""
+    target = _c128(target, "target")
+    g = _c128(gates, "gates")
+    single = g.dim() == 3
+    if single:
+        g = g.unsqueeze(0)
+    locs = _locs(locations)
+    n = _nqubits(target)
+    S, p = g.shape[0], g.shape[1]
+    envs = torch.empty_like(g)
+    costs = (ct.c_double * S)()
+    trs = np.zeros(S, dtype=np.complex128)
+    check(_lib().qf_cost_and_env(_ptr(target), n, p, _ptr(locs), S, _ptr(g), costs, _ptr(envs),
+                                 ct.c_void_p(trs.ctypes.data), _stream_handle(stream)))
+    c = np.array(costs[:])
+    if single:
+        return c[0], envs[0], trs[0]
+    return c, envs, trs
+
+
+class Plan:
+    """Device-resident multistart state (qf_plan_*)."""
+
+    def __init__(self, n_qubits, locations, n_starts, precision=QF_C128):
+        self.locs = _locs(locations)
+        self.n = int(n_qubits)
+        self.p = int(self.locs.shape[0])
+        self.S = int(n_starts)
+        h = ct.c_void_p()
+        check(_lib().qf_plan_create(self.n, self.p, _ptr(self.locs), self.S, int(precision),
+                                    ct.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib().qf_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, target, gates, stream=None):
+        self._t = _c128(target, "target")
+        self._g = _c128(gates, "gates")
+        check(_lib().qf_plan_load(self.h, _ptr(self._t), _ptr(self._g), _stream_handle(stream)))
+
+    def sweep(self, n_sweeps=1, reset_iter=40, beta=0.0):
+        check(_lib().qf_plan_sweep(self.h, int(n_sweeps), int(reset_iter), float(beta)))
+
+    def rebuild(self, precision):
+        check(_lib().qf_plan_rebuild(self.h, int(precision)))
+
+    def costs(self):
+        out = (ct.c_double * self.S)()
+        check(_lib().qf_plan_costs(self.h, out, None))
+        return np.array(out[:])
+
+    def gates(self, device="cpu"):
+        out = torch.empty((self.S, self.p, 4, 4), dtype=torch.complex128, device=device)
+        check(_lib().qf_plan_get_gates(self.h, _ptr(out)))
+        return out
+
+    def enable_pass_timing(self, enable=True):
+        check(_lib().qf_plan_enable_pass_timing(self.h, int(bool(enable))))
+
+    def pass_stats(self):
+        ms = ct.c_double()
+        pl = ct.c_int64()
+        al = ct.c_int64()
+        check(_lib().qf_plan_pass_stats(self.h, ct.byref(ms), ct.byref(pl), ct.byref(al)))
+        return ms.value, pl.value, al.value
+
+    def status(self):
+        return _lib().qf_plan_status(self.h)
+
+
+# ------------------------------------------------------------ single steps
+
+
+def _dev(t, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    return t.contiguous()
+
+
+def _tensor_prec(T):
+    if T.dtype == torch.complex128:
+        return QF_C128
+    if T.dtype == torch.complex64:
+        return QF_C64
+    raise TypeError("circuit tensor must be complex64 or complex128")
+
+
+def init_tensor(target, locations, gates, dtype=torch.complex128, stream=None):
+    """InitCircuitTensor for S starts: gates (S, p, 4, 4) -> T (S, N, N)."""
+    target = _dev(_c128(target, "target"), "target")
+    g = _dev(_c128(gates, "gates"), "gates")
+    if g.dim() == 3:
+        g = g.unsqueeze(0)
+    locs = _locs(locations)
+    n = _nqubits(target)
+    N = 1 << n
+    T = torch.empty((g.shape[0], N, N), dtype=dtype, device=target.device)
+    check(_lib().qf_init_tensor(_ptr(target), n, g.shape[1], _ptr(locs), g.shape[0], _ptr(g),
+                                _ptr(T), _tensor_prec(T), _stream_handle(stream)))
+    return T
+
+
+def apply_pair(T, a, b, L=None, R=None, stream=None):
+    """In place: T_s <- (L_s on (a,b)) T_s (R_s on (a,b)); L, R (S, 4, 4)."""
+    T = _dev(T, "T")
+    S, N = T.shape[0], T.shape[-1]
+    n = int(N).bit_length() - 1
+    Lp = _ptr(_dev(_c128(L, "L"), "L")) if L is not None else None
+    Rp = _ptr(_dev(_c128(R, "R"), "R")) if R is not None else None
+    check(_lib().qf_apply_pair(_ptr(T), n, S, int(a), int(b), Lp, Rp, _tensor_prec(T),
+                               _stream_handle(stream)))
+    return T
+
+
+def partial_trace(T, a, b, stream=None):
+    T = _dev(T, "T")
+    S, N = T.shape[0], T.shape[-1]
+    n = int(N).bit_length() - 1
+    P = torch.empty((S, 4, 4), dtype=torch.complex128, device=T.device)
+    check(_lib().qf_partial_trace(_ptr(T), n, S, int(a), int(b), _ptr(P), _tensor_prec(T),
+                                  _stream_handle(stream)))
+    return P
+
+
+def optimize_gates(E, u_old=None, beta=0.0, stream=None):
+    E = _dev(_c128(E, "E"), "E")
+    count = E.numel() // 16
+    U = torch.empty_like(E)
+    sig = torch.empty(E.shape[:-2], dtype=torch.float64, device=E.device)
+    up = _ptr(_dev(_c128(u_old, "u_old"), "u_old")) if u_old is not None else None
+    check(_lib().qf_optimize_gates(_ptr(E), up, float(beta), count, _ptr(U), _ptr(sig),
+                                   _stream_handle(stream)))
+    return U, sig
+
+
+def trace(T, stream=None):
+    T = _dev(T, "T")
+    S, N = T.shape[0], T.shape[-1]
+    n = int(N).bit_length() - 1
+    tr = torch.empty((S,), dtype=torch.complex128, device=T.device)
+    check(_lib().qf_trace(_ptr(T), n, S, _ptr(tr), _tensor_prec(T), _stream_handle(stream)))
+    return tr
+
+
+def circuit_unitary(n_qubits, locations, gates, device="cuda", stream=None):
+    g = _c128(gates, "gates").to(device)
+    locs = _locs(locations)
+    N = 1 << int(n_qubits)
+    C = torch.empty((N, N), dtype=torch.complex128, device=device)
+    check(_lib().qf_circuit_unitary(int(n_qubits), g.shape[0], _ptr(locs), _ptr(g), _ptr(C),
+                                    _stream_handle(stream)))
+    return C

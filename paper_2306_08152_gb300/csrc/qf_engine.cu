@@ -1,0 +1,696 @@
+// Host engine of the QFactor library: argument checks, workspace, the sweep
+// driver (Alg. 1: TwoSidedSweep inside the Qfactor loop), the stopping rules
+// (Sec. III-A2, Sec. IV-A) and the exported C ABI of include/qfactor.h.
+//
+// Per gate update the engine enqueues two kernels on the caller's stream:
+//   update  environment of the gate from the band of the current tensor plus
+//           the FP64 4x4 update (one CTA per start);
+//   pass    the fused B <- L B R over every 4x4 block of every start's
+//           tensor (one read and one write of T).
+// Nothing returns to the host inside a sweep; costs are read once per sweep.
+
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "qf_internal.h"
+#include "qfactor.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define QF_CUDA(call)                                                          \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess)                                                     \
+      return set_error(e_ == cudaErrorMemoryAllocation ? QF_ENOMEM : QF_ECUDA, \
+                       "%s failed: %s", #call, cudaGetErrorString(e_));        \
+  } while (0)
+
+#define QF_TRY(expr)         \
+  do {                       \
+    int r_ = (expr);         \
+    if (r_ != QF_OK) return r_; \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int check_sizes(int n, int p) {
+  if (n < QF_MIN_QUBITS || n > QF_MAX_QUBITS)
+    return set_error(QF_EINVAL, "n_qubits=%d outside [%d, %d]", n, QF_MIN_QUBITS, QF_MAX_QUBITS);
+  if (p < 1) return set_error(QF_EINVAL, "n_gates=%d must be >= 1", p);
+  return QF_OK;
+}
+
+int check_prec(int prec) {
+  if (prec != QF_C128 && prec != QF_C64)
+    return set_error(QF_EINVAL, "precision=%d must be QF_C128 or QF_C64 here", prec);
+  return QF_OK;
+}
+
+// Copy locations (host or device) to a host vector and validate them.
+int fetch_locations(const qf_loc* locs, int n, int p, std::vector<qf_loc>* out) {
+  if (!locs) return set_error(QF_EINVAL, "locations is NULL");
+  out->resize(p);
+  if (is_device_ptr(locs)) {
+    QF_CUDA(cudaMemcpy(out->data(), locs, sizeof(qf_loc) * p, cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(out->data(), locs, sizeof(qf_loc) * p);
+  }
+  for (int k = 0; k < p; ++k) {
+    const qf_loc& l = (*out)[k];
+    if (l.a < 0 || l.a >= n || l.b < 0 || l.b >= n || l.a == l.b)
+      return set_error(QF_EINVAL, "location %d = (%d, %d) invalid for %d qubits", k, l.a, l.b, n);
+  }
+  return QF_OK;
+}
+
+int check_finite_host(const qf_c128* v, size_t count, const char* what) {
+  for (size_t i = 0; i < count; ++i)
+    if (!std::isfinite(v[i].re) || !std::isfinite(v[i].im))
+      return set_error(QF_ENONFINITE, "%s[%zu] is not finite", what, i);
+  return QF_OK;
+}
+
+// Device buffer owned for the duration of a call.
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  int alloc(size_t bytes) {
+    if (p) {
+      cudaFree(p);
+      p = nullptr;
+    }
+    if (bytes == 0) return QF_OK;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return set_error(QF_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return QF_OK;
+  }
+  template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Make a device copy of a host-or-device input (or borrow it if already on
+// the device).  Host inputs are checked for non-finite values.
+int stage_input(const qf_c128* src, size_t count, DevBuf* buf, const double2** dev,
+                cudaStream_t st, const char* what) {
+  if (!src) return set_error(QF_EINVAL, "%s is NULL", what);
+  if (is_device_ptr(src)) {
+    *dev = reinterpret_cast<const double2*>(src);
+    return QF_OK;
+  }
+  QF_TRY(check_finite_host(src, count, what));
+  QF_TRY(buf->alloc(count * sizeof(double2)));
+  QF_CUDA(cudaMemcpyAsync(buf->p, src, count * sizeof(double2), cudaMemcpyHostToDevice, st));
+  *dev = buf->as<double2>();
+  return QF_OK;
+}
+
+int store_output(qf_c128* dst, const double2* dev, size_t count, cudaStream_t st) {
+  if (!dst) return set_error(QF_EINVAL, "output pointer is NULL");
+  if (reinterpret_cast<const void*>(dst) == reinterpret_cast<const void*>(dev)) return QF_OK;
+  QF_CUDA(cudaMemcpyAsync(dst, dev, count * sizeof(double2), cudaMemcpyDefault, st));
+  return QF_OK;
+}
+
+size_t elem_bytes(int prec) { return prec == QF_C128 ? 16 : 8; }
+
+}  // namespace
+
+// ============================================================ the plan
+
+struct qf_plan {
+  int n = 0, p = 0, S = 0, prec = QF_C128;
+  size_t N = 0, NN = 0;
+  std::vector<qf_loc> locs;
+  DevBuf T, V, gates, LR, sigma, tr, status;
+  size_t T_capacity = 0;  // bytes
+  cudaStream_t stream = nullptr;
+  long long sweeps_since_load = 0;
+  // pass timing
+  bool timing = false;
+  std::vector<cudaEvent_t> events;  // pairs
+  size_t events_used = 0;
+  long long pass_launches = 0, all_launches = 0;
+};
+
+namespace {
+
+int plan_ensure_T(qf_plan* P, int prec) {
+  const size_t need = (size_t)P->S * P->NN * elem_bytes(prec);
+  if (need > P->T_capacity) {
+    QF_TRY(P->T.alloc(need));
+    P->T_capacity = need;
+  }
+  P->prec = prec;
+  return QF_OK;
+}
+
+int plan_pass(qf_plan* P, int a, int b, const double2* L, long long Ls, const double2* R,
+              long long Rs) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (P->timing) {
+    if (P->events_used + 2 > P->events.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        QF_CUDA(cudaEventCreate(&e));
+        P->events.push_back(e);
+      }
+    }
+    e0 = P->events[P->events_used];
+    e1 = P->events[P->events_used + 1];
+    P->events_used += 2;
+    QF_CUDA(cudaEventRecord(e0, P->stream));
+  }
+  QF_CUDA(qf::launch_pass(P->T.p, P->n, P->S, a, b, L, Ls, R, Rs, P->prec == QF_C128 ? 0 : 1,
+                          P->stream));
+  if (P->timing) QF_CUDA(cudaEventRecord(e1, P->stream));
+  P->pass_launches++;
+  P->all_launches++;
+  return QF_OK;
+}
+
+// InitCircuitTensor (Alg. 1) for every start.
+int plan_build(qf_plan* P) {
+  const int pr = P->prec == QF_C128 ? 0 : 1;
+  QF_CUDA(qf::launch_conj_transpose(P->V.as<double2>(), P->T.p, P->n, P->S, pr, P->stream));
+  P->all_launches++;
+  for (int k = 0; k < P->p; ++k) {
+    QF_TRY(plan_pass(P, P->locs[k].a, P->locs[k].b, nullptr, 0,
+                     P->gates.as<double2>() + (size_t)k * 16, (long long)P->p * 16));
+  }
+  return QF_OK;
+}
+
+int plan_update(qf_plan* P, int k, int mode, double beta, double2* env_out, long long env_stride) {
+  const int pr = P->prec == QF_C128 ? 0 : 1;
+  QF_CUDA(qf::launch_update(P->T.p, P->n, P->S, P->locs[k].a, P->locs[k].b,
+                            P->gates.as<double2>() + (size_t)k * 16, (long long)P->p * 16, mode,
+                            beta, P->LR.as<double2>(), env_out, env_stride,
+                            P->sigma.as<double>(), P->status.as<int>(), pr, P->stream));
+  P->all_launches++;
+  return QF_OK;
+}
+
+// TwoSidedSweep (Alg. 1).  Backward half: for k = p-1..0 the environment of
+// gate k (still on the tensor's right), its update, and the pass that
+// removes u_k from the right and applies u_k' on the left.  Forward half:
+// the mirror image, k = 0..p-1.
+int plan_sweep_once(qf_plan* P, double beta) {
+  const double2* LR = P->LR.as<double2>();
+  for (int k = P->p - 1; k >= 0; --k) {
+    QF_TRY(plan_update(P, k, qf::kBackward, beta, nullptr, 0));
+    QF_TRY(plan_pass(P, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
+  }
+  for (int k = 0; k < P->p; ++k) {
+    QF_TRY(plan_update(P, k, qf::kForward, beta, nullptr, 0));
+    QF_TRY(plan_pass(P, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
+  }
+  return QF_OK;
+}
+
+int plan_costs_impl(qf_plan* P, double* costs, qf_c128* traces) {
+  const int pr = P->prec == QF_C128 ? 0 : 1;
+  QF_CUDA(qf::launch_trace(P->T.p, P->n, P->S, P->tr.as<double2>(), pr, P->stream));
+  P->all_launches++;
+  std::vector<double2> h(P->S);
+  QF_CUDA(cudaMemcpyAsync(h.data(), P->tr.p, sizeof(double2) * P->S, cudaMemcpyDeviceToHost,
+                          P->stream));
+  QF_CUDA(cudaStreamSynchronize(P->stream));
+  for (int s = 0; s < P->S; ++s) {
+    if (costs) costs[s] = 1.0 - std::hypot(h[s].x, h[s].y) / (double)P->N;
+    if (traces) {
+      traces[s].re = h[s].x;
+      traces[s].im = h[s].y;
+    }
+  }
+  return QF_OK;
+}
+
+int plan_create_impl(int n, int p, const qf_loc* locs, int S, int prec, qf_plan** out) {
+  if (!out) return set_error(QF_EINVAL, "out_plan is NULL");
+  *out = nullptr;
+  QF_TRY(check_sizes(n, p));
+  QF_TRY(check_prec(prec));
+  if (S < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", S);
+  qf_plan* P = new qf_plan();
+  P->n = n;
+  P->p = p;
+  P->S = S;
+  P->N = (size_t)1 << n;
+  P->NN = P->N * P->N;
+  int rc = fetch_locations(locs, n, p, &P->locs);
+  if (rc == QF_OK) rc = plan_ensure_T(P, prec);
+  if (rc == QF_OK) rc = P->V.alloc(P->NN * sizeof(double2));
+  if (rc == QF_OK) rc = P->gates.alloc((size_t)S * p * 16 * sizeof(double2));
+  if (rc == QF_OK) rc = P->LR.alloc((size_t)S * 32 * sizeof(double2));
+  if (rc == QF_OK) rc = P->sigma.alloc((size_t)S * sizeof(double));
+  if (rc == QF_OK) rc = P->tr.alloc((size_t)S * sizeof(double2));
+  if (rc == QF_OK) rc = P->status.alloc(sizeof(int));
+  if (rc == QF_OK && cudaMemset(P->status.p, 0, sizeof(int)) != cudaSuccess)
+    rc = set_error(QF_ECUDA, "cudaMemset of the status word failed");
+  if (rc != QF_OK) {
+    delete P;
+    return rc;
+  }
+  *out = P;
+  return QF_OK;
+}
+
+int plan_load_impl(qf_plan* P, const qf_c128* target, const qf_c128* gates, cudaStream_t st) {
+  P->stream = st;
+  if (!target || !gates) return set_error(QF_EINVAL, "target or gates is NULL");
+  const size_t gcount = (size_t)P->S * P->p * 16;
+  if (!is_device_ptr(target)) QF_TRY(check_finite_host(target, P->NN, "target"));
+  if (!is_device_ptr(gates)) QF_TRY(check_finite_host(gates, gcount, "gates"));
+  QF_CUDA(cudaMemcpyAsync(P->V.p, target, P->NN * sizeof(double2), cudaMemcpyDefault, st));
+  QF_CUDA(cudaMemcpyAsync(P->gates.p, gates, gcount * sizeof(double2), cudaMemcpyDefault, st));
+  QF_CUDA(cudaMemsetAsync(P->status.p, 0, sizeof(int), st));
+  P->sweeps_since_load = 0;
+  return plan_build(P);
+}
+
+int plan_sweep_impl(qf_plan* P, int n_sweeps, int reset_iter, double beta) {
+  for (int i = 0; i < n_sweeps; ++i) {
+    QF_TRY(plan_sweep_once(P, beta));
+    P->sweeps_since_load++;
+    if (reset_iter > 0 && P->sweeps_since_load % reset_iter == 0) QF_TRY(plan_build(P));
+  }
+  return QF_OK;
+}
+
+int plan_status_impl(qf_plan* P) {
+  int st = 0;
+  QF_CUDA(cudaMemcpyAsync(&st, P->status.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  QF_CUDA(cudaStreamSynchronize(P->stream));
+  if (st != 0) return set_error(st, "an environment or update was not finite");
+  return QF_OK;
+}
+
+// Plateau tests of Sec. III-A2 (readings documented in qfactor.h).
+bool plateau(const std::vector<double>& h, int it, const qf_options& o) {
+  const double c = h.back();
+  if ((o.diff_tol_a > 0.0 || o.diff_tol_r > 0.0) && h.size() >= 2) {
+    if (h[h.size() - 2] - c <= o.diff_tol_a + o.diff_tol_r * c) return true;
+  }
+  const int L = o.long_diff_count;
+  if (L > 0 && it >= L) {
+    const double old = h[h.size() - 1 - L];
+    if (old - c < o.long_diff_r * old) return true;
+  }
+  return false;
+}
+
+struct PlanGuard {
+  qf_plan* p = nullptr;
+  ~PlanGuard() {
+    if (p) qf_plan_destroy(p);
+  }
+};
+
+}  // namespace
+
+// ============================================================ C ABI
+
+extern "C" {
+
+const char* qf_last_error(void) { return g_last_error.c_str(); }
+
+int qf_version(void) { return 100; }
+
+int qf_options_default(qf_options* o) {
+  if (!o) return set_error(QF_EINVAL, "opts is NULL");
+  o->dist_tol = 1e-10;
+  o->max_sweeps = 500;
+  o->min_sweeps = 0;
+  o->reset_iter = 40;
+  o->long_diff_count = 0;
+  o->diff_tol_a = 0.0;
+  o->diff_tol_r = 0.0;
+  o->long_diff_r = 0.1;
+  o->beta = 0.0;
+  o->precision = QF_C128;
+  o->max_c64_sweeps = 1000;
+  o->switch_tol = 1e-6;
+  return QF_OK;
+}
+
+int qf_plan_create(int n_qubits, int n_gates, const qf_loc* locations, int n_starts,
+                   int precision, qf_plan** out_plan) {
+  return plan_create_impl(n_qubits, n_gates, locations, n_starts, precision, out_plan);
+}
+
+int qf_plan_destroy(qf_plan* plan) {
+  if (!plan) return QF_OK;
+  if (plan->stream) cudaStreamSynchronize(plan->stream);
+  for (cudaEvent_t e : plan->events) cudaEventDestroy(e);
+  delete plan;
+  return QF_OK;
+}
+
+int qf_plan_load(qf_plan* plan, const qf_c128* target, const qf_c128* gates, void* stream) {
+  if (!plan) return set_error(QF_EINVAL, "plan is NULL");
+  return plan_load_impl(plan, target, gates, as_stream(stream));
+}
+
+int qf_plan_sweep(qf_plan* plan, int n_sweeps, int reset_iter, double beta) {
+  if (!plan) return set_error(QF_EINVAL, "plan is NULL");
+  if (n_sweeps < 0) return set_error(QF_EINVAL, "n_sweeps=%d < 0", n_sweeps);
+  return plan_sweep_impl(plan, n_sweeps, reset_iter, beta);
+}
+
+int qf_plan_rebuild(qf_plan* plan, int precision) {
+  if (!plan) return set_error(QF_EINVAL, "plan is NULL");
+  QF_TRY(check_prec(precision));
+  if (precision != plan->prec) {
+    QF_CUDA(cudaStreamSynchronize(plan->stream));
+    QF_TRY(plan_ensure_T(plan, precision));
+  }
+  return plan_build(plan);
+}
+
+int qf_plan_costs(qf_plan* plan, double* out_costs, qf_c128* out_trace) {
+  if (!plan) return set_error(QF_EINVAL, "plan is NULL");
+  return plan_costs_impl(plan, out_costs, out_trace);
+}
+
+int qf_plan_get_gates(qf_plan* plan, qf_c128* out) {
+  if (!plan) return set_error(QF_EINVAL, "plan is NULL");
+  QF_TRY(store_output(out, plan->gates.as<double2>(), (size_t)plan->S * plan->p * 16,
+                      plan->stream));
+  QF_CUDA(cudaStreamSynchronize(plan->stream));
+  return QF_OK;
+}
+
+int qf_plan_enable_pass_timing(qf_plan* plan, int enable) {
+  if (!plan) return set_error(QF_EINVAL, "plan is NULL");
+  plan->timing = enable != 0;
+  return QF_OK;
+}
+
+int qf_plan_pass_stats(qf_plan* plan, double* pass_ms, int64_t* pass_launches,
+                       int64_t* all_launches) {
+  if (!plan) return set_error(QF_EINVAL, "plan is NULL");
+  QF_CUDA(cudaStreamSynchronize(plan->stream));
+  double ms = 0.0;
+  for (size_t i = 0; i + 1 < plan->events_used; i += 2) {
+    float t = 0.f;
+    QF_CUDA(cudaEventElapsedTime(&t, plan->events[i], plan->events[i + 1]));
+    ms += t;
+  }
+  if (pass_ms) *pass_ms = ms;
+  if (pass_launches) *pass_launches = plan->pass_launches;
+  if (all_launches) *all_launches = plan->all_launches;
+  plan->events_used = 0;
+  plan->pass_launches = 0;
+  plan->all_launches = 0;
+  return QF_OK;
+}
+
+int qf_plan_status(qf_plan* plan) {
+  if (!plan) return set_error(QF_EINVAL, "plan is NULL");
+  return plan_status_impl(plan);
+}
+
+int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
+                      const qf_loc* locations, int n_starts, const qf_c128* initial_gates,
+                      const qf_options* opts, qf_c128* out_gates, double* out_costs,
+                      qf_result* out_result, void* stream) {
+  qf_options o;
+  qf_options_default(&o);
+  if (opts) o = *opts;
+  QF_TRY(check_sizes(n_qubits, n_gates));
+  if (n_starts < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", n_starts);
+  if (o.max_sweeps < 1) return set_error(QF_EINVAL, "max_sweeps=%d must be >= 1", o.max_sweeps);
+  if (o.precision != QF_C128 && o.precision != QF_C64 && o.precision != QF_C64_REFINE64)
+    return set_error(QF_EINVAL, "precision=%d unknown", o.precision);
+  if (!(o.beta >= 0.0 && o.beta <= 1.0))
+    return set_error(QF_EINVAL, "beta=%g outside [0, 1]", o.beta);
+  if (!out_gates) return set_error(QF_EINVAL, "out_gates is NULL");
+  cudaStream_t st = as_stream(stream);
+  const int S = n_starts, p = n_gates;
+
+  PlanGuard g;
+  const int tensor_prec = o.precision == QF_C128 ? QF_C128 : QF_C64;
+  QF_TRY(plan_create_impl(n_qubits, p, locations, S, tensor_prec, &g.p));
+  qf_plan* P = g.p;
+  if (o.precision == QF_C64_REFINE64) {
+    // reserve the complex128 tensor up front so the switch cannot fail late
+    QF_TRY(plan_ensure_T(P, QF_C128));
+    P->prec = QF_C64;
+  }
+  QF_TRY(plan_load_impl(P, target, initial_gates, st));
+
+  std::vector<std::vector<double>> hist(S);
+  std::vector<double> c(S);
+  QF_TRY(plan_costs_impl(P, c.data(), nullptr));
+  for (int s = 0; s < S; ++s) hist[s].push_back(c[s]);
+  std::vector<char> plateaued(S, 0);
+  bool c64_phase = (o.precision == QF_C64_REFINE64);
+  int reason = QF_STOP_MAX_SWEEPS, it = 0, c64_sweeps = 0;
+  for (it = 1; it <= o.max_sweeps; ++it) {
+    QF_TRY(plan_sweep_once(P, o.beta));
+    P->sweeps_since_load++;
+    if (o.reset_iter > 0 && P->sweeps_since_load % o.reset_iter == 0) QF_TRY(plan_build(P));
+    QF_TRY(plan_costs_impl(P, c.data(), nullptr));
+    QF_TRY(plan_status_impl(P));
+    if (c64_phase) {
+      ++c64_sweeps;
+      double best = c[0];
+      bool progress = false;
+      for (int s = 0; s < S; ++s) {
+        best = std::min(best, c[s]);
+        const double prev = hist[s].back();
+        if (prev - c[s] > 1e-3 * std::fabs(prev)) progress = true;
+      }
+      for (int s = 0; s < S; ++s) hist[s].push_back(c[s]);
+      if (best <= o.switch_tol || !progress || c64_sweeps >= o.max_c64_sweeps) {
+        // K9: rebuild every tensor in complex128 from V and the FP64 gates
+        P->prec = QF_C128;
+        QF_TRY(plan_build(P));
+        QF_TRY(plan_costs_impl(P, c.data(), nullptr));
+        for (int s = 0; s < S; ++s) hist[s].back() = c[s];
+        c64_phase = false;
+      } else {
+        continue;
+      }
+    } else {
+      for (int s = 0; s < S; ++s) hist[s].push_back(c[s]);
+    }
+    if (it >= o.min_sweeps) {
+      bool conv = false;
+      for (int s = 0; s < S; ++s) conv = conv || (c[s] <= o.dist_tol);
+      if (conv) {
+        reason = QF_STOP_CONVERGED;
+        break;
+      }
+      bool all = true;
+      for (int s = 0; s < S; ++s) {
+        if (plateau(hist[s], it, o)) plateaued[s] = 1;
+        all = all && plateaued[s];
+      }
+      if (all) {
+        reason = QF_STOP_PLATEAU;
+        break;
+      }
+    }
+  }
+  if (it > o.max_sweeps) it = o.max_sweeps;
+  int best = 0;
+  for (int s = 1; s < S; ++s)
+    if (c[s] < c[best]) best = s;
+  QF_TRY(store_output(out_gates, P->gates.as<double2>(), (size_t)S * p * 16, st));
+  QF_CUDA(cudaStreamSynchronize(st));
+  if (out_costs)
+    for (int s = 0; s < S; ++s) out_costs[s] = c[s];
+  if (out_result) {
+    out_result->best_start = best;
+    out_result->sweeps = it;
+    out_result->c64_sweeps = c64_sweeps;
+    out_result->reason = reason;
+    out_result->best_cost = c[best];
+  }
+  return QF_OK;
+}
+
+int qf_instantiate(const qf_c128* target, int n_qubits, int n_gates, const qf_loc* locations,
+                   const qf_c128* initial_gates, double tol, int max_sweeps,
+                   qf_c128* out_gates, double* out_cost, int* out_sweeps, void* stream) {
+  qf_options o;
+  qf_options_default(&o);
+  o.dist_tol = tol;
+  o.max_sweeps = max_sweeps;
+  qf_result r;
+  double cost = 0.0;
+  QF_TRY(qf_instantiate_ex(target, n_qubits, n_gates, locations, 1, initial_gates, &o, out_gates,
+                           &cost, &r, stream));
+  if (out_cost) *out_cost = cost;
+  if (out_sweeps) *out_sweeps = r.sweeps;
+  return QF_OK;
+}
+
+int qf_cost_and_env(const qf_c128* target, int n_qubits, int n_gates, const qf_loc* locations,
+                    int n_sets, const qf_c128* gates, double* out_cost, qf_c128* out_env,
+                    qf_c128* out_trace, void* stream) {
+  QF_TRY(check_sizes(n_qubits, n_gates));
+  if (n_sets < 1) return set_error(QF_EINVAL, "n_sets=%d must be >= 1", n_sets);
+  if (!out_env) return set_error(QF_EINVAL, "out_env is NULL");
+  cudaStream_t st = as_stream(stream);
+  const int S = n_sets, p = n_gates;
+  PlanGuard g;
+  QF_TRY(plan_create_impl(n_qubits, p, locations, S, QF_C128, &g.p));
+  qf_plan* P = g.p;
+  QF_TRY(plan_load_impl(P, target, gates, st));
+  std::vector<double> c(S);
+  std::vector<qf_c128> tr(S);
+  QF_TRY(plan_costs_impl(P, c.data(), tr.data()));
+  // environments land in a device buffer laid out like out_env
+  DevBuf envb;
+  double2* env_dev = nullptr;
+  const size_t ecount = (size_t)S * p * 16;
+  if (is_device_ptr(out_env)) {
+    env_dev = reinterpret_cast<double2*>(out_env);
+  } else {
+    QF_TRY(envb.alloc(ecount * sizeof(double2)));
+    env_dev = envb.as<double2>();
+  }
+  const double2* LR = P->LR.as<double2>();
+  for (int k = p - 1; k >= 0; --k) {
+    QF_TRY(plan_update(P, k, qf::kEnvOnly, 0.0, env_dev + (size_t)k * 16, (long long)p * 16));
+    if (k > 0) QF_TRY(plan_pass(P, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
+  }
+  if (!is_device_ptr(out_env))
+    QF_CUDA(cudaMemcpyAsync(out_env, env_dev, ecount * sizeof(double2), cudaMemcpyDeviceToHost,
+                            st));
+  QF_CUDA(cudaStreamSynchronize(st));
+  if (out_cost)
+    for (int s = 0; s < S; ++s) out_cost[s] = c[s];
+  if (out_trace)
+    for (int s = 0; s < S; ++s) out_trace[s] = tr[s];
+  return QF_OK;
+}
+
+// ------------------------------------------------------------ single steps
+
+int qf_init_tensor(const qf_c128* target, int n_qubits, int n_gates, const qf_loc* locations,
+                   int n_starts, const qf_c128* gates, void* T, int precision, void* stream) {
+  QF_TRY(check_sizes(n_qubits, n_gates));
+  QF_TRY(check_prec(precision));
+  if (n_starts < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", n_starts);
+  if (!target || !gates || !T) return set_error(QF_EINVAL, "NULL device pointer");
+  std::vector<qf_loc> locs;
+  QF_TRY(fetch_locations(locations, n_qubits, n_gates, &locs));
+  cudaStream_t st = as_stream(stream);
+  const int pr = precision == QF_C128 ? 0 : 1;
+  QF_CUDA(qf::launch_conj_transpose(reinterpret_cast<const double2*>(target), T, n_qubits,
+                                    n_starts, pr, st));
+  for (int k = 0; k < n_gates; ++k)
+    QF_CUDA(qf::launch_pass(T, n_qubits, n_starts, locs[k].a, locs[k].b, nullptr, 0,
+                            reinterpret_cast<const double2*>(gates) + (size_t)k * 16,
+                            (long long)n_gates * 16, pr, st));
+  return QF_OK;
+}
+
+int qf_apply_pair(void* T, int n_qubits, int n_starts, int a, int b, const qf_c128* L,
+                  const qf_c128* R, int precision, void* stream) {
+  QF_TRY(check_sizes(n_qubits, 1));
+  QF_TRY(check_prec(precision));
+  if (n_starts < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", n_starts);
+  if (!T) return set_error(QF_EINVAL, "T is NULL");
+  if (a < 0 || a >= n_qubits || b < 0 || b >= n_qubits || a == b)
+    return set_error(QF_EINVAL, "location (%d, %d) invalid for %d qubits", a, b, n_qubits);
+  QF_CUDA(qf::launch_pass(T, n_qubits, n_starts, a, b, reinterpret_cast<const double2*>(L), 16,
+                          reinterpret_cast<const double2*>(R), 16, precision == QF_C128 ? 0 : 1,
+                          as_stream(stream)));
+  return QF_OK;
+}
+
+int qf_partial_trace(const void* T, int n_qubits, int n_starts, int a, int b, qf_c128* P,
+                     int precision, void* stream) {
+  QF_TRY(check_sizes(n_qubits, 1));
+  QF_TRY(check_prec(precision));
+  if (n_starts < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", n_starts);
+  if (!T || !P) return set_error(QF_EINVAL, "NULL device pointer");
+  if (a < 0 || a >= n_qubits || b < 0 || b >= n_qubits || a == b)
+    return set_error(QF_EINVAL, "location (%d, %d) invalid for %d qubits", a, b, n_qubits);
+  QF_CUDA(qf::launch_partial_trace(T, n_qubits, n_starts, a, b, reinterpret_cast<double2*>(P),
+                                   precision == QF_C128 ? 0 : 1, as_stream(stream)));
+  return QF_OK;
+}
+
+int qf_optimize_gates(const qf_c128* E, const qf_c128* u_old, double beta, int count,
+                      qf_c128* u_out, double* sigma_out, void* stream) {
+  if (count < 0) return set_error(QF_EINVAL, "count=%d < 0", count);
+  if (count == 0) return QF_OK;
+  if (!E || !u_out) return set_error(QF_EINVAL, "NULL device pointer");
+  if (beta != 0.0 && !u_old) return set_error(QF_EINVAL, "beta != 0 needs u_old");
+  if (!(beta >= 0.0 && beta <= 1.0)) return set_error(QF_EINVAL, "beta=%g outside [0, 1]", beta);
+  QF_CUDA(qf::launch_optimize(reinterpret_cast<const double2*>(E),
+                              reinterpret_cast<const double2*>(u_old), beta, count,
+                              reinterpret_cast<double2*>(u_out), sigma_out, as_stream(stream)));
+  return QF_OK;
+}
+
+int qf_trace(const void* T, int n_qubits, int n_starts, qf_c128* tr_out, int precision,
+             void* stream) {
+  QF_TRY(check_sizes(n_qubits, 1));
+  QF_TRY(check_prec(precision));
+  if (n_starts < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", n_starts);
+  if (!T || !tr_out) return set_error(QF_EINVAL, "NULL device pointer");
+  QF_CUDA(qf::launch_trace(T, n_qubits, n_starts, reinterpret_cast<double2*>(tr_out),
+                           precision == QF_C128 ? 0 : 1, as_stream(stream)));
+  return QF_OK;
+}
+
+int qf_circuit_unitary(int n_qubits, int n_gates, const qf_loc* locations, const qf_c128* gates,
+                       qf_c128* C_out, void* stream) {
+  QF_TRY(check_sizes(n_qubits, n_gates));
+  if (!gates || !C_out) return set_error(QF_EINVAL, "NULL device pointer");
+  std::vector<qf_loc> locs;
+  QF_TRY(fetch_locations(locations, n_qubits, n_gates, &locs));
+  const size_t N = (size_t)1 << n_qubits;
+  cudaStream_t st = as_stream(stream);
+  // identity target: V^dagger = I
+  DevBuf I;
+  QF_TRY(I.alloc(N * N * sizeof(double2)));
+  QF_CUDA(qf::launch_set_identity(I.as<double2>(), n_qubits, st));
+  int rc = qf_init_tensor(reinterpret_cast<const qf_c128*>(I.p), n_qubits, n_gates, locs.data(),
+                          1, gates, C_out, QF_C128, stream);
+  QF_CUDA(cudaStreamSynchronize(st));
+  return rc;
+}
+
+}  // extern "C"

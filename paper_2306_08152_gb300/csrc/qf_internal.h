@@ -1,0 +1,59 @@
+// Internal launch interface between the host engine (qf_engine.cu) and the
+// kernels (qf_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qf {
+
+// Modes of the update kernel (environment + 4x4 update of one gate).
+enum UpdateMode {
+  kBackward = 0,  // E = P u^dagger; u' = polar; L = u', R = u^dagger
+  kForward = 1,   // E = u^dagger P; u' = polar; L = u^dagger, R = u'
+  kEnvOnly = 2,   // E = P u^dagger written out; L = u, R = u^dagger
+};
+
+// Bit position of qubit q in an n-bit row or column index (qubit 0 = MSB).
+inline int qubit_bit(int n, int q) { return n - 1 - q; }
+
+// T_s <- V^dagger for every start s (prec: 0 = c128, 1 = c64).
+cudaError_t launch_conj_transpose(const double2* V, void* T, int n, int S,
+                                  int prec, cudaStream_t st);
+
+// T_s <- (L_s on (a,b)) T_s (R_s on (a,b)); L_s = L + s*Lstride (16 FP64
+// complex values), likewise R; a NULL operand is the identity.
+cudaError_t launch_pass(void* T, int n, int S, int a, int b, const double2* L,
+                        long long Lstride, const double2* R, long long Rstride,
+                        int prec, cudaStream_t st);
+
+// Environment of gate k from the tensor before its removal, then the FP64
+// update.  gates_k = gates + k*16, start stride gstride.  LR (S x 32 FP64)
+// receives the pass operators; env_out (nullable) receives E with start
+// stride env_stride; sigma_out (nullable, S) receives the singular-value sum.
+cudaError_t launch_update(const void* T, int n, int S, int a, int b,
+                          double2* gates_k, long long gstride, int mode,
+                          double beta, double2* LR, double2* env_out,
+                          long long env_stride, double* sigma_out, int* status,
+                          int prec, cudaStream_t st);
+
+// P_s = partial trace of T_s over every qubit except (a, b), FP64.
+cudaError_t launch_partial_trace(const void* T, int n, int S, int a, int b,
+                                 double2* P, int prec, cudaStream_t st);
+
+// u_i = polar update of E_i (Eq. opt_u) for i < count.
+cudaError_t launch_optimize(const double2* E, const double2* u_old, double beta,
+                            int count, double2* u_out, double* sigma_out,
+                            cudaStream_t st);
+
+// tr_s = Tr T_s (FP64 accumulation).
+cudaError_t launch_trace(const void* T, int n, int S, double2* tr, int prec,
+                         cudaStream_t st);
+
+// M <- identity (N x N, FP64 complex).
+cudaError_t launch_set_identity(double2* M, int n, cudaStream_t st);
+
+// Number of SMs of the current device (cached).
+int sm_count();
+
+}  // namespace qf

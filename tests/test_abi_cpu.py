@@ -1,0 +1,137 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, it
+exports every function include/qfactor.h declares, option defaults, and
+argument validation that returns before any CUDA call."""
+import ctypes as ct
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qfactor.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2306_08152_gb300 import _build, _native
+
+    if not os.path.exists(_build.LIB_PATH):
+        _build.build()
+    return _native.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qf_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("qf_instantiate", "qf_cost_and_env", "qf_instantiate_ex",
+                     "qf_last_error", "qf_init_tensor", "qf_apply_pair",
+                     "qf_partial_trace", "qf_optimize_gates", "qf_trace"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2306_08152_gb300 import _build
+
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB_PATH],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (qf_[a-z0-9_]+)", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+    for f in declared_functions():
+        assert hasattr(lib, f)
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2306_08152_gb300 import _native
+
+    assert set(declared_functions()) <= set(_native.SIGNATURES)
+
+
+def test_options_defaults(lib):
+    from paper_2306_08152_gb300 import _native as nat
+
+    o = nat.qf_options()
+    assert lib.qf_options_default(ct.byref(o)) == 0
+    assert o.dist_tol == 1e-10 and o.max_sweeps == 500 and o.reset_iter == 40
+    assert o.beta == 0.0 and o.precision == nat.QF_C128
+    assert lib.qf_options_default(None) == nat.QF_EINVAL
+    assert b"NULL" in lib.qf_last_error()
+    assert lib.qf_version() >= 100
+
+
+def test_struct_layouts_match_header(lib):
+    from paper_2306_08152_gb300 import _native as nat
+
+    assert ct.sizeof(nat.qf_options) == 72
+    assert ct.sizeof(nat.qf_result) == 24
+
+
+def _call_instantiate(lib, n, p, locs):
+    N = 2**n
+    V = np.eye(N, dtype=np.complex128)
+    g = np.tile(np.eye(4, dtype=np.complex128), (max(p, 1), 1, 1))
+    locs = np.ascontiguousarray(np.asarray(locs, dtype=np.int32).reshape(-1, 2))
+    out = np.zeros_like(g)
+    cost = ct.c_double()
+    return lib.qf_instantiate(V.ctypes.data, n, p, locs.ctypes.data, g.ctypes.data, 1e-10, 10,
+                              out.ctypes.data, ct.byref(cost), None, None)
+
+
+def test_invalid_sizes_are_rejected_before_any_cuda_call(lib):
+    from paper_2306_08152_gb300 import _native as nat
+
+    assert _call_instantiate(lib, 1, 1, [[0, 1]]) == nat.QF_EINVAL
+    assert b"n_qubits" in lib.qf_last_error()
+    assert _call_instantiate(lib, 15, 1, [[0, 1]]) == nat.QF_EINVAL
+    assert _call_instantiate(lib, 3, 0, [[0, 1]]) == nat.QF_EINVAL
+    assert b"n_gates" in lib.qf_last_error()
+
+
+@pytest.mark.parametrize("bad", [[[0, 0]], [[0, 3]], [[-1, 1]], [[1, 2], [2, 2]]])
+def test_invalid_locations_are_rejected(lib, bad):
+    from paper_2306_08152_gb300 import _native as nat
+
+    locs = np.ascontiguousarray(np.asarray(bad, dtype=np.int32))
+    h = ct.c_void_p()
+    rc = lib.qf_plan_create(3, len(bad), locs.ctypes.data, 1, nat.QF_C128, ct.byref(h))
+    assert rc == nat.QF_EINVAL
+    assert b"location" in lib.qf_last_error()
+    assert not h.value
+
+
+def test_invalid_plan_arguments(lib):
+    from paper_2306_08152_gb300 import _native as nat
+
+    locs = np.array([[0, 1]], dtype=np.int32)
+    h = ct.c_void_p()
+    assert lib.qf_plan_create(3, 1, locs.ctypes.data, 0, nat.QF_C128, ct.byref(h)) == nat.QF_EINVAL
+    assert lib.qf_plan_create(3, 1, locs.ctypes.data, 1, 7, ct.byref(h)) == nat.QF_EINVAL
+    assert lib.qf_plan_create(3, 1, None, 1, nat.QF_C128, ct.byref(h)) == nat.QF_EINVAL
+    assert lib.qf_plan_sweep(None, 1, 40, 0.0) == nat.QF_EINVAL
+    assert lib.qf_optimize_gates(None, None, 0.5, 1, None, None, None) == nat.QF_EINVAL
+    assert lib.qf_optimize_gates(None, None, 0.0, 0, None, None, None) == 0
+
+
+def test_invalid_options_are_rejected(lib):
+    from paper_2306_08152_gb300 import _native as nat
+
+    o = nat.qf_options()
+    lib.qf_options_default(ct.byref(o))
+    V = np.eye(8, dtype=np.complex128)
+    g = np.eye(4, dtype=np.complex128)[None]
+    locs = np.array([[0, 1]], dtype=np.int32)
+    out = np.zeros_like(g)
+    for field, value in (("beta", 1.5), ("precision", 9), ("max_sweeps", 0)):
+        bad = nat.qf_options()
+        ct.memmove(ct.byref(bad), ct.byref(o), ct.sizeof(o))
+        setattr(bad, field, value)
+        rc = lib.qf_instantiate_ex(V.ctypes.data, 3, 1, locs.ctypes.data, 1, g.ctypes.data,
+                                   ct.byref(bad), out.ctypes.data, None, None, None)
+        assert rc == nat.QF_EINVAL, field
