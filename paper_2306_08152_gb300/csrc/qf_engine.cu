@@ -156,7 +156,7 @@ struct qf_plan {
   int n = 0, p = 0, S = 0, prec = QF_C128;
   size_t N = 0, NN = 0;
   std::vector<qf_loc> locs;
-  DevBuf T, V, gates, LR, sigma, tr, status;
+  DevBuf T, V, gates, LR, sigma, tr, status, part, counters;
   size_t T_capacity = 0;  // bytes
   cudaStream_t stream = nullptr;
   long long sweeps_since_load = 0;
@@ -220,7 +220,8 @@ int plan_update(qf_plan* P, int k, int mode, double beta, double2* env_out, long
   QF_CUDA(qf::launch_update(P->T.p, P->n, P->S, P->locs[k].a, P->locs[k].b,
                             P->gates.as<double2>() + (size_t)k * 16, (long long)P->p * 16, mode,
                             beta, P->LR.as<double2>(), env_out, env_stride,
-                            P->sigma.as<double>(), P->status.as<int>(), pr, P->stream));
+                            P->sigma.as<double>(), P->status.as<int>(), P->part.as<double>(),
+                            P->counters.as<unsigned>(), pr, P->stream));
   P->all_launches++;
   return QF_OK;
 }
@@ -280,8 +281,11 @@ int plan_create_impl(int n, int p, const qf_loc* locs, int S, int prec, qf_plan*
   if (rc == QF_OK) rc = P->sigma.alloc((size_t)S * sizeof(double));
   if (rc == QF_OK) rc = P->tr.alloc((size_t)S * sizeof(double2));
   if (rc == QF_OK) rc = P->status.alloc(sizeof(int));
-  if (rc == QF_OK && cudaMemset(P->status.p, 0, sizeof(int)) != cudaSuccess)
-    rc = set_error(QF_ECUDA, "cudaMemset of the status word failed");
+  if (rc == QF_OK) rc = P->part.alloc((size_t)S * qf::env_ctas(n) * 32 * sizeof(double));
+  if (rc == QF_OK) rc = P->counters.alloc((size_t)S * sizeof(unsigned));
+  if (rc == QF_OK && (cudaMemset(P->status.p, 0, sizeof(int)) != cudaSuccess ||
+                      cudaMemset(P->counters.p, 0, (size_t)S * sizeof(unsigned)) != cudaSuccess))
+    rc = set_error(QF_ECUDA, "cudaMemset of the plan's status words failed");
   if (rc != QF_OK) {
     delete P;
     return rc;
@@ -646,8 +650,22 @@ int qf_partial_trace(const void* T, int n_qubits, int n_starts, int a, int b, qf
   if (!T || !P) return set_error(QF_EINVAL, "NULL device pointer");
   if (a < 0 || a >= n_qubits || b < 0 || b >= n_qubits || a == b)
     return set_error(QF_EINVAL, "location (%d, %d) invalid for %d qubits", a, b, n_qubits);
-  QF_CUDA(qf::launch_partial_trace(T, n_qubits, n_starts, a, b, reinterpret_cast<double2*>(P),
-                                   precision == QF_C128 ? 0 : 1, as_stream(stream)));
+  // stream-ordered scratch for the environment kernel's cross-CTA partials
+  cudaStream_t st = as_stream(stream);
+  const size_t part_bytes = (size_t)n_starts * qf::env_ctas(n_qubits) * 32 * sizeof(double);
+  const size_t cnt_bytes = (size_t)n_starts * sizeof(unsigned);
+  void* scratch = nullptr;
+  QF_CUDA(cudaMallocAsync(&scratch, part_bytes + cnt_bytes, st));
+  unsigned* counters = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(scratch) + part_bytes);
+  cudaError_t e = cudaMemsetAsync(counters, 0, cnt_bytes, st);
+  if (e == cudaSuccess)
+    e = qf::launch_update(T, n_qubits, n_starts, a, b, nullptr, 0, qf::kTraceOnly, 0.0, nullptr,
+                          reinterpret_cast<double2*>(P), 16, nullptr, nullptr,
+                          reinterpret_cast<double*>(scratch), counters,
+                          precision == QF_C128 ? 0 : 1, st);
+  cudaError_t e2 = cudaFreeAsync(scratch, st);
+  if (e != cudaSuccess) return set_error(QF_ECUDA, "partial trace launch failed: %s", cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return set_error(QF_ECUDA, "cudaFreeAsync failed: %s", cudaGetErrorString(e2));
   return QF_OK;
 }
 

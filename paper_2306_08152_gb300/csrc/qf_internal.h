@@ -1,5 +1,5 @@
 // Internal launch interface between the host engine (qf_engine.cu) and the
-// kernels (qf_kernels.cu).  Not part of the public ABI.
+// kernels (qf_pass.cu, qf_update.cu).  Not part of the public ABI.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -7,11 +7,12 @@
 
 namespace qf {
 
-// Modes of the update kernel (environment + 4x4 update of one gate).
+// Modes of the environment kernel.
 enum UpdateMode {
-  kBackward = 0,  // E = P u^dagger; u' = polar; L = u', R = u^dagger
-  kForward = 1,   // E = u^dagger P; u' = polar; L = u^dagger, R = u'
-  kEnvOnly = 2,   // E = P u^dagger written out; L = u, R = u^dagger
+  kBackward = 0,   // E = P u^dagger; u' = polar; L = u', R = u^dagger
+  kForward = 1,    // E = u^dagger P; u' = polar; L = u^dagger, R = u'
+  kEnvOnly = 2,    // E = P u^dagger written out; L = u, R = u^dagger
+  kTraceOnly = 3,  // P written out
 };
 
 // Bit position of qubit q in an n-bit row or column index (qubit 0 = MSB).
@@ -27,19 +28,22 @@ cudaError_t launch_pass(void* T, int n, int S, int a, int b, const double2* L,
                         long long Lstride, const double2* R, long long Rstride,
                         int prec, cudaStream_t st);
 
+// CTAs per start of the environment kernel.
+int env_ctas(int n);
+
 // Environment of gate k from the tensor before its removal, then the FP64
 // update.  gates_k = gates + k*16, start stride gstride.  LR (S x 32 FP64)
-// receives the pass operators; env_out (nullable) receives E with start
-// stride env_stride; sigma_out (nullable, S) receives the singular-value sum.
+// receives the pass operators; out (nullable) receives E (or P in
+// kTraceOnly mode) with start stride out_stride; sigma_out (nullable, S)
+// receives the singular-value sum.  part (S * env_ctas(n) * 32 doubles) and
+// counters (S unsigned: zero before the first launch, left zero after each
+// launch) are scratch owned by the caller.
 cudaError_t launch_update(const void* T, int n, int S, int a, int b,
                           double2* gates_k, long long gstride, int mode,
-                          double beta, double2* LR, double2* env_out,
-                          long long env_stride, double* sigma_out, int* status,
-                          int prec, cudaStream_t st);
-
-// P_s = partial trace of T_s over every qubit except (a, b), FP64.
-cudaError_t launch_partial_trace(const void* T, int n, int S, int a, int b,
-                                 double2* P, int prec, cudaStream_t st);
+                          double beta, double2* LR, double2* out,
+                          long long out_stride, double* sigma_out, int* status,
+                          double* part, unsigned* counters, int prec,
+                          cudaStream_t st);
 
 // u_i = polar update of E_i (Eq. opt_u) for i < count.
 cudaError_t launch_optimize(const double2* E, const double2* u_old, double beta,

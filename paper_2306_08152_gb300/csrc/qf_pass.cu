@@ -1,0 +1,432 @@
+// Gate-application kernels of the QFactor sweep for sm_103a: the initial
+// conjugate transpose, the fused pass B <- L B R, the trace, and helpers.
+//
+// Layout: a circuit tensor T is N x N row-major (N = 2^n), interleaved
+// complex (float2 for complex64, double2 for complex128); start s occupies
+// entries [s*N*N, (s+1)*N*N).  Qubit q is bit n-1-q of a row index and of a
+// column index, so a gate on (a, b) touches row bits {pa, pb} and column bits
+// {pa, pb} with pa = n-1-a, pb = n-1-b; its local index is 2*bit_pa + bit_pb.
+//
+// Every 16 entries that share all non-gate row and column bits form one 4x4
+// block B (rows x = local row index, columns y = local column index).  The
+// fused update of Alg. 1 (remove the old gate on one side, apply the new one
+// on the other) is B <- L B R for every block: one read and one write of T.
+// The 4x4 work is far too small to be a dense contraction worth tensor
+// cores (32 complex FMAs per 16 entries): the complex64 pass is bound by HBM
+// and the complex128 pass by the FP64 pipe.
+
+#include "qf_device.cuh"
+#include "qf_internal.h"
+
+namespace qf {
+namespace {
+
+using namespace dev;
+
+// ------------------------------------------------------ InitCircuitTensor
+//
+// T_s <- V^dagger: conjugate transpose through a 32 x 33 shared tile so that
+// both the read of V and the write of T are coalesced.
+
+template <typename R>
+__global__ void __launch_bounds__(256) conj_transpose_kernel(
+    const double2* __restrict__ V, typename Cplx<R>::T* __restrict__ T, int N) {
+  __shared__ double2 tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  const int s = blockIdx.z;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    int r = by + j, c = bx + threadIdx.x;
+    if (r < N && c < N) tile[j][threadIdx.x] = V[(size_t)r * N + c];
+  }
+  __syncthreads();
+  typename Cplx<R>::T* Ts = T + (size_t)s * N * N;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    int r = bx + j, c = by + threadIdx.x;
+    if (r < N && c < N) {
+      double2 v = tile[threadIdx.x][j];
+      v.y = -v.y;
+      Ts[(size_t)r * N + c] = cmake(v, R());
+    }
+  }
+}
+
+constexpr int kPassThreads = 256;
+
+template <typename R, bool HL, bool HR>
+__device__ __forceinline__ void load_ops(typename Cplx<R>::T* sL, typename Cplx<R>::T* sR,
+                                         const double2* __restrict__ L, long long Ls,
+                                         const double2* __restrict__ Rm, long long Rs, int s) {
+  if (threadIdx.x < 16) {
+    if (HL) sL[threadIdx.x] = cmake(L[s * Ls + threadIdx.x], R());
+    if (HR) sR[threadIdx.x] = cmake(Rm[s * Rs + threadIdx.x], R());
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------- the pass
+//
+// Block mapping: one thread owns one 4x4 block per loop trip, consecutive
+// threads taking consecutive values of the column rest index.  Every warp
+// load then reads 32 entries that are contiguous, or made of runs of at
+// least 4 entries (full 32-byte sectors), whenever the gate's lower column
+// bit is bit 2 or above.
+
+template <typename R, bool HL, bool HR>
+__global__ void __launch_bounds__(kPassThreads, (sizeof(R) == 4 ? 3 : 1))
+pass_block_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, int pa, int pb,
+                  const double2* __restrict__ L, long long Ls, const double2* __restrict__ Rm,
+                  long long Rs) {
+  typedef typename Cplx<R>::T C;
+  __shared__ C sL[16], sR[16];
+  const int s = blockIdx.y;
+  load_ops<R, HL, HR>(sL, sR, L, Ls, Rm, Rs, s);
+
+  const unsigned N = 1u << n;
+  const int lnc = n - 2;
+  const unsigned cmask = (1u << lnc) - 1u;
+  const unsigned nblk = 1u << (2 * lnc);
+  C* __restrict__ Ts = T + (size_t)s * N * N;
+  const unsigned o1 = 1u << pb, o2 = 1u << pa;
+  const unsigned off[4] = {0u, o1, o2, o1 | o2};
+
+  for (unsigned blk = blockIdx.x * blockDim.x + threadIdx.x; blk < nblk;
+       blk += gridDim.x * blockDim.x) {
+    const unsigned r0 = dep2(blk >> lnc, plo, phi);
+    const unsigned c0 = dep2(blk & cmask, plo, phi);
+    C bm[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const unsigned rb = (r0 | off[x]) * N;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) bm[x][y] = Ts[rb + (c0 | off[y])];
+    }
+    if (HR) {  // B <- B R, one row at a time
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        C t[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) t[y] = czero<C>();
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) t[y] = cfma(bm[x][k], sR[k * 4 + y], t[y]);
+#pragma unroll
+        for (int y = 0; y < 4; ++y) bm[x][y] = t[y];
+      }
+    }
+    if (HL) {  // B <- L B, one column at a time
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        C t[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          C acc = czero<C>();
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc = cfma(sL[x * 4 + k], bm[k][y], acc);
+          t[x] = acc;
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) bm[x][y] = t[x];
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const unsigned rb = (r0 | off[x]) * N;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) Ts[rb + (c0 | off[y])] = bm[x][y];
+    }
+  }
+}
+
+// Lane mapping, for gates whose lower column bit is bit 0 or 1 (there the
+// block mapping would leave half of every sector to another instruction).
+// Lanes own 32 consecutive columns of one row, so every warp load and store
+// is one contiguous run.  A thread holds, for its column c and the 4 rows of
+// its row block, the entries at c and (MODE 1) at c with the gate's upper
+// column bit set; the block partners that differ in a gate column bit
+// below 5 live in other lanes and are fetched with shuffles.
+//   MODE 1: one gate column bit (lb) below 5, the other (tb) at 5 or above.
+//   MODE 2: both gate column bits below 5.
+
+template <typename R, int MODE, bool HL, bool HR>
+__global__ void __launch_bounds__(kPassThreads, (sizeof(R) == 4 ? 3 : 1))
+pass_lane_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, int pa, int pb,
+                 const double2* __restrict__ L, long long Ls, const double2* __restrict__ Rm,
+                 long long Rs) {
+  typedef typename Cplx<R>::T C;
+  __shared__ C sL[16], sR[16];
+  const int s = blockIdx.y;
+  load_ops<R, HL, HR>(sL, sR, L, Ls, Rm, Rs, s);
+
+  const unsigned N = 1u << n;
+  C* __restrict__ Ts = T + (size_t)s * N * N;
+  const unsigned o1 = 1u << pb, o2 = 1u << pa;
+  const unsigned off[4] = {0u, o1, o2, o1 | o2};
+  const int lane = threadIdx.x & 31;
+  // MODE 1: which gate column bit lives in the lane index
+  const bool lb_is_a = (MODE == 1) && (pa < 5);
+  const int lb = lb_is_a ? pa : pb;
+  const int tb = lb_is_a ? pb : pa;
+  const int lcols = (MODE == 1) ? n - 1 : n;  // log2 of column units per row block
+  const unsigned units = (N >> 2) << lcols;   // a multiple of 32: whole warps
+
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < units;
+       t += gridDim.x * blockDim.x) {
+    const unsigned tc = t & ((1u << lcols) - 1u);
+    const unsigned r0 = dep2(t >> lcols, plo, phi);
+    if (MODE == 2) {
+      const unsigned c = tc;
+      C e[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) e[x] = Ts[(r0 | off[x]) * N + c];
+      if (HR) {
+        const int yown = 2 * ((c >> pa) & 1) + ((c >> pb) & 1);
+        const unsigned cb = (c & ~(o1 | o2)) & 31u;
+        C t4[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          C acc = czero<C>();
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const C v = shfl(e[x], (int)(cb | off[k]));
+            acc = cfma(v, sR[k * 4 + yown], acc);
+          }
+          t4[x] = acc;
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) e[x] = t4[x];
+      }
+      if (HL) {
+        C t4[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          C acc = czero<C>();
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc = cfma(sL[x * 4 + k], e[k], acc);
+          t4[x] = acc;
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) e[x] = t4[x];
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x) Ts[(r0 | off[x]) * N + c] = e[x];
+    } else {
+      const unsigned c = dep1(tc, tb);
+      const unsigned ot = 1u << tb;
+      C e[4][2];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const unsigned rb = (r0 | off[x]) * N;
+        e[x][0] = Ts[rb + c];
+        e[x][1] = Ts[rb + (c | ot)];
+      }
+      if (HR) {
+        const int lbv = (c >> lb) & 1;
+        const int partner = lane ^ (1 << lb);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const C q0 = shfl(e[x][0], partner), q1 = shfl(e[x][1], partner);
+          // B[x][k] for k = 0..3: k's lane bit picks own/partner, its
+          // thread bit picks the variant
+          C bk[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int kl = lb_is_a ? (k >> 1) : (k & 1);
+            const int kt = lb_is_a ? (k & 1) : (k >> 1);
+            const C own = kt ? e[x][1] : e[x][0];
+            const C oth = kt ? q1 : q0;
+            bk[k] = (kl == lbv) ? own : oth;
+          }
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            const int y = lb_is_a ? (2 * lbv + v) : (2 * v + lbv);
+            C acc = czero<C>();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc = cfma(bk[k], sR[k * 4 + y], acc);
+            e[x][v] = acc;
+          }
+        }
+      }
+      if (HL) {
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          C t4[4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            C acc = czero<C>();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc = cfma(sL[x * 4 + k], e[k][v], acc);
+            t4[x] = acc;
+          }
+#pragma unroll
+          for (int x = 0; x < 4; ++x) e[x][v] = t4[x];
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const unsigned rb = (r0 | off[x]) * N;
+        Ts[rb + c] = e[x][0];
+        Ts[rb + (c | ot)] = e[x][1];
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------- trace
+
+constexpr int kTraceThreads = 256;
+
+template <typename R>
+__global__ void __launch_bounds__(kTraceThreads) trace_kernel(
+    const typename Cplx<R>::T* __restrict__ T, int n, double2* __restrict__ tr) {
+  __shared__ double red[2 * (kTraceThreads / 32)];
+  const int s = blockIdx.x;
+  const size_t N = (size_t)1 << n;
+  const typename Cplx<R>::T* Ts = T + (size_t)s * N * N;
+  double re = 0.0, im = 0.0;
+  for (size_t i = threadIdx.x; i < N; i += blockDim.x) {
+    double2 e = to_d2(Ts[i * (N + 1)]);
+    re += e.x;
+    im += e.y;
+  }
+  for (int h = 16; h >= 1; h >>= 1) {
+    re += __shfl_xor_sync(kFull, re, h);
+    im += __shfl_xor_sync(kFull, im, h);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[2 * w] = re;
+    red[2 * w + 1] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[2 * k];
+      b += red[2 * k + 1];
+    }
+    tr[s] = make_double2(a, b);
+  }
+}
+
+__global__ void set_identity_kernel(double2* __restrict__ M, int n) {
+  const size_t N = (size_t)1 << n;
+  const size_t NN = N * N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < NN;
+       i += (size_t)gridDim.x * blockDim.x)
+    M[i] = make_double2((i / N == i % N) ? 1.0 : 0.0, 0.0);
+}
+
+// ------------------------------------------------------------- dispatch
+
+template <typename R, bool HL, bool HR>
+void launch_block(void* T, int n, int S, int plo, int phi, int pa, int pb, const double2* L,
+                  long long Ls, const double2* Rm, long long Rs, cudaStream_t st) {
+  typedef typename Cplx<R>::T C;
+  const unsigned nblk = 1u << (2 * (n - 2));
+  const int per_sm = sizeof(R) == 4 ? 3 : 1;
+  long long want = (nblk + kPassThreads - 1) / kPassThreads;
+  long long cap = ((long long)sm_count() * per_sm + S - 1) / S;
+  if (cap < 1) cap = 1;
+  dim3 grid((unsigned)(want < cap ? want : cap), S);
+  pass_block_kernel<R, HL, HR><<<grid, kPassThreads, 0, st>>>((C*)T, n, plo, phi, pa, pb, L, Ls,
+                                                              Rm, Rs);
+}
+
+template <typename R, int MODE, bool HL, bool HR>
+void launch_lane(void* T, int n, int S, int plo, int phi, int pa, int pb, const double2* L,
+                 long long Ls, const double2* Rm, long long Rs, cudaStream_t st) {
+  typedef typename Cplx<R>::T C;
+  const int lcols = MODE == 1 ? n - 1 : n;
+  const unsigned units = (1u << (n - 2)) << lcols;
+  const int per_sm = sizeof(R) == 4 ? 3 : 1;
+  long long want = (units + kPassThreads - 1) / kPassThreads;
+  long long cap = ((long long)sm_count() * per_sm + S - 1) / S;
+  if (cap < 1) cap = 1;
+  dim3 grid((unsigned)(want < cap ? want : cap), S);
+  pass_lane_kernel<R, MODE, HL, HR><<<grid, kPassThreads, 0, st>>>((C*)T, n, plo, phi, pa, pb,
+                                                                   L, Ls, Rm, Rs);
+}
+
+template <typename R, bool HL, bool HR>
+void pass_dispatch(void* T, int n, int S, int pa, int pb, const double2* L, long long Ls,
+                   const double2* Rm, long long Rs, cudaStream_t st) {
+  const int plo = pa < pb ? pa : pb, phi = pa < pb ? pb : pa;
+  if (n >= 6 && plo <= 1) {
+    if (phi < 5)
+      launch_lane<R, 2, HL, HR>(T, n, S, plo, phi, pa, pb, L, Ls, Rm, Rs, st);
+    else
+      launch_lane<R, 1, HL, HR>(T, n, S, plo, phi, pa, pb, L, Ls, Rm, Rs, st);
+  } else {
+    launch_block<R, HL, HR>(T, n, S, plo, phi, pa, pb, L, Ls, Rm, Rs, st);
+  }
+}
+
+template <typename R>
+void pass_ops(void* T, int n, int S, int pa, int pb, const double2* L, long long Ls,
+              const double2* Rm, long long Rs, cudaStream_t st) {
+  if (L && Rm)
+    pass_dispatch<R, true, true>(T, n, S, pa, pb, L, Ls, Rm, Rs, st);
+  else if (L)
+    pass_dispatch<R, true, false>(T, n, S, pa, pb, L, Ls, Rm, Rs, st);
+  else if (Rm)
+    pass_dispatch<R, false, true>(T, n, S, pa, pb, L, Ls, Rm, Rs, st);
+}
+
+}  // namespace
+
+// ================================================================ launchers
+
+int sm_count() {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+      v = 152;
+    cached = v;
+  }
+  return cached;
+}
+
+cudaError_t launch_set_identity(double2* M, int n, cudaStream_t st) {
+  const size_t NN = (size_t)1 << (2 * n);
+  size_t blocks = (NN + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  set_identity_kernel<<<(unsigned)blocks, 256, 0, st>>>(M, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conj_transpose(const double2* V, void* T, int n, int S, int prec,
+                                  cudaStream_t st) {
+  const int N = 1 << n;
+  dim3 grid((N + 31) / 32, (N + 31) / 32, S), block(32, 8);
+  if (prec == 0)
+    conj_transpose_kernel<double><<<grid, block, 0, st>>>(V, (double2*)T, N);
+  else
+    conj_transpose_kernel<float><<<grid, block, 0, st>>>(V, (float2*)T, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass(void* T, int n, int S, int a, int b, const double2* L,
+                        long long Lstride, const double2* R, long long Rstride, int prec,
+                        cudaStream_t st) {
+  if (!L && !R) return cudaSuccess;
+  const int pa = qubit_bit(n, a), pb = qubit_bit(n, b);
+  if (prec == 0)
+    pass_ops<double>(T, n, S, pa, pb, L, Lstride, R, Rstride, st);
+  else
+    pass_ops<float>(T, n, S, pa, pb, L, Lstride, R, Rstride, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const void* T, int n, int S, double2* tr, int prec, cudaStream_t st) {
+  if (prec == 0)
+    trace_kernel<double><<<S, kTraceThreads, 0, st>>>((const double2*)T, n, tr);
+  else
+    trace_kernel<float><<<S, kTraceThreads, 0, st>>>((const float2*)T, n, tr);
+  return cudaGetLastError();
+}
+
+}  // namespace qf

@@ -65,13 +65,18 @@ def test_one_update_at_full_size(qf, problem, dtype, S, tol):
     P = qf.partial_trace(T, a, b).cpu().numpy()
     Tc = T[s].cpu().numpy().astype(np.complex128)
     P_ref = orc.calc_env_mat(Tc, a, b, n)
-    assert _relerr(P[s], P_ref) <= 1e-11
+    if dtype == torch.complex128:
+        assert _relerr(P[s], P_ref) <= 1e-11
+    else:  # FP32 band sums (see test_partial_trace_matches_oracle)
+        bound = 1e-6 * orc.calc_env_mat(np.abs(Tc).astype(np.complex128), a, b, n).real
+        assert np.all(np.abs(P[s] - P_ref) <= bound)
     E = np.einsum("sij,skj->sik", P, u.conj())  # E = P u^dagger
     U, sig = qf.optimize_gates(torch.from_numpy(E).cuda())
     U = U.cpu().numpy()
     T_rem = orc.apply_right(Tc, u[s].conj().T, a, b, n)
     u_ref, s_ref = orc.optimize_gate(orc.calc_env_mat(T_rem, a, b, n))
-    assert np.max(np.abs(U[s] - u_ref)) <= 1e-9
+    # complex64: the environment carries the FP32 band-sum error above
+    assert np.max(np.abs(U[s] - u_ref)) <= (1e-9 if dtype == torch.complex128 else 1e-5)
     qf.apply_pair(T, a, b, torch.from_numpy(U).cuda(), torch.from_numpy(u.conj().transpose(0, 2, 1).copy()).cuda())
     T_new_ref = orc.apply_left(T_rem, U[s], a, b, n)
     e_upd = _relerr(T[s].cpu().numpy(), T_new_ref)

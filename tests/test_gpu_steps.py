@@ -73,19 +73,32 @@ def test_apply_pair_matches_oracle(qf, n, dtype):
     print(f"apply_pair n={n} {dtype}: max rel err {worst:.2e}")
 
 
-@pytest.mark.parametrize("n", [2, 3, 6, 8])
+@pytest.mark.parametrize("n", [2, 3, 6, 8, 10])
 @pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
 def test_partial_trace_matches_oracle(qf, n, dtype):
+    """complex128: FP64 sums, 1e-12 of the largest entry.  complex64: each
+    thread sums its band entries in FP32 and the warps reduce in FP32 before
+    the FP64 cross-CTA sum, so the error is bounded by (about) log2(terms)
+    FP32 roundings of the sum of |terms|: 1e-6 x Tr_rest(|T|) entrywise."""
     g = qi.rng(2000 + n)
     S = 2
     T0 = _rand_T(S, n, g)
     Tg = torch.from_numpy(T0).to(dtype).cuda()
     Tc = Tg.cpu().numpy().astype(np.complex128)  # the values the kernel sees
+    worst = 0.0
     for a, b in _pairs(n):
         P = qf.partial_trace(Tg, a, b).cpu().numpy()
         for s in range(S):
             ref = orc.calc_env_mat(Tc[s], a, b, n)
-            assert _relerr(P[s], ref) <= 1e-12, (a, b, s)
+            if dtype == torch.complex128:
+                assert _relerr(P[s], ref) <= 1e-12, (a, b, s)
+            else:
+                bound = 1e-6 * orc.calc_env_mat(np.abs(Tc[s]).astype(np.complex128), a, b, n).real
+                err = np.abs(P[s] - ref)
+                worst = max(worst, float(np.max(err / bound)))
+                assert np.all(err <= bound), (a, b, s, float(np.max(err / bound)))
+    if dtype == torch.complex64:
+        print(f"partial trace c64 n={n}: worst error / bound = {worst:.3f}")
 
 
 def test_optimize_gates_matches_oracle(qf):
