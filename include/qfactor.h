@@ -269,6 +269,26 @@ int qf_optimize_gates(const qf_c128* E, const qf_c128* u_old, double beta,
 int qf_trace(const void* T, int n_qubits, int n_starts, qf_c128* tr_out,
              int precision, void* stream);
 
+/*
+ * qf_partial_trace_noalloc -- qf_partial_trace without any device allocation.
+ * The paper has no counterpart: this is a service to callers that cannot
+ * allocate device memory inside the call (code that must not stall or
+ * synchronise the device, embedders whose own caching allocator holds all
+ * free device memory, code that must not fail on allocation once set up).
+ * Same arguments, layout and result as qf_partial_trace.  The environment
+ * kernel's scratch (n_starts * CTAs-per-start * 256 bytes of partial sums,
+ * plus n_starts counters) lives in one static device array of
+ * QF_NOALLOC_SCRATCH_BYTES per device, held until the process exits; a call
+ * that needs more returns QF_EINVAL.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  Every call shares the array:
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it and must be serialised by the caller.  Enqueue only.
+ */
+#define QF_NOALLOC_SCRATCH_BYTES (64 * 1024)
+int qf_partial_trace_noalloc(const void* T, int n_qubits, int n_starts, int a,
+                             int b, qf_c128* P, int precision, void* stream);
+
 /* C = G_0 G_1 ... G_{p-1} (InitCircuitTensor with the identity target), FP64.
  *   locations host or device; gates device p x 16; C_out device N x N. */
 int qf_circuit_unitary(int n_qubits, int n_gates, const qf_loc* locations,

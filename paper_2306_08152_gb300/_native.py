@@ -20,6 +20,8 @@ QF_C128 = 0
 QF_C64 = 1
 QF_C64_REFINE64 = 2
 
+QF_NOALLOC_SCRATCH_BYTES = 64 * 1024
+
 QF_STOP_CONVERGED = 1
 QF_STOP_PLATEAU = 2
 QF_STOP_MAX_SWEEPS = 3
@@ -83,6 +85,7 @@ SIGNATURES = {
     "qf_init_tensor": (I, [P, I, I, P, I, P, P, I, P]),
     "qf_apply_pair": (I, [P, I, I, I, I, P, P, I, P]),
     "qf_partial_trace": (I, [P, I, I, I, I, P, I, P]),
+    "qf_partial_trace_noalloc": (I, [P, I, I, I, I, P, I, P]),
     "qf_optimize_gates": (I, [P, P, D, I, P, P, P]),
     "qf_trace": (I, [P, I, I, P, I, P]),
     "qf_circuit_unitary": (I, [I, I, P, P, P, P]),

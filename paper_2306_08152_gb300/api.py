@@ -19,7 +19,7 @@ from ._native import check
 __all__ = [
     "QF_C128", "QF_C64", "QF_C64_REFINE64", "Options", "instantiate",
     "instantiate_ex", "cost_and_env", "Plan", "init_tensor", "apply_pair",
-    "partial_trace", "optimize_gates", "trace", "circuit_unitary",
+    "partial_trace", "partial_trace_noalloc", "optimize_gates", "trace", "circuit_unitary",
 ]
 
 QF_C128 = nat.QF_C128
@@ -259,6 +259,20 @@ def partial_trace(T, a, b, stream=None):
     P = torch.empty((S, 4, 4), dtype=torch.complex128, device=T.device)
     check(_lib().qf_partial_trace(_ptr(T), n, S, int(a), int(b), _ptr(P), _tensor_prec(T),
                                   _stream_handle(stream)))
+    return P
+
+
+def partial_trace_noalloc(T, a, b, P=None, stream=None):
+    """Like partial_trace, computed by the allocation-free entry point (the
+    library allocates nothing; the caller provides the output P, S x 4 x 4
+    complex128 on the device, or it is created here)."""
+    T = _dev(T, "T")
+    S, N = T.shape[0], T.shape[-1]
+    n = int(N).bit_length() - 1
+    if P is None:
+        P = torch.empty((S, 4, 4), dtype=torch.complex128, device=T.device)
+    check(_lib().qf_partial_trace_noalloc(_ptr(T), n, S, int(a), int(b), _ptr(P),
+                                          _tensor_prec(T), _stream_handle(stream)))
     return P
 
 

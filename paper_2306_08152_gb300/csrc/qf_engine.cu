@@ -150,6 +150,11 @@ size_t elem_bytes(int prec) { return prec == QF_C128 ? 16 : 8; }
 
 }  // namespace
 
+int qf_internal_set_error(int code, const char* what, const char* detail) {
+  if (detail && detail[0]) return set_error(code, "%s: %s", what, detail);
+  return set_error(code, "%s", what);
+}
+
 // ============================================================ the plan
 
 struct qf_plan {

@@ -61,3 +61,8 @@ cudaError_t launch_set_identity(double2* M, int n, cudaStream_t st);
 int sm_count();
 
 }  // namespace qf
+
+// Record an error for qf_last_error() from another translation unit and
+// return `code`; the message is "<what>: <detail>" (detail may be "").
+__attribute__((visibility("hidden"))) int qf_internal_set_error(int code, const char* what,
+                                                                const char* detail);
