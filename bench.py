@@ -149,7 +149,7 @@ def kernel_traffic(precision, starts, n):
     """DRAM bytes per pass launch from a committed ncu summary, if it was
     taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "pass_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_2306_08152_gb300", "csrc", "qf_kernels.cu")
+    src = os.path.join(ROOT, "paper_2306_08152_gb300", "csrc", "qf_pass.cu")
     if not os.path.exists(path):
         return None
     with open(path) as f:

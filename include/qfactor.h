@@ -182,6 +182,22 @@ int qf_cost_and_env(const qf_c128* target, int n_qubits, int n_gates,
                     const qf_c128* gates, double* out_cost, qf_c128* out_env,
                     qf_c128* out_trace, void* stream);
 
+/*
+ * qf_cost_grad -- the differentiable cost: cost_s = 1 - |t_s|/N with
+ * t_s = Tr(V^dagger C_s), and its gradient with respect to every gate entry
+ * in the convention of PyTorch's complex autograd (d/dRe + i d/dIm):
+ * grad_{s,k} = -(t_s / (N |t_s|)) E_{s,k}^dagger (E as in qf_cost_and_env,
+ * Sec. III; a zero trace gives a zero gradient).  One forward trace plus one
+ * adjoint walk gives all p gradients with O(4^n) memory.
+ *   gates     host-or-device, n_sets x p x 16.
+ *   out_cost  host, n_sets; may be NULL.
+ *   out_grad  host-or-device, n_sets x p x 16.
+ * Synchronises `stream`.
+ */
+int qf_cost_grad(const qf_c128* target, int n_qubits, int n_gates,
+                 const qf_loc* locations, int n_sets, const qf_c128* gates,
+                 double* out_cost, qf_c128* out_grad, void* stream);
+
 /* ------------------------------------------------------------------------
  * Resident plan: device-resident tensors, target and gates for repeated
  * sweeps (the form the benchmark times).

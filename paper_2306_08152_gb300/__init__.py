@@ -9,3 +9,4 @@ from .api import *  # noqa: F401,F403
 from .api import __all__  # noqa: F401
 from . import _native  # noqa: F401
 from ._native import QFactorError  # noqa: F401
+from .autograd import QFactorCost, qfactor_cost  # noqa: F401

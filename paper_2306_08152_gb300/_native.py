@@ -72,6 +72,7 @@ SIGNATURES = {
     "qf_instantiate_ex": (I, [P, I, I, P, I, P, ct.POINTER(qf_options), P, DP,
                               ct.POINTER(qf_result), P]),
     "qf_cost_and_env": (I, [P, I, I, P, I, P, DP, P, P, P]),
+    "qf_cost_grad": (I, [P, I, I, P, I, P, DP, P, P]),
     "qf_plan_create": (I, [I, I, P, I, I, ct.POINTER(P)]),
     "qf_plan_destroy": (I, [P]),
     "qf_plan_load": (I, [P, P, P, P]),

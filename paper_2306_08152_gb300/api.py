@@ -18,7 +18,7 @@ from ._native import check
 
 __all__ = [
     "QF_C128", "QF_C64", "QF_C64_REFINE64", "Options", "instantiate",
-    "instantiate_ex", "cost_and_env", "Plan", "init_tensor", "apply_pair",
+    "instantiate_ex", "cost_and_env", "cost_grad", "costs", "Plan", "init_tensor", "apply_pair",
     "partial_trace", "partial_trace_noalloc", "optimize_gates", "trace", "circuit_unitary",
 ]
 
@@ -147,6 +147,43 @@ def cost_and_env(target, locations, gates, stream=None):
     if single:
         return c[0], envs[0], trs[0]
     return c, envs, trs
+
+
+def cost_grad(target, locations, gates, stream=None):
+    """Costs and their gradients with respect to the gates (qf_cost_grad),
+    in PyTorch's complex-autograd convention.  ``gates`` (S, p, 4, 4) or
+    (p, 4, 4); returns (costs (S,) numpy, grads like gates)."""
+    target = _c128(target, "target")
+    g = _c128(gates, "gates")
+    single = g.dim() == 3
+    if single:
+        g = g.unsqueeze(0)
+    locs = _locs(locations)
+    n = _nqubits(target)
+    S, p = g.shape[0], g.shape[1]
+    grads = torch.empty_like(g)
+    costs = (ct.c_double * S)()
+    check(_lib().qf_cost_grad(_ptr(target), n, p, _ptr(locs), S, _ptr(g), costs, _ptr(grads),
+                              _stream_handle(stream)))
+    c = np.array(costs[:])
+    if single:
+        return c[0], grads[0]
+    return c, grads
+
+
+def costs(target, locations, gates, stream=None):
+    """Costs 1 - |Tr(V^dagger C)|/N of gate sets (S, p, 4, 4), without
+    environments: InitCircuitTensor plus an FP64 trace on the GPU."""
+    g = _c128(gates, "gates")
+    if g.dim() == 3:
+        g = g.unsqueeze(0)
+    target = _c128(target, "target")
+    plan = Plan(_nqubits(target), locations, g.shape[0], QF_C128)
+    try:
+        plan.load(target, g, stream=stream)
+        return plan.costs()
+    finally:
+        plan.close()
 
 
 class Plan:

@@ -571,12 +571,18 @@ int qf_instantiate(const qf_c128* target, int n_qubits, int n_gates, const qf_lo
   return QF_OK;
 }
 
-int qf_cost_and_env(const qf_c128* target, int n_qubits, int n_gates, const qf_loc* locations,
-                    int n_sets, const qf_c128* gates, double* out_cost, qf_c128* out_env,
-                    qf_c128* out_trace, void* stream) {
+namespace {
+
+// The adjoint walk shared by qf_cost_and_env and qf_cost_grad: build every
+// tensor, take its trace, then move each gate from the tensor's right to its
+// left (one pass, L = u, R = u^dagger), reading its environment on the way.
+// With `grad`, the environments are turned into cost gradients on the device.
+int adjoint_walk(const qf_c128* target, int n_qubits, int n_gates, const qf_loc* locations,
+                 int n_sets, const qf_c128* gates, double* out_cost, qf_c128* out_env,
+                 qf_c128* out_trace, bool grad, void* stream) {
   QF_TRY(check_sizes(n_qubits, n_gates));
   if (n_sets < 1) return set_error(QF_EINVAL, "n_sets=%d must be >= 1", n_sets);
-  if (!out_env) return set_error(QF_EINVAL, "out_env is NULL");
+  if (!out_env) return set_error(QF_EINVAL, "output array is NULL");
   cudaStream_t st = as_stream(stream);
   const int S = n_sets, p = n_gates;
   PlanGuard g;
@@ -590,7 +596,8 @@ int qf_cost_and_env(const qf_c128* target, int n_qubits, int n_gates, const qf_l
   DevBuf envb;
   double2* env_dev = nullptr;
   const size_t ecount = (size_t)S * p * 16;
-  if (is_device_ptr(out_env)) {
+  const bool out_on_device = is_device_ptr(out_env);
+  if (out_on_device) {
     env_dev = reinterpret_cast<double2*>(out_env);
   } else {
     QF_TRY(envb.alloc(ecount * sizeof(double2)));
@@ -601,7 +608,9 @@ int qf_cost_and_env(const qf_c128* target, int n_qubits, int n_gates, const qf_l
     QF_TRY(plan_update(P, k, qf::kEnvOnly, 0.0, env_dev + (size_t)k * 16, (long long)p * 16));
     if (k > 0) QF_TRY(plan_pass(P, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
   }
-  if (!is_device_ptr(out_env))
+  if (grad)
+    QF_CUDA(qf::launch_grad_from_env(env_dev, P->tr.as<double2>(), n_qubits, S, p, st));
+  if (!out_on_device)
     QF_CUDA(cudaMemcpyAsync(out_env, env_dev, ecount * sizeof(double2), cudaMemcpyDeviceToHost,
                             st));
   QF_CUDA(cudaStreamSynchronize(st));
@@ -610,6 +619,22 @@ int qf_cost_and_env(const qf_c128* target, int n_qubits, int n_gates, const qf_l
   if (out_trace)
     for (int s = 0; s < S; ++s) out_trace[s] = tr[s];
   return QF_OK;
+}
+
+}  // namespace
+
+int qf_cost_and_env(const qf_c128* target, int n_qubits, int n_gates, const qf_loc* locations,
+                    int n_sets, const qf_c128* gates, double* out_cost, qf_c128* out_env,
+                    qf_c128* out_trace, void* stream) {
+  return adjoint_walk(target, n_qubits, n_gates, locations, n_sets, gates, out_cost, out_env,
+                      out_trace, false, stream);
+}
+
+int qf_cost_grad(const qf_c128* target, int n_qubits, int n_gates, const qf_loc* locations,
+                 int n_sets, const qf_c128* gates, double* out_cost, qf_c128* out_grad,
+                 void* stream) {
+  return adjoint_walk(target, n_qubits, n_gates, locations, n_sets, gates, out_cost, out_grad,
+                      nullptr, true, stream);
 }
 
 // ------------------------------------------------------------ single steps

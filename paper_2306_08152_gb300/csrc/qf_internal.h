@@ -50,6 +50,10 @@ cudaError_t launch_optimize(const double2* E, const double2* u_old, double beta,
                             int count, double2* u_out, double* sigma_out,
                             cudaStream_t st);
 
+// env[s][k] <- -(t_s / (N |t_s|)) env[s][k]^dagger in place (t = tr[s]).
+cudaError_t launch_grad_from_env(double2* env, const double2* tr, int n, int S, int p,
+                                 cudaStream_t st);
+
 // tr_s = Tr T_s (FP64 accumulation).
 cudaError_t launch_trace(const void* T, int n, int S, double2* tr, int prec,
                          cudaStream_t st);
