@@ -94,8 +94,9 @@ typedef struct { int32_t a, b; } qf_loc;     /* gate location: qubits a != b  */
  *   beta          the update takes the SVD of (1-beta) E + beta u^dagger.
  *   precision     QF_C128, QF_C64 or QF_C64_REFINE64.
  *   switch_tol    QF_C64_REFINE64: leave the c64 phase once the best cost is
- *                 <= switch_tol, or once a c64 sweep lowers no start's cost
- *                 by more than 1e-3 of its value, or after max_c64_sweeps.
+ *                 <= switch_tol, or once ten c64 sweeps have lowered the cost
+ *                 by less than 1e-7 (the complex64 noise floor), or after
+ *                 max_c64_sweeps.  Reported costs are always FP64 traces.
  */
 typedef struct {
     double dist_tol;
@@ -197,6 +198,43 @@ int qf_cost_and_env(const qf_c128* target, int n_qubits, int n_gates,
 int qf_cost_grad(const qf_c128* target, int n_qubits, int n_gates,
                  const qf_loc* locations, int n_sets, const qf_c128* gates,
                  double* out_cost, qf_c128* out_grad, void* stream);
+
+/*
+ * qf_instantiate_batched -- many small instantiations in one persistent
+ * launch (captured as a CUDA graph).  Each (instance, start) problem runs the
+ * whole Qfactor loop of Alg. 1 on one warp with its circuit tensor in shared
+ * memory; the starts of an instance run side by side and stop at their next
+ * sweep boundary once any of them has reached dist_tol, or once all of them
+ * have met a plateau test (Sec. IV-A, without lock-step).  The number of
+ * warps per CTA is chosen by a built-in autotuner (timed trial runs, cached
+ * per largest qubit count, precision and device).
+ *   n_qubits, n_gates  host, n_instances each; 2 <= n_qubits <= QF_BATCH_MAX_QUBITS.
+ *   locations          host-or-device, concatenated over instances.
+ *   targets            host-or-device, concatenated N_i x N_i targets.
+ *   initial_gates      host-or-device, [instance][start][gate][16].
+ *   opts               host; NULL = defaults (long_diff_count <= 127).
+ *   out_gates          host-or-device, layout of initial_gates.
+ *   out_costs          host, n_instances * n_starts final costs.
+ *   out_sweeps         host, n_instances * n_starts; may be NULL.
+ *   out_best           host, n_instances best start indices; may be NULL.
+ *   stats              host; may be NULL.
+ * Synchronises `stream`.
+ */
+#define QF_BATCH_MAX_QUBITS 6
+typedef struct {
+    int32_t warps_per_cta;     /* chosen by the autotuner                   */
+    int32_t ctas;              /* persistent CTAs launched                  */
+    double kernel_ms;          /* device time of the persistent launch      */
+    int64_t total_sweeps;      /* over all problems                          */
+    int64_t total_c64_sweeps;  /* of which in complex64                      */
+} qf_batch_stats;
+int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
+                           const int32_t* n_gates, const qf_loc* locations,
+                           const qf_c128* targets, int n_starts,
+                           const qf_c128* initial_gates, const qf_options* opts,
+                           qf_c128* out_gates, double* out_costs,
+                           int32_t* out_sweeps, int32_t* out_best,
+                           qf_batch_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------
  * Resident plan: device-resident tensors, target and gates for repeated

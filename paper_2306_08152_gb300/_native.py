@@ -21,6 +21,7 @@ QF_C64 = 1
 QF_C64_REFINE64 = 2
 
 QF_NOALLOC_SCRATCH_BYTES = 64 * 1024
+QF_BATCH_MAX_QUBITS = 6
 
 QF_STOP_CONVERGED = 1
 QF_STOP_PLATEAU = 2
@@ -57,6 +58,16 @@ class qf_result(ct.Structure):
     ]
 
 
+class qf_batch_stats(ct.Structure):
+    _fields_ = [
+        ("warps_per_cta", ct.c_int32),
+        ("ctas", ct.c_int32),
+        ("kernel_ms", ct.c_double),
+        ("total_sweeps", ct.c_int64),
+        ("total_c64_sweeps", ct.c_int64),
+    ]
+
+
 P = ct.c_void_p
 I = ct.c_int
 D = ct.c_double
@@ -73,6 +84,8 @@ SIGNATURES = {
                               ct.POINTER(qf_result), P]),
     "qf_cost_and_env": (I, [P, I, I, P, I, P, DP, P, P, P]),
     "qf_cost_grad": (I, [P, I, I, P, I, P, DP, P, P]),
+    "qf_instantiate_batched": (I, [I, P, P, P, P, I, P, ct.POINTER(qf_options), P, DP, P, P,
+                                   ct.POINTER(qf_batch_stats), P]),
     "qf_plan_create": (I, [I, I, P, I, I, ct.POINTER(P)]),
     "qf_plan_destroy": (I, [P]),
     "qf_plan_load": (I, [P, P, P, P]),

@@ -18,7 +18,7 @@ from ._native import check
 
 __all__ = [
     "QF_C128", "QF_C64", "QF_C64_REFINE64", "Options", "instantiate",
-    "instantiate_ex", "cost_and_env", "cost_grad", "costs", "Plan", "init_tensor", "apply_pair",
+    "instantiate_ex", "instantiate_batched", "cost_and_env", "cost_grad", "costs", "Plan", "init_tensor", "apply_pair",
     "partial_trace", "partial_trace_noalloc", "optimize_gates", "trace", "circuit_unitary",
 ]
 
@@ -147,6 +147,56 @@ def cost_and_env(target, locations, gates, stream=None):
     if single:
         return c[0], envs[0], trs[0]
     return c, envs, trs
+
+
+def instantiate_batched(instances, options=None, stream=None, **kw):
+    """Many small instantiations in one persistent launch
+    (qf_instantiate_batched).  ``instances`` is a sequence of
+    (target (N,N), locations (p,2), starts (S,p,4,4)) with the same S; arrays
+    may be numpy or CPU tensors.  Returns a dict with per-(instance, start)
+    costs and sweeps, per-instance best start, the gates and launch stats."""
+    targets, locs, starts, nq, ng = [], [], [], [], []
+    S = None
+    for V, L, G in instances:
+        V = np.ascontiguousarray(np.asarray(V, dtype=np.complex128))
+        L = np.ascontiguousarray(np.asarray(L, dtype=np.int32)).reshape(-1, 2)
+        G = np.ascontiguousarray(np.asarray(G, dtype=np.complex128))
+        if S is None:
+            S = G.shape[0]
+        if G.shape[0] != S or G.shape[1] != L.shape[0]:
+            raise ValueError("every instance needs the same number of starts and p gates per start")
+        nq.append(int(V.shape[0]).bit_length() - 1)
+        ng.append(L.shape[0])
+        targets.append(V.reshape(-1))
+        locs.append(L)
+        starts.append(G.reshape(-1))
+    I = len(nq)
+    nq = np.asarray(nq, dtype=np.int32)
+    ng = np.asarray(ng, dtype=np.int32)
+    tg = np.concatenate(targets)
+    lc = np.ascontiguousarray(np.concatenate(locs))
+    st = np.concatenate(starts)
+    out = np.empty_like(st)
+    costs = np.empty(I * S, dtype=np.float64)
+    sweeps = np.empty(I * S, dtype=np.int32)
+    best = np.empty(I, dtype=np.int32)
+    stats = nat.qf_batch_stats()
+    opts = options if options is not None else Options(**kw)
+    check(_lib().qf_instantiate_batched(
+        I, ct.c_void_p(nq.ctypes.data), ct.c_void_p(ng.ctypes.data), ct.c_void_p(lc.ctypes.data),
+        ct.c_void_p(tg.ctypes.data), S, ct.c_void_p(st.ctypes.data), ct.byref(opts.c),
+        ct.c_void_p(out.ctypes.data), costs.ctypes.data_as(ct.POINTER(ct.c_double)),
+        ct.c_void_p(sweeps.ctypes.data), ct.c_void_p(best.ctypes.data), ct.byref(stats),
+        _stream_handle(stream)))
+    gates, off = [], 0
+    for i in range(I):
+        k = S * ng[i] * 16
+        gates.append(out[off:off + k].reshape(S, ng[i], 4, 4))
+        off += k
+    return {"costs": costs.reshape(I, S), "sweeps": sweeps.reshape(I, S), "best": best,
+            "gates": gates, "warps_per_cta": stats.warps_per_cta, "ctas": stats.ctas,
+            "kernel_ms": stats.kernel_ms, "total_sweeps": stats.total_sweeps,
+            "total_c64_sweeps": stats.total_c64_sweeps}
 
 
 def cost_grad(target, locations, gates, stream=None):

@@ -1,0 +1,643 @@
+// Batched instantiation of many small circuits in one persistent launch.
+//
+// Each warp runs a whole Qfactor (Alg. 1) for one (instance, start) problem:
+// InitCircuitTensor, TwoSidedSweeps, the cost after every sweep, the
+// stopping rules and the periodic rebuild, with the circuit tensor in the
+// warp's own slice of shared memory (4^n entries: 1 KB at 3 qubits, 16 KB at
+// 5 qubits in complex128).  Warps take problems from an atomic work counter,
+// instance-major, so the starts of an instance run side by side.  Starts of
+// one instance meet only through two per-instance words in global memory:
+// a "converged" flag and a plateau count (Sec. IV-A: stop when any start
+// converges, or once every start has met a plateau test).  Nothing waits on
+// them; a warp reads them at its sweep boundaries.
+//
+// The gate update is the warp polar of qf_polar.cuh; in QF_C64_REFINE64 the
+// bulk sweeps run on a complex64 tensor and the warp switches to a
+// complex128 tensor rebuilt from the target and its FP64 gates.
+
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "qf_device.cuh"
+#include "qf_internal.h"
+#include "qf_polar.cuh"
+#include "qfactor.h"
+
+namespace qf {
+namespace {
+
+using namespace dev;
+
+struct BatchInst {
+  int n, p;
+  long long loc_off;   // first location of the instance
+  long long tgt_off;   // first target entry
+  long long gate_off;  // first gate entry of start 0 ([start][p][16])
+};
+
+constexpr int kRing = 128;  // cost history kept per warp (long plateau window)
+
+struct BatchParams {
+  const BatchInst* inst;
+  int n_inst, S;
+  const int2* locs;
+  const double2* targets;
+  double2* gates;
+  double* cost_out;
+  int* sweeps_out;
+  int* c64_out;
+  int* reason_out;
+  int* conv_flag;
+  int* plat_count;
+  int* status;
+  unsigned* work;
+  double dist_tol, diff_a, diff_r, long_r, beta, switch_tol;
+  int max_sweeps, min_sweeps, reset_iter, long_L, precision, max_c64;
+  int tmax_bytes;  // tensor capacity of a warp slice (complex128, largest n)
+  int warp_bytes;  // whole warp slice
+};
+
+template <typename R>
+struct W {
+  typedef typename Cplx<R>::T C;
+
+  // T <- V^dagger
+  static __device__ void conj_transpose(C* T, const double2* __restrict__ V, int n) {
+    const int NN = 1 << (2 * n);
+    const int lane = threadIdx.x & 31;
+    for (int idx = lane; idx < NN; idx += 32) {
+      const int r = idx >> n, c = idx & ((1 << n) - 1);
+      const double2 v = V[idx];
+      T[(c << n) | r] = cmake(make_double2(v.x, -v.y), R());
+    }
+    __syncwarp();
+  }
+
+  // T <- (L on (a,b)) T (R on (a,b)); operators in shared memory.
+  template <bool HL, bool HR>
+  static __device__ void pass(C* T, int n, int pa, int pb, const C* Lm, const C* Rm) {
+    const int lane = threadIdx.x & 31;
+    const int plo = pa < pb ? pa : pb, phi = pa < pb ? pb : pa;
+    const int lnc = n - 2;
+    const unsigned N = 1u << n, cmask = (1u << lnc) - 1u, nblk = 1u << (2 * lnc);
+    const unsigned o1 = 1u << pb, o2 = 1u << pa;
+    const unsigned off[4] = {0u, o1, o2, o1 | o2};
+    for (unsigned blk = lane; blk < nblk; blk += 32) {
+      const unsigned r0 = dep2(blk >> lnc, plo, phi), c0 = dep2(blk & cmask, plo, phi);
+      C bm[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) bm[x][y] = T[(r0 | off[x]) * N + (c0 | off[y])];
+      if (HR) {
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          C t[4];
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            C acc = czero<C>();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc = cfma(bm[x][k], Rm[k * 4 + y], acc);
+            t[y] = acc;
+          }
+#pragma unroll
+          for (int y = 0; y < 4; ++y) bm[x][y] = t[y];
+        }
+      }
+      if (HL) {
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          C t[4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            C acc = czero<C>();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc = cfma(Lm[x * 4 + k], bm[k][y], acc);
+            t[x] = acc;
+          }
+#pragma unroll
+          for (int x = 0; x < 4; ++x) bm[x][y] = t[x];
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) T[(r0 | off[x]) * N + (c0 | off[y])] = bm[x][y];
+    }
+    __syncwarp();
+  }
+
+  // Band partial trace on (a, b): returns P[i][j] on lane (i, j).
+  static __device__ double2 band(const C* T, int n, int pa, int pb, const Lane& L) {
+    const int plo = pa < pb ? pa : pb, phi = pa < pb ? pb : pa;
+    const unsigned N = 1u << n, nr = 1u << (n - 2);
+    const unsigned o1 = 1u << pb, o2 = 1u << pa;
+    const unsigned off[4] = {0u, o1, o2, o1 | o2};
+    R v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = R(0);
+    for (unsigned r = L.l; r < nr; r += 32) {
+      const unsigned d = dep2(r, plo, phi);
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const C e = T[(d | off[x]) * N + (d | off[y])];
+          v[2 * (x * 4 + y)] += e.x;
+          v[2 * (x * 4 + y) + 1] += e.y;
+        }
+    }
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+      const bool up = (L.l & h) != 0;
+#pragma unroll
+      for (int i = 0; i < h; ++i) {
+        const R keep = up ? v[i + h] : v[i];
+        const R send = up ? v[i] : v[i + h];
+        v[i] = keep + __shfl_xor_sync(kFull, send, h);
+      }
+    }
+    const double acc = (double)v[0];
+    const int e = L.l & 15;
+    return make_double2(__shfl_sync(kFull, acc, 2 * e), __shfl_sync(kFull, acc, 2 * e + 1));
+  }
+
+  // 1 - |Tr T| / N (FP64 sum)
+  static __device__ double cost(const C* T, int n) {
+    const int N = 1 << n, lane = threadIdx.x & 31;
+    double re = 0.0, im = 0.0;
+    for (int i = lane; i < N; i += 32) {
+      const double2 e = to_d2(T[i * (N + 1)]);
+      re += e.x;
+      im += e.y;
+    }
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+      re += __shfl_xor_sync(kFull, re, h);
+      im += __shfl_xor_sync(kFull, im, h);
+    }
+    return 1.0 - sqrt(re * re + im * im) / (double)N;
+  }
+
+  // InitCircuitTensor: T <- V^dagger, then T <- T (u_k on loc_k) for all k.
+  static __device__ void build(C* T, C* LRs, const double2* V, const double2* g, const int2* locs,
+                               int n, int p, const Lane& L) {
+    conj_transpose(T, V, n);
+    for (int k = 0; k < p; ++k) {
+      if (L.l < 16) LRs[16 + L.l] = cmake(g[k * 16 + L.l], R());
+      __syncwarp();
+      const int2 lc = locs[k];
+      pass<false, true>(T, n, n - 1 - lc.x, n - 1 - lc.y, LRs, LRs + 16);
+    }
+  }
+
+  // One gate update: environment from the band, the FP64 warp polar, the
+  // pass operators into shared memory, then the fused pass.
+  static __device__ void update(C* T, C* LRs, float2* scratch, double2* g, int2 lc, int n,
+                                bool forward, double beta, const Lane& L, int* bad) {
+    const int pa = n - 1 - lc.x, pb = n - 1 - lc.y;
+    const double2 P = band(T, n, pa, pb, L);
+    const int e = L.l & 15;
+    const double2 u = g[e];
+    const double2 ud = wdag(L, u);
+    const double2 E = forward ? wmm_dn(L, u, P) : wmm_nd(L, P, u);
+    double2 A = E;
+    if (beta != 0.0)
+      A = make_double2((1.0 - beta) * E.x + beta * ud.x, (1.0 - beta) * E.y + beta * ud.y);
+    double2 un;
+    double sg;
+    if (!warp_polar(L, A, scratch, &un, &sg)) {
+      *bad = 1;
+      un = u;
+    }
+    if (L.l < 16) {
+      g[e] = un;
+      LRs[e] = cmake(forward ? ud : un, R());
+      LRs[16 + e] = cmake(forward ? un : ud, R());
+    }
+    __syncwarp();
+    pass<true, true>(T, n, pa, pb, LRs, LRs + 16);
+  }
+
+  // TwoSidedSweep (Alg. 1).
+  static __device__ void sweep(C* T, C* LRs, float2* scratch, double2* g, const int2* locs,
+                               int n, int p, double beta, const Lane& L, int* bad) {
+    for (int k = p - 1; k >= 0; --k)
+      update(T, LRs, scratch, g + k * 16, locs[k], n, false, beta, L, bad);
+    for (int k = 0; k < p; ++k)
+      update(T, LRs, scratch, g + k * 16, locs[k], n, true, beta, L, bad);
+  }
+};
+
+__device__ bool plateau_test(const double* ring, int len, int it, const BatchParams& bp) {
+  const double c = ring[(len - 1) % kRing];
+  if ((bp.diff_a > 0.0 || bp.diff_r > 0.0) && len >= 2) {
+    if (ring[(len - 2) % kRing] - c <= bp.diff_a + bp.diff_r * c) return true;
+  }
+  if (bp.long_L > 0 && it >= bp.long_L) {
+    const double old = ring[(len - 1 - bp.long_L) % kRing];
+    if (old - c < bp.long_r * old) return true;
+  }
+  return false;
+}
+
+__global__ void batched_kernel(BatchParams bp) {
+  extern __shared__ __align__(256) unsigned char smem[];
+  const int wid = threadIdx.x >> 5;
+  unsigned char* ws = smem + (size_t)wid * bp.warp_bytes;
+  void* Tbuf = ws;
+  unsigned char* after = ws + bp.tmax_bytes;
+  double2* LRd = reinterpret_cast<double2*>(after);            // 32 x 16 B
+  float2* scratch = reinterpret_cast<float2*>(after + 512);    // 32 x 8 B
+  double* ring = reinterpret_cast<double*>(after + 768);       // kRing x 8 B
+  const Lane L;
+  const unsigned total = (unsigned)bp.n_inst * (unsigned)bp.S;
+  for (;;) {
+    unsigned prob = 0;
+    if (L.l == 0) prob = atomicAdd(bp.work, 1u);
+    prob = __shfl_sync(kFull, prob, 0);
+    if (prob >= total) break;
+    const int i = (int)(prob / bp.S), s = (int)(prob % bp.S);
+    const BatchInst in = bp.inst[i];
+    const int n = in.n, p = in.p;
+    double2* g = bp.gates + in.gate_off + (long long)s * p * 16;
+    const double2* V = bp.targets + in.tgt_off;
+    const int2* locs = bp.locs + in.loc_off;
+    volatile int* conv = bp.conv_flag + i;
+    volatile int* plat = bp.plat_count + i;
+    bool c64 = bp.precision != QF_C128;
+    const bool refine = bp.precision == QF_C64_REFINE64;
+    int bad = 0;
+    float2* LRf = reinterpret_cast<float2*>(LRd);
+    if (c64)
+      W<float>::build((float2*)Tbuf, LRf, V, g, locs, n, p, L);
+    else
+      W<double>::build((double2*)Tbuf, LRd, V, g, locs, n, p, L);
+    double c = c64 ? W<float>::cost((float2*)Tbuf, n) : W<double>::cost((double2*)Tbuf, n);
+    int len = 0;
+    if (L.l == 0) ring[0] = c;
+    len = 1;
+    __syncwarp();
+    int it = 0, c64_sw = 0, reason = QF_STOP_MAX_SWEEPS;
+    bool plateaued = false;
+    for (it = 1; it <= bp.max_sweeps; ++it) {
+      if (*conv) {  // another start of this instance reached dist_tol
+        reason = QF_STOP_CONVERGED;
+        --it;
+        break;
+      }
+      if (c64)
+        W<float>::sweep((float2*)Tbuf, LRf, scratch, g, locs, n, p, bp.beta, L, &bad);
+      else
+        W<double>::sweep((double2*)Tbuf, LRd, scratch, g, locs, n, p, bp.beta, L, &bad);
+      if (bp.reset_iter > 0 && it % bp.reset_iter == 0) {
+        if (c64)
+          W<float>::build((float2*)Tbuf, LRf, V, g, locs, n, p, L);
+        else
+          W<double>::build((double2*)Tbuf, LRd, V, g, locs, n, p, L);
+      }
+      const double prev = c;
+      c = c64 ? W<float>::cost((float2*)Tbuf, n) : W<double>::cost((double2*)Tbuf, n);
+      if (c64 && refine) {
+        ++c64_sw;
+        // leave complex64 once the cost is below switch_tol, or once ten c64
+        // sweeps have lowered it by less than the complex64 noise floor
+        const bool stalled = len > 10 && ring[(len - 10) % kRing] - c < 1e-7;
+        if (c <= bp.switch_tol || stalled || c64_sw >= bp.max_c64) {
+          // rebuild in complex128 from the target and the FP64 gates
+          W<double>::build((double2*)Tbuf, LRd, V, g, locs, n, p, L);
+          c = W<double>::cost((double2*)Tbuf, n);
+          c64 = false;
+        } else {
+          if (L.l == 0) ring[len % kRing] = c;
+          ++len;
+          __syncwarp();
+          if (*plat >= bp.S) {  // every other start plateaued and this one still runs
+            reason = QF_STOP_PLATEAU;
+            break;
+          }
+          continue;
+        }
+      }
+      if (L.l == 0) ring[len % kRing] = c;
+      ++len;
+      __syncwarp();
+      if (it >= bp.min_sweeps) {
+        if (c <= bp.dist_tol) {
+          if (L.l == 0) atomicExch(bp.conv_flag + i, 1);
+          reason = QF_STOP_CONVERGED;
+          break;
+        }
+        if (!plateaued && plateau_test(ring, len, it, bp)) {
+          plateaued = true;
+          if (L.l == 0) atomicAdd(bp.plat_count + i, 1);
+        }
+        __syncwarp();
+        if (*plat >= bp.S) {
+          reason = QF_STOP_PLATEAU;
+          break;
+        }
+      }
+    }
+    if (it > bp.max_sweeps) it = bp.max_sweeps;
+    if (c64) {  // report an FP64 cost: rebuild the tensor in complex128 once
+      W<double>::build((double2*)Tbuf, LRd, V, g, locs, n, p, L);
+      c = W<double>::cost((double2*)Tbuf, n);
+    }
+    if (L.l == 0) {
+      bp.cost_out[prob] = c;
+      bp.sweeps_out[prob] = it;
+      bp.c64_out[prob] = c64_sw;
+      bp.reason_out[prob] = reason;
+      if (bad) atomicExch(bp.status, QF_ENONFINITE);
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ host
+
+struct DevMem {
+  void* p = nullptr;
+  ~DevMem() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t b) { return cudaMalloc(&p, b ? b : 16); }
+};
+
+bool is_dev(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Autotuner: warps per CTA chosen by timing a short run (two sweeps of a
+// prefix of the problems) for every candidate that fits in shared memory,
+// cached per (largest qubit count, precision).
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int>, int> g_tuned;
+
+cudaError_t launch_batch(const BatchParams& bp, int wpc, int smem_limit, cudaStream_t st,
+                         int* ctas_out) {
+  const int smem = wpc * bp.warp_bytes;
+  cudaError_t e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_limit);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, 32 * wpc, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long problems = (long long)bp.n_inst * bp.S;
+  long long ctas = (long long)sm_count() * per_sm;
+  const long long need = (problems + wpc - 1) / wpc;
+  if (ctas > need) ctas = need;
+  if (ctas < 1) ctas = 1;
+  if (ctas_out) *ctas_out = (int)ctas;
+  batched_kernel<<<(unsigned)ctas, 32 * wpc, smem, st>>>(bp);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace qf
+
+using namespace qf;
+
+extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
+                                      const int32_t* n_gates, const qf_loc* locations,
+                                      const qf_c128* targets, int n_starts,
+                                      const qf_c128* initial_gates, const qf_options* opts,
+                                      qf_c128* out_gates, double* out_costs, int32_t* out_sweeps,
+                                      int32_t* out_best, qf_batch_stats* stats, void* stream) {
+  qf_options o;
+  qf_options_default(&o);
+  if (opts) o = *opts;
+  if (n_instances < 1 || n_starts < 1)
+    return qf_internal_set_error(QF_EINVAL, "n_instances and n_starts must be >= 1", "");
+  if (!n_qubits || !n_gates || !locations || !targets || !initial_gates || !out_gates ||
+      !out_costs)
+    return qf_internal_set_error(QF_EINVAL, "NULL argument", "");
+  if (o.max_sweeps < 1) return qf_internal_set_error(QF_EINVAL, "max_sweeps must be >= 1", "");
+  if (o.precision != QF_C128 && o.precision != QF_C64 && o.precision != QF_C64_REFINE64)
+    return qf_internal_set_error(QF_EINVAL, "unknown precision", "");
+  if (!(o.beta >= 0.0 && o.beta <= 1.0))
+    return qf_internal_set_error(QF_EINVAL, "beta outside [0, 1]", "");
+  if (o.long_diff_count < 0 || o.long_diff_count >= kRing)
+    return qf_internal_set_error(QF_EINVAL, "long_diff_count must be in [0, 127] here", "");
+  // sizes and offsets (host arrays)
+  std::vector<BatchInst> inst(n_instances);
+  long long loc_total = 0, tgt_total = 0, gate_total = 0;
+  int nmax = 0;
+  for (int i = 0; i < n_instances; ++i) {
+    const int n = n_qubits[i], p = n_gates[i];
+    if (n < QF_MIN_QUBITS || n > QF_BATCH_MAX_QUBITS)
+      return qf_internal_set_error(QF_EINVAL, "an instance's qubit count is outside [2, QF_BATCH_MAX_QUBITS]", "");
+    if (p < 1) return qf_internal_set_error(QF_EINVAL, "an instance has no gates", "");
+    inst[i] = BatchInst{n, p, loc_total, tgt_total, gate_total};
+    loc_total += p;
+    tgt_total += 1ll << (2 * n);
+    gate_total += (long long)n_starts * p * 16;
+    if (n > nmax) nmax = n;
+  }
+  // locations to the host for validation
+  std::vector<qf_loc> hl(loc_total);
+  if (is_dev(locations)) {
+    if (cudaMemcpy(hl.data(), locations, sizeof(qf_loc) * loc_total, cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return qf_internal_set_error(QF_ECUDA, "copying locations failed", "");
+  } else {
+    memcpy(hl.data(), locations, sizeof(qf_loc) * loc_total);
+  }
+  for (int i = 0; i < n_instances; ++i)
+    for (int k = 0; k < inst[i].p; ++k) {
+      const qf_loc l = hl[inst[i].loc_off + k];
+      if (l.a < 0 || l.a >= inst[i].n || l.b < 0 || l.b >= inst[i].n || l.a == l.b)
+        return qf_internal_set_error(QF_EINVAL, "an instance has an invalid location", "");
+    }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const long long problems = (long long)n_instances * n_starts;
+  // device buffers
+  DevMem d_inst, d_locs, d_tgt, d_gates, d_cost, d_sw, d_c64, d_reason, d_flags;
+  if (d_inst.alloc(sizeof(BatchInst) * n_instances) != cudaSuccess ||
+      d_locs.alloc(sizeof(qf_loc) * loc_total) != cudaSuccess ||
+      d_tgt.alloc(sizeof(double2) * tgt_total) != cudaSuccess ||
+      d_gates.alloc(sizeof(double2) * gate_total) != cudaSuccess ||
+      d_cost.alloc(sizeof(double) * problems) != cudaSuccess ||
+      d_sw.alloc(sizeof(int) * problems) != cudaSuccess ||
+      d_c64.alloc(sizeof(int) * problems) != cudaSuccess ||
+      d_reason.alloc(sizeof(int) * problems) != cudaSuccess ||
+      d_flags.alloc(sizeof(int) * (2 * (size_t)n_instances + 2)) != cudaSuccess) {
+    cudaGetLastError();
+    return qf_internal_set_error(QF_ENOMEM, "device allocation for the batch failed", "");
+  }
+  cudaError_t e = cudaMemcpyAsync(d_inst.p, inst.data(), sizeof(BatchInst) * n_instances,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_locs.p, hl.data(), sizeof(qf_loc) * loc_total, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_tgt.p, targets, sizeof(double2) * tgt_total, cudaMemcpyDefault, st);
+  if (e != cudaSuccess)
+    return qf_internal_set_error(QF_ECUDA, "copying the batch inputs failed", cudaGetErrorString(e));
+
+  BatchParams bp;
+  bp.inst = (const BatchInst*)d_inst.p;
+  bp.n_inst = n_instances;
+  bp.S = n_starts;
+  bp.locs = (const int2*)d_locs.p;
+  bp.targets = (const double2*)d_tgt.p;
+  bp.gates = (double2*)d_gates.p;
+  bp.cost_out = (double*)d_cost.p;
+  bp.sweeps_out = (int*)d_sw.p;
+  bp.c64_out = (int*)d_c64.p;
+  bp.reason_out = (int*)d_reason.p;
+  int* flags = (int*)d_flags.p;
+  bp.conv_flag = flags;
+  bp.plat_count = flags + n_instances;
+  bp.status = flags + 2 * n_instances;
+  bp.work = (unsigned*)(flags + 2 * n_instances + 1);
+  bp.dist_tol = o.dist_tol;
+  bp.diff_a = o.diff_tol_a;
+  bp.diff_r = o.diff_tol_r;
+  bp.long_r = o.long_diff_r;
+  bp.beta = o.beta;
+  bp.switch_tol = o.switch_tol;
+  bp.max_sweeps = o.max_sweeps;
+  bp.min_sweeps = o.min_sweeps;
+  bp.reset_iter = o.reset_iter;
+  bp.long_L = o.long_diff_count;
+  bp.precision = o.precision;
+  bp.max_c64 = o.max_c64_sweeps;
+  bp.tmax_bytes = (1 << (2 * nmax)) * 16;
+  bp.warp_bytes = ((bp.tmax_bytes + 768 + kRing * 8) + 255) & ~255;
+  const size_t flag_bytes = sizeof(int) * (2 * (size_t)n_instances + 2);
+
+  int dev = 0, smem_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int max_wpc = smem_optin / bp.warp_bytes;
+  if (max_wpc < 1)
+    return qf_internal_set_error(QF_EINVAL, "the largest instance does not fit in shared memory", "");
+
+  // choose warps per CTA
+  int wpc = 0;
+  const auto key = std::make_tuple(nmax, o.precision, dev);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) wpc = it->second;
+  }
+  if (wpc == 0 || wpc > max_wpc) {
+    float best_ms = 1e30f;
+    BatchParams tp = bp;
+    tp.max_sweeps = 2;
+    tp.n_inst = (int)std::min<long long>(n_instances, std::max<long long>(1, 4096 / n_starts));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int cand : {1, 2, 4, 8}) {
+      if (cand > max_wpc) break;
+      e = cudaMemcpyAsync(d_gates.p, initial_gates, sizeof(double2) * gate_total, cudaMemcpyDefault, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(d_flags.p, 0, flag_bytes, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) e = launch_batch(tp, cand, smem_optin, st, nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        wpc = cand;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess)
+      return qf_internal_set_error(QF_ECUDA, "autotuning launch failed", cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[key] = wpc;
+  }
+
+  // the run: reset, then one persistent launch, captured as a CUDA graph
+  e = cudaMemcpyAsync(d_gates.p, initial_gates, sizeof(double2) * gate_total, cudaMemcpyDefault, st);
+  if (e != cudaSuccess)
+    return qf_internal_set_error(QF_ECUDA, "copying the initial gates failed", cudaGetErrorString(e));
+  cudaStream_t cap = nullptr;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+    return qf_internal_set_error(QF_ECUDA, "stream creation failed", "");
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int ctas = 0;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = cudaMemsetAsync(d_flags.p, 0, flag_bytes, cap);
+    cudaError_t e2 = e1 == cudaSuccess ? launch_batch(bp, wpc, smem_optin, cap, &ctas) : e1;
+    e = cudaStreamEndCapture(cap, &graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaEvent_t k0 = nullptr, k1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&k0);
+  if (e == cudaSuccess) e = cudaEventCreate(&k1);
+  if (e == cudaSuccess) e = cudaEventRecord(k0, st);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+  if (e == cudaSuccess) e = cudaEventRecord(k1, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float kms = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&kms, k0, k1);
+  if (k0) cudaEventDestroy(k0);
+  if (k1) cudaEventDestroy(k1);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess)
+    return qf_internal_set_error(QF_ECUDA, "batched launch failed", cudaGetErrorString(e));
+
+  // outputs
+  std::vector<int> hsw(problems), hreason(problems), hc64(problems);
+  int hstatus = 0;
+  e = cudaMemcpy(out_costs, d_cost.p, sizeof(double) * problems, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hsw.data(), d_sw.p, sizeof(int) * problems, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(&hstatus, bp.status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hc64.data(), d_c64.p, sizeof(int) * problems, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(out_gates, d_gates.p, sizeof(double2) * gate_total, cudaMemcpyDefault);
+  if (e != cudaSuccess)
+    return qf_internal_set_error(QF_ECUDA, "copying the batch results failed", cudaGetErrorString(e));
+  if (out_sweeps)
+    for (long long q = 0; q < problems; ++q) out_sweeps[q] = hsw[q];
+  if (out_best)
+    for (int i = 0; i < n_instances; ++i) {
+      int b = 0;
+      for (int s = 1; s < n_starts; ++s)
+        if (out_costs[(long long)i * n_starts + s] < out_costs[(long long)i * n_starts + b]) b = s;
+      out_best[i] = b;
+    }
+  if (stats) {
+    stats->warps_per_cta = wpc;
+    stats->ctas = ctas;
+    stats->kernel_ms = kms;
+    long long c64 = 0, sw = 0;
+    for (long long q = 0; q < problems; ++q) {
+      c64 += hc64[q];
+      sw += hsw[q];
+    }
+    stats->total_sweeps = sw;
+    stats->total_c64_sweeps = c64;
+  }
+  if (hstatus != 0)
+    return qf_internal_set_error(QF_ENONFINITE, "an environment or update was not finite", "");
+  return QF_OK;
+}

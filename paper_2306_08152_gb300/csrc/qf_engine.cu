@@ -498,16 +498,18 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
     QF_TRY(plan_status_impl(P));
     if (c64_phase) {
       ++c64_sweeps;
+      // leave complex64 once the best cost is below switch_tol, or once ten
+      // c64 sweeps have lowered every start's cost by less than the
+      // complex64 noise floor (1e-7)
       double best = c[0];
-      bool progress = false;
+      bool stalled = hist[0].size() > 10;
       for (int s = 0; s < S; ++s) {
         best = std::min(best, c[s]);
-        const double prev = hist[s].back();
-        if (prev - c[s] > 1e-3 * std::fabs(prev)) progress = true;
+        if (hist[s].size() > 10 && hist[s][hist[s].size() - 10] - c[s] >= 1e-7) stalled = false;
       }
       for (int s = 0; s < S; ++s) hist[s].push_back(c[s]);
-      if (best <= o.switch_tol || !progress || c64_sweeps >= o.max_c64_sweeps) {
-        // K9: rebuild every tensor in complex128 from V and the FP64 gates
+      if (best <= o.switch_tol || stalled || c64_sweeps >= o.max_c64_sweeps) {
+        // rebuild every tensor in complex128 from V and the FP64 gates
         P->prec = QF_C128;
         QF_TRY(plan_build(P));
         QF_TRY(plan_costs_impl(P, c.data(), nullptr));
@@ -538,6 +540,11 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
     }
   }
   if (it > o.max_sweeps) it = o.max_sweeps;
+  if (c64_phase) {  // report FP64 costs: rebuild the tensors in complex128 once
+    P->prec = QF_C128;
+    QF_TRY(plan_build(P));
+    QF_TRY(plan_costs_impl(P, c.data(), nullptr));
+  }
   int best = 0;
   for (int s = 1; s < S; ++s)
     if (c[s] < c[best]) best = s;

@@ -25,7 +25,7 @@ namespace dev {
 // orthonormal completion.  Lane 0 runs modified Gram-Schmidt over the
 // columns of W in order of decreasing singular value, falling back to
 // standard basis vectors; `sm` is 32 float2 of shared scratch for this warp.
-__device__ __noinline__ float2 complete_left_vectors(const Lane& L, float2 w, const float* s4, float smax,
+static __device__ __noinline__ float2 complete_left_vectors(const Lane& L, float2 w, const float* s4, float smax,
                                         float2* sm) {
   if (L.l < 16) sm[L.l] = w;
   __syncwarp();
@@ -81,7 +81,7 @@ __device__ __noinline__ float2 complete_left_vectors(const Lane& L, float2 w, co
 // Warp-cooperative polar update.  Every lane passes element (L.i, L.j) of A
 // (FP64) and receives element (L.i, L.j) of u = argmax Re Tr(A u); *sig gets
 // the sum of singular values of A.  Returns false for a non-finite A.
-__device__ __forceinline__ bool warp_polar(const Lane& L, double2 a, float2* sm, double2* u_out, double* sig) {
+static __device__ __forceinline__ bool warp_polar(const Lane& L, double2 a, float2* sm, double2* u_out, double* sig) {
   const bool fin = __all_sync(kFull, isfinite(a.x) && isfinite(a.y));
   if (!fin) return false;
   const float amax = warp_max(fmaxf(fabsf((float)a.x), fabsf((float)a.y)));
