@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-c128", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=4096)
+    ap.add_argument("--no-configs", action="store_true")
     return ap.parse_args()
 
 
@@ -79,6 +80,31 @@ def config_dict(args, inst):
             inst.n_starts * 4**inst.n * (8 if args.precision == "c64" else 16) / 1e9),
         "parallelism": "replicas (independent starts per GPU)",
     }
+
+
+# ------------------------------------------------------------------ ranks
+
+
+def replica_seed(rank):
+    """Each rank runs its own seeded starts (replicas: no data exchange)."""
+    return SEED + 1000 * int(rank)
+
+
+def max_over_ranks(x, dist, device):
+    """Largest value of x over all ranks (the job's time is its slowest rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, steps, ms_max):
+    """Whole-job units per second: every rank's units over the slowest
+    rank's time."""
+    return units_per_rank * world * steps / (ms_max / 1e3)
 
 
 # ------------------------------------------------------------------ clocks
@@ -347,6 +373,95 @@ def run_c128(args, qf, torch, dev, inst, V, starts):
                          "flops_per_launch": flops}}
 
 
+def run_configs(args, qf, torch, dev):
+    """Correctness and time per sweep of the smaller workloads:
+    3-qubit alternating circuit (6 U(4) gates, 1 start, to 1e-10 or 500
+    sweeps); 6-qubit brickwork (30 gates, 16 starts) on a Haar-random target
+    and on a reachable one, complex128 vs complex64 with FP64 refinement, on
+    the plan engine and on the batched kernel; the 8-qubit differentiable
+    cost (56 gates, 32 gate sets); the 13-qubit complex64 sweep (72 gates,
+    8 starts)."""
+    out = {}
+    sync = torch.cuda.synchronize
+
+    # 3 qubits, 6 gates alternating on (0,1),(1,2)
+    locs = np.array([[0, 1], [1, 2]] * 3, dtype=np.int32)
+    inst = qi.make_problem(3, locs, 1, seed=SEED)
+    V = qf.circuit_unitary(3, locs, torch.from_numpy(inst.target_gates), device=dev)
+    t = time.perf_counter()
+    r = qf.instantiate_ex(V, locs, torch.from_numpy(inst.starts).to(dev), dist_tol=1e-10, max_sweeps=500)
+    w = time.perf_counter() - t
+    out["3q_6gates"] = {"cost": r["best_cost"], "sweeps": r["sweeps"], "reason": r["reason"],
+                        "ms_per_sweep": 1e3 * w / max(r["sweeps"], 1), "path": "qf_instantiate_ex, complex128"}
+
+    # 6 qubits, brickwork of 30 gates, 16 starts
+    locs = qi.brickwork_locations(6, 12)
+    inst = qi.make_problem(6, locs, 16, seed=SEED)
+    Vr = qf.circuit_unitary(6, locs, torch.from_numpy(inst.target_gates), device=dev)
+    Vh = torch.from_numpy(qi.haar_unitary(64, qi.rng(SEED))).to(dev)
+    starts = torch.from_numpy(inst.starts).to(dev)
+    rows = {}
+    for tname, V in (("haar", Vh), ("reachable", Vr)):
+        for pname, prec in (("c128", qf.QF_C128), ("c64_refine64", qf.QF_C64_REFINE64)):
+            t = time.perf_counter()
+            r = qf.instantiate_ex(V, locs, starts, dist_tol=1e-10, max_sweeps=500, precision=prec)
+            w = time.perf_counter() - t
+            t = time.perf_counter()
+            rb = qf.instantiate_batched([(V.cpu().numpy(), locs, inst.starts)], dist_tol=1e-10,
+                                        max_sweeps=500, precision=prec)
+            wb = time.perf_counter() - t
+            rows[f"{tname}/{pname}"] = {
+                "engine": {"best_cost": r["best_cost"], "sweeps": r["sweeps"], "c64_sweeps": r["c64_sweeps"],
+                           "reason": r["reason"], "s": w, "ms_per_sweep": 1e3 * w / max(r["sweeps"], 1)},
+                "batched": {"best_cost": float(rb["costs"][0].min()), "max_sweeps": int(rb["sweeps"].max()),
+                            "s": wb, "kernel_ms": rb["kernel_ms"]}}
+    out["6q_30gates_16starts"] = rows
+
+    # 8 qubits, 56 gates, 32 gate sets: differentiable cost (forward + backward)
+    locs = qi.brickwork_locations(8, 16)
+    g = qi.rng(SEED)
+    gates = torch.from_numpy(np.stack([qi.haar_gates(len(locs), g) for _ in range(32)])).to(dev)
+    V = torch.from_numpy(qi.haar_unitary(256, g)).to(dev)
+    x = gates.clone().requires_grad_(True)
+    qf.QFactorCost.apply(x, V, locs).sum().backward()
+    sync()
+    t = time.perf_counter()
+    reps = 5
+    for _ in range(reps):
+        x.grad = None
+        qf.QFactorCost.apply(x, V, locs).sum().backward()
+    sync()
+    out["8q_56gates_32sets_grad"] = {"ms_per_forward_backward": 1e3 * (time.perf_counter() - t) / reps,
+                                     "gradients_per_call": 32 * len(locs)}
+
+    # 13 qubits, 72 gates, 8 starts, complex64
+    locs = qi.brickwork_locations(13, LAYERS)
+    inst = qi.make_problem(13, locs, 8, seed=SEED)
+    V = qf.circuit_unitary(13, locs, torch.from_numpy(inst.target_gates), device=dev)
+    plan = qf.Plan(13, locs, 8, qf.QF_C64)
+    stream = torch.cuda.current_stream(dev)
+    plan.load(V, torch.from_numpy(inst.starts).to(dev), stream=stream)
+    plan.sweep(1, reset_iter=0)
+    plan.costs()
+    plan.pass_stats()
+    plan.enable_pass_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.sweep(2, reset_iter=0)
+    e1.record(stream)
+    sync()
+    ms = e0.elapsed_time(e1)
+    pass_ms, launches, _ = plan.pass_stats()
+    plan.close()
+    alg = 8 * 4**13 * 16
+    peak, _ = measured_peaks()
+    gbs = alg / ((pass_ms / 1e3) / max(launches, 1)) / 1e9
+    out["13q_72gates_8starts_c64"] = {"value": 8 * 2 * len(locs) * 2 / (ms / 1e3), "unit": "gate-updates/s",
+                                      "pass_gbs": gbs, "frac": gbs / peak, "ms_per_sweep": ms / 2}
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 
 
@@ -371,7 +486,7 @@ def run_ours(args):
     n, locs = inst.n, inst.locs
     # replicas: rank r runs its own seeded starts (seed offset by rank)
     if rank > 0:
-        inst = qi.make_problem(n, locs, args.starts, seed=SEED + 1000 * rank)
+        inst = qi.make_problem(n, locs, args.starts, seed=replica_seed(rank))
     prec = qf.QF_C64 if args.precision == "c64" else qf.QF_C128
     stream = torch.cuda.current_stream(dev)
     V = qf.circuit_unitary(n, locs, torch.from_numpy(inst.target_gates), device=dev)
@@ -403,12 +518,9 @@ def run_ours(args):
     if plan.status() != 0:
         raise RuntimeError("device status reports a non-finite update")
     costs = plan.costs()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     updates_per_step = inst.n_starts * 2 * inst.p * world
-    value = updates_per_step * args.steps / (ms / 1e3)
+    value = job_throughput(inst.n_starts * 2 * inst.p, world, args.steps, ms)
 
     # roofline of the dominant kernel (the fused pass)
     eb = 8 if args.precision == "c64" else 16
@@ -450,10 +562,7 @@ def run_ours(args):
             r = qf.instantiate_ex(V_h, locs, starts_h, options=opts, stream=stream)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dist, dev)
         h2d = V_h.numel() * 16 + starts_h.numel() * 16 + locs.size * 4
         d2h = starts_h.numel() * 16 + inst.n_starts * 8
         e2e = {"value": updates_per_step * e2e_steps / e2e_s, "unit": UNIT,
@@ -469,6 +578,9 @@ def run_ours(args):
     batched = None
     if not args.no_batched and world == 1:
         batched = run_batched(args, qf, torch, dev)
+    configs = None
+    if not args.no_configs and world == 1:
+        configs = run_configs(args, qf, torch, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -487,7 +599,7 @@ def run_ours(args):
             "data": "synthetic", "config": config_dict(args, inst),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(all_launches), "clocks": clock_info,
-            "c128": extra_c128, "batched": batched,
+            "c128": extra_c128, "batched": batched, "configs": configs,
             "final_costs": [float(c) for c in costs],
         }
         print(json.dumps(line))

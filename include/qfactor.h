@@ -319,6 +319,12 @@ int qf_optimize_gates(const qf_c128* E, const qf_c128* u_old, double beta,
                       int count, qf_c128* u_out, double* sigma_out,
                       void* stream);
 
+/* Step a7, periodic re-unitarisation (Sec. III-A2, reset_iter): two FP64
+ * Newton-Schulz steps u <- u (3I - u^dagger u) / 2 on each of `count` device
+ * gates (count x 16), in place.  The sweep engines run it on every gate
+ * before each periodic rebuild of the circuit tensors. */
+int qf_reunitarize_gates(qf_c128* gates, int count, void* stream);
+
 /* Step a6: tr_out_s = Tr T_s (FP64 accumulation).  tr_out: device n_starts. */
 int qf_trace(const void* T, int n_qubits, int n_starts, qf_c128* tr_out,
              int precision, void* stream);

@@ -102,6 +102,7 @@ SIGNATURES = {
     "qf_partial_trace_noalloc": (I, [P, I, I, I, I, P, I, P]),
     "qf_optimize_gates": (I, [P, P, D, I, P, P, P]),
     "qf_trace": (I, [P, I, I, P, I, P]),
+    "qf_reunitarize_gates": (I, [P, I, P]),
     "qf_circuit_unitary": (I, [I, I, P, P, P, P]),
 }
 

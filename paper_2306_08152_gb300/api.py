@@ -19,7 +19,7 @@ from ._native import check
 __all__ = [
     "QF_C128", "QF_C64", "QF_C64_REFINE64", "Options", "instantiate",
     "instantiate_ex", "instantiate_batched", "cost_and_env", "cost_grad", "costs", "Plan", "init_tensor", "apply_pair",
-    "partial_trace", "partial_trace_noalloc", "optimize_gates", "trace", "circuit_unitary",
+    "partial_trace", "partial_trace_noalloc", "optimize_gates", "reunitarize_gates", "trace", "circuit_unitary",
 ]
 
 QF_C128 = nat.QF_C128
@@ -372,6 +372,15 @@ def optimize_gates(E, u_old=None, beta=0.0, stream=None):
     check(_lib().qf_optimize_gates(_ptr(E), up, float(beta), count, _ptr(U), _ptr(sig),
                                    _stream_handle(stream)))
     return U, sig
+
+
+def reunitarize_gates(gates, stream=None):
+    """In place: two FP64 Newton-Schulz steps on every 4x4 gate (CUDA)."""
+    g = _dev(gates, "gates")
+    if g.dtype != torch.complex128 or not g.is_contiguous():
+        raise TypeError("gates must be a contiguous complex128 CUDA tensor")
+    check(_lib().qf_reunitarize_gates(_ptr(g), g.numel() // 16, _stream_handle(stream)))
+    return g
 
 
 def trace(T, stream=None):

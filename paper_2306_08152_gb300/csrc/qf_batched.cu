@@ -235,6 +235,23 @@ struct W {
   }
 };
 
+// Periodic re-unitarisation (reset_iter): two FP64 Newton-Schulz steps per
+// gate, u <- u (3I - u^dagger u) / 2.
+__device__ void reunitarize(double2* g, int p, const Lane& L) {
+  const int e = L.l & 15;
+  for (int k = 0; k < p; ++k) {
+    double2 u = g[k * 16 + e];
+    for (int step = 0; step < 2; ++step) {
+      const double2 P = wmm_dn(L, u, u);
+      const double2 Q = make_double2((L.i == L.j ? 1.5 : 0.0) - 0.5 * P.x, -0.5 * P.y);
+      u = wmm(L, u, Q);
+    }
+    __syncwarp();
+    if (L.l < 16) g[k * 16 + e] = u;
+    __syncwarp();
+  }
+}
+
 __device__ bool plateau_test(const double* ring, int len, int it, const BatchParams& bp) {
   const double c = ring[(len - 1) % kRing];
   if ((bp.diff_a > 0.0 || bp.diff_r > 0.0) && len >= 2) {
@@ -297,6 +314,7 @@ __global__ void batched_kernel(BatchParams bp) {
       else
         W<double>::sweep((double2*)Tbuf, LRd, scratch, g, locs, n, p, bp.beta, L, &bad);
       if (bp.reset_iter > 0 && it % bp.reset_iter == 0) {
+        reunitarize(g, p, L);
         if (c64)
           W<float>::build((float2*)Tbuf, LRf, V, g, locs, n, p, L);
         else

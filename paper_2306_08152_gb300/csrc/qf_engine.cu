@@ -312,11 +312,19 @@ int plan_load_impl(qf_plan* P, const qf_c128* target, const qf_c128* gates, cuda
   return plan_build(P);
 }
 
+// The periodic reset (Sec. III-A2, reset_iter): re-unitarise every gate in
+// FP64, then rebuild every tensor from V and the gates.
+int plan_reset(qf_plan* P) {
+  QF_CUDA(qf::launch_reunitarize(P->gates.as<double2>(), P->S * P->p, P->stream));
+  P->all_launches++;
+  return plan_build(P);
+}
+
 int plan_sweep_impl(qf_plan* P, int n_sweeps, int reset_iter, double beta) {
   for (int i = 0; i < n_sweeps; ++i) {
     QF_TRY(plan_sweep_once(P, beta));
     P->sweeps_since_load++;
-    if (reset_iter > 0 && P->sweeps_since_load % reset_iter == 0) QF_TRY(plan_build(P));
+    if (reset_iter > 0 && P->sweeps_since_load % reset_iter == 0) QF_TRY(plan_reset(P));
   }
   return QF_OK;
 }
@@ -493,7 +501,7 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
   for (it = 1; it <= o.max_sweeps; ++it) {
     QF_TRY(plan_sweep_once(P, o.beta));
     P->sweeps_since_load++;
-    if (o.reset_iter > 0 && P->sweeps_since_load % o.reset_iter == 0) QF_TRY(plan_build(P));
+    if (o.reset_iter > 0 && P->sweeps_since_load % o.reset_iter == 0) QF_TRY(plan_reset(P));
     QF_TRY(plan_costs_impl(P, c.data(), nullptr));
     QF_TRY(plan_status_impl(P));
     if (c64_phase) {
@@ -716,6 +724,14 @@ int qf_optimize_gates(const qf_c128* E, const qf_c128* u_old, double beta, int c
   QF_CUDA(qf::launch_optimize(reinterpret_cast<const double2*>(E),
                               reinterpret_cast<const double2*>(u_old), beta, count,
                               reinterpret_cast<double2*>(u_out), sigma_out, as_stream(stream)));
+  return QF_OK;
+}
+
+int qf_reunitarize_gates(qf_c128* gates, int count, void* stream) {
+  if (count < 0) return set_error(QF_EINVAL, "count=%d < 0", count);
+  if (count == 0) return QF_OK;
+  if (!gates) return set_error(QF_EINVAL, "gates is NULL");
+  QF_CUDA(qf::launch_reunitarize(reinterpret_cast<double2*>(gates), count, as_stream(stream)));
   return QF_OK;
 }
 

@@ -54,6 +54,9 @@ cudaError_t launch_optimize(const double2* E, const double2* u_old, double beta,
 cudaError_t launch_grad_from_env(double2* env, const double2* tr, int n, int S, int p,
                                  cudaStream_t st);
 
+// Two FP64 Newton-Schulz steps on each of `count` gates, in place.
+cudaError_t launch_reunitarize(double2* gates, int count, cudaStream_t st);
+
 // tr_s = Tr T_s (FP64 accumulation).
 cudaError_t launch_trace(const void* T, int n, int S, double2* tr, int prec,
                          cudaStream_t st);

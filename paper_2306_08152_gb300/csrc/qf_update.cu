@@ -191,9 +191,33 @@ __global__ void grad_from_env_kernel(double2* __restrict__ env, const double2* _
     for (int j = 0; j < 4; ++j) E[i * 4 + j] = cmul(f, cconj(e[j * 4 + i]));
 }
 
+// Periodic re-unitarisation of gates in FP64 (reset_iter, Sec. III-A2): two
+// Newton-Schulz steps u <- u (3I - u^dagger u) / 2 per gate, one warp per gate.
+// Each step squares the deviation from unitarity; on gates that are already
+// unitary to FP64 rounding they change nothing beyond rounding.
+__global__ void __launch_bounds__(128) reunitarize_kernel(double2* __restrict__ gates, int count) {
+  const int m = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (m >= count) return;  // whole warps leave together
+  const Lane L;
+  const int e = L.l & 15;
+  double2 u = gates[(size_t)m * 16 + e];
+  for (int step = 0; step < 2; ++step) {
+    const double2 P = wmm_dn(L, u, u);
+    const double2 Q = make_double2((L.i == L.j ? 1.5 : 0.0) - 0.5 * P.x, -0.5 * P.y);
+    u = wmm(L, u, Q);
+  }
+  if (L.l < 16) gates[(size_t)m * 16 + e] = u;
+}
+
 }  // namespace
 
 // ================================================================ launchers
+
+cudaError_t launch_reunitarize(double2* gates, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  reunitarize_kernel<<<(count + 3) / 4, 128, 0, st>>>(gates, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_grad_from_env(double2* env, const double2* tr, int n, int S, int p,
                                  cudaStream_t st) {

@@ -183,3 +183,41 @@ def test_circuit_unitary_matches_oracle(qf):
         gates = qi.haar_gates(len(locs), g)
         C = qf.circuit_unitary(n, locs, torch.from_numpy(gates)).cpu().numpy()
         assert _relerr(C, orc.circuit_unitary(gates, locs, n)) <= 1e-12
+
+
+def test_reunitarize_gates_returns_the_nearest_unitary(qf):
+    """Two Newton-Schulz steps take a gate 1e-4 away from unitary to its polar
+    factor (the nearest unitary), which the oracle gives as
+    optimize_gate(M^dagger) (Sec. III-A1: the update is the polar factor of
+    E^dagger)."""
+    g = qi.rng(6000)
+    count = 64
+    M = np.stack([qi.haar_unitary(4, g) for _ in range(count)])
+    M = M + 1e-4 * (g.standard_normal(M.shape) + 1j * g.standard_normal(M.shape))
+    t = torch.from_numpy(M.copy()).cuda()
+    qf.reunitarize_gates(t)
+    U = t.cpu().numpy()
+    for i in range(count):
+        ref, _ = orc.optimize_gate(M[i].conj().T)
+        assert np.max(np.abs(U[i] - ref)) <= 1e-12
+        assert np.max(np.abs(U[i].conj().T @ U[i] - np.eye(4))) <= 1e-13  # FP64 rounding of two 4x4 products
+
+
+def test_device_side_nonfinite_environment_is_reported(qf):
+    """A NaN inside a device-resident target is not seen by the host checks;
+    the update kernel finds a non-finite environment, keeps the old gate and
+    raises the plan's status word, which the call reports as QF_ENONFINITE."""
+    from paper_2306_08152_gb300 import QFactorError
+
+    n = 4
+    V = qi.haar_unitary(16, qi.rng(6001))
+    V[3, 5] = np.nan
+    locs = qi.brickwork_locations(n, 2)
+    starts = torch.from_numpy(qi.haar_gates(len(locs), qi.rng(6002))[None]).cuda()
+    with pytest.raises(QFactorError) as ei:
+        qf.instantiate_ex(torch.from_numpy(V).cuda(), locs, starts, max_sweeps=3)
+    assert ei.value.code == -4
+    # the context stays usable
+    ok = qf.instantiate_ex(torch.from_numpy(qi.haar_unitary(16, qi.rng(6003))).cuda(), locs, starts,
+                           max_sweeps=2)
+    assert ok["sweeps"] == 2
