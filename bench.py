@@ -360,10 +360,10 @@ def run_c128(args, qf, torch, dev, inst, V, starts):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    pass_ms, launches, _ = plan.pass_stats()
+    pass_ms, launches, _, pbytes = plan.pass_stats()
     plan.close()
     updates = inst.n_starts * 2 * inst.p * steps
-    flops = inst.n_starts * 4**inst.n * 64
+    flops = pbytes / max(launches, 1) / 32 * 64  # 16-byte entries, read + write
     achieved = flops / ((pass_ms / 1e3) / max(launches, 1)) / 1e9
     return {"metric": "gate-updates/s at 12 qubits, complex128", "unit": "gate-updates/s",
             "value": updates / (ms / 1e3), "ms_per_sweep": ms / steps, "dtype": "c128",
@@ -452,9 +452,9 @@ def run_configs(args, qf, torch, dev):
     e1.record(stream)
     sync()
     ms = e0.elapsed_time(e1)
-    pass_ms, launches, _ = plan.pass_stats()
+    pass_ms, launches, _, pbytes = plan.pass_stats()
     plan.close()
-    alg = 8 * 4**13 * 16
+    alg = pbytes / max(launches, 1)
     peak, _ = measured_peaks()
     gbs = alg / ((pass_ms / 1e3) / max(launches, 1)) / 1e9
     out["13q_72gates_8starts_c64"] = {"value": 8 * 2 * len(locs) * 2 / (ms / 1e3), "unit": "gate-updates/s",
@@ -513,8 +513,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     clock_info = clocks.stop()
     ms = e0.elapsed_time(e1)
-    pass_ms, pass_launches, all_launches = plan.pass_stats()
+    pass_ms, pass_launches, all_launches, pass_bytes = plan.pass_stats()
     plan.enable_pass_timing(False)
+    # the same steps replayed as a captured sweep graph (no timing events)
+    plan.sweep(1, reset_iter=40)
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        plan.sweep(1, reset_iter=40)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = g0.elapsed_time(g1) / args.steps
     if plan.status() != 0:
         raise RuntimeError("device status reports a non-finite update")
     costs = plan.costs()
@@ -522,22 +533,27 @@ def run_ours(args):
     updates_per_step = inst.n_starts * 2 * inst.p * world
     value = job_throughput(inst.n_starts * 2 * inst.p, world, args.steps, ms)
 
-    # roofline of the dominant kernel (the fused pass)
+    # roofline of the dominant kernel (the fused pass): algorithmic bytes of
+    # every timed pass launch (one read + one write of the tensors it covers)
+    # over the summed launch durations
     eb = 8 if args.precision == "c64" else 16
-    alg_bytes = inst.n_starts * 4**n * 2 * eb  # one read + one write of every tensor
+    alg_bytes = pass_bytes / max(pass_launches, 1)
     avg_pass_s = (pass_ms / 1e3) / max(pass_launches, 1)
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / avg_pass_s / 1e9
     traffic = kernel_traffic(args.precision, inst.n_starts, n)
+    if traffic is not None:
+        traffic *= alg_bytes / (inst.n_starts * 4**n * 2 * eb)  # per launch of this size
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "pass_kernel (fused B <- L B R over every 4x4 block)",
+                "kernel": "pass kernels (fused B <- L B R over every 4x4 block)",
                 "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_pass_s * 1e3,
+                "pass_launches": pass_launches,
                 "pass_share_of_step": (pass_ms / ms) if ms > 0 else None}
     if args.precision == "c128":
         fp64_peak = 1250.0  # GFLOP/s nominal FP64 (no measured FP64 peak on this machine)
-        flops = inst.n_starts * 4**n * 64
+        flops = alg_bytes / (2 * eb) * 64
         roofline_fp64 = flops / avg_pass_s / 1e9
         roofline = {"bound": "alu", "achieved": roofline_fp64, "peak": fp64_peak, "unit": "GFLOP/s",
                     "frac": roofline_fp64 / fp64_peak, "traffic": traffic,
@@ -599,6 +615,7 @@ def run_ours(args):
             "data": "synthetic", "config": config_dict(args, inst),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(all_launches), "clocks": clock_info,
+            "ms_per_step_graph": ms_graph,
             "c128": extra_c128, "batched": batched, "configs": configs,
             "final_costs": [float(c) for c in costs],
         }

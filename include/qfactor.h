@@ -258,7 +258,11 @@ int qf_plan_load(qf_plan* plan, const qf_c128* target, const qf_c128* gates,
 
 /* Run n_sweeps two-sided sweeps on every start; the tensors are rebuilt after
  * every reset_iter-th sweep counted since qf_plan_load (reset_iter <= 0:
- * never).  Enqueue only. */
+ * never).  With two or more starts the starts form two groups whose
+ * environment kernels and passes run on two internal streams, so that one
+ * group's gate update overlaps the other group's pass.  Without pass timing,
+ * a sweep is captured once as a CUDA graph (per beta and precision) and
+ * replayed.  Enqueue only. */
 int qf_plan_sweep(qf_plan* plan, int n_sweeps, int reset_iter, double beta);
 
 /* Rebuild every tensor from the target and the current gates, in
@@ -274,12 +278,15 @@ int qf_plan_costs(qf_plan* plan, double* out_costs, qf_c128* out_trace);
 int qf_plan_get_gates(qf_plan* plan, qf_c128* out);
 
 /* Kernel timing of the gate-application pass: when enabled, every pass
- * launch is bracketed by CUDA events on the plan's stream; qf_plan_pass_stats
- * synchronises and returns the summed pass time (ms), the pass-launch count
- * and the count of all kernel launches since the last reset, then resets. */
+ * launch is bracketed by CUDA events on the stream it runs on (sweeps then
+ * run as live launches instead of a replayed graph).  qf_plan_pass_stats
+ * synchronises and returns, since the last call: the summed duration of the
+ * timed passes (ms), their algorithmic bytes (one read and one write of every
+ * tensor entry they cover; may be NULL), the pass-launch count and the count
+ * of all kernel launches; then it resets them. */
 int qf_plan_enable_pass_timing(qf_plan* plan, int enable);
 int qf_plan_pass_stats(qf_plan* plan, double* pass_ms, int64_t* pass_launches,
-                       int64_t* all_launches);
+                       int64_t* all_launches, double* pass_bytes);
 
 /* Current device status word of the plan (0 = clean; QF_ENONFINITE if an
  * update met a non-finite environment).  Synchronises. */
@@ -319,7 +326,7 @@ int qf_optimize_gates(const qf_c128* E, const qf_c128* u_old, double beta,
                       int count, qf_c128* u_out, double* sigma_out,
                       void* stream);
 
-/* Step a7, periodic re-unitarisation (Sec. III-A2, reset_iter): two FP64
+/* Step a7, periodic re-unitarisation (Sec. III-A2, reset_iter): three FP64
  * Newton-Schulz steps u <- u (3I - u^dagger u) / 2 on each of `count` device
  * gates (count x 16), in place.  The sweep engines run it on every gate
  * before each periodic rebuild of the circuit tensors. */

@@ -94,7 +94,7 @@ SIGNATURES = {
     "qf_plan_costs": (I, [P, DP, P]),
     "qf_plan_get_gates": (I, [P, P]),
     "qf_plan_enable_pass_timing": (I, [P, I]),
-    "qf_plan_pass_stats": (I, [P, DP, I64P, I64P]),
+    "qf_plan_pass_stats": (I, [P, DP, I64P, I64P, DP]),
     "qf_plan_status": (I, [P]),
     "qf_init_tensor": (I, [P, I, I, P, I, P, P, I, P]),
     "qf_apply_pair": (I, [P, I, I, I, I, P, P, I, P]),

@@ -285,11 +285,15 @@ class Plan:
         check(_lib().qf_plan_enable_pass_timing(self.h, int(bool(enable))))
 
     def pass_stats(self):
+        """(pass ms, pass launches, all launches, pass algorithmic bytes)
+        since the last call."""
         ms = ct.c_double()
         pl = ct.c_int64()
         al = ct.c_int64()
-        check(_lib().qf_plan_pass_stats(self.h, ct.byref(ms), ct.byref(pl), ct.byref(al)))
-        return ms.value, pl.value, al.value
+        by = ct.c_double()
+        check(_lib().qf_plan_pass_stats(self.h, ct.byref(ms), ct.byref(pl), ct.byref(al),
+                                        ct.byref(by)))
+        return ms.value, pl.value, al.value, by.value
 
     def status(self):
         return _lib().qf_plan_status(self.h)
@@ -375,7 +379,7 @@ def optimize_gates(E, u_old=None, beta=0.0, stream=None):
 
 
 def reunitarize_gates(gates, stream=None):
-    """In place: two FP64 Newton-Schulz steps on every 4x4 gate (CUDA)."""
+    """In place: three FP64 Newton-Schulz steps on every 4x4 gate (CUDA)."""
     g = _dev(gates, "gates")
     if g.dtype != torch.complex128 or not g.is_contiguous():
         raise TypeError("gates must be a contiguous complex128 CUDA tensor")

@@ -235,13 +235,13 @@ struct W {
   }
 };
 
-// Periodic re-unitarisation (reset_iter): two FP64 Newton-Schulz steps per
+// Periodic re-unitarisation (reset_iter): three FP64 Newton-Schulz steps per
 // gate, u <- u (3I - u^dagger u) / 2.
 __device__ void reunitarize(double2* g, int p, const Lane& L) {
   const int e = L.l & 15;
   for (int k = 0; k < p; ++k) {
     double2 u = g[k * 16 + e];
-    for (int step = 0; step < 2; ++step) {
+    for (int step = 0; step < 3; ++step) {
       const double2 P = wmm_dn(L, u, u);
       const double2 Q = make_double2((L.i == L.j ? 1.5 : 0.0) - 0.5 * P.x, -0.5 * P.y);
       u = wmm(L, u, Q);

@@ -170,6 +170,18 @@ struct qf_plan {
   std::vector<cudaEvent_t> events;  // pairs
   size_t events_used = 0;
   long long pass_launches = 0, all_launches = 0;
+  double pass_bytes = 0.0;  // algorithmic bytes (one read + one write) of timed passes
+  // start groups: the environment kernels of one group run on s_env while
+  // the other group's pass runs on s_pass (passes stay serialised)
+  int G = 1;
+  cudaStream_t s_env = nullptr, s_pass = nullptr, s_cap = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join_env = nullptr, ev_join_pass = nullptr;
+  cudaEvent_t ev_env[2] = {nullptr, nullptr}, ev_pass[2] = {nullptr, nullptr};
+  // one sweep captured as a CUDA graph (used when pass timing is off)
+  cudaGraphExec_t graph = nullptr;
+  double graph_beta = 0.0;
+  int graph_prec = -1;
+  bool use_graph = true;
 };
 
 namespace {
@@ -184,8 +196,17 @@ int plan_ensure_T(qf_plan* P, int prec) {
   return QF_OK;
 }
 
-int plan_pass(qf_plan* P, int a, int b, const double2* L, long long Ls, const double2* R,
-              long long Rs) {
+// A slice of the starts [s0, s0 + Sg) and the stream its work goes to.
+struct Slice {
+  int s0, Sg;
+  cudaStream_t st;
+};
+
+Slice all_starts(qf_plan* P, cudaStream_t st) { return Slice{0, P->S, st}; }
+Slice all_starts(qf_plan* P) { return all_starts(P, P->stream); }
+
+int plan_pass(qf_plan* P, const Slice& sl, int a, int b, const double2* L, long long Ls,
+              const double2* R, long long Rs) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (P->timing) {
     if (P->events_used + 2 > P->events.size()) {
@@ -198,11 +219,15 @@ int plan_pass(qf_plan* P, int a, int b, const double2* L, long long Ls, const do
     e0 = P->events[P->events_used];
     e1 = P->events[P->events_used + 1];
     P->events_used += 2;
-    QF_CUDA(cudaEventRecord(e0, P->stream));
+    QF_CUDA(cudaEventRecord(e0, sl.st));
   }
-  QF_CUDA(qf::launch_pass(P->T.p, P->n, P->S, a, b, L, Ls, R, Rs, P->prec == QF_C128 ? 0 : 1,
-                          P->stream));
-  if (P->timing) QF_CUDA(cudaEventRecord(e1, P->stream));
+  void* T = static_cast<char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
+  QF_CUDA(qf::launch_pass(T, P->n, sl.Sg, a, b, L ? L + sl.s0 * Ls : nullptr, Ls,
+                          R ? R + sl.s0 * Rs : nullptr, Rs, P->prec == QF_C128 ? 0 : 1, sl.st));
+  if (P->timing) {
+    QF_CUDA(cudaEventRecord(e1, sl.st));
+    P->pass_bytes += 2.0 * (double)sl.Sg * (double)P->NN * (double)elem_bytes(P->prec);
+  }
   P->pass_launches++;
   P->all_launches++;
   return QF_OK;
@@ -214,37 +239,121 @@ int plan_build(qf_plan* P) {
   QF_CUDA(qf::launch_conj_transpose(P->V.as<double2>(), P->T.p, P->n, P->S, pr, P->stream));
   P->all_launches++;
   for (int k = 0; k < P->p; ++k) {
-    QF_TRY(plan_pass(P, P->locs[k].a, P->locs[k].b, nullptr, 0,
+    QF_TRY(plan_pass(P, all_starts(P), P->locs[k].a, P->locs[k].b, nullptr, 0,
                      P->gates.as<double2>() + (size_t)k * 16, (long long)P->p * 16));
   }
   return QF_OK;
 }
 
-int plan_update(qf_plan* P, int k, int mode, double beta, double2* env_out, long long env_stride) {
+int plan_update(qf_plan* P, const Slice& sl, int k, int mode, double beta, double2* env_out,
+                long long env_stride) {
   const int pr = P->prec == QF_C128 ? 0 : 1;
-  QF_CUDA(qf::launch_update(P->T.p, P->n, P->S, P->locs[k].a, P->locs[k].b,
-                            P->gates.as<double2>() + (size_t)k * 16, (long long)P->p * 16, mode,
-                            beta, P->LR.as<double2>(), env_out, env_stride,
-                            P->sigma.as<double>(), P->status.as<int>(), P->part.as<double>(),
-                            P->counters.as<unsigned>(), pr, P->stream));
+  const int B = qf::env_ctas(P->n);
+  const void* T = static_cast<const char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
+  QF_CUDA(qf::launch_update(
+      T, P->n, sl.Sg, P->locs[k].a, P->locs[k].b,
+      P->gates.as<double2>() + (size_t)sl.s0 * P->p * 16 + (size_t)k * 16, (long long)P->p * 16,
+      mode, beta, P->LR.as<double2>() + (size_t)sl.s0 * 32,
+      env_out ? env_out + sl.s0 * env_stride : nullptr, env_stride,
+      P->sigma.as<double>() + sl.s0, P->status.as<int>(),
+      P->part.as<double>() + (size_t)sl.s0 * B * 32, P->counters.as<unsigned>() + sl.s0, pr, sl.st));
   P->all_launches++;
+  return QF_OK;
+}
+
+int plan_streams(qf_plan* P) {
+  if (P->s_env) return QF_OK;
+  QF_CUDA(cudaStreamCreateWithFlags(&P->s_env, cudaStreamNonBlocking));
+  QF_CUDA(cudaStreamCreateWithFlags(&P->s_pass, cudaStreamNonBlocking));
+  QF_CUDA(cudaStreamCreateWithFlags(&P->s_cap, cudaStreamNonBlocking));
+  cudaEvent_t* evs[] = {&P->ev_fork, &P->ev_join_env, &P->ev_join_pass, &P->ev_env[0],
+                        &P->ev_env[1], &P->ev_pass[0], &P->ev_pass[1]};
+  for (cudaEvent_t* e : evs) QF_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   return QF_OK;
 }
 
 // TwoSidedSweep (Alg. 1).  Backward half: for k = p-1..0 the environment of
 // gate k (still on the tensor's right), its update, and the pass that
 // removes u_k from the right and applies u_k' on the left.  Forward half:
-// the mirror image, k = 0..p-1.
-int plan_sweep_once(qf_plan* P, double beta) {
+// the mirror image, k = 0..p-1.  With two start groups the environment
+// kernels go to s_env and the passes to s_pass, so the environment of one
+// group overlaps the pass of the other:
+//   env_0(u) | pass_0(u) + env_1(u) | pass_1(u) + env_0(u+1) | ...
+int enqueue_sweep(qf_plan* P, double beta, cudaStream_t origin) {
   const double2* LR = P->LR.as<double2>();
-  for (int k = P->p - 1; k >= 0; --k) {
-    QF_TRY(plan_update(P, k, qf::kBackward, beta, nullptr, 0));
-    QF_TRY(plan_pass(P, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
+  if (P->G == 1) {
+    const Slice sl = all_starts(P, origin);
+    for (int k = P->p - 1; k >= 0; --k) {
+      QF_TRY(plan_update(P, sl, k, qf::kBackward, beta, nullptr, 0));
+      QF_TRY(plan_pass(P, sl, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
+    }
+    for (int k = 0; k < P->p; ++k) {
+      QF_TRY(plan_update(P, sl, k, qf::kForward, beta, nullptr, 0));
+      QF_TRY(plan_pass(P, sl, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
+    }
+    return QF_OK;
   }
-  for (int k = 0; k < P->p; ++k) {
-    QF_TRY(plan_update(P, k, qf::kForward, beta, nullptr, 0));
-    QF_TRY(plan_pass(P, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
+  QF_TRY(plan_streams(P));
+  const int half = P->S / 2;
+  const Slice env_sl[2] = {{0, half, P->s_env}, {half, P->S - half, P->s_env}};
+  const Slice pass_sl[2] = {{0, half, P->s_pass}, {half, P->S - half, P->s_pass}};
+  QF_CUDA(cudaEventRecord(P->ev_fork, origin));
+  QF_CUDA(cudaStreamWaitEvent(P->s_env, P->ev_fork, 0));
+  QF_CUDA(cudaStreamWaitEvent(P->s_pass, P->ev_fork, 0));
+  for (int u = 0; u < 2 * P->p; ++u) {
+    const bool backward = u < P->p;
+    const int k = backward ? P->p - 1 - u : u - P->p;
+    for (int g = 0; g < 2; ++g) {
+      if (u > 0) QF_CUDA(cudaStreamWaitEvent(P->s_env, P->ev_pass[g], 0));
+      QF_TRY(plan_update(P, env_sl[g], k, backward ? qf::kBackward : qf::kForward, beta, nullptr, 0));
+      QF_CUDA(cudaEventRecord(P->ev_env[g], P->s_env));
+      QF_CUDA(cudaStreamWaitEvent(P->s_pass, P->ev_env[g], 0));
+      QF_TRY(plan_pass(P, pass_sl[g], P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
+      QF_CUDA(cudaEventRecord(P->ev_pass[g], P->s_pass));
+    }
   }
+  QF_CUDA(cudaEventRecord(P->ev_join_env, P->s_env));
+  QF_CUDA(cudaEventRecord(P->ev_join_pass, P->s_pass));
+  QF_CUDA(cudaStreamWaitEvent(origin, P->ev_join_env, 0));
+  QF_CUDA(cudaStreamWaitEvent(origin, P->ev_join_pass, 0));
+  return QF_OK;
+}
+
+// One sweep: live launches when pass timing is on (every pass bracketed by
+// events), otherwise the sweep is captured once as a CUDA graph per (beta,
+// precision) and replayed.
+int plan_sweep_once(qf_plan* P, double beta) {
+  if (P->timing || !P->use_graph) return enqueue_sweep(P, beta, P->stream);
+  if (!P->graph || P->graph_beta != beta || P->graph_prec != P->prec) {
+    if (P->graph) {
+      cudaGraphExecDestroy(P->graph);
+      P->graph = nullptr;
+    }
+    QF_TRY(plan_streams(P));
+    // captured on an internal stream (the caller's may be the legacy default
+    // stream, which cannot be captured), launched on the caller's stream
+    const long long pl = P->pass_launches, al = P->all_launches;
+    cudaGraph_t g = nullptr;
+    QF_CUDA(cudaStreamBeginCapture(P->s_cap, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_sweep(P, beta, P->s_cap);
+    const cudaError_t e = cudaStreamEndCapture(P->s_cap, &g);
+    if (rc != QF_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return set_error(QF_ECUDA, "sweep capture failed: %s", cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(&P->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess)
+      return set_error(QF_ECUDA, "sweep graph instantiation failed: %s", cudaGetErrorString(ei));
+    P->graph_beta = beta;
+    P->graph_prec = P->prec;
+    P->pass_launches = pl;  // capture launches nothing
+    P->all_launches = al;
+  }
+  QF_CUDA(cudaGraphLaunch(P->graph, P->stream));
+  P->pass_launches += 2 * P->p * P->G;
+  P->all_launches += 4 * P->p * P->G;
   return QF_OK;
 }
 
@@ -276,6 +385,7 @@ int plan_create_impl(int n, int p, const qf_loc* locs, int S, int prec, qf_plan*
   P->n = n;
   P->p = p;
   P->S = S;
+  P->G = S >= 2 ? 2 : 1;
   P->N = (size_t)1 << n;
   P->NN = P->N * P->N;
   int rc = fetch_locations(locs, n, p, &P->locs);
@@ -394,6 +504,14 @@ int qf_plan_destroy(qf_plan* plan) {
   if (!plan) return QF_OK;
   if (plan->stream) cudaStreamSynchronize(plan->stream);
   for (cudaEvent_t e : plan->events) cudaEventDestroy(e);
+  if (plan->graph) cudaGraphExecDestroy(plan->graph);
+  cudaEvent_t evs[] = {plan->ev_fork, plan->ev_join_env, plan->ev_join_pass, plan->ev_env[0],
+                       plan->ev_env[1], plan->ev_pass[0], plan->ev_pass[1]};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (plan->s_env) cudaStreamDestroy(plan->s_env);
+  if (plan->s_pass) cudaStreamDestroy(plan->s_pass);
+  if (plan->s_cap) cudaStreamDestroy(plan->s_cap);
   delete plan;
   return QF_OK;
 }
@@ -439,7 +557,7 @@ int qf_plan_enable_pass_timing(qf_plan* plan, int enable) {
 }
 
 int qf_plan_pass_stats(qf_plan* plan, double* pass_ms, int64_t* pass_launches,
-                       int64_t* all_launches) {
+                       int64_t* all_launches, double* pass_bytes) {
   if (!plan) return set_error(QF_EINVAL, "plan is NULL");
   QF_CUDA(cudaStreamSynchronize(plan->stream));
   double ms = 0.0;
@@ -451,9 +569,11 @@ int qf_plan_pass_stats(qf_plan* plan, double* pass_ms, int64_t* pass_launches,
   if (pass_ms) *pass_ms = ms;
   if (pass_launches) *pass_launches = plan->pass_launches;
   if (all_launches) *all_launches = plan->all_launches;
+  if (pass_bytes) *pass_bytes = plan->pass_bytes;
   plan->events_used = 0;
   plan->pass_launches = 0;
   plan->all_launches = 0;
+  plan->pass_bytes = 0.0;
   return QF_OK;
 }
 
@@ -620,8 +740,10 @@ int adjoint_walk(const qf_c128* target, int n_qubits, int n_gates, const qf_loc*
   }
   const double2* LR = P->LR.as<double2>();
   for (int k = p - 1; k >= 0; --k) {
-    QF_TRY(plan_update(P, k, qf::kEnvOnly, 0.0, env_dev + (size_t)k * 16, (long long)p * 16));
-    if (k > 0) QF_TRY(plan_pass(P, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
+    QF_TRY(plan_update(P, all_starts(P), k, qf::kEnvOnly, 0.0, env_dev + (size_t)k * 16,
+                       (long long)p * 16));
+    if (k > 0)
+      QF_TRY(plan_pass(P, all_starts(P), P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
   }
   if (grad)
     QF_CUDA(qf::launch_grad_from_env(env_dev, P->tr.as<double2>(), n_qubits, S, p, st));

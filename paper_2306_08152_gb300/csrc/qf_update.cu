@@ -191,7 +191,7 @@ __global__ void grad_from_env_kernel(double2* __restrict__ env, const double2* _
     for (int j = 0; j < 4; ++j) E[i * 4 + j] = cmul(f, cconj(e[j * 4 + i]));
 }
 
-// Periodic re-unitarisation of gates in FP64 (reset_iter, Sec. III-A2): two
+// Periodic re-unitarisation of gates in FP64 (reset_iter, Sec. III-A2): three
 // Newton-Schulz steps u <- u (3I - u^dagger u) / 2 per gate, one warp per gate.
 // Each step squares the deviation from unitarity; on gates that are already
 // unitary to FP64 rounding they change nothing beyond rounding.
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(128) reunitarize_kernel(double2* __restrict__ 
   const Lane L;
   const int e = L.l & 15;
   double2 u = gates[(size_t)m * 16 + e];
-  for (int step = 0; step < 2; ++step) {
+  for (int step = 0; step < 3; ++step) {
     const double2 P = wmm_dn(L, u, u);
     const double2 Q = make_double2((L.i == L.j ? 1.5 : 0.0) - 0.5 * P.x, -0.5 * P.y);
     u = wmm(L, u, Q);

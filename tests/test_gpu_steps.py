@@ -186,7 +186,7 @@ def test_circuit_unitary_matches_oracle(qf):
 
 
 def test_reunitarize_gates_returns_the_nearest_unitary(qf):
-    """Two Newton-Schulz steps take a gate 1e-4 away from unitary to its polar
+    """Three Newton-Schulz steps take a gate 1e-4 away from unitary to its polar
     factor (the nearest unitary), which the oracle gives as
     optimize_gate(M^dagger) (Sec. III-A1: the update is the polar factor of
     E^dagger)."""
