@@ -272,6 +272,110 @@ pass_lane_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, i
   }
 }
 
+// Window mapping, for gates whose two column bits both lie in bits 0..2
+// (the last pairs of a linear brickwork).  A thread owns, in each of the 4
+// rows of its row block, the aligned window of W = 4 (bits {0,1}) or W = 8
+// entries that contains the gate's column partners, i.e. 1 or 2 whole 4x4
+// blocks, and moves it with 32-byte vector loads and stores: consecutive
+// threads take consecutive windows, so every warp access is one contiguous
+// run of full sectors and no shuffles are needed.  PA and PB are the gate's
+// bit positions (pa = n-1-a, pb = n-1-b).
+
+__device__ __forceinline__ void vld32(const float2* p, float2* v) {
+  asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0].x), "=f"(v[0].y), "=f"(v[1].x), "=f"(v[1].y), "=f"(v[2].x),
+                 "=f"(v[2].y), "=f"(v[3].x), "=f"(v[3].y)
+               : "l"(p));
+}
+__device__ __forceinline__ void vst32(float2* p, const float2* v) {
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0].x),
+               "f"(v[0].y), "f"(v[1].x), "f"(v[1].y), "f"(v[2].x), "f"(v[2].y), "f"(v[3].x),
+               "f"(v[3].y)
+               : "memory");
+}
+__device__ __forceinline__ void vld32(const double2* p, double2* v) {
+  asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];"
+               : "=d"(v[0].x), "=d"(v[0].y), "=d"(v[1].x), "=d"(v[1].y)
+               : "l"(p));
+}
+__device__ __forceinline__ void vst32(double2* p, const double2* v) {
+  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(v[0].x), "d"(v[0].y),
+               "d"(v[1].x), "d"(v[1].y)
+               : "memory");
+}
+
+template <typename R, int PA, int PB>
+__global__ void __launch_bounds__(kPassThreads, (sizeof(R) == 4 ? 2 : 1))
+pass_window_kernel(typename Cplx<R>::T* __restrict__ T, int n, const double2* __restrict__ L,
+                   long long Ls, const double2* __restrict__ Rm, long long Rs) {
+  typedef typename Cplx<R>::T C;
+  constexpr int HI = PA > PB ? PA : PB;
+  constexpr int W = HI <= 1 ? 4 : 8;          // window entries
+  constexpr int NBLK = W / 4;                 // 4x4 blocks per window
+  constexpr int FREE = 3 - PA - PB;           // the free bit of an 8-entry window
+  constexpr int PER = 32 / (int)sizeof(C);    // entries per 32-byte access
+  __shared__ C sL[16], sR[16];
+  const int s = blockIdx.y;
+  load_ops<R, true, true>(sL, sR, L, Ls, Rm, Rs, s);
+  const int lo = PA < PB ? PA : PB;
+  const unsigned N = 1u << n;
+  const int lw = n - (W == 4 ? 2 : 3);  // log2 windows per row
+  const unsigned units = (N >> 2) << lw;
+  C* __restrict__ Ts = T + (size_t)s * N * N;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < units;
+       t += gridDim.x * blockDim.x) {
+    const unsigned r0 = dep2(t >> lw, lo, HI);
+    const unsigned cb = (t & ((1u << lw) - 1u)) * W;
+    // row bits of the gate sit at the same positions as its column bits
+    const unsigned roff[4] = {0u, 1u << PB, 1u << PA, (1u << PA) | (1u << PB)};
+    C win[4][W];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const C* row = Ts + (r0 | roff[x]) * N + cb;
+#pragma unroll
+      for (int v = 0; v < W / PER; ++v) vld32(row + v * PER, &win[x][v * PER]);
+    }
+#pragma unroll
+    for (int b = 0; b < NBLK; ++b) {
+      // column position of local index y in block b
+#define QF_POS(y) (((((y) >> 1) & 1) << PA) | (((y) & 1) << PB) | (NBLK == 2 ? (b << FREE) : 0))
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {  // B <- B R
+        C t4[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          C acc = czero<C>();
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc = cfma(win[x][QF_POS(k)], sR[k * 4 + y], acc);
+          t4[y] = acc;
+        }
+#pragma unroll
+        for (int y = 0; y < 4; ++y) win[x][QF_POS(y)] = t4[y];
+      }
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {  // B <- L B
+        C t4[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          C acc = czero<C>();
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc = cfma(sL[x * 4 + k], win[k][QF_POS(y)], acc);
+          t4[x] = acc;
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) win[x][QF_POS(y)] = t4[x];
+      }
+#undef QF_POS
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      C* row = Ts + (r0 | roff[x]) * N + cb;
+#pragma unroll
+      for (int v = 0; v < W / PER; ++v) vst32(row + v * PER, &win[x][v * PER]);
+    }
+  }
+}
+
 // ----------------------------------------------------------------- trace
 
 constexpr int kTraceThreads = 256;
@@ -348,10 +452,39 @@ void launch_lane(void* T, int n, int S, int plo, int phi, int pa, int pb, const 
                                                                    L, Ls, Rm, Rs);
 }
 
+template <typename R, int PA, int PB>
+void launch_window(void* T, int n, int S, const double2* L, long long Ls, const double2* Rm,
+                   long long Rs, cudaStream_t st) {
+  typedef typename Cplx<R>::T C;
+  constexpr int W = (PA > PB ? PA : PB) <= 1 ? 4 : 8;
+  const unsigned units = (1u << (n - 2)) << (n - (W == 4 ? 2 : 3));
+  const int per_sm = sizeof(R) == 4 ? 2 : 1;
+  long long want = (units + kPassThreads - 1) / kPassThreads;
+  long long cap = ((long long)sm_count() * per_sm + S - 1) / S;
+  if (cap < 1) cap = 1;
+  dim3 grid((unsigned)(want < cap ? want : cap), S);
+  pass_window_kernel<R, PA, PB><<<grid, kPassThreads, 0, st>>>((C*)T, n, L, Ls, Rm, Rs);
+}
+
+template <typename R>
+bool try_window(void* T, int n, int S, int pa, int pb, const double2* L, long long Ls,
+                const double2* Rm, long long Rs, cudaStream_t st) {
+  if (n < 3 || pa > 2 || pb > 2) return false;
+#define QF_W(A, B)                                                \
+  if (pa == A && pb == B) {                                       \
+    launch_window<R, A, B>(T, n, S, L, Ls, Rm, Rs, st);           \
+    return true;                                                  \
+  }
+  QF_W(1, 0) QF_W(0, 1) QF_W(2, 1) QF_W(1, 2) QF_W(2, 0) QF_W(0, 2)
+#undef QF_W
+  return false;
+}
+
 template <typename R, bool HL, bool HR>
 void pass_dispatch(void* T, int n, int S, int pa, int pb, const double2* L, long long Ls,
                    const double2* Rm, long long Rs, cudaStream_t st) {
   const int plo = pa < pb ? pa : pb, phi = pa < pb ? pb : pa;
+  if (HL && HR && try_window<R>(T, n, S, pa, pb, L, Ls, Rm, Rs, st)) return;
   if (n >= 6 && plo <= 1) {
     if (phi < 5)
       launch_lane<R, 2, HL, HR>(T, n, S, plo, phi, pa, pb, L, Ls, Rm, Rs, st);
