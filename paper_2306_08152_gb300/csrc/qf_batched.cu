@@ -45,6 +45,7 @@ constexpr int kRing = 128;  // cost history kept per warp (long plateau window)
 
 struct BatchParams {
   const BatchInst* inst;
+  const int* order;  // instances in the order their problems are handed out
   int n_inst, S;
   const int2* locs;
   const double2* targets;
@@ -62,6 +63,13 @@ struct BatchParams {
   int tmax_bytes;  // tensor capacity of a warp slice (complex128, largest n)
   int warp_bytes;  // whole warp slice
 };
+
+// One out-of-line copy of the warp polar for the whole kernel: inlined at
+// every call site of both precisions the kernel outgrew the instruction cache.
+__device__ __noinline__ bool polar_once(double2 a, float2* scratch, double2* u_out, double* sig) {
+  const Lane L;
+  return warp_polar(L, a, scratch, u_out, sig);
+}
 
 template <typename R>
 struct W {
@@ -186,7 +194,8 @@ struct W {
   }
 
   // InitCircuitTensor: T <- V^dagger, then T <- T (u_k on loc_k) for all k.
-  static __device__ void build(C* T, C* LRs, const double2* V, const double2* g, const int2* locs,
+  static __device__ __noinline__ void build(C* T, C* LRs, const double2* V, const double2* g,
+                                            const int2* locs,
                                int n, int p, const Lane& L) {
     conj_transpose(T, V, n);
     for (int k = 0; k < p; ++k) {
@@ -199,7 +208,8 @@ struct W {
 
   // One gate update: environment from the band, the FP64 warp polar, the
   // pass operators into shared memory, then the fused pass.
-  static __device__ void update(C* T, C* LRs, float2* scratch, double2* g, int2 lc, int n,
+  static __device__ __noinline__ void update(C* T, C* LRs, float2* scratch, double2* g, int2 lc,
+                                             int n,
                                 bool forward, double beta, const Lane& L, int* bad) {
     const int pa = n - 1 - lc.x, pb = n - 1 - lc.y;
     const double2 P = band(T, n, pa, pb, L);
@@ -212,7 +222,7 @@ struct W {
       A = make_double2((1.0 - beta) * E.x + beta * ud.x, (1.0 - beta) * E.y + beta * ud.y);
     double2 un;
     double sg;
-    if (!warp_polar(L, A, scratch, &un, &sg)) {
+    if (!polar_once(A, scratch, &un, &sg)) {
       *bad = 1;
       un = u;
     }
@@ -226,7 +236,8 @@ struct W {
   }
 
   // TwoSidedSweep (Alg. 1).
-  static __device__ void sweep(C* T, C* LRs, float2* scratch, double2* g, const int2* locs,
+  static __device__ __noinline__ void sweep(C* T, C* LRs, float2* scratch, double2* g,
+                                            const int2* locs,
                                int n, int p, double beta, const Lane& L, int* bad) {
     for (int k = p - 1; k >= 0; --k)
       update(T, LRs, scratch, g + k * 16, locs[k], n, false, beta, L, bad);
@@ -280,7 +291,7 @@ __global__ void batched_kernel(BatchParams bp) {
     if (L.l == 0) prob = atomicAdd(bp.work, 1u);
     prob = __shfl_sync(kFull, prob, 0);
     if (prob >= total) break;
-    const int i = (int)(prob / bp.S), s = (int)(prob % bp.S);
+    const int i = bp.order[prob / bp.S], s = (int)(prob % bp.S);
     const BatchInst in = bp.inst[i];
     const int n = in.n, p = in.p;
     double2* g = bp.gates + in.gate_off + (long long)s * p * 16;
@@ -369,10 +380,11 @@ __global__ void batched_kernel(BatchParams bp) {
       c = W<double>::cost((double2*)Tbuf, n);
     }
     if (L.l == 0) {
-      bp.cost_out[prob] = c;
-      bp.sweeps_out[prob] = it;
-      bp.c64_out[prob] = c64_sw;
-      bp.reason_out[prob] = reason;
+      const long long q = (long long)i * bp.S + s;  // outputs in instance order
+      bp.cost_out[q] = c;
+      bp.sweeps_out[q] = it;
+      bp.c64_out[q] = c64_sw;
+      bp.reason_out[q] = reason;
       if (bad) atomicExch(bp.status, QF_ENONFINITE);
     }
     __syncwarp();
@@ -484,8 +496,16 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const long long problems = (long long)n_instances * n_starts;
   // device buffers
-  DevMem d_inst, d_locs, d_tgt, d_gates, d_cost, d_sw, d_c64, d_reason, d_flags;
+  // hand out the biggest instances first (work ~ 4^n * p per sweep), so the
+  // last warps to finish hold short problems
+  std::vector<int> order(n_instances);
+  for (int i = 0; i < n_instances; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return ((long long)inst[x].p << (2 * inst[x].n)) > ((long long)inst[y].p << (2 * inst[y].n));
+  });
+  DevMem d_inst, d_order, d_locs, d_tgt, d_gates, d_cost, d_sw, d_c64, d_reason, d_flags;
   if (d_inst.alloc(sizeof(BatchInst) * n_instances) != cudaSuccess ||
+      d_order.alloc(sizeof(int) * n_instances) != cudaSuccess ||
       d_locs.alloc(sizeof(qf_loc) * loc_total) != cudaSuccess ||
       d_tgt.alloc(sizeof(double2) * tgt_total) != cudaSuccess ||
       d_gates.alloc(sizeof(double2) * gate_total) != cudaSuccess ||
@@ -500,6 +520,8 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
   cudaError_t e = cudaMemcpyAsync(d_inst.p, inst.data(), sizeof(BatchInst) * n_instances,
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_order.p, order.data(), sizeof(int) * n_instances, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_locs.p, hl.data(), sizeof(qf_loc) * loc_total, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_tgt.p, targets, sizeof(double2) * tgt_total, cudaMemcpyDefault, st);
@@ -508,6 +530,7 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
 
   BatchParams bp;
   bp.inst = (const BatchInst*)d_inst.p;
+  bp.order = (const int*)d_order.p;
   bp.n_inst = n_instances;
   bp.S = n_starts;
   bp.locs = (const int2*)d_locs.p;
