@@ -285,6 +285,21 @@ int qf_plan_get_gates(qf_plan* plan, qf_c128* out);
  * tensor entry they cover; may be NULL), the pass-launch count and the count
  * of all kernel launches; then it resets them. */
 int qf_plan_enable_pass_timing(qf_plan* plan, int enable);
+
+/* Look-ahead sweeps (complex64 plans with n_qubits >= 8; elsewhere the flag
+ * is kept but sweeps run one update per pass).  Each half-sweep (Alg. 1) is
+ * split greedily into windows: two consecutive updates whose gates act on
+ * four distinct qubits form a window, any other update a window of its own.
+ * In a two-update window the second gate's environment is taken from the
+ * tensor before the first update's pass, by carrying that pending update
+ * through the partial trace (the same quantity as after the pass, so the
+ * sweep follows the one-update order of Alg. 1 up to rounding), and one
+ * pass applies both updates: half the tensor traffic for the pair.
+ * qf_plan_lookahead_windows returns the two-update windows per sweep (0 when
+ * look-ahead is off or unsupported for the plan).  Synchronises when
+ * enabling (the tile geometry is uploaded once). */
+int qf_plan_set_lookahead(qf_plan* plan, int enable);
+int qf_plan_lookahead_windows(qf_plan* plan, int* pairs_per_sweep);
 int qf_plan_pass_stats(qf_plan* plan, double* pass_ms, int64_t* pass_launches,
                        int64_t* all_launches, double* pass_bytes);
 
@@ -312,6 +327,32 @@ int qf_init_tensor(const qf_c128* target, int n_qubits, int n_gates,
 int qf_apply_pair(void* T, int n_qubits, int n_starts, int a, int b,
                   const qf_c128* L, const qf_c128* R, int precision,
                   void* stream);
+
+/* Steps a2+a5 for two updates on disjoint pairs in one pass (look-ahead):
+ * T_s <- (L1_s on (a1,b1)) (L2_s on (a2,b2)) T_s (R1_s on (a1,b1))
+ *        (R2_s on (a2,b2)).
+ * a1, b1, a2, b2 must be four distinct qubits.  L1, R1, L2, R2: device
+ * n_starts x 16 (FP64; cast to the tensor's precision).  complex64 tensors
+ * with n_qubits >= 8 take the tiled one-pass kernel (one read and one write
+ * of T); other cases run the two single-pair passes in order.  Allocates a
+ * small geometry block stream-ordered (cudaMallocAsync). */
+int qf_apply_two_pairs(void* T, int n_qubits, int n_starts, int a1, int b1,
+                       const qf_c128* L1, const qf_c128* R1, int a2, int b2,
+                       const qf_c128* L2, const qf_c128* R2, int precision,
+                       void* stream);
+
+/* Look-ahead environment (Alg. 1 CalcEnvMat for the second gate of a
+ * window): P_s = partial trace over every qubit except (a, b) of
+ * (L1_s on (a1,b1)) T_s (R1_s on (a1,b1)), computed from T_s without
+ * applying the pending update: with M = R1 L1,
+ *   P[x][y] = sum_rest sum_{i,j} M[j][i] T[(rest,i,x),(rest,j,y)]
+ * (i, j: local indices of (a1, b1); x, y: of (a, b)); 16 N entries of T are
+ * read.  n_qubits >= 4; a1, b1, a, b four distinct qubits.  L1, R1: device
+ * n_starts x 16; P: device n_starts x 16.  Accumulates in the tensor's
+ * precision per CTA and in FP64 across CTAs. */
+int qf_partial_trace_after(const void* T, int n_qubits, int n_starts, int a1,
+                           int b1, const qf_c128* L1, const qf_c128* R1, int a,
+                           int b, qf_c128* P, int precision, void* stream);
 
 /* Step a3, CalcEnvMat (Alg. 1): P_s = partial trace of T_s over every qubit
  * except (a, b), accumulated in FP64.  P: device n_starts x 16. */

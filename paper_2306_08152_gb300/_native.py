@@ -73,6 +73,7 @@ I = ct.c_int
 D = ct.c_double
 DP = ct.POINTER(ct.c_double)
 I64P = ct.POINTER(ct.c_int64)
+IP = ct.POINTER(ct.c_int)
 
 # name -> (restype, argtypes)
 SIGNATURES = {
@@ -95,10 +96,14 @@ SIGNATURES = {
     "qf_plan_get_gates": (I, [P, P]),
     "qf_plan_enable_pass_timing": (I, [P, I]),
     "qf_plan_pass_stats": (I, [P, DP, I64P, I64P, DP]),
+    "qf_plan_set_lookahead": (I, [P, I]),
+    "qf_plan_lookahead_windows": (I, [P, IP]),
     "qf_plan_status": (I, [P]),
     "qf_init_tensor": (I, [P, I, I, P, I, P, P, I, P]),
     "qf_apply_pair": (I, [P, I, I, I, I, P, P, I, P]),
     "qf_partial_trace": (I, [P, I, I, I, I, P, I, P]),
+    "qf_apply_two_pairs": (I, [P, I, I, I, I, P, P, I, I, P, P, I, P]),
+    "qf_partial_trace_after": (I, [P, I, I, I, I, P, P, I, I, P, I, P]),
     "qf_partial_trace_noalloc": (I, [P, I, I, I, I, P, I, P]),
     "qf_optimize_gates": (I, [P, P, D, I, P, P, P]),
     "qf_trace": (I, [P, I, I, P, I, P]),

@@ -19,7 +19,7 @@ from ._native import check
 __all__ = [
     "QF_C128", "QF_C64", "QF_C64_REFINE64", "Options", "instantiate",
     "instantiate_ex", "instantiate_batched", "cost_and_env", "cost_grad", "costs", "Plan", "init_tensor", "apply_pair",
-    "partial_trace", "partial_trace_noalloc", "optimize_gates", "reunitarize_gates", "trace", "circuit_unitary",
+    "partial_trace", "partial_trace_noalloc", "apply_two_pairs", "partial_trace_after", "optimize_gates", "reunitarize_gates", "trace", "circuit_unitary",
 ]
 
 QF_C128 = nat.QF_C128
@@ -284,6 +284,14 @@ class Plan:
     def enable_pass_timing(self, enable=True):
         check(_lib().qf_plan_enable_pass_timing(self.h, int(bool(enable))))
 
+    def set_lookahead(self, enable=True):
+        """Two consecutive updates on disjoint pairs per pass (complex64,
+        n >= 8); returns the two-update windows per sweep (0 = none)."""
+        check(_lib().qf_plan_set_lookahead(self.h, int(bool(enable))))
+        w = ct.c_int()
+        check(_lib().qf_plan_lookahead_windows(self.h, ct.byref(w)))
+        return w.value
+
     def pass_stats(self):
         """(pass ms, pass launches, all launches, pass algorithmic bytes)
         since the last call."""
@@ -350,6 +358,35 @@ def partial_trace(T, a, b, stream=None):
     P = torch.empty((S, 4, 4), dtype=torch.complex128, device=T.device)
     check(_lib().qf_partial_trace(_ptr(T), n, S, int(a), int(b), _ptr(P), _tensor_prec(T),
                                   _stream_handle(stream)))
+    return P
+
+
+def apply_two_pairs(T, a1, b1, L1, R1, a2, b2, L2, R2, stream=None):
+    """In place: T_s <- (L1_s on (a1,b1)) (L2_s on (a2,b2)) T_s
+    (R1_s on (a1,b1)) (R2_s on (a2,b2)); four distinct qubits; operators
+    (S, 4, 4)."""
+    T = _dev(T, "T")
+    S, N = T.shape[0], T.shape[-1]
+    n = int(N).bit_length() - 1
+    ops = [_dev(_c128(X, nm), nm) for X, nm in ((L1, "L1"), (R1, "R1"), (L2, "L2"), (R2, "R2"))]
+    check(_lib().qf_apply_two_pairs(_ptr(T), n, S, int(a1), int(b1), _ptr(ops[0]), _ptr(ops[1]),
+                                    int(a2), int(b2), _ptr(ops[2]), _ptr(ops[3]),
+                                    _tensor_prec(T), _stream_handle(stream)))
+    return T
+
+
+def partial_trace_after(T, a1, b1, L1, R1, a, b, stream=None):
+    """Partial trace over every qubit but (a, b) of (L1 on (a1,b1)) T
+    (R1 on (a1,b1)), computed without applying the pending update."""
+    T = _dev(T, "T")
+    S, N = T.shape[0], T.shape[-1]
+    n = int(N).bit_length() - 1
+    L1 = _dev(_c128(L1, "L1"), "L1")
+    R1 = _dev(_c128(R1, "R1"), "R1")
+    P = torch.empty((S, 4, 4), dtype=torch.complex128, device=T.device)
+    check(_lib().qf_partial_trace_after(_ptr(T), n, S, int(a1), int(b1), _ptr(L1), _ptr(R1),
+                                        int(a), int(b), _ptr(P), _tensor_prec(T),
+                                        _stream_handle(stream)))
     return P
 
 

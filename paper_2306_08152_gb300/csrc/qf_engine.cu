@@ -181,7 +181,14 @@ struct qf_plan {
   cudaGraphExec_t graph = nullptr;
   double graph_beta = 0.0;
   int graph_prec = -1;
+  bool graph_look = false;
+  long long graph_pass_launches = 0, graph_all_launches = 0;  // per replay
   bool use_graph = true;
+  // look-ahead: consecutive updates on disjoint pairs share one pass
+  bool lookahead = false;
+  DevBuf LR2, geo;                 // second operator set; tile geometries
+  std::vector<int> win_first;      // per half-sweep order position: 1 = starts a pair
+  std::vector<int> geo_index;      // per window start (order position): geometry slot
 };
 
 namespace {
@@ -261,6 +268,102 @@ int plan_update(qf_plan* P, const Slice& sl, int k, int mode, double beta, doubl
   return QF_OK;
 }
 
+// Look-ahead update of gate k2, whose environment sees the pending update of
+// gate k1 (operators in LR) through the light cone; its own operators go to LR2.
+int plan_update_look(qf_plan* P, const Slice& sl, int k1, int k2, int mode, double beta) {
+  const int pr = P->prec == QF_C128 ? 0 : 1;
+  const int B = qf::env_ctas(P->n);
+  const void* T = static_cast<const char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
+  const double2* LR = P->LR.as<double2>() + (size_t)sl.s0 * 32;
+  QF_CUDA(qf::launch_update_lookahead(
+      T, P->n, sl.Sg, P->locs[k1].a, P->locs[k1].b, LR, LR + 16, 32, P->locs[k2].a, P->locs[k2].b,
+      P->gates.as<double2>() + (size_t)sl.s0 * P->p * 16 + (size_t)k2 * 16, (long long)P->p * 16,
+      mode, beta, P->LR2.as<double2>() + (size_t)sl.s0 * 32, nullptr, 0,
+      P->sigma.as<double>() + sl.s0, P->status.as<int>(),
+      P->part.as<double>() + (size_t)sl.s0 * B * 32, P->counters.as<unsigned>() + sl.s0, pr, sl.st));
+  P->all_launches++;
+  return QF_OK;
+}
+
+// The pass of a look-ahead window: both updates' operators in one pass.
+int plan_pair_pass(qf_plan* P, const Slice& sl, int slot) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (P->timing) {
+    if (P->events_used + 2 > P->events.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        QF_CUDA(cudaEventCreate(&e));
+        P->events.push_back(e);
+      }
+    }
+    e0 = P->events[P->events_used];
+    e1 = P->events[P->events_used + 1];
+    P->events_used += 2;
+    QF_CUDA(cudaEventRecord(e0, sl.st));
+  }
+  void* T = static_cast<char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
+  const double2* LR = P->LR.as<double2>() + (size_t)sl.s0 * 32;
+  const double2* LR2 = P->LR2.as<double2>() + (size_t)sl.s0 * 32;
+  const void* geo = static_cast<const char*>(P->geo.p) + (size_t)slot * qf::pair_geom_bytes();
+  QF_CUDA(qf::launch_pair_pass(T, P->n, sl.Sg, geo, LR, LR + 16, 32, LR2, LR2 + 16, 32, sl.st));
+  if (P->timing) {
+    QF_CUDA(cudaEventRecord(e1, sl.st));
+    P->pass_bytes += 2.0 * (double)sl.Sg * (double)P->NN * (double)elem_bytes(P->prec);
+  }
+  P->pass_launches++;
+  P->all_launches++;
+  return QF_OK;
+}
+
+// Gate order of half-sweep h (0 = backward k = p-1..0, 1 = forward k = 0..p-1).
+int order_gate(const qf_plan* P, int h, int i) { return h == 0 ? P->p - 1 - i : i; }
+
+bool disjoint(const qf_loc& x, const qf_loc& y) {
+  return x.a != y.a && x.a != y.b && x.b != y.a && x.b != y.b;
+}
+
+// Windows of both half-sweeps: greedily pair position i with i+1 when their
+// gates act on disjoint pairs and the tiled pass supports the case, and
+// write one tile geometry per pair.
+int plan_windows(qf_plan* P) {
+  if (!P->win_first.empty()) return QF_OK;
+  P->win_first.assign(2 * P->p, 0);
+  P->geo_index.assign(2 * P->p, -1);
+  int slots = 0;
+  for (int h = 0; h < 2; ++h)
+    for (int i = 0; i + 1 < P->p;) {
+      const qf_loc& x = P->locs[order_gate(P, h, i)];
+      const qf_loc& y = P->locs[order_gate(P, h, i + 1)];
+      if (disjoint(x, y) && qf::pair_pass_supported(P->n, x.a, x.b, y.a, y.b, 1)) {
+        P->win_first[h * P->p + i] = 1;
+        P->geo_index[h * P->p + i] = slots++;
+        i += 2;
+      } else {
+        i += 1;
+      }
+    }
+  if (slots > 0) {
+    QF_TRY(P->geo.alloc((size_t)slots * qf::pair_geom_bytes()));
+    for (int h = 0; h < 2; ++h)
+      for (int i = 0; i < P->p; ++i) {
+        const int slot = P->geo_index[h * P->p + i];
+        if (slot < 0) continue;
+        const qf_loc& x = P->locs[order_gate(P, h, i)];
+        const qf_loc& y = P->locs[order_gate(P, h, i + 1)];
+        QF_CUDA(qf::make_pair_geom(P->n, x.a, x.b, y.a, y.b,
+                                   static_cast<char*>(P->geo.p) + (size_t)slot * qf::pair_geom_bytes(),
+                                   P->stream));
+      }
+    QF_CUDA(cudaStreamSynchronize(P->stream));
+  }
+  if (!P->LR2.p) QF_TRY(P->LR2.alloc((size_t)P->S * 32 * sizeof(double2)));
+  return QF_OK;
+}
+
+bool plan_uses_lookahead(const qf_plan* P) {
+  return P->lookahead && P->prec == QF_C64 && P->n >= 8;
+}
+
 int plan_streams(qf_plan* P) {
   if (P->s_env) return QF_OK;
   QF_CUDA(cudaStreamCreateWithFlags(&P->s_env, cudaStreamNonBlocking));
@@ -279,7 +382,72 @@ int plan_streams(qf_plan* P) {
 // kernels go to s_env and the passes to s_pass, so the environment of one
 // group overlaps the pass of the other:
 //   env_0(u) | pass_0(u) + env_1(u) | pass_1(u) + env_0(u+1) | ...
+//
+// With look-ahead on, a window of two consecutive updates on disjoint pairs
+// runs as: the first gate's environment and update (operators -> LR), the
+// second gate's environment through the first's pending update and its
+// update (-> LR2), then one pass applying both; the sweep's result is that
+// of the single-update order, up to rounding.
+int enqueue_window(qf_plan* P, const Slice& env_sl, const Slice& pass_sl, int h, int i,
+                   double beta, bool look) {
+  const int k = order_gate(P, h, i);
+  const int mode = h == 0 ? qf::kBackward : qf::kForward;
+  QF_TRY(plan_update(P, env_sl, k, mode, beta, nullptr, 0));
+  if (look && P->win_first[h * P->p + i]) {
+    const int k2 = order_gate(P, h, i + 1);
+    QF_TRY(plan_update_look(P, env_sl, k, k2, mode, beta));
+    if (env_sl.st != pass_sl.st) return QF_OK;  // the caller forks to the pass stream
+    return plan_pair_pass(P, pass_sl, P->geo_index[h * P->p + i]);
+  }
+  if (env_sl.st != pass_sl.st) return QF_OK;
+  const double2* LR = P->LR.as<double2>();
+  return plan_pass(P, pass_sl, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32);
+}
+
+int enqueue_window_pass(qf_plan* P, const Slice& pass_sl, int h, int i, bool look) {
+  if (look && P->win_first[h * P->p + i]) return plan_pair_pass(P, pass_sl, P->geo_index[h * P->p + i]);
+  const int k = order_gate(P, h, i);
+  const double2* LR = P->LR.as<double2>();
+  return plan_pass(P, pass_sl, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32);
+}
+
 int enqueue_sweep(qf_plan* P, double beta, cudaStream_t origin) {
+  const bool look = plan_uses_lookahead(P);
+  if (look) QF_TRY(plan_windows(P));
+  if (look) {
+    if (P->G == 1) {
+      const Slice sl = all_starts(P, origin);
+      for (int h = 0; h < 2; ++h)
+        for (int i = 0; i < P->p; i += (P->win_first[h * P->p + i] ? 2 : 1))
+          QF_TRY(enqueue_window(P, sl, sl, h, i, beta, true));
+      return QF_OK;
+    }
+    QF_TRY(plan_streams(P));
+    const int half = P->S / 2;
+    const Slice env_sl[2] = {{0, half, P->s_env}, {half, P->S - half, P->s_env}};
+    const Slice pass_sl[2] = {{0, half, P->s_pass}, {half, P->S - half, P->s_pass}};
+    QF_CUDA(cudaEventRecord(P->ev_fork, origin));
+    QF_CUDA(cudaStreamWaitEvent(P->s_env, P->ev_fork, 0));
+    QF_CUDA(cudaStreamWaitEvent(P->s_pass, P->ev_fork, 0));
+    bool first = true;
+    for (int h = 0; h < 2; ++h)
+      for (int i = 0; i < P->p; i += (P->win_first[h * P->p + i] ? 2 : 1)) {
+        for (int g = 0; g < 2; ++g) {
+          if (!first) QF_CUDA(cudaStreamWaitEvent(P->s_env, P->ev_pass[g], 0));
+          QF_TRY(enqueue_window(P, env_sl[g], pass_sl[g], h, i, beta, true));
+          QF_CUDA(cudaEventRecord(P->ev_env[g], P->s_env));
+          QF_CUDA(cudaStreamWaitEvent(P->s_pass, P->ev_env[g], 0));
+          QF_TRY(enqueue_window_pass(P, pass_sl[g], h, i, true));
+          QF_CUDA(cudaEventRecord(P->ev_pass[g], P->s_pass));
+        }
+        first = false;
+      }
+    QF_CUDA(cudaEventRecord(P->ev_join_env, P->s_env));
+    QF_CUDA(cudaEventRecord(P->ev_join_pass, P->s_pass));
+    QF_CUDA(cudaStreamWaitEvent(origin, P->ev_join_env, 0));
+    QF_CUDA(cudaStreamWaitEvent(origin, P->ev_join_pass, 0));
+    return QF_OK;
+  }
   const double2* LR = P->LR.as<double2>();
   if (P->G == 1) {
     const Slice sl = all_starts(P, origin);
@@ -324,12 +492,14 @@ int enqueue_sweep(qf_plan* P, double beta, cudaStream_t origin) {
 // precision) and replayed.
 int plan_sweep_once(qf_plan* P, double beta) {
   if (P->timing || !P->use_graph) return enqueue_sweep(P, beta, P->stream);
-  if (!P->graph || P->graph_beta != beta || P->graph_prec != P->prec) {
+  const bool look = plan_uses_lookahead(P);
+  if (!P->graph || P->graph_beta != beta || P->graph_prec != P->prec || P->graph_look != look) {
     if (P->graph) {
       cudaGraphExecDestroy(P->graph);
       P->graph = nullptr;
     }
     QF_TRY(plan_streams(P));
+    if (look) QF_TRY(plan_windows(P));  // synchronises: not inside the capture
     // captured on an internal stream (the caller's may be the legacy default
     // stream, which cannot be captured), launched on the caller's stream
     const long long pl = P->pass_launches, al = P->all_launches;
@@ -348,12 +518,15 @@ int plan_sweep_once(qf_plan* P, double beta) {
       return set_error(QF_ECUDA, "sweep graph instantiation failed: %s", cudaGetErrorString(ei));
     P->graph_beta = beta;
     P->graph_prec = P->prec;
+    P->graph_look = look;
+    P->graph_pass_launches = P->pass_launches - pl;  // what one replay launches
+    P->graph_all_launches = P->all_launches - al;
     P->pass_launches = pl;  // capture launches nothing
     P->all_launches = al;
   }
   QF_CUDA(cudaGraphLaunch(P->graph, P->stream));
-  P->pass_launches += 2 * P->p * P->G;
-  P->all_launches += 4 * P->p * P->G;
+  P->pass_launches += P->graph_pass_launches;
+  P->all_launches += P->graph_all_launches;
   return QF_OK;
 }
 
@@ -547,6 +720,22 @@ int qf_plan_get_gates(qf_plan* plan, qf_c128* out) {
   QF_TRY(store_output(out, plan->gates.as<double2>(), (size_t)plan->S * plan->p * 16,
                       plan->stream));
   QF_CUDA(cudaStreamSynchronize(plan->stream));
+  return QF_OK;
+}
+
+int qf_plan_set_lookahead(qf_plan* plan, int enable) {
+  if (!plan) return set_error(QF_EINVAL, "plan is NULL");
+  plan->lookahead = enable != 0;
+  if (plan->lookahead) QF_TRY(plan_windows(plan));
+  return QF_OK;
+}
+
+int qf_plan_lookahead_windows(qf_plan* plan, int* pairs_per_sweep) {
+  if (!plan || !pairs_per_sweep) return set_error(QF_EINVAL, "NULL argument");
+  *pairs_per_sweep = 0;
+  if (!plan_uses_lookahead(plan)) return QF_OK;
+  QF_TRY(plan_windows(plan));
+  for (int v : plan->win_first) *pairs_per_sweep += v;
   return QF_OK;
 }
 
@@ -831,6 +1020,74 @@ int qf_partial_trace(const void* T, int n_qubits, int n_starts, int a, int b, qf
                           reinterpret_cast<double*>(scratch), counters,
                           precision == QF_C128 ? 0 : 1, st);
   cudaError_t e2 = cudaFreeAsync(scratch, st);
+  if (e != cudaSuccess) return set_error(QF_ECUDA, "partial trace launch failed: %s", cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return set_error(QF_ECUDA, "cudaFreeAsync failed: %s", cudaGetErrorString(e2));
+  return QF_OK;
+}
+
+int qf_apply_two_pairs(void* T, int n_qubits, int n_starts, int a1, int b1, const qf_c128* L1,
+                       const qf_c128* R1, int a2, int b2, const qf_c128* L2, const qf_c128* R2,
+                       int precision, void* stream) {
+  QF_TRY(check_sizes(n_qubits, 1));
+  QF_TRY(check_prec(precision));
+  if (n_starts < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", n_starts);
+  if (!T || !L1 || !R1 || !L2 || !R2) return set_error(QF_EINVAL, "NULL device pointer");
+  const int q[4] = {a1, b1, a2, b2};
+  for (int i = 0; i < 4; ++i) {
+    if (q[i] < 0 || q[i] >= n_qubits)
+      return set_error(QF_EINVAL, "qubit %d invalid for %d qubits", q[i], n_qubits);
+    for (int j = 0; j < i; ++j)
+      if (q[i] == q[j]) return set_error(QF_EINVAL, "the two pairs must be four distinct qubits");
+  }
+  cudaStream_t st = as_stream(stream);
+  const int pr = precision == QF_C128 ? 0 : 1;
+  auto d = [](const qf_c128* x) { return reinterpret_cast<const double2*>(x); };
+  if (!qf::pair_pass_supported(n_qubits, a1, b1, a2, b2, pr)) {
+    // the two single-pair passes in order
+    QF_CUDA(qf::launch_pass(T, n_qubits, n_starts, a1, b1, d(L1), 16, d(R1), 16, pr, st));
+    QF_CUDA(qf::launch_pass(T, n_qubits, n_starts, a2, b2, d(L2), 16, d(R2), 16, pr, st));
+    return QF_OK;
+  }
+  void* geo = nullptr;
+  QF_CUDA(cudaMallocAsync(&geo, qf::pair_geom_bytes(), st));
+  cudaError_t e = qf::make_pair_geom(n_qubits, a1, b1, a2, b2, geo, st);
+  if (e == cudaSuccess)
+    e = qf::launch_pair_pass(T, n_qubits, n_starts, geo, d(L1), d(R1), 16, d(L2), d(R2), 16, st);
+  const cudaError_t e2 = cudaFreeAsync(geo, st);
+  if (e != cudaSuccess) return set_error(QF_ECUDA, "pair pass failed: %s", cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return set_error(QF_ECUDA, "cudaFreeAsync failed: %s", cudaGetErrorString(e2));
+  return QF_OK;
+}
+
+int qf_partial_trace_after(const void* T, int n_qubits, int n_starts, int a1, int b1,
+                           const qf_c128* L1, const qf_c128* R1, int a, int b, qf_c128* P,
+                           int precision, void* stream) {
+  QF_TRY(check_sizes(n_qubits, 1));
+  QF_TRY(check_prec(precision));
+  if (n_qubits < 4) return set_error(QF_EINVAL, "n_qubits=%d: two disjoint pairs need >= 4", n_qubits);
+  if (n_starts < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", n_starts);
+  if (!T || !L1 || !R1 || !P) return set_error(QF_EINVAL, "NULL device pointer");
+  const int q[4] = {a1, b1, a, b};
+  for (int i = 0; i < 4; ++i) {
+    if (q[i] < 0 || q[i] >= n_qubits)
+      return set_error(QF_EINVAL, "qubit %d invalid for %d qubits", q[i], n_qubits);
+    for (int j = 0; j < i; ++j)
+      if (q[i] == q[j]) return set_error(QF_EINVAL, "the two pairs must be four distinct qubits");
+  }
+  cudaStream_t st = as_stream(stream);
+  const size_t part_bytes = (size_t)n_starts * qf::env_ctas(n_qubits) * 32 * sizeof(double);
+  const size_t cnt_bytes = (size_t)n_starts * sizeof(unsigned);
+  void* scratch = nullptr;
+  QF_CUDA(cudaMallocAsync(&scratch, part_bytes + cnt_bytes, st));
+  unsigned* counters = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(scratch) + part_bytes);
+  cudaError_t e = cudaMemsetAsync(counters, 0, cnt_bytes, st);
+  if (e == cudaSuccess)
+    e = qf::launch_update_lookahead(
+        T, n_qubits, n_starts, a1, b1, reinterpret_cast<const double2*>(L1),
+        reinterpret_cast<const double2*>(R1), 16, a, b, nullptr, 0, qf::kTraceOnly, 0.0, nullptr,
+        reinterpret_cast<double2*>(P), 16, nullptr, nullptr, reinterpret_cast<double*>(scratch),
+        counters, precision == QF_C128 ? 0 : 1, st);
+  const cudaError_t e2 = cudaFreeAsync(scratch, st);
   if (e != cudaSuccess) return set_error(QF_ECUDA, "partial trace launch failed: %s", cudaGetErrorString(e));
   if (e2 != cudaSuccess) return set_error(QF_ECUDA, "cudaFreeAsync failed: %s", cudaGetErrorString(e2));
   return QF_OK;

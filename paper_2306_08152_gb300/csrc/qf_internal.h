@@ -45,6 +45,32 @@ cudaError_t launch_update(const void* T, int n, int S, int a, int b,
                           double* part, unsigned* counters, int prec,
                           cudaStream_t st);
 
+// launch_update for a gate on (a, b) whose environment is taken from a tensor
+// that still lacks the pending update of the preceding gate on the disjoint
+// pair (a1, b1) (look-ahead): L1, R1 (start stride stride1) are that
+// update's pass operators.  Needs n >= 4; part and counters as for
+// launch_update.
+cudaError_t launch_update_lookahead(const void* T, int n, int S, int a1, int b1,
+                                    const double2* L1, const double2* R1, long long stride1,
+                                    int a, int b, double2* gates_k,
+                                    long long gstride, int mode, double beta, double2* LR,
+                                    double2* out, long long out_stride, double* sigma_out,
+                                    int* status, double* part, unsigned* counters, int prec,
+                                    cudaStream_t st);
+
+// Two consecutive updates on disjoint pairs in one pass (complex64 only):
+// T_s <- (L1 (x) L2) T_s (R1 (x) R2); L1, R1 have start stride s1, L2, R2
+// start stride s2.  pair_pass_supported tells whether the tiled pass
+// handles the case (complex64, n >= 8, disjoint pairs); make_pair_geom
+// writes the tile geometry (pair_geom_bytes() bytes) to device memory.
+bool pair_pass_supported(int n, int a1, int b1, int a2, int b2, int prec);
+size_t pair_geom_bytes();
+cudaError_t make_pair_geom(int n, int a1, int b1, int a2, int b2, void* geo_dev,
+                           cudaStream_t st);
+cudaError_t launch_pair_pass(void* T, int n, int S, const void* geo_dev, const double2* L1,
+                             const double2* R1, long long s1, const double2* L2,
+                             const double2* R2, long long s2, cudaStream_t st);
+
 // u_i = polar update of E_i (Eq. opt_u) for i < count.
 cudaError_t launch_optimize(const double2* E, const double2* u_old, double beta,
                             int count, double2* u_out, double* sigma_out,

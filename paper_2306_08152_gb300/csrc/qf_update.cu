@@ -27,23 +27,35 @@ constexpr int kEnvThreads = 256;
 // start to finish (atomic ticket, no waiting) adds the B partials in a fixed
 // order, so results do not depend on timing, and runs the gate update.
 
-template <typename R>
+// Look-ahead geometry: the environment of a gate on (pa, pb) taken from a
+// tensor that still lacks the pending update (L1, R1) of the preceding gate
+// on the disjoint pair (pa1, pb1).
+struct LookGeom {
+  int q[4];                 // the four gate bit positions, ascending
+  int pa1, pb1;             // bit positions of the pending update's pair
+  const double2 *L1, *R1;   // its pass operators, start stride `stride`
+  long long stride;
+};
+
+template <typename R, bool kLook>
 __global__ void __launch_bounds__(kEnvThreads) env_kernel(
     const typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, int pa, int pb,
     int mode, double2* __restrict__ gates_k, long long gstride, double beta,
     double2* __restrict__ LR, double2* __restrict__ out, long long out_stride,
     double* __restrict__ sigma_out, int* __restrict__ status, double* __restrict__ part,
-    unsigned* __restrict__ counters) {
+    unsigned* __restrict__ counters, LookGeom lg) {
+  using CT = typename Cplx<R>::T;
   __shared__ double red[32 * (kEnvThreads / 32)];
   __shared__ float2 scratch[32];
+  __shared__ CT sM[16];
   __shared__ bool is_last;
   const int s = blockIdx.y, B = gridDim.x, b = blockIdx.x;
   const unsigned N = 1u << n;
-  const unsigned nr = 1u << (n - 2);
+  const unsigned nr = kLook ? N : 1u << (n - 2);
   const unsigned chunk = (nr + B - 1) / B;
   const unsigned r_beg = b * chunk;
   const unsigned r_end = min(nr, r_beg + chunk);
-  const typename Cplx<R>::T* Ts = T + (size_t)s * N * N;
+  const CT* Ts = T + (size_t)s * N * N;
   const unsigned o1 = 1u << pb, o2 = 1u << pa;
   const unsigned off[4] = {0u, o1, o2, o1 | o2};
 
@@ -51,16 +63,49 @@ __global__ void __launch_bounds__(kEnvThreads) env_kernel(
   R v[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = R(0);
-  for (unsigned r = r_beg + threadIdx.x; r < r_end; r += blockDim.x) {
-    const unsigned d = dep2(r, plo, phi);
+  if (!kLook) {
+    for (unsigned r = r_beg + threadIdx.x; r < r_end; r += blockDim.x) {
+      const unsigned d = dep2(r, plo, phi);
 #pragma unroll
-    for (int x = 0; x < 4; ++x) {
-      const unsigned rb = (d | off[x]) * N + d;
+      for (int x = 0; x < 4; ++x) {
+        const unsigned rb = (d | off[x]) * N + d;
 #pragma unroll
-      for (int y = 0; y < 4; ++y) {
-        const typename Cplx<R>::T e = Ts[rb | off[y]];
-        v[2 * (x * 4 + y)] += e.x;
-        v[2 * (x * 4 + y) + 1] += e.y;
+        for (int y = 0; y < 4; ++y) {
+          const CT e = Ts[rb | off[y]];
+          v[2 * (x * 4 + y)] += e.x;
+          v[2 * (x * 4 + y) + 1] += e.y;
+        }
+      }
+    }
+  } else {
+    // After the pending update T' = (L1 on pair 1) T (R1 on pair 1), so
+    //   P[x][y] = sum_rest sum_i T'[(rest,i,x),(rest,i,y)]
+    //           = sum_rest sum_{i,j} M[j][i] T[(rest,i,x),(rest,j,y)],
+    // M = R1 L1: item (rest, i, j) reads 16 entries and weights them by M[j][i].
+    if (threadIdx.x < 16) {
+      const double2* l1 = lg.L1 + s * lg.stride;
+      const double2* r1 = lg.R1 + s * lg.stride;
+      const int r = threadIdx.x >> 2, c = threadIdx.x & 3;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = 0; k < 4; ++k) acc = cfma(r1[r * 4 + k], l1[k * 4 + c], acc);
+      sM[threadIdx.x] = cmake(acc, R(0));
+    }
+    __syncthreads();
+    const unsigned p1 = 1u << lg.pb1, p2 = 1u << lg.pa1;
+    const unsigned off1[4] = {0u, p1, p2, p1 | p2};
+    for (unsigned r = r_beg + threadIdx.x; r < r_end; r += blockDim.x) {
+      const unsigned i = (r >> 2) & 3u, j = r & 3u;
+      const unsigned d = dep1(dep1(dep1(dep1(r >> 4, lg.q[0]), lg.q[1]), lg.q[2]), lg.q[3]);
+      const CT w = sM[j * 4 + i];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const unsigned rb = (d | off1[i] | off[x]) * N + (d | off1[j]);
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const CT e = Ts[rb | off[y]];
+          v[2 * (x * 4 + y)] += w.x * e.x - w.y * e.y;
+          v[2 * (x * 4 + y) + 1] += w.x * e.y + w.y * e.x;
+        }
       }
     }
   }
@@ -226,6 +271,39 @@ cudaError_t launch_grad_from_env(double2* env, const double2* tr, int n, int S, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_update_lookahead(const void* T, int n, int S, int a1, int b1, const double2* L1,
+                                    const double2* R1, long long stride1, int a, int b, double2* gates_k, long long gstride, int mode,
+                                    double beta, double2* LR, double2* out, long long out_stride,
+                                    double* sigma_out, int* status, double* part,
+                                    unsigned* counters, int prec, cudaStream_t st) {
+  const int pa = qubit_bit(n, a), pb = qubit_bit(n, b);
+  LookGeom lg;
+  lg.pa1 = qubit_bit(n, a1);
+  lg.pb1 = qubit_bit(n, b1);
+  lg.L1 = L1;
+  lg.R1 = R1;
+  lg.stride = stride1;
+  int q[4] = {pa, pb, lg.pa1, lg.pb1};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 3 - i; ++j)
+      if (q[j] > q[j + 1]) {
+        const int t = q[j];
+        q[j] = q[j + 1];
+        q[j + 1] = t;
+      }
+  for (int i = 0; i < 4; ++i) lg.q[i] = q[i];
+  dim3 grid(env_ctas(n), S);
+  if (prec == 0)
+    env_kernel<double, true><<<grid, kEnvThreads, 0, st>>>(
+        (const double2*)T, n, 0, 0, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
+        sigma_out, status, part, counters, lg);
+  else
+    env_kernel<float, true><<<grid, kEnvThreads, 0, st>>>(
+        (const float2*)T, n, 0, 0, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
+        sigma_out, status, part, counters, lg);
+  return cudaGetLastError();
+}
+
 int env_ctas(int n) {
   const unsigned rests = 1u << (n - 2);
   int b = (int)(rests / 256u);
@@ -242,13 +320,13 @@ cudaError_t launch_update(const void* T, int n, int S, int a, int b, double2* ga
   const int plo = pa < pb ? pa : pb, phi = pa < pb ? pb : pa;
   dim3 grid(env_ctas(n), S);
   if (prec == 0)
-    env_kernel<double><<<grid, kEnvThreads, 0, st>>>((const double2*)T, n, plo, phi, pa, pb, mode,
-                                                     gates_k, gstride, beta, LR, out, out_stride,
-                                                     sigma_out, status, part, counters);
+    env_kernel<double, false><<<grid, kEnvThreads, 0, st>>>(
+        (const double2*)T, n, plo, phi, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
+        sigma_out, status, part, counters, LookGeom{});
   else
-    env_kernel<float><<<grid, kEnvThreads, 0, st>>>((const float2*)T, n, plo, phi, pa, pb, mode,
-                                                    gates_k, gstride, beta, LR, out, out_stride,
-                                                    sigma_out, status, part, counters);
+    env_kernel<float, false><<<grid, kEnvThreads, 0, st>>>(
+        (const float2*)T, n, plo, phi, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
+        sigma_out, status, part, counters, LookGeom{});
   return cudaGetLastError();
 }
 
