@@ -296,8 +296,7 @@ int qf_plan_enable_pass_timing(qf_plan* plan, int enable);
  * sweep follows the one-update order of Alg. 1 up to rounding), and one
  * pass applies both updates: half the tensor traffic for the pair.
  * qf_plan_lookahead_windows returns the two-update windows per sweep (0 when
- * look-ahead is off or unsupported for the plan).  Synchronises when
- * enabling (the tile geometry is uploaded once). */
+ * look-ahead is off or unsupported for the plan). */
 int qf_plan_set_lookahead(qf_plan* plan, int enable);
 int qf_plan_lookahead_windows(qf_plan* plan, int* pairs_per_sweep);
 int qf_plan_pass_stats(qf_plan* plan, double* pass_ms, int64_t* pass_launches,
@@ -334,8 +333,7 @@ int qf_apply_pair(void* T, int n_qubits, int n_starts, int a, int b,
  * a1, b1, a2, b2 must be four distinct qubits.  L1, R1, L2, R2: device
  * n_starts x 16 (FP64; cast to the tensor's precision).  complex64 tensors
  * with n_qubits >= 8 take the tiled one-pass kernel (one read and one write
- * of T); other cases run the two single-pair passes in order.  Allocates a
- * small geometry block stream-ordered (cudaMallocAsync). */
+ * of T); other cases run the two single-pair passes in order. */
 int qf_apply_two_pairs(void* T, int n_qubits, int n_starts, int a1, int b1,
                        const qf_c128* L1, const qf_c128* R1, int a2, int b2,
                        const qf_c128* L2, const qf_c128* R2, int precision,

@@ -186,7 +186,8 @@ struct qf_plan {
   bool use_graph = true;
   // look-ahead: consecutive updates on disjoint pairs share one pass
   bool lookahead = false;
-  DevBuf LR2, geo;                 // second operator set; tile geometries
+  DevBuf LR2;                      // the second update's pass operators
+  std::vector<unsigned char> pair_params;  // launch geometry per pair window
   std::vector<int> win_first;      // per half-sweep order position: 1 = starts a pair
   std::vector<int> geo_index;      // per window start (order position): geometry slot
 };
@@ -304,8 +305,8 @@ int plan_pair_pass(qf_plan* P, const Slice& sl, int slot) {
   void* T = static_cast<char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
   const double2* LR = P->LR.as<double2>() + (size_t)sl.s0 * 32;
   const double2* LR2 = P->LR2.as<double2>() + (size_t)sl.s0 * 32;
-  const void* geo = static_cast<const char*>(P->geo.p) + (size_t)slot * qf::pair_geom_bytes();
-  QF_CUDA(qf::launch_pair_pass(T, P->n, sl.Sg, geo, LR, LR + 16, 32, LR2, LR2 + 16, 32, sl.st));
+  const void* pp = P->pair_params.data() + (size_t)slot * qf::pair_params_bytes();
+  QF_CUDA(qf::launch_pair_pass(T, P->n, sl.Sg, pp, LR, LR + 16, 32, LR2, LR2 + 16, 32, sl.st));
   if (P->timing) {
     QF_CUDA(cudaEventRecord(e1, sl.st));
     P->pass_bytes += 2.0 * (double)sl.Sg * (double)P->NN * (double)elem_bytes(P->prec);
@@ -324,7 +325,7 @@ bool disjoint(const qf_loc& x, const qf_loc& y) {
 
 // Windows of both half-sweeps: greedily pair position i with i+1 when their
 // gates act on disjoint pairs and the tiled pass supports the case, and
-// write one tile geometry per pair.
+// prepare one launch geometry per pair.
 int plan_windows(qf_plan* P) {
   if (!P->win_first.empty()) return QF_OK;
   P->win_first.assign(2 * P->p, 0);
@@ -342,20 +343,16 @@ int plan_windows(qf_plan* P) {
         i += 1;
       }
     }
-  if (slots > 0) {
-    QF_TRY(P->geo.alloc((size_t)slots * qf::pair_geom_bytes()));
-    for (int h = 0; h < 2; ++h)
-      for (int i = 0; i < P->p; ++i) {
-        const int slot = P->geo_index[h * P->p + i];
-        if (slot < 0) continue;
-        const qf_loc& x = P->locs[order_gate(P, h, i)];
-        const qf_loc& y = P->locs[order_gate(P, h, i + 1)];
-        QF_CUDA(qf::make_pair_geom(P->n, x.a, x.b, y.a, y.b,
-                                   static_cast<char*>(P->geo.p) + (size_t)slot * qf::pair_geom_bytes(),
-                                   P->stream));
-      }
-    QF_CUDA(cudaStreamSynchronize(P->stream));
-  }
+  P->pair_params.assign((size_t)slots * qf::pair_params_bytes(), 0);
+  for (int h = 0; h < 2; ++h)
+    for (int i = 0; i < P->p; ++i) {
+      const int slot = P->geo_index[h * P->p + i];
+      if (slot < 0) continue;
+      const qf_loc& x = P->locs[order_gate(P, h, i)];
+      const qf_loc& y = P->locs[order_gate(P, h, i + 1)];
+      qf::make_pair_params(P->n, x.a, x.b, y.a, y.b,
+                           P->pair_params.data() + (size_t)slot * qf::pair_params_bytes());
+    }
   if (!P->LR2.p) QF_TRY(P->LR2.alloc((size_t)P->S * 32 * sizeof(double2)));
   return QF_OK;
 }
@@ -499,7 +496,7 @@ int plan_sweep_once(qf_plan* P, double beta) {
       P->graph = nullptr;
     }
     QF_TRY(plan_streams(P));
-    if (look) QF_TRY(plan_windows(P));  // synchronises: not inside the capture
+    if (look) QF_TRY(plan_windows(P));  // allocates: not inside the capture
     // captured on an internal stream (the caller's may be the legacy default
     // stream, which cannot be captured), launched on the caller's stream
     const long long pl = P->pass_launches, al = P->all_launches;
@@ -1048,14 +1045,10 @@ int qf_apply_two_pairs(void* T, int n_qubits, int n_starts, int a1, int b1, cons
     QF_CUDA(qf::launch_pass(T, n_qubits, n_starts, a2, b2, d(L2), 16, d(R2), 16, pr, st));
     return QF_OK;
   }
-  void* geo = nullptr;
-  QF_CUDA(cudaMallocAsync(&geo, qf::pair_geom_bytes(), st));
-  cudaError_t e = qf::make_pair_geom(n_qubits, a1, b1, a2, b2, geo, st);
-  if (e == cudaSuccess)
-    e = qf::launch_pair_pass(T, n_qubits, n_starts, geo, d(L1), d(R1), 16, d(L2), d(R2), 16, st);
-  const cudaError_t e2 = cudaFreeAsync(geo, st);
-  if (e != cudaSuccess) return set_error(QF_ECUDA, "pair pass failed: %s", cudaGetErrorString(e));
-  if (e2 != cudaSuccess) return set_error(QF_ECUDA, "cudaFreeAsync failed: %s", cudaGetErrorString(e2));
+  std::vector<unsigned char> pp(qf::pair_params_bytes());
+  qf::make_pair_params(n_qubits, a1, b1, a2, b2, pp.data());
+  QF_CUDA(qf::launch_pair_pass(T, n_qubits, n_starts, pp.data(), d(L1), d(R1), 16, d(L2), d(R2), 16,
+                               st));
   return QF_OK;
 }
 

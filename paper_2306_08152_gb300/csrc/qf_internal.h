@@ -61,13 +61,13 @@ cudaError_t launch_update_lookahead(const void* T, int n, int S, int a1, int b1,
 // Two consecutive updates on disjoint pairs in one pass (complex64 only):
 // T_s <- (L1 (x) L2) T_s (R1 (x) R2); L1, R1 have start stride s1, L2, R2
 // start stride s2.  pair_pass_supported tells whether the tiled pass
-// handles the case (complex64, n >= 8, disjoint pairs); make_pair_geom
-// writes the tile geometry (pair_geom_bytes() bytes) to device memory.
+// handles the case (complex64, 8 <= n <= 18, disjoint pairs);
+// make_pair_params writes the launch geometry (pair_params_bytes() bytes of
+// host memory), which launch_pair_pass passes by value.
 bool pair_pass_supported(int n, int a1, int b1, int a2, int b2, int prec);
-size_t pair_geom_bytes();
-cudaError_t make_pair_geom(int n, int a1, int b1, int a2, int b2, void* geo_dev,
-                           cudaStream_t st);
-cudaError_t launch_pair_pass(void* T, int n, int S, const void* geo_dev, const double2* L1,
+size_t pair_params_bytes();
+void make_pair_params(int n, int a1, int b1, int a2, int b2, void* host_out);
+cudaError_t launch_pair_pass(void* T, int n, int S, const void* params, const double2* L1,
                              const double2* R1, long long s1, const double2* L2,
                              const double2* R2, long long s2, cudaStream_t st);
 

@@ -401,25 +401,23 @@ pass_window_kernel(typename Cplx<R>::T* __restrict__ T, int n, const double2* __
 constexpr int kPairThreads = 256;
 constexpr int kPairCols = 256;
 constexpr int kPairTileEntries = 16 * kPairCols;
+constexpr int kPairChunks = 3;  // 8-bit chunks of the tile index (n <= 18)
 
-struct PairGeom {
-  int pa1, pb1, pa2, pb2;   // gate bit positions
-  int row_rest_pos[16];     // positions of the n-4 non-gate row bits
-  int col_rest_pos[16];     // positions of the n-8 non-tile column bits
-  unsigned rowoff[16];      // global row offset of tile row t_r (gate bits)
-  unsigned coloff[256];     // global column offset of compressed column t_c
-  unsigned char gcomb[16];  // compressed column of column-local pair (y1, y2)
-  unsigned char winoff[16]; // compressed column of window index w
-  unsigned char rcomb[16];  // tile row of row-local pair (x1, x2)
+// Per-launch geometry, passed by value (constant bank: every lookup below
+// is warp-uniform).  Byte offsets are for complex64 entries.
+struct PairParams {
+  int n;
+  int tile_bits;                 // 2n - 12: tiles per start = 2^tile_bits
+  int tbit_pos[kPairChunks * 8]; // tile-index bit i -> row (>= 32: 32 + row bit) or column bit
+  int tcol_pos[8];               // compressed tile column bit -> global column bit
+  int win_cpos[4];               // window bit -> compressed tile column bit
+  int gsw[16];                   // swizzled compressed column of column-local pair (y1, y2)
+  int rsm[16];                   // shared-memory byte offset of tile row of pair (x1, x2)
+  long long rglob[16];           // global byte offset of the row of pair (x1, x2)
+  long long rtile[16];           // global byte offset of tile row t_r
 };
 
 __device__ __forceinline__ unsigned pswz(unsigned c) { return c ^ (((c >> 4) & 7u) << 1); }
-
-__device__ __forceinline__ unsigned deposit_list(unsigned x, const int* pos, int cnt) {
-  unsigned r = 0;
-  for (int i = 0; i < cnt; ++i) r |= ((x >> i) & 1u) << pos[i];
-  return r;
-}
 
 typedef unsigned long long f32x2;  // two packed floats (x in the low word)
 
@@ -454,170 +452,246 @@ __device__ __forceinline__ f32x2 cmad2(f32x2 acc, f32x2 a, f32x2 a_sw, OpE b) {
   return ffma2(b.im, a_sw, ffma2(b.re, a, acc));
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+__device__ __forceinline__ void cp_async16(unsigned smem_addr, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// 4x4 complex matrix applied along one index of a thread's 4x4 block:
+// out[c][j] = sum_k in[k][j] op[k][c] (kRight) or out[r][j] = sum_k op[r][k] in[k][j]
+// (left); j is the batch index.  in[k][j] is addressed through Get, out through Put.
+template <bool kRight, typename In, typename Out>
+__device__ __forceinline__ void apply4(const float4* op, In in, Out out) {
+  f32x2 o[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[i][j] = 0ull;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    f32x2 a[4], sw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      a[j] = in(k, j);
+      sw[j] = pswap(a[j]);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const OpE b = load_op(op, kRight ? k * 4 + c : c * 4 + k);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[c][j] = cmad2(o[c][j], a[j], sw[j], b);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out(c, j, o[c][j]);
+}
+
 __global__ void __launch_bounds__(kPairThreads, 2)
-pass_pair_kernel(float2* __restrict__ T, int n, const PairGeom* __restrict__ geo,
+pass_pair_kernel(float2* __restrict__ T, const __grid_constant__ PairParams pp,
                  const double2* __restrict__ L1, const double2* __restrict__ R1, long long s1,
                  const double2* __restrict__ L2, const double2* __restrict__ R2, long long s2) {
   extern __shared__ __align__(16) float4 pair_smem[];
-  f32x2* bufs = reinterpret_cast<f32x2*>(pair_smem);  // 2 x 4096 entries
   __shared__ float4 sop[4][16];  // L1, R1, L2, R2 as (b.x, b.x, -b.y, b.y)
-  __shared__ unsigned s_rowoff[16], s_coloff[kPairCols];
-  __shared__ unsigned char s_gcomb[16], s_winoff[16], s_rcomb[16];
-  __shared__ int s_rrpos[16], s_crpos[16];
+  __shared__ long long tab[kPairChunks][256];  // tile byte offset of each 8-bit chunk value
   const int s = blockIdx.y;
   const int tid = threadIdx.x;
+  const int n = pp.n;
+  const long long rowbytes = 8ll << n;
   if (tid < 64) {
     const int o = tid >> 4, e = tid & 15;
     const double2* src = o == 0 ? L1 + s * s1 : o == 1 ? R1 + s * s1 : o == 2 ? L2 + s * s2 : R2 + s * s2;
     const double2 v = src[e];
     sop[o][e] = make_float4((float)v.x, (float)v.x, -(float)v.y, (float)v.y);
   }
-  if (tid < 16) {
-    s_rowoff[tid] = geo->rowoff[tid];
-    s_gcomb[tid] = geo->gcomb[tid];
-    s_winoff[tid] = geo->winoff[tid];
-    s_rcomb[tid] = geo->rcomb[tid];
-    s_rrpos[tid] = geo->row_rest_pos[tid];
-    s_crpos[tid] = geo->col_rest_pos[tid];
-  }
-  s_coloff[tid] = geo->coloff[tid];
-  __syncthreads();
-  const unsigned N = 1u << n;
-  const int nrr = n - 4, ncr = n - 8;
-  const unsigned tiles = 1u << (nrr + ncr);
-  float2* __restrict__ Ts = T + (size_t)s * N * N;
-
-  auto issue = [&](unsigned t, f32x2* buf) {
-    const unsigned row_base = deposit_list(t >> ncr, s_rrpos, nrr);
-    const unsigned col_base = deposit_list(t & ((1u << ncr) - 1u), s_crpos, ncr);
+#pragma unroll
+  for (int j = 0; j < kPairChunks; ++j) {
+    long long off = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const unsigned q = (unsigned)i * kPairThreads + tid;
-      const unsigned tr = q >> 7, c = (q & 127u) * 2u;
-      cp_async16(buf + tr * kPairCols + pswz(c),
-                 Ts + (size_t)(row_base | s_rowoff[tr]) * N + (col_base | s_coloff[c]));
+      const int bit = j * 8 + i;
+      if (bit < pp.tile_bits && ((tid >> i) & 1)) {
+        const int ps = pp.tbit_pos[bit];
+        off += ps >= 32 ? (rowbytes << (ps - 32)) : (8ll << ps);
+      }
     }
+    tab[j][tid] = off;
+  }
+  // per-thread constants: the copy column, the column-phase block and the
+  // row-phase column
+  unsigned ccol = 0;  // global column of this thread's copy pair
+  {
+    const unsigned c = (unsigned)(tid & 127) * 2u;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) ccol |= ((c >> i) & 1u) << pp.tcol_pos[i];
+  }
+  unsigned rcol = 0;  // global column of this thread's row-phase tile column
+#pragma unroll
+  for (int i = 0; i < 8; ++i) rcol |= (((unsigned)tid >> i) & 1u) << pp.tcol_pos[i];
+  unsigned wcomp = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) wcomp |= (((unsigned)tid >> i) & 1u) << pp.win_cpos[i];
+  const unsigned cblock = (unsigned)(tid >> 4) * kPairCols + pswz(wcomp);  // entry index
+  const unsigned rsc = pswz((unsigned)tid) * 8u;                          // byte offset
+  const unsigned cp_dst = (unsigned)(tid >> 7) * kPairCols * 8u + pswz((unsigned)(tid & 127) * 2u) * 8u;
+  __syncthreads();
+
+  const unsigned tiles = 1u << pp.tile_bits;
+  char* Tb = reinterpret_cast<char*>(T + (size_t)s * ((size_t)1 << (2 * n)));
+  const unsigned smem0 = (unsigned)__cvta_generic_to_shared(pair_smem);
+  auto tile_off = [&](unsigned t) {
+    return tab[0][t & 255u] + tab[1][(t >> 8) & 255u] + tab[2][(t >> 16) & 255u];
+  };
+  auto issue = [&](long long toff, unsigned buf) {
+    const char* src = Tb + toff + ccol * 8u;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      cp_async16(smem0 + buf * (kPairTileEntries * 8u) + cp_dst + (unsigned)i * (2u * kPairCols * 8u),
+                 src + pp.rtile[2 * i + (tid >> 7)]);
   };
 
   unsigned t = blockIdx.x;
-  if (t < tiles) issue(t, bufs);
+  long long toff = t < tiles ? tile_off(t) : 0;
+  if (t < tiles) issue(toff, 0);
   cp_async_commit();
-  int cur = 0;
+  unsigned cur = 0;
   for (; t < tiles; t += gridDim.x) {
     const unsigned tn = t + gridDim.x;
-    if (tn < tiles) issue(tn, bufs + (cur ^ 1) * kPairTileEntries);
+    const long long tnoff = tn < tiles ? tile_off(tn) : 0;
+    if (tn < tiles) issue(tnoff, cur ^ 1u);
     cp_async_commit();
     cp_async_wait1();
     __syncthreads();
-    f32x2* tile = bufs + cur * kPairTileEntries;
+    f32x2* tile = reinterpret_cast<f32x2*>(pair_smem) + cur * kPairTileEntries;
+    char* tileb = reinterpret_cast<char*>(tile);
     {  // columns: B <- B (R1 (x) R2) on the 16 column partners of (row, window)
-      f32x2* rowp = tile + (tid >> 4) * kPairCols;
-      const unsigned wb = s_winoff[tid & 15];
       f32x2 e[4][4];  // [y1][y2]
 #pragma unroll
-      for (int y1 = 0; y1 < 4; ++y1)
-#pragma unroll
-        for (int y2 = 0; y2 < 4; ++y2) e[y1][y2] = rowp[pswz(wb | s_gcomb[y1 * 4 + y2])];
-      f32x2 o[4][4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) o[i][j] = 0ull;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {  // R1 on y1: o[c][y2] = sum_k e[k][y2] R1[k][c]
-        f32x2 sw[4];
-#pragma unroll
-        for (int y2 = 0; y2 < 4; ++y2) sw[y2] = pswap(e[k][y2]);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const OpE b = load_op(sop[1], k * 4 + c);
-#pragma unroll
-          for (int y2 = 0; y2 < 4; ++y2) o[c][y2] = cmad2(o[c][y2], e[k][y2], sw[y2], b);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) e[i][j] = 0ull;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {  // R2 on y2: e[y1][c] = sum_k o[y1][k] R2[k][c]
-        f32x2 sw[4];
-#pragma unroll
-        for (int y1 = 0; y1 < 4; ++y1) sw[y1] = pswap(o[y1][k]);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const OpE b = load_op(sop[3], k * 4 + c);
-#pragma unroll
-          for (int y1 = 0; y1 < 4; ++y1) e[y1][c] = cmad2(e[y1][c], o[y1][k], sw[y1], b);
-        }
-      }
-#pragma unroll
-      for (int y1 = 0; y1 < 4; ++y1)
-#pragma unroll
-        for (int y2 = 0; y2 < 4; ++y2) rowp[pswz(wb | s_gcomb[y1 * 4 + y2])] = e[y1][y2];
+      for (int k = 0; k < 16; ++k) e[k >> 2][k & 3] = tile[cblock ^ (unsigned)pp.gsw[k]];
+      f32x2 m[4][4];
+      apply4<true>(sop[1], [&](int k, int j) { return e[k][j]; },
+                   [&](int c, int j, f32x2 v) { m[c][j] = v; });
+      apply4<true>(sop[3], [&](int k, int j) { return m[j][k]; },
+                   [&](int c, int j, f32x2 v) { tile[cblock ^ (unsigned)pp.gsw[j * 4 + c]] = v; });
     }
     __syncthreads();
     {  // rows: B <- (L1 (x) L2) B on the 16 row partners of tile column tid
-      const unsigned sc = pswz(tid);
-      f32x2 f[4][4];  // [x1][x2]
-#pragma unroll
-      for (int x1 = 0; x1 < 4; ++x1)
-#pragma unroll
-        for (int x2 = 0; x2 < 4; ++x2) f[x1][x2] = tile[s_rcomb[x1 * 4 + x2] * kPairCols + sc];
-      f32x2 o[4][4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) o[i][j] = 0ull;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {  // L1 on x1: o[r][x2] = sum_k L1[r][k] f[k][x2]
-        f32x2 sw[4];
-#pragma unroll
-        for (int x2 = 0; x2 < 4; ++x2) sw[x2] = pswap(f[k][x2]);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const OpE b = load_op(sop[0], r * 4 + k);
-#pragma unroll
-          for (int x2 = 0; x2 < 4; ++x2) o[r][x2] = cmad2(o[r][x2], f[k][x2], sw[x2], b);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) f[i][j] = 0ull;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {  // L2 on x2: f[x1][r] = sum_k L2[r][k] o[x1][k]
-        f32x2 sw[4];
-#pragma unroll
-        for (int x1 = 0; x1 < 4; ++x1) sw[x1] = pswap(o[x1][k]);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const OpE b = load_op(sop[2], r * 4 + k);
-#pragma unroll
-          for (int x1 = 0; x1 < 4; ++x1) f[x1][r] = cmad2(f[x1][r], o[x1][k], sw[x1], b);
-        }
-      }
-      const unsigned row_base = deposit_list(t >> ncr, s_rrpos, nrr);
-      const unsigned col = deposit_list(t & ((1u << ncr) - 1u), s_crpos, ncr) | s_coloff[tid];
-#pragma unroll
-      for (int x1 = 0; x1 < 4; ++x1)
-#pragma unroll
-        for (int x2 = 0; x2 < 4; ++x2)
-          *reinterpret_cast<f32x2*>(Ts + (size_t)(row_base | s_rowoff[s_rcomb[x1 * 4 + x2]]) * N + col) =
-              f[x1][x2];
+      f32x2 m[4][4];
+      apply4<false>(sop[0], [&](int k, int j) {
+        return *reinterpret_cast<const f32x2*>(tileb + pp.rsm[k * 4 + j] + rsc); },
+                    [&](int c, int j, f32x2 v) { m[c][j] = v; });
+      char* dst = Tb + toff + rcol * 8u;
+      apply4<false>(sop[2], [&](int k, int j) { return m[j][k]; },
+                    [&](int c, int j, f32x2 v) {
+                      *reinterpret_cast<f32x2*>(dst + pp.rglob[j * 4 + c]) = v; });
     }
     __syncthreads();  // this buffer is refilled by the next iteration's prefetch
-    cur ^= 1;
+    cur ^= 1u;
+    toff = tnoff;
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
+
+}  // namespace
+
+bool pair_pass_supported(int n, int a1, int b1, int a2, int b2, int prec) {
+  if (prec != 1 || n < 8 || 2 * n - 12 > kPairChunks * 8) return false;
+  return a1 != a2 && a1 != b2 && b1 != a2 && b1 != b2 && a1 != b1 && a2 != b2;
+}
+
+size_t pair_params_bytes() { return sizeof(PairParams); }
+
+void make_pair_params(int n, int a1, int b1, int a2, int b2, void* host_out) {
+  PairParams g;
+  memset(&g, 0, sizeof(g));
+  g.n = n;
+  g.tile_bits = 2 * n - 12;
+  const int pa1 = qubit_bit(n, a1), pb1 = qubit_bit(n, b1);
+  const int pa2 = qubit_bit(n, a2), pb2 = qubit_bit(n, b2);
+  const unsigned gmask = (1u << pa1) | (1u << pb1) | (1u << pa2) | (1u << pb2);
+  // tile column bits: the 4 gate bits and the 4 lowest other bits (window)
+  unsigned tmask = gmask;
+  int win[4], nw = 0;
+  for (int b = 0; b < n && nw < 4; ++b)
+    if (!((gmask >> b) & 1u)) {
+      tmask |= 1u << b;
+      win[nw++] = b;
+    }
+  int ntb = 0;
+  for (int b = 0; b < n; ++b)
+    if ((tmask >> b) & 1u) g.tcol_pos[ntb++] = b;
+  auto cpos = [&](int b) {
+    for (int i = 0; i < 8; ++i)
+      if (g.tcol_pos[i] == b) return i;
+    return -1;
+  };
+  for (int i = 0; i < 4; ++i) g.win_cpos[i] = cpos(win[i]);
+  // tile index: the n-8 non-tile column bits (low), then the n-4 non-gate row bits
+  int nb = 0;
+  for (int b = 0; b < n; ++b)
+    if (!((tmask >> b) & 1u)) g.tbit_pos[nb++] = b;
+  for (int b = 0; b < n; ++b)
+    if (!((gmask >> b) & 1u)) g.tbit_pos[nb++] = 32 + b;
+  // tile rows: the 4 gate bits in increasing position order
+  int gs[4] = {pa1, pb1, pa2, pb2};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 3 - i; ++j)
+      if (gs[j] > gs[j + 1]) {
+        const int t = gs[j];
+        gs[j] = gs[j + 1];
+        gs[j + 1] = t;
+      }
+  auto rpos = [&](int b) {
+    for (int i = 0; i < 4; ++i)
+      if (gs[i] == b) return i;
+    return -1;
+  };
+  const long long rowbytes = 8ll << n;
+  for (int tr = 0; tr < 16; ++tr) {
+    long long r = 0;
+    for (int i = 0; i < 4; ++i) r |= (long long)((tr >> i) & 1) << gs[i];
+    g.rtile[tr] = r * rowbytes;
+  }
+  for (int v1 = 0; v1 < 4; ++v1)
+    for (int v2 = 0; v2 < 4; ++v2) {
+      // local index 2*bit(pa) + bit(pb) for each gate
+      const unsigned c = (((unsigned)(v1 >> 1) & 1u) << cpos(pa1)) | (((unsigned)v1 & 1u) << cpos(pb1)) |
+                         (((unsigned)(v2 >> 1) & 1u) << cpos(pa2)) | (((unsigned)v2 & 1u) << cpos(pb2));
+      // the gate bits and the window bits are disjoint and the swizzle is
+      // linear over XOR, so a partner's slot is block ^ pswz(gate part)
+      g.gsw[v1 * 4 + v2] = (int)(c ^ (((c >> 4) & 7u) << 1));
+      const unsigned r = (((unsigned)(v1 >> 1) & 1u) << rpos(pa1)) | (((unsigned)v1 & 1u) << rpos(pb1)) |
+                         (((unsigned)(v2 >> 1) & 1u) << rpos(pa2)) | (((unsigned)v2 & 1u) << rpos(pb2));
+      g.rsm[v1 * 4 + v2] = (int)(r * kPairCols * 8u);
+      g.rglob[v1 * 4 + v2] = g.rtile[r];
+    }
+  memcpy(host_out, &g, sizeof(g));
+}
+
+cudaError_t launch_pair_pass(void* T, int n, int S, const void* params, const double2* L1,
+                             const double2* R1, long long s1, const double2* L2,
+                             const double2* R2, long long s2, cudaStream_t st) {
+  const size_t smem = 2 * kPairTileEntries * sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(pass_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  PairParams pp;
+  memcpy(&pp, params, sizeof(pp));
+  const unsigned tiles = 1u << (2 * n - 12);
+  long long cap = ((long long)sm_count() * 2 + S - 1) / S;
+  if (cap < 1) cap = 1;
+  dim3 grid((unsigned)((long long)tiles < cap ? tiles : cap), S);
+  pass_pair_kernel<<<grid, kPairThreads, smem, st>>>((float2*)T, pp, L1, R1, s1, L2, R2, s2);
+  return cudaGetLastError();
+}
+
+namespace {
 
 // ----------------------------------------------------------------- trace
 
@@ -794,104 +868,6 @@ cudaError_t launch_pass(void* T, int n, int S, int a, int b, const double2* L,
     pass_ops<double>(T, n, S, pa, pb, L, Lstride, R, Rstride, st);
   else
     pass_ops<float>(T, n, S, pa, pb, L, Lstride, R, Rstride, st);
-  return cudaGetLastError();
-}
-
-bool pair_pass_supported(int n, int a1, int b1, int a2, int b2, int prec) {
-  if (prec != 1 || n < 8) return false;
-  return a1 != a2 && a1 != b2 && b1 != a2 && b1 != b2 && a1 != b1 && a2 != b2;
-}
-
-cudaError_t make_pair_geom(int n, int a1, int b1, int a2, int b2, void* geo_dev, cudaStream_t st) {
-  PairGeom g;
-  memset(&g, 0, sizeof(g));
-  g.pa1 = qubit_bit(n, a1);
-  g.pb1 = qubit_bit(n, b1);
-  g.pa2 = qubit_bit(n, a2);
-  g.pb2 = qubit_bit(n, b2);
-  const unsigned gmask = (1u << g.pa1) | (1u << g.pb1) | (1u << g.pa2) | (1u << g.pb2);
-  // tile column bits: the 4 gate bits and the 4 lowest other bits
-  unsigned tmask = gmask;
-  int win[4], nw = 0;
-  for (int b = 0; b < n && nw < 4; ++b)
-    if (!((gmask >> b) & 1u)) {
-      tmask |= 1u << b;
-      win[nw++] = b;
-    }
-  int tb[8], ntb = 0;
-  for (int b = 0; b < n; ++b)
-    if ((tmask >> b) & 1u) tb[ntb++] = b;
-  int nrr = 0, ncr = 0;
-  for (int b = 0; b < n; ++b) {
-    if (!((gmask >> b) & 1u)) g.row_rest_pos[nrr++] = b;
-    if (!((tmask >> b) & 1u)) g.col_rest_pos[ncr++] = b;
-  }
-  auto cpos = [&](int b) {  // compressed position of a tile column bit
-    for (int i = 0; i < 8; ++i)
-      if (tb[i] == b) return i;
-    return -1;
-  };
-  for (unsigned tc = 0; tc < 256; ++tc) {
-    unsigned c = 0;
-    for (int i = 0; i < 8; ++i) c |= ((tc >> i) & 1u) << tb[i];
-    g.coloff[tc] = c;
-  }
-  for (int w = 0; w < 16; ++w) {
-    unsigned c = 0;
-    for (int i = 0; i < 4; ++i) c |= ((unsigned)(w >> i) & 1u) << cpos(win[i]);
-    g.winoff[w] = (unsigned char)c;
-  }
-  // tile rows: the 4 gate bits in increasing position order
-  int gs[4] = {g.pa1, g.pb1, g.pa2, g.pb2};
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 3 - i; ++j)
-      if (gs[j] > gs[j + 1]) {
-        int t = gs[j];
-        gs[j] = gs[j + 1];
-        gs[j + 1] = t;
-      }
-  auto rpos = [&](int b) {
-    for (int i = 0; i < 4; ++i)
-      if (gs[i] == b) return i;
-    return -1;
-  };
-  for (int tr = 0; tr < 16; ++tr) {
-    unsigned r = 0;
-    for (int i = 0; i < 4; ++i) r |= ((unsigned)(tr >> i) & 1u) << gs[i];
-    g.rowoff[tr] = r;
-  }
-  for (int v1 = 0; v1 < 4; ++v1)
-    for (int v2 = 0; v2 < 4; ++v2) {
-      // local index 2*bit(pa) + bit(pb) for each gate
-      const unsigned c = (((unsigned)(v1 >> 1) & 1u) << cpos(g.pa1)) | (((unsigned)v1 & 1u) << cpos(g.pb1)) |
-                         (((unsigned)(v2 >> 1) & 1u) << cpos(g.pa2)) | (((unsigned)v2 & 1u) << cpos(g.pb2));
-      g.gcomb[v1 * 4 + v2] = (unsigned char)c;
-      const unsigned r = (((unsigned)(v1 >> 1) & 1u) << rpos(g.pa1)) | (((unsigned)v1 & 1u) << rpos(g.pb1)) |
-                         (((unsigned)(v2 >> 1) & 1u) << rpos(g.pa2)) | (((unsigned)v2 & 1u) << rpos(g.pb2));
-      g.rcomb[v1 * 4 + v2] = (unsigned char)r;
-    }
-  return cudaMemcpyAsync(geo_dev, &g, sizeof(g), cudaMemcpyHostToDevice, st);
-}
-
-size_t pair_geom_bytes() { return (sizeof(PairGeom) + 255) / 256 * 256; }
-
-cudaError_t launch_pair_pass(void* T, int n, int S, const void* geo_dev, const double2* L1,
-                             const double2* R1, long long s1, const double2* L2,
-                             const double2* R2, long long s2, cudaStream_t st) {
-  const size_t smem = 2 * kPairTileEntries * sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(pass_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const unsigned tiles = 1u << (2 * n - 12);
-  long long cap = ((long long)sm_count() * 2 + S - 1) / S;
-  if (cap < 1) cap = 1;
-  dim3 grid((unsigned)((long long)tiles < cap ? tiles : cap), S);
-  pass_pair_kernel<<<grid, kPairThreads, smem, st>>>((float2*)T, n, (const PairGeom*)geo_dev, L1, R1,
-                                                     s1, L2, R2, s2);
   return cudaGetLastError();
 }
 
