@@ -416,14 +416,24 @@ def run_lookahead(args, qf, torch, dev, inst, V, starts, one_update_costs):
     avg_pass_s = (pass_ms / 1e3) / max(pass_launches, 1)
     achieved = alg_bytes / avg_pass_s / 1e9
     updates = inst.n_starts * 2 * inst.p
-    return {"value": updates * args.steps / (ms / 1e3), "unit": UNIT,
+    value = updates * args.steps / (ms / 1e3)
+    # the one-update-per-pass roofline: one read and one write of a start's
+    # tensor per gate update at the measured copy bandwidth
+    one_pass_bytes = 2 * 8 * 4**n
+    one_pass_roofline = peak * 1e9 / one_pass_bytes
+    return {"value": value, "unit": UNIT,
+            "effective": {"frac_of_one_pass_roofline": value / one_pass_roofline,
+                          "one_pass_roofline_updates_per_s": one_pass_roofline,
+                          "effective_gbs": value * one_pass_bytes / 1e9,
+                          "note": "updates/s against the bytes one update per pass would move"},
             "value_graph": updates / (ms_graph / 1e3),
             "ms_per_step": ms / args.steps, "ms_per_step_graph": ms_graph,
             "pair_windows_per_sweep": windows,
             "passes_per_sweep": pass_launches / args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "kernel": "pass kernels of the look-ahead sweep (pair pass + single passes)",
+                         "kernel": "pass kernels of the look-ahead sweep (two-update pair pass; "
+                                   "single passes where a window holds one update)",
                          "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
                          "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_pass_s * 1e3},
             "gpu_launches": int(all_launches),

@@ -382,12 +382,14 @@ pass_window_kernel(typename Cplx<R>::T* __restrict__ T, int n, const double2* __
 //
 // Look-ahead pass for two consecutive updates on disjoint qubit pairs:
 // T <- (L1 (x) L2) T (R1 (x) R2), (L1, R1) on bit positions (pa1, pb1) and
-// (L2, R2) on (pa2, pb2).  A CTA works on tiles of 16 rows (every value of
-// the 4 gate row bits) x 256 columns (every value of the 4 gate column bits
-// and of the 4 lowest other column bits) = 4096 entries, 32 KB of complex64,
-// double-buffered: while one tile is transformed the next streams in with
-// 16-byte cp.async copies (bit positions 0..3 are always tile columns, so
-// every copy is 16-byte aligned and every warp reads whole 128-byte runs).
+// (L2, R2) on (pa2, pb2).  A CTA of 128 threads works on tiles of 16 rows
+// (every value of the 4 gate row bits) x 128 columns (every value of the 4
+// gate column bits and of the 3 lowest other column bits) = 2048 entries,
+// 16 KB of complex64, double-buffered: while one tile is transformed the
+// next streams in with 16-byte cp.async copies (bit positions 0..2 are
+// always tile columns, so every copy is 16-byte aligned and covers whole
+// 64-byte runs).  Four CTAs share an SM, so one CTA's barrier waits overlap
+// another's arithmetic.
 //   columns  each thread takes the 16 column partners of one (row, window)
 //            pair and applies R1 and R2;
 //   rows     each thread takes the 16 row partners of one tile column,
@@ -396,10 +398,12 @@ pass_window_kernel(typename Cplx<R>::T* __restrict__ T, int n, const double2* __
 // one write; they run as packed f32x2 FMAs (acc += (b.x,b.x)(a.x,a.y) +
 // (-b.y,b.y)(a.y,a.x)), each operator entry loaded once per stage and used
 // for four vectors.  Shared memory holds tile columns XOR-swizzled in
-// 16-byte units (bits 4..6 of the column into bits 1..3).
+// 16-byte units (bits 4..6 of the column into bits 1..3), and odd tile rows
+// XOR a per-launch mask into bits 1..3 that spreads the column phase's
+// half-warps (8 windows x 2 rows) over the banks.
 
-constexpr int kPairThreads = 256;
-constexpr int kPairCols = 256;
+constexpr int kPairThreads = 128;
+constexpr int kPairCols = 128;
 constexpr int kPairTileEntries = 16 * kPairCols;
 constexpr int kPairChunks = 3;  // 8-bit chunks of the tile index (n <= 18)
 
@@ -407,10 +411,11 @@ constexpr int kPairChunks = 3;  // 8-bit chunks of the tile index (n <= 18)
 // is warp-uniform).  Byte offsets are for complex64 entries.
 struct PairParams {
   int n;
-  int tile_bits;                 // 2n - 12: tiles per start = 2^tile_bits
+  int tile_bits;                 // 2n - 11: tiles per start = 2^tile_bits
   int tbit_pos[kPairChunks * 8]; // tile-index bit i -> row (>= 32: 32 + row bit) or column bit
   int tcol_pos[8];               // compressed tile column bit -> global column bit
-  int win_cpos[4];               // window bit -> compressed tile column bit
+  int win_cpos[4];               // window bit -> compressed tile column bit (3 used)
+  int rxmask;                    // slot XOR of odd tile rows (bank spread)
   int gsw[16];                   // swizzled compressed column of column-local pair (y1, y2)
   int rsm[16];                   // shared-memory byte offset of tile row of pair (x1, x2)
   long long rglob[16];           // global byte offset of the row of pair (x1, x2)
@@ -489,7 +494,7 @@ __device__ __forceinline__ void apply4(const float4* op, In in, Out out) {
     for (int j = 0; j < 4; ++j) out(c, j, o[c][j]);
 }
 
-__global__ void __launch_bounds__(kPairThreads, 2)
+__global__ void __launch_bounds__(kPairThreads, 4)
 pass_pair_kernel(float2* __restrict__ T, const __grid_constant__ PairParams pp,
                  const double2* __restrict__ L1, const double2* __restrict__ R1, long long s1,
                  const double2* __restrict__ L2, const double2* __restrict__ R2, long long s2) {
@@ -507,35 +512,39 @@ pass_pair_kernel(float2* __restrict__ T, const __grid_constant__ PairParams pp,
     sop[o][e] = make_float4((float)v.x, (float)v.x, -(float)v.y, (float)v.y);
   }
 #pragma unroll
-  for (int j = 0; j < kPairChunks; ++j) {
-    long long off = 0;
+  for (int j = 0; j < kPairChunks; ++j)
+    for (int v = tid; v < 256; v += kPairThreads) {
+      long long off = 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int bit = j * 8 + i;
-      if (bit < pp.tile_bits && ((tid >> i) & 1)) {
-        const int ps = pp.tbit_pos[bit];
-        off += ps >= 32 ? (rowbytes << (ps - 32)) : (8ll << ps);
+      for (int i = 0; i < 8; ++i) {
+        const int bit = j * 8 + i;
+        if (bit < pp.tile_bits && ((v >> i) & 1)) {
+          const int ps = pp.tbit_pos[bit];
+          off += ps >= 32 ? (rowbytes << (ps - 32)) : (8ll << ps);
+        }
       }
+      tab[j][v] = off;
     }
-    tab[j][tid] = off;
-  }
   // per-thread constants: the copy column, the column-phase block and the
   // row-phase column
   unsigned ccol = 0;  // global column of this thread's copy pair
   {
-    const unsigned c = (unsigned)(tid & 127) * 2u;
+    const unsigned c = (unsigned)(tid & 63) * 2u;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) ccol |= ((c >> i) & 1u) << pp.tcol_pos[i];
+    for (int i = 0; i < 7; ++i) ccol |= ((c >> i) & 1u) << pp.tcol_pos[i];
   }
   unsigned rcol = 0;  // global column of this thread's row-phase tile column
 #pragma unroll
-  for (int i = 0; i < 8; ++i) rcol |= (((unsigned)tid >> i) & 1u) << pp.tcol_pos[i];
+  for (int i = 0; i < 7; ++i) rcol |= (((unsigned)tid >> i) & 1u) << pp.tcol_pos[i];
   unsigned wcomp = 0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) wcomp |= (((unsigned)tid >> i) & 1u) << pp.win_cpos[i];
-  const unsigned cblock = (unsigned)(tid >> 4) * kPairCols + pswz(wcomp);  // entry index
-  const unsigned rsc = pswz((unsigned)tid) * 8u;                          // byte offset
-  const unsigned cp_dst = (unsigned)(tid >> 7) * kPairCols * 8u + pswz((unsigned)(tid & 127) * 2u) * 8u;
+  for (int i = 0; i < 3; ++i) wcomp |= (((unsigned)tid >> i) & 1u) << pp.win_cpos[i];
+  const unsigned ctr = (unsigned)tid >> 3;  // column-phase tile row
+  const unsigned cblock = ctr * kPairCols + (pswz(wcomp) ^ ((ctr & 1u) ? (unsigned)pp.rxmask : 0u));
+  const unsigned rsc = pswz((unsigned)tid) * 8u;  // byte offset (row slot masks are in rsm)
+  const unsigned hi = (unsigned)tid >> 6;         // copies go to rows 2i + hi
+  const unsigned cp_dst =
+      hi * kPairCols * 8u + (pswz((unsigned)(tid & 63) * 2u) ^ (hi ? (unsigned)pp.rxmask : 0u)) * 8u;
   __syncthreads();
 
   const unsigned tiles = 1u << pp.tile_bits;
@@ -549,7 +558,7 @@ pass_pair_kernel(float2* __restrict__ T, const __grid_constant__ PairParams pp,
 #pragma unroll
     for (int i = 0; i < 8; ++i)
       cp_async16(smem0 + buf * (kPairTileEntries * 8u) + cp_dst + (unsigned)i * (2u * kPairCols * 8u),
-                 src + pp.rtile[2 * i + (tid >> 7)]);
+                 src + pp.rtile[2 * i + hi]);
   };
 
   unsigned t = blockIdx.x;
@@ -580,7 +589,7 @@ pass_pair_kernel(float2* __restrict__ T, const __grid_constant__ PairParams pp,
     {  // rows: B <- (L1 (x) L2) B on the 16 row partners of tile column tid
       f32x2 m[4][4];
       apply4<false>(sop[0], [&](int k, int j) {
-        return *reinterpret_cast<const f32x2*>(tileb + pp.rsm[k * 4 + j] + rsc); },
+        return *reinterpret_cast<const f32x2*>(tileb + ((unsigned)pp.rsm[k * 4 + j] ^ rsc)); },
                     [&](int c, int j, f32x2 v) { m[c][j] = v; });
       char* dst = Tb + toff + rcol * 8u;
       apply4<false>(sop[2], [&](int k, int j) { return m[j][k]; },
@@ -597,7 +606,7 @@ pass_pair_kernel(float2* __restrict__ T, const __grid_constant__ PairParams pp,
 }  // namespace
 
 bool pair_pass_supported(int n, int a1, int b1, int a2, int b2, int prec) {
-  if (prec != 1 || n < 8 || 2 * n - 12 > kPairChunks * 8) return false;
+  if (prec != 1 || n < 8 || 2 * n - 11 > kPairChunks * 8) return false;
   return a1 != a2 && a1 != b2 && b1 != a2 && b1 != b2 && a1 != b1 && a2 != b2;
 }
 
@@ -607,14 +616,14 @@ void make_pair_params(int n, int a1, int b1, int a2, int b2, void* host_out) {
   PairParams g;
   memset(&g, 0, sizeof(g));
   g.n = n;
-  g.tile_bits = 2 * n - 12;
+  g.tile_bits = 2 * n - 11;
   const int pa1 = qubit_bit(n, a1), pb1 = qubit_bit(n, b1);
   const int pa2 = qubit_bit(n, a2), pb2 = qubit_bit(n, b2);
   const unsigned gmask = (1u << pa1) | (1u << pb1) | (1u << pa2) | (1u << pb2);
-  // tile column bits: the 4 gate bits and the 4 lowest other bits (window)
+  // tile column bits: the 4 gate bits and the 3 lowest other bits (window)
   unsigned tmask = gmask;
-  int win[4], nw = 0;
-  for (int b = 0; b < n && nw < 4; ++b)
+  int win[3], nw = 0;
+  for (int b = 0; b < n && nw < 3; ++b)
     if (!((gmask >> b) & 1u)) {
       tmask |= 1u << b;
       win[nw++] = b;
@@ -623,11 +632,11 @@ void make_pair_params(int n, int a1, int b1, int a2, int b2, void* host_out) {
   for (int b = 0; b < n; ++b)
     if ((tmask >> b) & 1u) g.tcol_pos[ntb++] = b;
   auto cpos = [&](int b) {
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 7; ++i)
       if (g.tcol_pos[i] == b) return i;
     return -1;
   };
-  for (int i = 0; i < 4; ++i) g.win_cpos[i] = cpos(win[i]);
+  for (int i = 0; i < 3; ++i) g.win_cpos[i] = cpos(win[i]);
   // tile index: the n-8 non-tile column bits (low), then the n-4 non-gate row bits
   int nb = 0;
   for (int b = 0; b < n; ++b)
@@ -654,6 +663,7 @@ void make_pair_params(int n, int a1, int b1, int a2, int b2, void* host_out) {
     for (int i = 0; i < 4; ++i) r |= (long long)((tr >> i) & 1) << gs[i];
     g.rtile[tr] = r * rowbytes;
   }
+  unsigned gcomb[16], rcomb[16];
   for (int v1 = 0; v1 < 4; ++v1)
     for (int v2 = 0; v2 < 4; ++v2) {
       // local index 2*bit(pa) + bit(pb) for each gate
@@ -662,11 +672,43 @@ void make_pair_params(int n, int a1, int b1, int a2, int b2, void* host_out) {
       // the gate bits and the window bits are disjoint and the swizzle is
       // linear over XOR, so a partner's slot is block ^ pswz(gate part)
       g.gsw[v1 * 4 + v2] = (int)(c ^ (((c >> 4) & 7u) << 1));
+      gcomb[v1 * 4 + v2] = c;
       const unsigned r = (((unsigned)(v1 >> 1) & 1u) << rpos(pa1)) | (((unsigned)v1 & 1u) << rpos(pb1)) |
                          (((unsigned)(v2 >> 1) & 1u) << rpos(pa2)) | (((unsigned)v2 & 1u) << rpos(pb2));
-      g.rsm[v1 * 4 + v2] = (int)(r * kPairCols * 8u);
+      rcomb[v1 * 4 + v2] = r;
       g.rglob[v1 * 4 + v2] = g.rtile[r];
     }
+  // slot XOR of odd rows: the mask (bits 1..3, keeping 16-byte pairs) with
+  // the fewest bank conflicts in the column phase, where a half-warp reads
+  // one partner of 8 windows in 2 adjacent rows
+  unsigned wins[8];
+  for (int w = 0; w < 8; ++w) {
+    unsigned c = 0;
+    for (int i = 0; i < 3; ++i) c |= ((unsigned)(w >> i) & 1u) << g.win_cpos[i];
+    wins[w] = c;
+  }
+  auto sw = [](unsigned c) { return c ^ (((c >> 4) & 7u) << 1); };
+  int best = 99;
+  for (unsigned mask = 0; mask < 16; mask += 2) {
+    int worst = 1;
+    for (int k = 0; k < 16; ++k)
+      for (int h = 0; h < 8; ++h) {
+        int cnt[16] = {0};
+        for (int rr = 0; rr < 2; ++rr)
+          for (int w = 0; w < 8; ++w) {
+            const unsigned tr = 2 * h + rr;
+            const unsigned slot = sw(wins[w] | gcomb[k]) ^ ((tr & 1u) ? mask : 0u);
+            const int b = (int)(slot & 15u);
+            if (++cnt[b] > worst) worst = cnt[b];
+          }
+      }
+    if (worst < best) {
+      best = worst;
+      g.rxmask = (int)mask;
+    }
+  }
+  for (int k = 0; k < 16; ++k)
+    g.rsm[k] = (int)((rcomb[k] * kPairCols + ((rcomb[k] & 1u) ? (unsigned)g.rxmask : 0u)) * 8u);
   memcpy(host_out, &g, sizeof(g));
 }
 
@@ -683,8 +725,8 @@ cudaError_t launch_pair_pass(void* T, int n, int S, const void* params, const do
   }
   PairParams pp;
   memcpy(&pp, params, sizeof(pp));
-  const unsigned tiles = 1u << (2 * n - 12);
-  long long cap = ((long long)sm_count() * 2 + S - 1) / S;
+  const unsigned tiles = 1u << (2 * n - 11);
+  long long cap = ((long long)sm_count() * 4 + S - 1) / S;
   if (cap < 1) cap = 1;
   dim3 grid((unsigned)((long long)tiles < cap ? tiles : cap), S);
   pass_pair_kernel<<<grid, kPairThreads, smem, st>>>((float2*)T, pp, L1, R1, s1, L2, R2, s2);
