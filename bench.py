@@ -374,6 +374,55 @@ def run_c128(args, qf, torch, dev, inst, V, starts):
                          "flops_per_launch": flops}}
 
 
+# FP32 pipe operations per tensor entry of a df64 pass (both operators):
+# 8 complex multiply-adds of 48 operations (two TwoProd, two TwoSum and the
+# lo-part gathering per real part) and 2 renormalisations of 6.
+DF64_OPS_PER_ENTRY = 8 * 48 + 2 * 6
+# FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz (maximum SM clock), one
+# operation per lane per cycle (an FMA counts once)
+FP32_PIPE_GOPS = 152 * 128 * 2.07
+
+
+def run_df64(args, qf, torch, dev, inst, V, starts):
+    """12-qubit sweep on double-FP32 tensors (QF_DF64): complex128-class
+    accuracy from FP32 error-free arithmetic, bound by the FP32 pipe."""
+    plan = qf.Plan(inst.n, inst.locs, inst.n_starts, qf.QF_DF64)
+    stream = torch.cuda.current_stream(dev)
+    plan.load(V, starts, stream=stream)
+    plan.sweep(1, reset_iter=0)
+    plan.costs()
+    plan.pass_stats()
+    plan.enable_pass_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    steps = 3
+    e0.record(stream)
+    plan.sweep(steps, reset_iter=0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pass_ms, launches, _, pbytes = plan.pass_stats()
+    costs = plan.costs()
+    plan.close()
+    updates = inst.n_starts * 2 * inst.p * steps
+    entries = pbytes / max(launches, 1) / 32  # 16-byte entries, read + write
+    ops = entries * DF64_OPS_PER_ENTRY
+    avg_s = (pass_ms / 1e3) / max(launches, 1)
+    achieved = ops / avg_s / 1e9
+    peak, _ = measured_peaks()
+    return {"metric": "gate-updates/s at 12 qubits, df64 (double-FP32 complex tensor)",
+            "unit": "gate-updates/s", "value": updates / (ms / 1e3), "ms_per_sweep": ms / steps,
+            "dtype": "df64",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PIPE_GOPS,
+                         "unit": "Gop/s", "frac": achieved / FP32_PIPE_GOPS,
+                         "peak_source": "FP32 pipe from unit counts and clock: 152 SMs x 128 lanes "
+                                        "x 2.07 GHz, one operation per lane per cycle",
+                         "ops_per_entry": DF64_OPS_PER_ENTRY, "avg_launch_ms": avg_s * 1e3,
+                         "hbm_gbs": pbytes / max(launches, 1) / avg_s / 1e9,
+                         "hbm_frac": pbytes / max(launches, 1) / avg_s / 1e9 / peak},
+            "final_costs": [float(c) for c in costs]}
+
+
 def run_lookahead(args, qf, torch, dev, inst, V, starts, one_update_costs):
     """The same sweeps with look-ahead windows: two consecutive updates on
     disjoint pairs share one pass (complex64).  Gate updates per second
@@ -660,9 +709,10 @@ def run_ours(args):
     lookahead = None
     if not args.no_lookahead and args.precision == "c64" and n >= 8 and world == 1:
         lookahead = run_lookahead(args, qf, torch, dev, inst, V, starts, costs)
-    extra_c128 = None
+    extra_c128 = extra_df64 = None
     if not args.no_c128 and args.precision == "c64" and world == 1:
         extra_c128 = run_c128(args, qf, torch, dev, inst, V, starts)
+        extra_df64 = run_df64(args, qf, torch, dev, inst, V, starts)
     batched = None
     if not args.no_batched and world == 1:
         batched = run_batched(args, qf, torch, dev)
@@ -688,7 +738,7 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(all_launches), "clocks": clock_info,
             "ms_per_step_graph": ms_graph,
-            "lookahead": lookahead, "c128": extra_c128, "batched": batched, "configs": configs,
+            "lookahead": lookahead, "c128": extra_c128, "df64": extra_df64, "batched": batched, "configs": configs,
             "final_costs": [float(c) for c in costs],
         }
         print(json.dumps(line))

@@ -66,6 +66,15 @@ typedef struct { int32_t a, b; } qf_loc;     /* gate location: qubits a != b  */
                                 runs in FP64 */
 #define QF_C64_REFINE64  2   /* bulk sweeps in QF_C64, then the tensor is
                                 rebuilt in QF_C128 for the final sweeps    */
+#define QF_DF64          3   /* double-FP32 complex tensor: each real part is
+                                an unevaluated sum hi + lo of two floats
+                                (about 48 significant bits), 16 bytes per
+                                entry laid out (re.hi, im.hi, re.lo, im.lo);
+                                gate application in FP32 error-free
+                                arithmetic (TwoSum, TwoProd), partial traces
+                                and the 4x4 update in FP64                  */
+#define QF_C64_REFINE_DF 4   /* bulk sweeps in QF_C64, then the tensor is
+                                rebuilt in QF_DF64 for the final sweeps    */
 
 /* Termination reasons. */
 #define QF_STOP_CONVERGED   1   /* some start reached dist_tol               */
@@ -92,8 +101,10 @@ typedef struct { int32_t a, b; } qf_loc;     /* gate location: qubits a != b  */
  *   long_diff_count/_r  long plateau: c_{i-L} - c_i < long_diff_r * c_{i-L},
  *                 L = long_diff_count (off when 0).
  *   beta          the update takes the SVD of (1-beta) E + beta u^dagger.
- *   precision     QF_C128, QF_C64 or QF_C64_REFINE64.
- *   switch_tol    QF_C64_REFINE64: leave the c64 phase once the best cost is
+ *   precision     QF_C128, QF_C64, QF_C64_REFINE64, QF_DF64 or
+ *                 QF_C64_REFINE_DF.
+ *   switch_tol    QF_C64_REFINE64 / QF_C64_REFINE_DF: leave the c64 phase
+ *                 once the best cost is
  *                 <= switch_tol, or once ten c64 sweeps have lowered the cost
  *                 by less than 1e-7 (the complex64 noise floor), or after
  *                 max_c64_sweeps.  Reported costs are always FP64 traces.
@@ -364,6 +375,16 @@ int qf_partial_trace(const void* T, int n_qubits, int n_starts, int a, int b,
 int qf_optimize_gates(const qf_c128* E, const qf_c128* u_old, double beta,
                       int count, qf_c128* u_out, double* sigma_out,
                       void* stream);
+
+/* Precision conversion (no counterpart in the paper): dst[i] <- src[i] for
+ * `count` tensor entries, src in src_precision and dst in dst_precision
+ * (QF_C128, QF_C64 or QF_DF64), through FP64: exact from QF_C64 and
+ * QF_DF64 sources; QF_C128 -> QF_DF64 keeps about 48 significant bits
+ * (hi = float(x), lo = float(x - hi)); -> QF_C64 rounds to FP32.  Device
+ * arrays; they must not overlap unless identical with equal precisions.
+ * Enqueue only. */
+int qf_convert_tensor(const void* src, int src_precision, void* dst,
+                      int dst_precision, int64_t count, void* stream);
 
 /* Step a7, periodic re-unitarisation (Sec. III-A2, reset_iter): three FP64
  * Newton-Schulz steps u <- u (3I - u^dagger u) / 2 on each of `count` device

@@ -19,6 +19,8 @@ QF_ENONFINITE = -4
 QF_C128 = 0
 QF_C64 = 1
 QF_C64_REFINE64 = 2
+QF_DF64 = 3
+QF_C64_REFINE_DF = 4
 
 QF_NOALLOC_SCRATCH_BYTES = 64 * 1024
 QF_BATCH_MAX_QUBITS = 6
@@ -103,6 +105,7 @@ SIGNATURES = {
     "qf_apply_pair": (I, [P, I, I, I, I, P, P, I, P]),
     "qf_partial_trace": (I, [P, I, I, I, I, P, I, P]),
     "qf_apply_two_pairs": (I, [P, I, I, I, I, P, P, I, I, P, P, I, P]),
+    "qf_convert_tensor": (I, [P, I, P, I, ct.c_int64, P]),
     "qf_partial_trace_after": (I, [P, I, I, I, I, P, P, I, I, P, I, P]),
     "qf_partial_trace_noalloc": (I, [P, I, I, I, I, P, I, P]),
     "qf_optimize_gates": (I, [P, P, D, I, P, P, P]),

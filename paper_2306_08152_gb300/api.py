@@ -17,14 +17,16 @@ from . import _native as nat
 from ._native import check
 
 __all__ = [
-    "QF_C128", "QF_C64", "QF_C64_REFINE64", "Options", "instantiate",
+    "QF_C128", "QF_C64", "QF_C64_REFINE64", "QF_DF64", "QF_C64_REFINE_DF", "Options", "instantiate",
     "instantiate_ex", "instantiate_batched", "cost_and_env", "cost_grad", "costs", "Plan", "init_tensor", "apply_pair",
-    "partial_trace", "partial_trace_noalloc", "apply_two_pairs", "partial_trace_after", "optimize_gates", "reunitarize_gates", "trace", "circuit_unitary",
+    "partial_trace", "partial_trace_noalloc", "apply_two_pairs", "partial_trace_after", "convert_tensor", "optimize_gates", "reunitarize_gates", "trace", "circuit_unitary",
 ]
 
 QF_C128 = nat.QF_C128
 QF_C64 = nat.QF_C64
 QF_C64_REFINE64 = nat.QF_C64_REFINE64
+QF_DF64 = nat.QF_DF64
+QF_C64_REFINE_DF = nat.QF_C64_REFINE_DF
 
 
 def _lib():
@@ -316,16 +318,55 @@ def _dev(t, name):
     return t.contiguous()
 
 
+def _is_df(T):
+    return T.dtype == torch.float32 and T.dim() >= 3 and T.shape[-1] == 4
+
+
 def _tensor_prec(T):
+    """complex128 -> QF_C128, complex64 -> QF_C64; a float32 tensor whose last
+    dimension is 4 holds double-FP32 entries (re.hi, im.hi, re.lo, im.lo) ->
+    QF_DF64."""
     if T.dtype == torch.complex128:
         return QF_C128
     if T.dtype == torch.complex64:
         return QF_C64
-    raise TypeError("circuit tensor must be complex64 or complex128")
+    if _is_df(T):
+        return QF_DF64
+    raise TypeError("circuit tensor must be complex64, complex128 or float32 (..., 4) df64")
+
+
+def _tensor_sn(T):
+    """(starts, N) of a circuit tensor of any precision."""
+    if _is_df(T):
+        return T.shape[0], T.shape[-2]
+    return T.shape[0], T.shape[-1]
+
+
+_PREC_SHAPE = {QF_C128: (torch.complex128, ()), QF_C64: (torch.complex64, ()),
+               QF_DF64: (torch.float32, (4,))}
+
+
+def _empty_tensor(S, N, precision, device):
+    dt, tail = _PREC_SHAPE[precision]
+    return torch.empty((S, N, N) + tail, dtype=dt, device=device)
+
+
+def convert_tensor(T, precision, stream=None):
+    """A copy of circuit tensor(s) T in `precision` (QF_C128, QF_C64 or
+    QF_DF64), converted on the device."""
+    T = _dev(T, "T")
+    src = _tensor_prec(T)
+    S, N = _tensor_sn(T)
+    out = _empty_tensor(S, N, precision, T.device)
+    check(_lib().qf_convert_tensor(_ptr(T), src, _ptr(out), int(precision), S * N * N,
+                                   _stream_handle(stream)))
+    return out
 
 
 def init_tensor(target, locations, gates, dtype=torch.complex128, stream=None):
-    """InitCircuitTensor for S starts: gates (S, p, 4, 4) -> T (S, N, N)."""
+    """InitCircuitTensor for S starts: gates (S, p, 4, 4) -> T (S, N, N).
+    dtype: torch.complex128, torch.complex64, or "df64" for a double-FP32
+    tensor (float32, shape (S, N, N, 4))."""
     target = _dev(_c128(target, "target"), "target")
     g = _dev(_c128(gates, "gates"), "gates")
     if g.dim() == 3:
@@ -333,7 +374,8 @@ def init_tensor(target, locations, gates, dtype=torch.complex128, stream=None):
     locs = _locs(locations)
     n = _nqubits(target)
     N = 1 << n
-    T = torch.empty((g.shape[0], N, N), dtype=dtype, device=target.device)
+    prec = QF_DF64 if dtype == "df64" else (QF_C128 if dtype == torch.complex128 else QF_C64)
+    T = _empty_tensor(g.shape[0], N, prec, target.device)
     check(_lib().qf_init_tensor(_ptr(target), n, g.shape[1], _ptr(locs), g.shape[0], _ptr(g),
                                 _ptr(T), _tensor_prec(T), _stream_handle(stream)))
     return T
@@ -342,7 +384,7 @@ def init_tensor(target, locations, gates, dtype=torch.complex128, stream=None):
 def apply_pair(T, a, b, L=None, R=None, stream=None):
     """In place: T_s <- (L_s on (a,b)) T_s (R_s on (a,b)); L, R (S, 4, 4)."""
     T = _dev(T, "T")
-    S, N = T.shape[0], T.shape[-1]
+    S, N = _tensor_sn(T)
     n = int(N).bit_length() - 1
     Lp = _ptr(_dev(_c128(L, "L"), "L")) if L is not None else None
     Rp = _ptr(_dev(_c128(R, "R"), "R")) if R is not None else None
@@ -353,7 +395,7 @@ def apply_pair(T, a, b, L=None, R=None, stream=None):
 
 def partial_trace(T, a, b, stream=None):
     T = _dev(T, "T")
-    S, N = T.shape[0], T.shape[-1]
+    S, N = _tensor_sn(T)
     n = int(N).bit_length() - 1
     P = torch.empty((S, 4, 4), dtype=torch.complex128, device=T.device)
     check(_lib().qf_partial_trace(_ptr(T), n, S, int(a), int(b), _ptr(P), _tensor_prec(T),
@@ -366,7 +408,7 @@ def apply_two_pairs(T, a1, b1, L1, R1, a2, b2, L2, R2, stream=None):
     (R1_s on (a1,b1)) (R2_s on (a2,b2)); four distinct qubits; operators
     (S, 4, 4)."""
     T = _dev(T, "T")
-    S, N = T.shape[0], T.shape[-1]
+    S, N = _tensor_sn(T)
     n = int(N).bit_length() - 1
     ops = [_dev(_c128(X, nm), nm) for X, nm in ((L1, "L1"), (R1, "R1"), (L2, "L2"), (R2, "R2"))]
     check(_lib().qf_apply_two_pairs(_ptr(T), n, S, int(a1), int(b1), _ptr(ops[0]), _ptr(ops[1]),
@@ -379,7 +421,7 @@ def partial_trace_after(T, a1, b1, L1, R1, a, b, stream=None):
     """Partial trace over every qubit but (a, b) of (L1 on (a1,b1)) T
     (R1 on (a1,b1)), computed without applying the pending update."""
     T = _dev(T, "T")
-    S, N = T.shape[0], T.shape[-1]
+    S, N = _tensor_sn(T)
     n = int(N).bit_length() - 1
     L1 = _dev(_c128(L1, "L1"), "L1")
     R1 = _dev(_c128(R1, "R1"), "R1")
@@ -395,7 +437,7 @@ def partial_trace_noalloc(T, a, b, P=None, stream=None):
     library allocates nothing; the caller provides the output P, S x 4 x 4
     complex128 on the device, or it is created here)."""
     T = _dev(T, "T")
-    S, N = T.shape[0], T.shape[-1]
+    S, N = _tensor_sn(T)
     n = int(N).bit_length() - 1
     if P is None:
         P = torch.empty((S, 4, 4), dtype=torch.complex128, device=T.device)
@@ -426,7 +468,7 @@ def reunitarize_gates(gates, stream=None):
 
 def trace(T, stream=None):
     T = _dev(T, "T")
-    S, N = T.shape[0], T.shape[-1]
+    S, N = _tensor_sn(T)
     n = int(N).bit_length() - 1
     tr = torch.empty((S,), dtype=torch.complex128, device=T.device)
     check(_lib().qf_trace(_ptr(T), n, S, _ptr(tr), _tensor_prec(T), _stream_handle(stream)))

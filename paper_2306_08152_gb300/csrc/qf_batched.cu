@@ -457,6 +457,8 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
       !out_costs)
     return qf_internal_set_error(QF_EINVAL, "NULL argument", "");
   if (o.max_sweeps < 1) return qf_internal_set_error(QF_EINVAL, "max_sweeps must be >= 1", "");
+  if (o.precision == QF_DF64 || o.precision == QF_C64_REFINE_DF)
+    return qf_internal_set_error(QF_EINVAL, "the batched kernel takes QF_C128, QF_C64 or QF_C64_REFINE64", "");
   if (o.precision != QF_C128 && o.precision != QF_C64 && o.precision != QF_C64_REFINE64)
     return qf_internal_set_error(QF_EINVAL, "unknown precision", "");
   if (!(o.beta >= 0.0 && o.beta <= 1.0))

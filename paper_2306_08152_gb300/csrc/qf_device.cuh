@@ -11,17 +11,45 @@ namespace dev {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Double-float ("df64") reals: a value is the unevaluated sum hi + lo of two
+// floats, |lo| <= ulp(hi)/2 after normalisation, about 48 significant bits
+// (Dekker 1971; the error-free transformations TwoSum (Knuth) and TwoProd
+// via FMA).  A complex df64 tensor entry is 16 bytes: (re.hi, im.hi) then
+// (re.lo, im.lo), so the hi and lo parts are each a float2.
+struct DF {};
+struct __align__(16) dfc {
+  float2 h, l;
+};
+
 template <typename R> struct Cplx;
 template <> struct Cplx<float> { typedef float2 T; };
 template <> struct Cplx<double> { typedef double2 T; };
+template <> struct Cplx<DF> { typedef dfc T; };
+
+// Accumulation type of sums over tensor entries (environment, trace).
+template <typename R> struct Acc { typedef R T; };
+template <> struct Acc<DF> { typedef double T; };
 
 __device__ __forceinline__ float2 cmake(double2 v, float) {
   return make_float2((float)v.x, (float)v.y);
 }
 __device__ __forceinline__ double2 cmake(double2 v, double) { return v; }
+__device__ __forceinline__ dfc cmake(double2 v, DF) {
+  dfc r;
+  r.h = make_float2((float)v.x, (float)v.y);
+  r.l = make_float2((float)(v.x - (double)r.h.x), (float)(v.y - (double)r.h.y));
+  return r;
+}
 
 __device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
 __device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(dfc v) {
+  return make_double2((double)v.h.x + (double)v.l.x, (double)v.h.y + (double)v.l.y);
+}
+// an entry in its accumulation type
+__device__ __forceinline__ float2 to_acc(float2 v) { return v; }
+__device__ __forceinline__ double2 to_acc(double2 v) { return v; }
+__device__ __forceinline__ double2 to_acc(dfc v) { return to_d2(v); }
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
 // c + a*b
@@ -57,6 +85,56 @@ __device__ __forceinline__ double2 cfma_cj(double2 a, double2 b, double2 c) {
 template <typename C2> __device__ __forceinline__ C2 czero();
 template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ dfc czero<dfc>() {
+  dfc r;
+  r.h = make_float2(0.f, 0.f);
+  r.l = make_float2(0.f, 0.f);
+  return r;
+}
+
+// df64: s + err = a + b exactly (TwoSum, 6 operations, any magnitudes)
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+// c + x1*y1 + x2*y2 for df64 reals: the hi*hi products exactly (TwoProd),
+// their sum with TwoSum; the rounding errors, the hi*lo cross terms and c's
+// lo part gather in lo (lo*lo terms, about 2^-48 relative, are dropped).
+// The result is not renormalised (cfinish does that once per sum).
+__device__ __forceinline__ void df_dot2_acc(float& ch, float& cl, float x1h, float x1l, float y1h,
+                                            float y1l, float x2h, float x2l, float y2h, float y2l) {
+  const float p1 = __fmul_rn(x1h, y1h);
+  const float e1 = __fmaf_rn(x1h, y1h, -p1);
+  const float p2 = __fmul_rn(x2h, y2h);
+  const float e2 = __fmaf_rn(x2h, y2h, -p2);
+  float t1, t2;
+  float s = two_sum(ch, p1, t1);
+  s = two_sum(s, p2, t2);
+  float lo = __fadd_rn(cl, __fadd_rn(__fadd_rn(t1, t2), __fadd_rn(e1, e2)));
+  lo = __fmaf_rn(x1h, y1l, lo);
+  lo = __fmaf_rn(x1l, y1h, lo);
+  lo = __fmaf_rn(x2h, y2l, lo);
+  lo = __fmaf_rn(x2l, y2h, lo);
+  ch = s;
+  cl = lo;
+}
+// c + a*b, complex df64
+__device__ __forceinline__ dfc cfma(dfc a, dfc b, dfc c) {
+  df_dot2_acc(c.h.x, c.l.x, a.h.x, a.l.x, b.h.x, b.l.x, -a.h.y, -a.l.y, b.h.y, b.l.y);
+  df_dot2_acc(c.h.y, c.l.y, a.h.x, a.l.x, b.h.y, b.l.y, a.h.y, a.l.y, b.h.x, b.l.x);
+  return c;
+}
+// Renormalise a sum built by cfma (identity for float2 / double2).
+__device__ __forceinline__ float2 cfinish(float2 v) { return v; }
+__device__ __forceinline__ double2 cfinish(double2 v) { return v; }
+__device__ __forceinline__ dfc cfinish(dfc v) {
+  const float hx = __fadd_rn(v.h.x, v.l.x), hy = __fadd_rn(v.h.y, v.l.y);
+  v.l = make_float2(__fsub_rn(v.l.x, __fsub_rn(hx, v.h.x)), __fsub_rn(v.l.y, __fsub_rn(hy, v.h.y)));
+  v.h = make_float2(hx, hy);
+  return v;
+}
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -72,6 +150,12 @@ __device__ __forceinline__ float2 shfl(float2 v, int src) {
 }
 __device__ __forceinline__ double2 shfl(double2 v, int src) {
   return make_double2(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src));
+}
+__device__ __forceinline__ dfc shfl(dfc v, int src) {
+  dfc r;
+  r.h = shfl(v.h, src);
+  r.l = shfl(v.l, src);
+  return r;
 }
 
 // Insert a zero bit at position p into x.

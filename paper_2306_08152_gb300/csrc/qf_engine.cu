@@ -71,10 +71,14 @@ int check_sizes(int n, int p) {
 }
 
 int check_prec(int prec) {
-  if (prec != QF_C128 && prec != QF_C64)
-    return set_error(QF_EINVAL, "precision=%d must be QF_C128 or QF_C64 here", prec);
+  if (prec != QF_C128 && prec != QF_C64 && prec != QF_DF64)
+    return set_error(QF_EINVAL, "precision=%d must be QF_C128, QF_C64 or QF_DF64 here", prec);
   return QF_OK;
 }
+
+// Tensor precision -> the kernels' precision code (0 complex128, 1 complex64,
+// 2 double-FP32).
+int kprec(int prec) { return prec == QF_C128 ? 0 : prec == QF_DF64 ? 2 : 1; }
 
 // Copy locations (host or device) to a host vector and validate them.
 int fetch_locations(const qf_loc* locs, int n, int p, std::vector<qf_loc>* out) {
@@ -146,7 +150,7 @@ int store_output(qf_c128* dst, const double2* dev, size_t count, cudaStream_t st
   return QF_OK;
 }
 
-size_t elem_bytes(int prec) { return prec == QF_C128 ? 16 : 8; }
+size_t elem_bytes(int prec) { return prec == QF_C64 ? 8 : 16; }
 
 }  // namespace
 
@@ -231,7 +235,7 @@ int plan_pass(qf_plan* P, const Slice& sl, int a, int b, const double2* L, long 
   }
   void* T = static_cast<char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
   QF_CUDA(qf::launch_pass(T, P->n, sl.Sg, a, b, L ? L + sl.s0 * Ls : nullptr, Ls,
-                          R ? R + sl.s0 * Rs : nullptr, Rs, P->prec == QF_C128 ? 0 : 1, sl.st));
+                          R ? R + sl.s0 * Rs : nullptr, Rs, kprec(P->prec), sl.st));
   if (P->timing) {
     QF_CUDA(cudaEventRecord(e1, sl.st));
     P->pass_bytes += 2.0 * (double)sl.Sg * (double)P->NN * (double)elem_bytes(P->prec);
@@ -243,7 +247,7 @@ int plan_pass(qf_plan* P, const Slice& sl, int a, int b, const double2* L, long 
 
 // InitCircuitTensor (Alg. 1) for every start.
 int plan_build(qf_plan* P) {
-  const int pr = P->prec == QF_C128 ? 0 : 1;
+  const int pr = kprec(P->prec);
   QF_CUDA(qf::launch_conj_transpose(P->V.as<double2>(), P->T.p, P->n, P->S, pr, P->stream));
   P->all_launches++;
   for (int k = 0; k < P->p; ++k) {
@@ -255,7 +259,7 @@ int plan_build(qf_plan* P) {
 
 int plan_update(qf_plan* P, const Slice& sl, int k, int mode, double beta, double2* env_out,
                 long long env_stride) {
-  const int pr = P->prec == QF_C128 ? 0 : 1;
+  const int pr = kprec(P->prec);
   const int B = qf::env_ctas(P->n);
   const void* T = static_cast<const char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
   QF_CUDA(qf::launch_update(
@@ -272,7 +276,7 @@ int plan_update(qf_plan* P, const Slice& sl, int k, int mode, double beta, doubl
 // Look-ahead update of gate k2, whose environment sees the pending update of
 // gate k1 (operators in LR) through the light cone; its own operators go to LR2.
 int plan_update_look(qf_plan* P, const Slice& sl, int k1, int k2, int mode, double beta) {
-  const int pr = P->prec == QF_C128 ? 0 : 1;
+  const int pr = kprec(P->prec);
   const int B = qf::env_ctas(P->n);
   const void* T = static_cast<const char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
   const double2* LR = P->LR.as<double2>() + (size_t)sl.s0 * 32;
@@ -528,7 +532,7 @@ int plan_sweep_once(qf_plan* P, double beta) {
 }
 
 int plan_costs_impl(qf_plan* P, double* costs, qf_c128* traces) {
-  const int pr = P->prec == QF_C128 ? 0 : 1;
+  const int pr = kprec(P->prec);
   QF_CUDA(qf::launch_trace(P->T.p, P->n, P->S, P->tr.as<double2>(), pr, P->stream));
   P->all_launches++;
   std::vector<double2> h(P->S);
@@ -778,7 +782,8 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
   QF_TRY(check_sizes(n_qubits, n_gates));
   if (n_starts < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", n_starts);
   if (o.max_sweeps < 1) return set_error(QF_EINVAL, "max_sweeps=%d must be >= 1", o.max_sweeps);
-  if (o.precision != QF_C128 && o.precision != QF_C64 && o.precision != QF_C64_REFINE64)
+  if (o.precision != QF_C128 && o.precision != QF_C64 && o.precision != QF_C64_REFINE64 &&
+      o.precision != QF_DF64 && o.precision != QF_C64_REFINE_DF)
     return set_error(QF_EINVAL, "precision=%d unknown", o.precision);
   if (!(o.beta >= 0.0 && o.beta <= 1.0))
     return set_error(QF_EINVAL, "beta=%g outside [0, 1]", o.beta);
@@ -787,12 +792,17 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
   const int S = n_starts, p = n_gates;
 
   PlanGuard g;
-  const int tensor_prec = o.precision == QF_C128 ? QF_C128 : QF_C64;
+  const bool refine = o.precision == QF_C64_REFINE64 || o.precision == QF_C64_REFINE_DF;
+  // the precision of the final (or only) phase
+  const int fine_prec = o.precision == QF_C64_REFINE_DF || o.precision == QF_DF64 ? QF_DF64
+                        : o.precision == QF_C64                                   ? QF_C64
+                                                                                  : QF_C128;
+  const int tensor_prec = refine ? QF_C64 : fine_prec;
   QF_TRY(plan_create_impl(n_qubits, p, locations, S, tensor_prec, &g.p));
   qf_plan* P = g.p;
-  if (o.precision == QF_C64_REFINE64) {
-    // reserve the complex128 tensor up front so the switch cannot fail late
-    QF_TRY(plan_ensure_T(P, QF_C128));
+  if (refine) {
+    // reserve the 16-byte tensor up front so the switch cannot fail late
+    QF_TRY(plan_ensure_T(P, fine_prec));
     P->prec = QF_C64;
   }
   QF_TRY(plan_load_impl(P, target, initial_gates, st));
@@ -802,7 +812,7 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
   QF_TRY(plan_costs_impl(P, c.data(), nullptr));
   for (int s = 0; s < S; ++s) hist[s].push_back(c[s]);
   std::vector<char> plateaued(S, 0);
-  bool c64_phase = (o.precision == QF_C64_REFINE64);
+  bool c64_phase = refine;
   int reason = QF_STOP_MAX_SWEEPS, it = 0, c64_sweeps = 0;
   for (it = 1; it <= o.max_sweeps; ++it) {
     QF_TRY(plan_sweep_once(P, o.beta));
@@ -823,8 +833,8 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
       }
       for (int s = 0; s < S; ++s) hist[s].push_back(c[s]);
       if (best <= o.switch_tol || stalled || c64_sweeps >= o.max_c64_sweeps) {
-        // rebuild every tensor in complex128 from V and the FP64 gates
-        P->prec = QF_C128;
+        // rebuild every tensor in the fine precision from V and the FP64 gates
+        P->prec = fine_prec;
         QF_TRY(plan_build(P));
         QF_TRY(plan_costs_impl(P, c.data(), nullptr));
         for (int s = 0; s < S; ++s) hist[s].back() = c[s];
@@ -854,8 +864,8 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
     }
   }
   if (it > o.max_sweeps) it = o.max_sweeps;
-  if (c64_phase) {  // report FP64 costs: rebuild the tensors in complex128 once
-    P->prec = QF_C128;
+  if (c64_phase) {  // report FP64 traces of fine tensors: rebuild once
+    P->prec = fine_prec;
     QF_TRY(plan_build(P));
     QF_TRY(plan_costs_impl(P, c.data(), nullptr));
   }
@@ -971,7 +981,7 @@ int qf_init_tensor(const qf_c128* target, int n_qubits, int n_gates, const qf_lo
   std::vector<qf_loc> locs;
   QF_TRY(fetch_locations(locations, n_qubits, n_gates, &locs));
   cudaStream_t st = as_stream(stream);
-  const int pr = precision == QF_C128 ? 0 : 1;
+  const int pr = kprec(precision);
   QF_CUDA(qf::launch_conj_transpose(reinterpret_cast<const double2*>(target), T, n_qubits,
                                     n_starts, pr, st));
   for (int k = 0; k < n_gates; ++k)
@@ -990,7 +1000,7 @@ int qf_apply_pair(void* T, int n_qubits, int n_starts, int a, int b, const qf_c1
   if (a < 0 || a >= n_qubits || b < 0 || b >= n_qubits || a == b)
     return set_error(QF_EINVAL, "location (%d, %d) invalid for %d qubits", a, b, n_qubits);
   QF_CUDA(qf::launch_pass(T, n_qubits, n_starts, a, b, reinterpret_cast<const double2*>(L), 16,
-                          reinterpret_cast<const double2*>(R), 16, precision == QF_C128 ? 0 : 1,
+                          reinterpret_cast<const double2*>(R), 16, kprec(precision),
                           as_stream(stream)));
   return QF_OK;
 }
@@ -1015,7 +1025,7 @@ int qf_partial_trace(const void* T, int n_qubits, int n_starts, int a, int b, qf
     e = qf::launch_update(T, n_qubits, n_starts, a, b, nullptr, 0, qf::kTraceOnly, 0.0, nullptr,
                           reinterpret_cast<double2*>(P), 16, nullptr, nullptr,
                           reinterpret_cast<double*>(scratch), counters,
-                          precision == QF_C128 ? 0 : 1, st);
+                          kprec(precision), st);
   cudaError_t e2 = cudaFreeAsync(scratch, st);
   if (e != cudaSuccess) return set_error(QF_ECUDA, "partial trace launch failed: %s", cudaGetErrorString(e));
   if (e2 != cudaSuccess) return set_error(QF_ECUDA, "cudaFreeAsync failed: %s", cudaGetErrorString(e2));
@@ -1037,7 +1047,7 @@ int qf_apply_two_pairs(void* T, int n_qubits, int n_starts, int a1, int b1, cons
       if (q[i] == q[j]) return set_error(QF_EINVAL, "the two pairs must be four distinct qubits");
   }
   cudaStream_t st = as_stream(stream);
-  const int pr = precision == QF_C128 ? 0 : 1;
+  const int pr = kprec(precision);
   auto d = [](const qf_c128* x) { return reinterpret_cast<const double2*>(x); };
   if (!qf::pair_pass_supported(n_qubits, a1, b1, a2, b2, pr)) {
     // the two single-pair passes in order
@@ -1079,7 +1089,7 @@ int qf_partial_trace_after(const void* T, int n_qubits, int n_starts, int a1, in
         T, n_qubits, n_starts, a1, b1, reinterpret_cast<const double2*>(L1),
         reinterpret_cast<const double2*>(R1), 16, a, b, nullptr, 0, qf::kTraceOnly, 0.0, nullptr,
         reinterpret_cast<double2*>(P), 16, nullptr, nullptr, reinterpret_cast<double*>(scratch),
-        counters, precision == QF_C128 ? 0 : 1, st);
+        counters, kprec(precision), st);
   const cudaError_t e2 = cudaFreeAsync(scratch, st);
   if (e != cudaSuccess) return set_error(QF_ECUDA, "partial trace launch failed: %s", cudaGetErrorString(e));
   if (e2 != cudaSuccess) return set_error(QF_ECUDA, "cudaFreeAsync failed: %s", cudaGetErrorString(e2));
@@ -1107,6 +1117,24 @@ int qf_reunitarize_gates(qf_c128* gates, int count, void* stream) {
   return QF_OK;
 }
 
+int qf_convert_tensor(const void* src, int src_precision, void* dst, int dst_precision,
+                      int64_t count, void* stream) {
+  QF_TRY(check_prec(src_precision));
+  QF_TRY(check_prec(dst_precision));
+  if (count < 0) return set_error(QF_EINVAL, "count=%lld < 0", (long long)count);
+  if (count == 0) return QF_OK;
+  if (!src || !dst) return set_error(QF_EINVAL, "NULL device pointer");
+  const char* s0 = static_cast<const char*>(src);
+  const char* d0 = static_cast<const char*>(dst);
+  const size_t sb = (size_t)count * elem_bytes(src_precision);
+  const size_t db = (size_t)count * elem_bytes(dst_precision);
+  if (s0 < d0 + db && d0 < s0 + sb && !(s0 == d0 && src_precision == dst_precision))
+    return set_error(QF_EINVAL, "src and dst overlap");
+  QF_CUDA(qf::launch_convert(src, kprec(src_precision), dst, kprec(dst_precision), (size_t)count,
+                             as_stream(stream)));
+  return QF_OK;
+}
+
 int qf_trace(const void* T, int n_qubits, int n_starts, qf_c128* tr_out, int precision,
              void* stream) {
   QF_TRY(check_sizes(n_qubits, 1));
@@ -1114,7 +1142,7 @@ int qf_trace(const void* T, int n_qubits, int n_starts, qf_c128* tr_out, int pre
   if (n_starts < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", n_starts);
   if (!T || !tr_out) return set_error(QF_EINVAL, "NULL device pointer");
   QF_CUDA(qf::launch_trace(T, n_qubits, n_starts, reinterpret_cast<double2*>(tr_out),
-                           precision == QF_C128 ? 0 : 1, as_stream(stream)));
+                           kprec(precision), as_stream(stream)));
   return QF_OK;
 }
 

@@ -83,6 +83,11 @@ cudaError_t launch_grad_from_env(double2* env, const double2* tr, int n, int S, 
 // Two FP64 Newton-Schulz steps on each of `count` gates, in place.
 cudaError_t launch_reunitarize(double2* gates, int count, cudaStream_t st);
 
+// dst[i] <- src[i] for `count` entries, converting between kernel precision
+// codes sp and dp (0 complex128, 1 complex64, 2 df64) through FP64.
+cudaError_t launch_convert(const void* src, int sp, void* dst, int dp, size_t count,
+                           cudaStream_t st);
+
 // tr_s = Tr T_s (FP64 accumulation).
 cudaError_t launch_trace(const void* T, int n, int S, double2* tr, int prec,
                          cudaStream_t st);

@@ -54,6 +54,17 @@ __global__ void __launch_bounds__(256) conj_transpose_kernel(
 
 constexpr int kPassThreads = 256;
 
+// Resident CTAs per SM the pass kernels are built for: complex64 passes are
+// memory-bound and want many bytes in flight, complex128 ones are bound by
+// the FP64 pipe at any occupancy, df64 ones need warps to hide the latency
+// of their dependent TwoSum chains.  WIDE: the window mapping's larger
+// per-thread state.
+template <typename R, bool WIDE> struct PassOcc { static constexpr int v = 1; };
+template <> struct PassOcc<float, false> { static constexpr int v = 3; };
+template <> struct PassOcc<float, true> { static constexpr int v = 2; };
+template <> struct PassOcc<DF, false> { static constexpr int v = 1; };
+template <> struct PassOcc<DF, true> { static constexpr int v = 1; };
+
 template <typename R, bool HL, bool HR>
 __device__ __forceinline__ void load_ops(typename Cplx<R>::T* sL, typename Cplx<R>::T* sR,
                                          const double2* __restrict__ L, long long Ls,
@@ -74,7 +85,7 @@ __device__ __forceinline__ void load_ops(typename Cplx<R>::T* sL, typename Cplx<
 // bit is bit 2 or above.
 
 template <typename R, bool HL, bool HR>
-__global__ void __launch_bounds__(kPassThreads, (sizeof(R) == 4 ? 3 : 1))
+__global__ void __launch_bounds__(kPassThreads, (PassOcc<R, false>::v))
 pass_block_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, int pa, int pb,
                   const double2* __restrict__ L, long long Ls, const double2* __restrict__ Rm,
                   long long Rs) {
@@ -113,7 +124,7 @@ pass_block_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, 
 #pragma unroll
           for (int y = 0; y < 4; ++y) t[y] = cfma(bm[x][k], sR[k * 4 + y], t[y]);
 #pragma unroll
-        for (int y = 0; y < 4; ++y) bm[x][y] = t[y];
+        for (int y = 0; y < 4; ++y) bm[x][y] = cfinish(t[y]);
       }
     }
     if (HL) {  // B <- L B, one column at a time
@@ -125,7 +136,7 @@ pass_block_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, 
           C acc = czero<C>();
 #pragma unroll
           for (int k = 0; k < 4; ++k) acc = cfma(sL[x * 4 + k], bm[k][y], acc);
-          t[x] = acc;
+          t[x] = cfinish(acc);
         }
 #pragma unroll
         for (int x = 0; x < 4; ++x) bm[x][y] = t[x];
@@ -136,6 +147,97 @@ pass_block_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, 
       const unsigned rb = (r0 | off[x]) * N;
 #pragma unroll
       for (int y = 0; y < 4; ++y) Ts[rb + (c0 | off[y])] = bm[x][y];
+    }
+  }
+}
+
+// Half-block mapping (df64): two adjacent lanes share one 4x4 block, the
+// even lane holding rows 0-1 and the odd lane rows 2-3.  Each applies R to
+// its two rows; one exchange of four entries through shuffles leaves the
+// even lane with columns 0-1 and the odd lane with columns 2-3 of all four
+// rows, and each applies L to its two columns.  Half the per-thread state of
+// the block mapping, so twice the resident warps for the long dependent
+// chains of double-FP32 arithmetic.  Blocks are ordered as in the block
+// mapping (consecutive lane pairs take consecutive column rest indices).
+
+template <typename R, bool HL, bool HR>
+__global__ void __launch_bounds__(kPassThreads, 2)
+pass_half_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, int pa, int pb,
+                 const double2* __restrict__ L, long long Ls, const double2* __restrict__ Rm,
+                 long long Rs) {
+  typedef typename Cplx<R>::T C;
+  __shared__ C sL[16], sR[16];
+  const int s = blockIdx.y;
+  load_ops<R, HL, HR>(sL, sR, L, Ls, Rm, Rs, s);
+
+  const unsigned N = 1u << n;
+  const int lnc = n - 2;
+  const unsigned cmask = (1u << lnc) - 1u;
+  const unsigned units = 2u << (2 * lnc);  // two lanes per block: a multiple of 32 (n >= 4)
+  C* __restrict__ Ts = T + (size_t)s * N * N;
+  const unsigned o1 = 1u << pb, o2 = 1u << pa;
+  const unsigned off[4] = {0u, o1, o2, o1 | o2};
+  const int h = threadIdx.x & 1;  // the row pair {2h, 2h+1}
+
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < units;
+       t += gridDim.x * blockDim.x) {
+    const unsigned blk = t >> 1;
+    const unsigned r0 = dep2(blk >> lnc, plo, phi);
+    const unsigned c0 = dep2(blk & cmask, plo, phi);
+    C e[2][4];  // rows 2h, 2h+1
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const unsigned rb = (r0 | off[2 * h + i]) * N;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) e[i][y] = Ts[rb + (c0 | off[y])];
+    }
+    if (HR) {  // rows <- rows R
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        C t4[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) t4[y] = czero<C>();
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) t4[y] = cfma(e[i][k], sR[k * 4 + y], t4[y]);
+#pragma unroll
+        for (int y = 0; y < 4; ++y) e[i][y] = cfinish(t4[y]);
+      }
+    }
+    if (HL) {
+      // exchange: the even lane gives columns 2-3 of its rows and takes
+      // columns 0-1 of rows 2-3; the odd lane the mirror image
+      C col[4][2];  // all four rows of columns {2h', 2h'+1}, h' = h
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const C give = e[i][2 * (1 - h) + j];
+          const C got = shfl(give, (int)(threadIdx.x & 31) ^ 1);
+          col[2 * h + i][j] = e[i][2 * h + j];
+          col[2 * (1 - h) + i][j] = got;
+        }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        C t4[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          C acc = czero<C>();
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc = cfma(sL[x * 4 + k], col[k][j], acc);
+          t4[x] = cfinish(acc);
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) Ts[(r0 | off[x]) * N + (c0 | off[2 * h + j])] = t4[x];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const unsigned rb = (r0 | off[2 * h + i]) * N;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) Ts[rb + (c0 | off[y])] = e[i][y];
+      }
     }
   }
 }
@@ -151,7 +253,7 @@ pass_block_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, 
 //   MODE 2: both gate column bits below 5.
 
 template <typename R, int MODE, bool HL, bool HR>
-__global__ void __launch_bounds__(kPassThreads, (sizeof(R) == 4 ? 3 : 1))
+__global__ void __launch_bounds__(kPassThreads, (PassOcc<R, false>::v))
 pass_lane_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, int pa, int pb,
                  const double2* __restrict__ L, long long Ls, const double2* __restrict__ Rm,
                  long long Rs) {
@@ -193,7 +295,7 @@ pass_lane_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, i
             const C v = shfl(e[x], (int)(cb | off[k]));
             acc = cfma(v, sR[k * 4 + yown], acc);
           }
-          t4[x] = acc;
+          t4[x] = cfinish(acc);
         }
 #pragma unroll
         for (int x = 0; x < 4; ++x) e[x] = t4[x];
@@ -205,7 +307,7 @@ pass_lane_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, i
           C acc = czero<C>();
 #pragma unroll
           for (int k = 0; k < 4; ++k) acc = cfma(sL[x * 4 + k], e[k], acc);
-          t4[x] = acc;
+          t4[x] = cfinish(acc);
         }
 #pragma unroll
         for (int x = 0; x < 4; ++x) e[x] = t4[x];
@@ -245,7 +347,7 @@ pass_lane_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, i
             C acc = czero<C>();
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc = cfma(bk[k], sR[k * 4 + y], acc);
-            e[x][v] = acc;
+            e[x][v] = cfinish(acc);
           }
         }
       }
@@ -258,7 +360,7 @@ pass_lane_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, i
             C acc = czero<C>();
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc = cfma(sL[x * 4 + k], e[k][v], acc);
-            t4[x] = acc;
+            t4[x] = cfinish(acc);
           }
 #pragma unroll
           for (int x = 0; x < 4; ++x) e[x][v] = t4[x];
@@ -306,8 +408,21 @@ __device__ __forceinline__ void vst32(double2* p, const double2* v) {
                : "memory");
 }
 
+__device__ __forceinline__ void vld32(const dfc* p, dfc* v) {
+  asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0].h.x), "=f"(v[0].h.y), "=f"(v[0].l.x), "=f"(v[0].l.y), "=f"(v[1].h.x),
+                 "=f"(v[1].h.y), "=f"(v[1].l.x), "=f"(v[1].l.y)
+               : "l"(p));
+}
+__device__ __forceinline__ void vst32(dfc* p, const dfc* v) {
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0].h.x),
+               "f"(v[0].h.y), "f"(v[0].l.x), "f"(v[0].l.y), "f"(v[1].h.x), "f"(v[1].h.y),
+               "f"(v[1].l.x), "f"(v[1].l.y)
+               : "memory");
+}
+
 template <typename R, int PA, int PB>
-__global__ void __launch_bounds__(kPassThreads, (sizeof(R) == 4 ? 2 : 1))
+__global__ void __launch_bounds__(kPassThreads, (PassOcc<R, true>::v))
 pass_window_kernel(typename Cplx<R>::T* __restrict__ T, int n, const double2* __restrict__ L,
                    long long Ls, const double2* __restrict__ Rm, long long Rs) {
   typedef typename Cplx<R>::T C;
@@ -349,7 +464,7 @@ pass_window_kernel(typename Cplx<R>::T* __restrict__ T, int n, const double2* __
           C acc = czero<C>();
 #pragma unroll
           for (int k = 0; k < 4; ++k) acc = cfma(win[x][QF_POS(k)], sR[k * 4 + y], acc);
-          t4[y] = acc;
+          t4[y] = cfinish(acc);
         }
 #pragma unroll
         for (int y = 0; y < 4; ++y) win[x][QF_POS(y)] = t4[y];
@@ -362,7 +477,7 @@ pass_window_kernel(typename Cplx<R>::T* __restrict__ T, int n, const double2* __
           C acc = czero<C>();
 #pragma unroll
           for (int k = 0; k < 4; ++k) acc = cfma(sL[x * 4 + k], win[k][QF_POS(y)], acc);
-          t4[x] = acc;
+          t4[x] = cfinish(acc);
         }
 #pragma unroll
         for (int x = 0; x < 4; ++x) win[x][QF_POS(y)] = t4[x];
@@ -737,6 +852,32 @@ namespace {
 
 // ----------------------------------------------------------------- trace
 
+// Entry-wise conversion between tensor precisions through FP64 (exact from
+// complex64 and df64; complex128 -> df64 keeps about 48 bits).
+template <typename RS, typename RD>
+__global__ void __launch_bounds__(256) convert_kernel(const typename Cplx<RS>::T* __restrict__ src,
+                                                      typename Cplx<RD>::T* __restrict__ dst,
+                                                      size_t count) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = cmake(to_d2(src[i]), RD());
+}
+
+template <typename RS>
+void convert_from(const void* src, void* dst, int dp, size_t count, cudaStream_t st) {
+  size_t blocks = (count + 255) / 256;
+  const size_t cap = (size_t)sm_count() * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  typedef typename Cplx<RS>::T CS;
+  if (dp == 0)
+    convert_kernel<RS, double><<<(unsigned)blocks, 256, 0, st>>>((const CS*)src, (double2*)dst, count);
+  else if (dp == 2)
+    convert_kernel<RS, DF><<<(unsigned)blocks, 256, 0, st>>>((const CS*)src, (dfc*)dst, count);
+  else
+    convert_kernel<RS, float><<<(unsigned)blocks, 256, 0, st>>>((const CS*)src, (float2*)dst, count);
+}
+
 constexpr int kTraceThreads = 256;
 
 template <typename R>
@@ -787,7 +928,7 @@ void launch_block(void* T, int n, int S, int plo, int phi, int pa, int pb, const
                   long long Ls, const double2* Rm, long long Rs, cudaStream_t st) {
   typedef typename Cplx<R>::T C;
   const unsigned nblk = 1u << (2 * (n - 2));
-  const int per_sm = sizeof(R) == 4 ? 3 : 1;
+  const int per_sm = PassOcc<R, false>::v;
   long long want = (nblk + kPassThreads - 1) / kPassThreads;
   long long cap = ((long long)sm_count() * per_sm + S - 1) / S;
   if (cap < 1) cap = 1;
@@ -802,7 +943,7 @@ void launch_lane(void* T, int n, int S, int plo, int phi, int pa, int pb, const 
   typedef typename Cplx<R>::T C;
   const int lcols = MODE == 1 ? n - 1 : n;
   const unsigned units = (1u << (n - 2)) << lcols;
-  const int per_sm = sizeof(R) == 4 ? 3 : 1;
+  const int per_sm = PassOcc<R, false>::v;
   long long want = (units + kPassThreads - 1) / kPassThreads;
   long long cap = ((long long)sm_count() * per_sm + S - 1) / S;
   if (cap < 1) cap = 1;
@@ -817,7 +958,7 @@ void launch_window(void* T, int n, int S, const double2* L, long long Ls, const 
   typedef typename Cplx<R>::T C;
   constexpr int W = (PA > PB ? PA : PB) <= 1 ? 4 : 8;
   const unsigned units = (1u << (n - 2)) << (n - (W == 4 ? 2 : 3));
-  const int per_sm = sizeof(R) == 4 ? 2 : 1;
+  const int per_sm = PassOcc<R, true>::v;
   long long want = (units + kPassThreads - 1) / kPassThreads;
   long long cap = ((long long)sm_count() * per_sm + S - 1) / S;
   if (cap < 1) cap = 1;
@@ -829,6 +970,10 @@ template <typename R>
 bool try_window(void* T, int n, int S, int pa, int pb, const double2* L, long long Ls,
                 const double2* Rm, long long Rs, cudaStream_t st) {
   if (n < 3 || pa > 2 || pb > 2) return false;
+  // df64 is bound by the FP32 pipe; a window's 4 x 8 entries of 16 bytes
+  // per thread leave too few warps to hide its arithmetic latency, so the
+  // lane and half-block mappings take these gates
+  if (sizeof(R) == 1) return false;
 #define QF_W(A, B)                                                \
   if (pa == A && pb == B) {                                       \
     launch_window<R, A, B>(T, n, S, L, Ls, Rm, Rs, st);           \
@@ -837,6 +982,19 @@ bool try_window(void* T, int n, int S, int pa, int pb, const double2* L, long lo
   QF_W(1, 0) QF_W(0, 1) QF_W(2, 1) QF_W(1, 2) QF_W(2, 0) QF_W(0, 2)
 #undef QF_W
   return false;
+}
+
+template <typename R, bool HL, bool HR>
+void launch_half(void* T, int n, int S, int plo, int phi, int pa, int pb, const double2* L,
+                 long long Ls, const double2* Rm, long long Rs, cudaStream_t st) {
+  typedef typename Cplx<R>::T C;
+  const long long units = 2ll << (2 * (n - 2));
+  long long want = (units + kPassThreads - 1) / kPassThreads;
+  long long cap = ((long long)sm_count() * 2 + S - 1) / S;
+  if (cap < 1) cap = 1;
+  dim3 grid((unsigned)(want < cap ? want : cap), S);
+  pass_half_kernel<R, HL, HR><<<grid, kPassThreads, 0, st>>>((C*)T, n, plo, phi, pa, pb, L, Ls, Rm,
+                                                              Rs);
 }
 
 template <typename R, bool HL, bool HR>
@@ -850,6 +1008,14 @@ void pass_dispatch(void* T, int n, int S, int pa, int pb, const double2* L, long
     else
       launch_lane<R, 1, HL, HR>(T, n, S, plo, phi, pa, pb, L, Ls, Rm, Rs, st);
   } else {
+    if constexpr (sizeof(R) == 1) {  // df64
+      // the half-block kernel's shuffles need whole warps: 2^(2n-3) units
+      // are a multiple of 32 from n = 4 on
+      if (n >= 4) {
+        launch_half<R, HL, HR>(T, n, S, plo, phi, pa, pb, L, Ls, Rm, Rs, st);
+        return;
+      }
+    }
     launch_block<R, HL, HR>(T, n, S, plo, phi, pa, pb, L, Ls, Rm, Rs, st);
   }
 }
@@ -896,6 +1062,8 @@ cudaError_t launch_conj_transpose(const double2* V, void* T, int n, int S, int p
   dim3 grid((N + 31) / 32, (N + 31) / 32, S), block(32, 8);
   if (prec == 0)
     conj_transpose_kernel<double><<<grid, block, 0, st>>>(V, (double2*)T, N);
+  else if (prec == 2)
+    conj_transpose_kernel<DF><<<grid, block, 0, st>>>(V, (dfc*)T, N);
   else
     conj_transpose_kernel<float><<<grid, block, 0, st>>>(V, (float2*)T, N);
   return cudaGetLastError();
@@ -908,14 +1076,29 @@ cudaError_t launch_pass(void* T, int n, int S, int a, int b, const double2* L,
   const int pa = qubit_bit(n, a), pb = qubit_bit(n, b);
   if (prec == 0)
     pass_ops<double>(T, n, S, pa, pb, L, Lstride, R, Rstride, st);
+  else if (prec == 2)
+    pass_ops<DF>(T, n, S, pa, pb, L, Lstride, R, Rstride, st);
   else
     pass_ops<float>(T, n, S, pa, pb, L, Lstride, R, Rstride, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const void* src, int sp, void* dst, int dp, size_t count, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  if (sp == 0)
+    convert_from<double>(src, dst, dp, count, st);
+  else if (sp == 2)
+    convert_from<DF>(src, dst, dp, count, st);
+  else
+    convert_from<float>(src, dst, dp, count, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trace(const void* T, int n, int S, double2* tr, int prec, cudaStream_t st) {
   if (prec == 0)
     trace_kernel<double><<<S, kTraceThreads, 0, st>>>((const double2*)T, n, tr);
+  else if (prec == 2)
+    trace_kernel<DF><<<S, kTraceThreads, 0, st>>>((const dfc*)T, n, tr);
   else
     trace_kernel<float><<<S, kTraceThreads, 0, st>>>((const float2*)T, n, tr);
   return cudaGetLastError();

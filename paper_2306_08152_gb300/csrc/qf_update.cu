@@ -44,10 +44,12 @@ __global__ void __launch_bounds__(kEnvThreads) env_kernel(
     double2* __restrict__ LR, double2* __restrict__ out, long long out_stride,
     double* __restrict__ sigma_out, int* __restrict__ status, double* __restrict__ part,
     unsigned* __restrict__ counters, LookGeom lg) {
-  using CT = typename Cplx<R>::T;
+  using CT = typename Cplx<R>::T;   // tensor entry
+  using Ar = typename Acc<R>::T;    // accumulation real (FP32 for complex64, else FP64)
+  using AT = typename Cplx<Ar>::T;
   __shared__ double red[32 * (kEnvThreads / 32)];
   __shared__ float2 scratch[32];
-  __shared__ CT sM[16];
+  __shared__ AT sM[16];
   __shared__ bool is_last;
   const int s = blockIdx.y, B = gridDim.x, b = blockIdx.x;
   const unsigned N = 1u << n;
@@ -59,10 +61,10 @@ __global__ void __launch_bounds__(kEnvThreads) env_kernel(
   const unsigned o1 = 1u << pb, o2 = 1u << pa;
   const unsigned off[4] = {0u, o1, o2, o1 | o2};
 
-  // band partial sums (FP32 accumulation for complex64, FP64 for complex128)
-  R v[32];
+  // band partial sums (FP32 accumulation for complex64, FP64 otherwise)
+  Ar v[32];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = R(0);
+  for (int i = 0; i < 32; ++i) v[i] = Ar(0);
   if (!kLook) {
     for (unsigned r = r_beg + threadIdx.x; r < r_end; r += blockDim.x) {
       const unsigned d = dep2(r, plo, phi);
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(kEnvThreads) env_kernel(
         const unsigned rb = (d | off[x]) * N + d;
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
-          const CT e = Ts[rb | off[y]];
+          const AT e = to_acc(Ts[rb | off[y]]);
           v[2 * (x * 4 + y)] += e.x;
           v[2 * (x * 4 + y) + 1] += e.y;
         }
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(kEnvThreads) env_kernel(
       const int r = threadIdx.x >> 2, c = threadIdx.x & 3;
       double2 acc = make_double2(0.0, 0.0);
       for (int k = 0; k < 4; ++k) acc = cfma(r1[r * 4 + k], l1[k * 4 + c], acc);
-      sM[threadIdx.x] = cmake(acc, R(0));
+      sM[threadIdx.x] = cmake(acc, Ar(0));
     }
     __syncthreads();
     const unsigned p1 = 1u << lg.pb1, p2 = 1u << lg.pa1;
@@ -96,13 +98,13 @@ __global__ void __launch_bounds__(kEnvThreads) env_kernel(
     for (unsigned r = r_beg + threadIdx.x; r < r_end; r += blockDim.x) {
       const unsigned i = (r >> 2) & 3u, j = r & 3u;
       const unsigned d = dep1(dep1(dep1(dep1(r >> 4, lg.q[0]), lg.q[1]), lg.q[2]), lg.q[3]);
-      const CT w = sM[j * 4 + i];
+      const AT w = sM[j * 4 + i];
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
         const unsigned rb = (d | off1[i] | off[x]) * N + (d | off1[j]);
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
-          const CT e = Ts[rb | off[y]];
+          const AT e = to_acc(Ts[rb | off[y]]);
           v[2 * (x * 4 + y)] += w.x * e.x - w.y * e.y;
           v[2 * (x * 4 + y) + 1] += w.x * e.y + w.y * e.x;
         }
@@ -117,8 +119,8 @@ __global__ void __launch_bounds__(kEnvThreads) env_kernel(
     const bool up = (lane & h) != 0;
 #pragma unroll
     for (int i = 0; i < h; ++i) {
-      const R keep = up ? v[i + h] : v[i];
-      const R send = up ? v[i] : v[i + h];
+      const Ar keep = up ? v[i + h] : v[i];
+      const Ar send = up ? v[i] : v[i + h];
       v[i] = keep + __shfl_xor_sync(kFull, send, h);
     }
   }
@@ -297,6 +299,10 @@ cudaError_t launch_update_lookahead(const void* T, int n, int S, int a1, int b1,
     env_kernel<double, true><<<grid, kEnvThreads, 0, st>>>(
         (const double2*)T, n, 0, 0, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
         sigma_out, status, part, counters, lg);
+  else if (prec == 2)
+    env_kernel<DF, true><<<grid, kEnvThreads, 0, st>>>(
+        (const dfc*)T, n, 0, 0, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
+        sigma_out, status, part, counters, lg);
   else
     env_kernel<float, true><<<grid, kEnvThreads, 0, st>>>(
         (const float2*)T, n, 0, 0, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
@@ -322,6 +328,10 @@ cudaError_t launch_update(const void* T, int n, int S, int a, int b, double2* ga
   if (prec == 0)
     env_kernel<double, false><<<grid, kEnvThreads, 0, st>>>(
         (const double2*)T, n, plo, phi, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
+        sigma_out, status, part, counters, LookGeom{});
+  else if (prec == 2)
+    env_kernel<DF, false><<<grid, kEnvThreads, 0, st>>>(
+        (const dfc*)T, n, plo, phi, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
         sigma_out, status, part, counters, LookGeom{});
   else
     env_kernel<float, false><<<grid, kEnvThreads, 0, st>>>(
