@@ -263,7 +263,9 @@ int qf_plan_destroy(qf_plan* plan);
 
 /* Copy the target (host-or-device, N x N) and gates (host-or-device,
  * n_starts x p x 16) into the plan and build every tensor (InitCircuitTensor).
- * Enqueued on `stream`; the plan records `stream` for its later calls. */
+ * Enqueued on `stream`; the plan records `stream` for its later calls.  The
+ * copies are checked for NaN/Inf on the device: a non-finite input sets the
+ * plan's status word, which qf_plan_status reports as QF_ENONFINITE. */
 int qf_plan_load(qf_plan* plan, const qf_c128* target, const qf_c128* gates,
                  void* stream);
 

@@ -250,6 +250,17 @@ int plan_build(qf_plan* P) {
   const int pr = kprec(P->prec);
   QF_CUDA(qf::launch_conj_transpose(P->V.as<double2>(), P->T.p, P->n, P->S, pr, P->stream));
   P->all_launches++;
+  if (qf::build_rows_supported(P->n, P->p, pr)) {
+    std::vector<int> pa(P->p), pb(P->p);
+    for (int k = 0; k < P->p; ++k) {
+      pa[k] = qf::qubit_bit(P->n, P->locs[k].a);
+      pb[k] = qf::qubit_bit(P->n, P->locs[k].b);
+    }
+    QF_CUDA(qf::launch_build_rows(P->T.p, P->n, P->S, P->p, pa.data(), pb.data(),
+                                  P->gates.as<double2>(), (long long)P->p * 16, P->stream));
+    P->all_launches++;
+    return QF_OK;
+  }
   for (int k = 0; k < P->p; ++k) {
     QF_TRY(plan_pass(P, all_starts(P), P->locs[k].a, P->locs[k].b, nullptr, 0,
                      P->gates.as<double2>() + (size_t)k * 16, (long long)P->p * 16));
@@ -587,11 +598,12 @@ int plan_load_impl(qf_plan* P, const qf_c128* target, const qf_c128* gates, cuda
   P->stream = st;
   if (!target || !gates) return set_error(QF_EINVAL, "target or gates is NULL");
   const size_t gcount = (size_t)P->S * P->p * 16;
-  if (!is_device_ptr(target)) QF_TRY(check_finite_host(target, P->NN, "target"));
-  if (!is_device_ptr(gates)) QF_TRY(check_finite_host(gates, gcount, "gates"));
   QF_CUDA(cudaMemcpyAsync(P->V.p, target, P->NN * sizeof(double2), cudaMemcpyDefault, st));
   QF_CUDA(cudaMemcpyAsync(P->gates.p, gates, gcount * sizeof(double2), cudaMemcpyDefault, st));
   QF_CUDA(cudaMemsetAsync(P->status.p, 0, sizeof(int), st));
+  // non-finite inputs raise the status word (read at the next status check)
+  QF_CUDA(qf::launch_check_finite(P->V.as<double>(), P->NN * 2, P->status.as<int>(), st));
+  QF_CUDA(qf::launch_check_finite(P->gates.as<double>(), gcount * 2, P->status.as<int>(), st));
   P->sweeps_since_load = 0;
   return plan_build(P);
 }
@@ -810,6 +822,7 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
   std::vector<std::vector<double>> hist(S);
   std::vector<double> c(S);
   QF_TRY(plan_costs_impl(P, c.data(), nullptr));
+  QF_TRY(plan_status_impl(P));  // non-finite target or start gates
   for (int s = 0; s < S; ++s) hist[s].push_back(c[s]);
   std::vector<char> plateaued(S, 0);
   bool c64_phase = refine;
@@ -984,6 +997,17 @@ int qf_init_tensor(const qf_c128* target, int n_qubits, int n_gates, const qf_lo
   const int pr = kprec(precision);
   QF_CUDA(qf::launch_conj_transpose(reinterpret_cast<const double2*>(target), T, n_qubits,
                                     n_starts, pr, st));
+  if (qf::build_rows_supported(n_qubits, n_gates, pr)) {
+    std::vector<int> pa(n_gates), pb(n_gates);
+    for (int k = 0; k < n_gates; ++k) {
+      pa[k] = qf::qubit_bit(n_qubits, locs[k].a);
+      pb[k] = qf::qubit_bit(n_qubits, locs[k].b);
+    }
+    QF_CUDA(qf::launch_build_rows(T, n_qubits, n_starts, n_gates, pa.data(), pb.data(),
+                                  reinterpret_cast<const double2*>(gates), (long long)n_gates * 16,
+                                  st));
+    return QF_OK;
+  }
   for (int k = 0; k < n_gates; ++k)
     QF_CUDA(qf::launch_pass(T, n_qubits, n_starts, locs[k].a, locs[k].b, nullptr, 0,
                             reinterpret_cast<const double2*>(gates) + (size_t)k * 16,

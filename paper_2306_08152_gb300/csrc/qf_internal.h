@@ -83,6 +83,19 @@ cudaError_t launch_grad_from_env(double2* env, const double2* tr, int n, int S, 
 // Two FP64 Newton-Schulz steps on each of `count` gates, in place.
 cudaError_t launch_reunitarize(double2* gates, int count, cudaStream_t st);
 
+// *status <- -4 (QF_ENONFINITE) if any of the `count` doubles at x is not
+// finite; otherwise *status is left alone.
+cudaError_t launch_check_finite(const double* x, size_t count, int* status, cudaStream_t st);
+
+// One-pass InitCircuitTensor after the conjugate transpose: every row of
+// each T_s takes T <- T (u_k on (pa[k], pb[k])) for k = 0..p-1 in shared
+// memory.  gates + s*gstride holds start s's p gates.  Supported
+// (build_rows_supported) for complex64 tensors with n >= 10 whose row and
+// gates fit in shared memory; other cases use the per-gate passes.
+bool build_rows_supported(int n, int p, int prec);
+cudaError_t launch_build_rows(void* T, int n, int S, int p, const int* pa, const int* pb,
+                              const double2* gates, long long gstride, cudaStream_t st);
+
 // dst[i] <- src[i] for `count` entries, converting between kernel precision
 // codes sp and dp (0 complex128, 1 complex64, 2 df64) through FP64.
 cudaError_t launch_convert(const void* src, int sp, void* dst, int dp, size_t count,

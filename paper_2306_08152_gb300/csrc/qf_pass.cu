@@ -852,6 +852,118 @@ namespace {
 
 // ----------------------------------------------------------------- trace
 
+// ------------------------------------------------ one-pass InitCircuitTensor
+//
+// After T_s <- V^dagger, every gate of Alg. 1's InitCircuitTensor acts on
+// the column index only (T <- T (u_k on (a_k, b_k))), so each row of T_s can
+// take all p gates in order on its own.  A CTA loads a row (N entries) into
+// shared memory once, applies the gates there and writes the row back: one
+// read and one write of T instead of p.  The gate list is cut into steps of
+// one gate, or of two consecutive gates on four distinct qubits (they
+// commute, so one step applies both); each step is one barrier.
+//   two-gate step: a thread owns a 16-entry block (the 4 gate bits) and
+//                  applies the first gate along its 2 bits, then the second;
+//   one-gate step: a thread owns four 4-entry tuples and applies the gate to
+//                  each.
+// Packed f32x2 FMAs as in the pair pass; the row is XOR-swizzled in shared
+// memory (bits 4..7 of a column into bits 0..3), which keeps the 16 lanes of
+// a half-warp on distinct banks when the gate bits are the lowest ones.
+// Used for complex64, where the per-gate passes are bound by HBM.
+
+constexpr int kBuildThreads = 256;
+constexpr int kBuildMaxSteps = 960;
+
+struct BuildParams {
+  int n, steps;
+  // per step: bit positions (pa1 | pb1 << 4, pa2 | pb2 << 4) and the first
+  // gate's index; bit 15 of `gate` marks a two-gate step (gates k, k+1)
+  unsigned char bits[kBuildMaxSteps][2];
+  unsigned short gate[kBuildMaxSteps];
+};
+
+__device__ __forceinline__ unsigned bswz(unsigned c) { return c ^ ((c >> 4) & 15u); }
+
+__global__ void __launch_bounds__(kBuildThreads)
+build_rows_kernel(float2* __restrict__ T, const __grid_constant__ BuildParams bp,
+                  const double2* __restrict__ gates, long long gstride, int p) {
+  extern __shared__ __align__(16) unsigned char build_smem[];
+  const int n = bp.n;
+  const unsigned N = 1u << n;
+  float4* ops = reinterpret_cast<float4*>(build_smem);     // p x 16: (u.x, u.x, -u.y, u.y)
+  f32x2* row = reinterpret_cast<f32x2*>(ops + p * 16);     // N entries, swizzled
+  const int s = blockIdx.y;
+  const double2* g = gates + s * gstride;
+  for (int i = threadIdx.x; i < p * 16; i += blockDim.x) {
+    const double2 v = g[i];
+    ops[i] = make_float4((float)v.x, (float)v.x, -(float)v.y, (float)v.y);
+  }
+  f32x2* __restrict__ Ts = reinterpret_cast<f32x2*>(T + (size_t)s * N * N);
+  const unsigned items = N >> 4;  // 16-entry blocks, or 4 tuples of 4
+  for (unsigned r = blockIdx.x; r < N; r += gridDim.x) {
+    f32x2* src = Ts + (size_t)r * N;
+    for (unsigned i = threadIdx.x; i < N; i += blockDim.x) row[bswz(i)] = src[i];
+    __syncthreads();
+    for (int st = 0; st < bp.steps; ++st) {
+      const unsigned b0 = bp.bits[st][0], b1 = bp.bits[st][1];
+      const unsigned gk = bp.gate[st];
+      const int k = (int)(gk & 0x7fffu);
+      const int pa1 = b0 & 15, pb1 = b0 >> 4;
+      if (gk & 0x8000u) {
+        const int pa2 = b1 & 15, pb2 = b1 >> 4;
+        // the 4 gate bits in ascending order, for the block base
+        int q[4] = {pa1, pb1, pa2, pb2};
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3 - i; ++j)
+            if (q[j] > q[j + 1]) {
+              const int t = q[j];
+              q[j] = q[j + 1];
+              q[j + 1] = t;
+            }
+        unsigned off[16];  // swizzled offset of entry (x1, x2)
+#pragma unroll
+        for (int x1 = 0; x1 < 4; ++x1)
+#pragma unroll
+          for (int x2 = 0; x2 < 4; ++x2)
+            off[x1 * 4 + x2] = bswz((((unsigned)x1 >> 1) << pa1) | (((unsigned)x1 & 1u) << pb1) |
+                                    (((unsigned)x2 >> 1) << pa2) | (((unsigned)x2 & 1u) << pb2));
+        for (unsigned t = threadIdx.x; t < items; t += blockDim.x) {
+          const unsigned base = bswz(dep1(dep1(dep1(dep1(t, q[0]), q[1]), q[2]), q[3]));
+          f32x2 m[4][4];
+          apply4<true>(ops + k * 16, [&](int kk, int j) { return row[base ^ off[kk * 4 + j]]; },
+                       [&](int c, int j, f32x2 v) { m[c][j] = v; });
+          apply4<true>(ops + (k + 1) * 16, [&](int kk, int j) { return m[j][kk]; },
+                       [&](int c, int j, f32x2 v) { row[base ^ off[j * 4 + c]] = v; });
+        }
+      } else {
+        const int plo = pa1 < pb1 ? pa1 : pb1, phi = pa1 < pb1 ? pb1 : pa1;
+        const unsigned o[4] = {0u, bswz(1u << pb1), bswz(1u << pa1), bswz((1u << pa1) | (1u << pb1))};
+        for (unsigned t = threadIdx.x; t < items; t += blockDim.x) {
+          unsigned base[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) base[j] = bswz(dep2(t + (unsigned)j * items, plo, phi));
+          apply4<true>(ops + k * 16, [&](int kk, int j) { return row[base[j] ^ o[kk]]; },
+                       [&](int c, int j, f32x2 v) { row[base[j] ^ o[c]] = v; });
+        }
+      }
+      __syncthreads();
+    }
+    for (unsigned i = threadIdx.x; i < N; i += blockDim.x) src[i] = row[bswz(i)];
+    __syncthreads();
+  }
+}
+
+// status <- QF_ENONFINITE (-4) if any of the `count` doubles is NaN or Inf.
+__global__ void __launch_bounds__(256) check_finite_kernel(const double* __restrict__ x, size_t count,
+                                                           int* __restrict__ status) {
+  bool bad = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicExch(status, -4);
+}
+
 // Entry-wise conversion between tensor precisions through FP64 (exact from
 // complex64 and df64; complex128 -> df64 keeps about 48 bits).
 template <typename RS, typename RD>
@@ -1080,6 +1192,62 @@ cudaError_t launch_pass(void* T, int n, int S, int a, int b, const double2* L,
     pass_ops<DF>(T, n, S, pa, pb, L, Lstride, R, Rstride, st);
   else
     pass_ops<float>(T, n, S, pa, pb, L, Lstride, R, Rstride, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const double* x, size_t count, int* status, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  size_t blocks = (count + 255) / 256;
+  const size_t cap = (size_t)sm_count() * 8;
+  if (blocks > cap) blocks = cap;
+  check_finite_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, count, status);
+  return cudaGetLastError();
+}
+
+bool build_rows_supported(int n, int p, int prec) {
+  if (prec != 1 || n < 10 || n > 15 || p > kBuildMaxSteps) return false;
+  const size_t smem = ((size_t)1 << n) * sizeof(float2) + (size_t)p * 16 * sizeof(float4);
+  return smem <= 200 * 1024;
+}
+
+cudaError_t launch_build_rows(void* T, int n, int S, int p, const int* pa, const int* pb,
+                              const double2* gates, long long gstride, cudaStream_t st) {
+  BuildParams bp;
+  memset(&bp, 0, sizeof(bp));
+  bp.n = n;
+  int steps = 0;
+  for (int k = 0; k < p;) {
+    bp.bits[steps][0] = (unsigned char)(pa[k] | (pb[k] << 4));
+    const bool pair = k + 1 < p && pa[k + 1] != pa[k] && pa[k + 1] != pb[k] && pb[k + 1] != pa[k] &&
+                      pb[k + 1] != pb[k];
+    if (pair) {
+      bp.bits[steps][1] = (unsigned char)(pa[k + 1] | (pb[k + 1] << 4));
+      bp.gate[steps] = (unsigned short)(k | 0x8000);
+      k += 2;
+    } else {
+      bp.gate[steps] = (unsigned short)k;
+      k += 1;
+    }
+    ++steps;
+  }
+  bp.steps = steps;
+  const size_t smem = ((size_t)1 << n) * sizeof(float2) + (size_t)p * 16 * sizeof(float4);
+  static size_t attr = 0;
+  if (smem > attr) {
+    const cudaError_t e = cudaFuncSetAttribute(build_rows_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
+  int per_sm = (int)((224 * 1024) / (smem + 1024));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 8) per_sm = 8;
+  long long cap = ((long long)sm_count() * per_sm + S - 1) / S;
+  const long long rows = 1ll << n;
+  const unsigned threads = (unsigned)(((1u << n) >> 4) < (unsigned)kBuildThreads ? ((1u << n) >> 4)
+                                                                                  : kBuildThreads);
+  dim3 grid((unsigned)(rows < cap ? rows : cap), S);
+  build_rows_kernel<<<grid, threads, smem, st>>>((float2*)T, bp, gates, gstride, p);
   return cudaGetLastError();
 }
 

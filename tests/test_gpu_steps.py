@@ -176,6 +176,47 @@ def test_init_tensor_and_trace_match_oracle(qf, n, dtype):
         assert abs(tr[s] - np.trace(Tn[s].astype(np.complex128))) <= 1e-12 * 2**n
 
 
+@pytest.mark.parametrize("n,p", [(10, 40), (11, 31), (12, 66)])
+def test_one_pass_init_tensor_matches_oracle(qf, n, p):
+    """complex64 tensors from 10 qubits are built by the one-pass row kernel
+    (every gate applied to a row in shared memory); compare with the
+    oracle's gate-by-gate InitCircuitTensor.  Gates on random pairs, both
+    orders, including the lowest and highest bit positions.  Tolerance:
+    p successive FP32 4x4 products, 2e-5 of the largest entry."""
+    g = qi.rng(4100 + n)
+    locs = np.array([tuple(int(x) for x in g.choice(n, 2, replace=False)) for _ in range(p)],
+                    dtype=np.int32)
+    locs[0] = (0, n - 1)
+    locs[1] = (n - 1, n - 2)
+    S = 2
+    starts = np.stack([qi.haar_gates(p, g) for _ in range(S)])
+    V = qi.haar_unitary(2**n, g)
+    T = qf.init_tensor(torch.from_numpy(V).cuda(), locs, torch.from_numpy(starts).cuda(),
+                       dtype=torch.complex64).cpu().numpy()
+    worst = 0.0
+    for s in range(S):
+        ref = orc.init_circuit_tensor(V, starts[s], locs, n)
+        e = _relerr(T[s], ref)
+        worst = max(worst, e)
+        assert e <= 2e-5, (s, e)
+    print(f"one-pass init n={n} p={p}: max rel err {worst:.2e}")
+
+
+def test_nonfinite_start_gates_are_reported(qf):
+    """The device-side input check: a NaN in device-resident start gates is
+    reported as QF_ENONFINITE before the first sweep."""
+    from paper_2306_08152_gb300 import QFactorError
+
+    n = 4
+    locs = qi.brickwork_locations(n, 2)
+    starts = qi.haar_gates(len(locs), qi.rng(6010))[None].copy()
+    starts[0, 1, 2, 3] = np.inf
+    V = qi.haar_unitary(16, qi.rng(6011))
+    with pytest.raises(QFactorError) as ei:
+        qf.instantiate_ex(torch.from_numpy(V).cuda(), locs, torch.from_numpy(starts).cuda(), max_sweeps=3)
+    assert ei.value.code == -4
+
+
 def test_circuit_unitary_matches_oracle(qf):
     g = qi.rng(5000)
     for n in (2, 4, 7):
