@@ -104,10 +104,13 @@ typedef struct { int32_t a, b; } qf_loc;     /* gate location: qubits a != b  */
  *   precision     QF_C128, QF_C64, QF_C64_REFINE64, QF_DF64 or
  *                 QF_C64_REFINE_DF.
  *   switch_tol    QF_C64_REFINE64 / QF_C64_REFINE_DF: leave the c64 phase
- *                 once the best cost is
- *                 <= switch_tol, or once ten c64 sweeps have lowered the cost
- *                 by less than 1e-7 (the complex64 noise floor), or after
- *                 max_c64_sweeps.  Reported costs are always FP64 traces.
+ *                 once the best cost is <= switch_tol, or once ten c64
+ *                 sweeps have lowered the cost by less than 1e-7 (the
+ *                 complex64 noise floor) while the best cost is <= 1e-5 (a
+ *                 stall at a larger cost is the method's own plateau and
+ *                 stays in c64), or after max_c64_sweeps.  The plateau rules
+ *                 apply in both phases.  Reported costs are always FP64
+ *                 traces.
  */
 typedef struct {
     double dist_tol;

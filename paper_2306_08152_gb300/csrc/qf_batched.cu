@@ -275,6 +275,11 @@ __device__ bool plateau_test(const double* ring, int len, int it, const BatchPar
   return false;
 }
 
+// A complex64 start whose cost stalls at or below this switches to FP64
+// (the stall is then the complex64 noise floor, ~1e-7); above it the stall
+// is the method's own plateau and the start stays in complex64.
+constexpr double kStallSwitchCost = 1e-5;
+
 __global__ void batched_kernel(BatchParams bp) {
   extern __shared__ __align__(256) unsigned char smem[];
   const int wid = threadIdx.x >> 5;
@@ -336,9 +341,12 @@ __global__ void batched_kernel(BatchParams bp) {
       if (c64 && refine) {
         ++c64_sw;
         // leave complex64 once the cost is below switch_tol, or once ten c64
-        // sweeps have lowered it by less than the complex64 noise floor
+        // sweeps have lowered it by less than the complex64 noise floor while
+        // the cost is near that floor (<= kStallSwitchCost); a stall at a
+        // larger cost is the method's own plateau, which FP64 sweeps do not
+        // lift, so the start stays in complex64
         const bool stalled = len > 10 && ring[(len - 10) % kRing] - c < 1e-7;
-        if (c <= bp.switch_tol || stalled || c64_sw >= bp.max_c64) {
+        if (c <= bp.switch_tol || (stalled && c <= kStallSwitchCost) || c64_sw >= bp.max_c64) {
           // rebuild in complex128 from the target and the FP64 gates
           W<double>::build((double2*)Tbuf, LRd, V, g, locs, n, p, L);
           c = W<double>::cost((double2*)Tbuf, n);
@@ -347,7 +355,12 @@ __global__ void batched_kernel(BatchParams bp) {
           if (L.l == 0) ring[len % kRing] = c;
           ++len;
           __syncwarp();
-          if (*plat >= bp.S) {  // every other start plateaued and this one still runs
+          if (it >= bp.min_sweeps && !plateaued && plateau_test(ring, len, it, bp)) {
+            plateaued = true;
+            if (L.l == 0) atomicAdd(bp.plat_count + i, 1);
+          }
+          __syncwarp();
+          if (*plat >= bp.S) {  // every start of the instance plateaued
             reason = QF_STOP_PLATEAU;
             break;
           }

@@ -784,6 +784,11 @@ int qf_plan_status(qf_plan* plan) {
   return plan_status_impl(plan);
 }
 
+// A complex64 run whose best cost stalls at or below this switches to FP64
+// (the complex64 noise floor is ~1e-7); above it the stall is the method's
+// own plateau.
+constexpr double kStallSwitchCost = 1e-5;
+
 int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
                       const qf_loc* locations, int n_starts, const qf_c128* initial_gates,
                       const qf_options* opts, qf_c128* out_gates, double* out_costs,
@@ -837,7 +842,9 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
       ++c64_sweeps;
       // leave complex64 once the best cost is below switch_tol, or once ten
       // c64 sweeps have lowered every start's cost by less than the
-      // complex64 noise floor (1e-7)
+      // complex64 noise floor (1e-7) while the best cost is near that floor
+      // (<= 1e-5; a stall above it is the method's own plateau, which FP64
+      // sweeps do not lift)
       double best = c[0];
       bool stalled = hist[0].size() > 10;
       for (int s = 0; s < S; ++s) {
@@ -845,7 +852,8 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
         if (hist[s].size() > 10 && hist[s][hist[s].size() - 10] - c[s] >= 1e-7) stalled = false;
       }
       for (int s = 0; s < S; ++s) hist[s].push_back(c[s]);
-      if (best <= o.switch_tol || stalled || c64_sweeps >= o.max_c64_sweeps) {
+      if (best <= o.switch_tol || (stalled && best <= kStallSwitchCost) ||
+          c64_sweeps >= o.max_c64_sweeps) {
         // rebuild every tensor in the fine precision from V and the FP64 gates
         P->prec = fine_prec;
         QF_TRY(plan_build(P));
@@ -853,6 +861,18 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
         for (int s = 0; s < S; ++s) hist[s].back() = c[s];
         c64_phase = false;
       } else {
+        // the plateau rules apply in the complex64 phase too
+        if (it >= o.min_sweeps) {
+          bool all = true;
+          for (int s = 0; s < S; ++s) {
+            if (plateau(hist[s], it, o)) plateaued[s] = 1;
+            all = all && plateaued[s];
+          }
+          if (all) {
+            reason = QF_STOP_PLATEAU;
+            break;
+          }
+        }
         continue;
       }
     } else {
