@@ -66,3 +66,61 @@ def dense_environment(V, gates, locs, n, k):
         right = right @ full_operator(gates[j], int(locs[j][0]), int(locs[j][1]), n)
     R = left @ np.asarray(V).conj().T @ right
     return dense_partial_trace(R, int(locs[k][0]), int(locs[k][1]), n)
+
+
+# ---- gates on any number k of qubits: local index sum_i bit(q_i) 2^(k-1-i)
+
+def local_index_k(i, qubits, n):
+    x = 0
+    for q in qubits:
+        x = 2 * x + bit(i, q, n)
+    return x
+
+
+def rest_bits_k(i, qubits, n):
+    mask = 0
+    for q in qubits:
+        mask |= 1 << (n - 1 - q)
+    return i & ~mask
+
+
+def full_operator_k(u, qubits, n):
+    """N x N matrix of u on `qubits`: G[i, j] = u[loc(i), loc(j)] if i and j
+    agree on every other qubit, else 0."""
+    N = 2**n
+    G = np.zeros((N, N), dtype=np.complex128)
+    for i in range(N):
+        for j in range(N):
+            if rest_bits_k(i, qubits, n) == rest_bits_k(j, qubits, n):
+                G[i, j] = u[local_index_k(i, qubits, n), local_index_k(j, qubits, n)]
+    return G
+
+
+def dense_circuit_k(gates, locs, n):
+    C = np.eye(2**n, dtype=np.complex128)
+    for u, q in zip(gates, locs):
+        C = C @ full_operator_k(u, tuple(q), n)
+    return C
+
+
+def dense_partial_trace_k(M, qubits, n):
+    N = 2**n
+    d = 2 ** len(qubits)
+    P = np.zeros((d, d), dtype=np.complex128)
+    for i in range(N):
+        for j in range(N):
+            if rest_bits_k(i, qubits, n) == rest_bits_k(j, qubits, n):
+                P[local_index_k(i, qubits, n), local_index_k(j, qubits, n)] += M[i, j]
+    return P
+
+
+def dense_environment_k(V, gates, locs, n, k):
+    N = 2**n
+    left = np.eye(N, dtype=np.complex128)
+    for j in range(k + 1, len(gates)):
+        left = left @ full_operator_k(gates[j], tuple(locs[j]), n)
+    right = np.eye(N, dtype=np.complex128)
+    for j in range(k):
+        right = right @ full_operator_k(gates[j], tuple(locs[j]), n)
+    R = left @ np.asarray(V).conj().T @ right
+    return dense_partial_trace_k(R, tuple(locs[k]), n)
