@@ -251,6 +251,64 @@ int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
                            qf_batch_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Gates on more than two qubits (the paper's method extends to k-qubit
+ * unitaries with a 2^k x 2^k environment, Sec. III).  Supported: k = 2 and
+ * k = 3, mixed freely in one circuit.
+ *
+ * A gate on k qubits (q[0], ..., q[k-1]) acts on the local index
+ * sum_i bit(q[i]) 2^(k-1-i) (k = 2: 2*bit(q[0]) + bit(q[1]), as qf_loc).
+ * Gate arrays are concatenated per start in gate order: gate i has 4^k_i
+ * entries (row-major 2^k x 2^k), a start's gates take E = sum_i 4^k_i
+ * entries and start s's begin at s*E.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t k;     /* 2 or 3 */
+    int32_t q[3];  /* qubits in local-index order; q[2] unused for k = 2 */
+} qf_gate_loc;
+
+/* qf_instantiate_ex for a circuit of 2- and 3-qubit gates.  locations:
+ * host-or-device, n_gates entries; initial_gates and out_gates:
+ * host-or-device, n_starts x E entries (see above).  The three-qubit
+ * updates use the 8x8 FP64 polar (one-sided Jacobi on one warp); the
+ * look-ahead and the one-pass InitCircuitTensor apply to two-qubit-only
+ * circuits.  Errors as qf_instantiate_ex, QF_EINVAL for k outside {2, 3},
+ * repeated or out-of-range qubits. */
+int qf_instantiate_k(const qf_c128* target, int n_qubits, int n_gates,
+                     const qf_gate_loc* locations, int n_starts,
+                     const qf_c128* initial_gates, const qf_options* opts,
+                     qf_c128* out_gates, double* out_costs,
+                     qf_result* out_result, void* stream);
+
+/* Steps for one gate of size k (parity tests; enqueue only):
+ *   qf_apply_gate_k     T_s <- (L_s on q) T_s (R_s on q); L, R device
+ *                       n_starts x 4^k (either may be NULL for identity).
+ *   qf_partial_trace_k  P_s = partial trace of T_s over every qubit not in
+ *                       q (CalcEnvMat, Alg. 1); P device n_starts x 4^k.
+ *                       k = 3 allocates its scratch stream-ordered.
+ *   qf_optimize_gates_k OptimizeGate (Eq. opt_u) on `count` dim x dim
+ *                       matrices, dim 4 or 8 (see qf_optimize_gates).
+ *   qf_init_tensor_k    InitCircuitTensor with k-qubit gates (gates device,
+ *                       n_starts x E).
+ *   qf_circuit_unitary_k C = G_0 ... G_{p-1} (complex128, device N x N;
+ *                       gates device, E entries).  Synchronises. */
+int qf_apply_gate_k(void* T, int n_qubits, int n_starts,
+                    const qf_gate_loc* location, const qf_c128* L,
+                    const qf_c128* R, int precision, void* stream);
+int qf_partial_trace_k(const void* T, int n_qubits, int n_starts,
+                       const qf_gate_loc* location, qf_c128* P, int precision,
+                       void* stream);
+int qf_optimize_gates_k(const qf_c128* E, int dim, const qf_c128* u_old,
+                        double beta, int count, qf_c128* u_out,
+                        double* sigma_out, void* stream);
+int qf_init_tensor_k(const qf_c128* target, int n_qubits, int n_gates,
+                     const qf_gate_loc* locations, int n_starts,
+                     const qf_c128* gates, void* T, int precision,
+                     void* stream);
+int qf_circuit_unitary_k(int n_qubits, int n_gates,
+                         const qf_gate_loc* locations, const qf_c128* gates,
+                         qf_c128* C_out, void* stream);
+
+/* ------------------------------------------------------------------------
  * Resident plan: device-resident tensors, target and gates for repeated
  * sweeps (the form the benchmark times).
  * ---------------------------------------------------------------------- */
@@ -321,6 +379,13 @@ int qf_plan_pass_stats(qf_plan* plan, double* pass_ms, int64_t* pass_launches,
 /* Current device status word of the plan (0 = clean; QF_ENONFINITE if an
  * update met a non-finite environment).  Synchronises. */
 int qf_plan_status(qf_plan* plan);
+
+/* A resident plan for a circuit of 2- and 3-qubit gates (as qf_plan_create;
+ * qf_plan_load / qf_plan_get_gates then use the concatenated gate layout,
+ * n_starts x E entries, E from qf_plan_gate_entries). */
+int qf_plan_create_k(int n_qubits, int n_gates, const qf_gate_loc* locations,
+                     int n_starts, int precision, qf_plan** out_plan);
+int qf_plan_gate_entries(qf_plan* plan, int64_t* entries_per_start);
 
 /* ------------------------------------------------------------------------
  * Single steps of the sweep (Alg. 1), on device arrays, enqueue only.

@@ -60,6 +60,10 @@ class qf_result(ct.Structure):
     ]
 
 
+class qf_gate_loc(ct.Structure):
+    _fields_ = [("k", ct.c_int32), ("q", ct.c_int32 * 3)]
+
+
 class qf_batch_stats(ct.Structure):
     _fields_ = [
         ("warps_per_cta", ct.c_int32),
@@ -112,6 +116,15 @@ SIGNATURES = {
     "qf_trace": (I, [P, I, I, P, I, P]),
     "qf_reunitarize_gates": (I, [P, I, P]),
     "qf_circuit_unitary": (I, [I, I, P, P, P, P]),
+    "qf_instantiate_k": (I, [P, I, I, P, I, P, ct.POINTER(qf_options), P, DP,
+                             ct.POINTER(qf_result), P]),
+    "qf_plan_create_k": (I, [I, I, P, I, I, ct.POINTER(P)]),
+    "qf_plan_gate_entries": (I, [P, I64P]),
+    "qf_apply_gate_k": (I, [P, I, I, P, P, P, I, P]),
+    "qf_partial_trace_k": (I, [P, I, I, P, P, I, P]),
+    "qf_optimize_gates_k": (I, [P, I, P, D, I, P, P, P]),
+    "qf_init_tensor_k": (I, [P, I, I, P, I, P, P, I, P]),
+    "qf_circuit_unitary_k": (I, [I, I, P, P, P, P]),
 }
 
 _lib = None

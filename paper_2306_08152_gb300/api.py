@@ -19,7 +19,9 @@ from ._native import check
 __all__ = [
     "QF_C128", "QF_C64", "QF_C64_REFINE64", "QF_DF64", "QF_C64_REFINE_DF", "Options", "instantiate",
     "instantiate_ex", "instantiate_batched", "cost_and_env", "cost_grad", "costs", "Plan", "init_tensor", "apply_pair",
-    "partial_trace", "partial_trace_noalloc", "apply_two_pairs", "partial_trace_after", "convert_tensor", "optimize_gates", "reunitarize_gates", "trace", "circuit_unitary",
+    "partial_trace", "partial_trace_noalloc", "apply_two_pairs", "partial_trace_after", "convert_tensor",
+    "instantiate_k", "apply_gate_k", "partial_trace_k", "optimize_gates_k", "init_tensor_k",
+    "circuit_unitary_k", "flatten_gates", "unflatten_gates", "gate_entries", "optimize_gates", "reunitarize_gates", "trace", "circuit_unitary",
 ]
 
 QF_C128 = nat.QF_C128
@@ -63,6 +65,54 @@ def _locs(locations):
 
 def _ptr(t):
     return ct.c_void_p(t.data_ptr())
+
+
+def _is_pairs(locations):
+    """True when every location is a qubit pair (the two-qubit entry points)."""
+    if isinstance(locations, torch.Tensor) or isinstance(locations, np.ndarray):
+        return np.asarray(locations).ndim == 2 and np.asarray(locations).shape[1] == 2
+    return all(len(q) == 2 for q in locations)
+
+
+def _gate_locs(locations):
+    """ctypes array of qf_gate_loc from a sequence of qubit tuples (2 or 3)."""
+    locs = [tuple(int(x) for x in q) for q in (locations.tolist() if hasattr(locations, "tolist")
+                                                else locations)]
+    arr = (nat.qf_gate_loc * len(locs))()
+    for i, q in enumerate(locs):
+        if len(q) not in (2, 3):
+            raise ValueError("a location has 2 or 3 qubits")
+        arr[i].k = len(q)
+        for j, x in enumerate(q):
+            arr[i].q[j] = x
+    return arr, locs
+
+
+def gate_entries(locations):
+    """Entries of one start's concatenated gate array: sum of 4^k."""
+    return sum(4 ** len(tuple(q)) for q in locations)
+
+
+def flatten_gates(gate_sets):
+    """Concatenated layout (S, E) complex128 from S lists of 2^k x 2^k
+    arrays (one list per start, gates in circuit order)."""
+    rows = [np.concatenate([np.asarray(g, dtype=np.complex128).reshape(-1) for g in gs])
+            for gs in gate_sets]
+    return torch.from_numpy(np.ascontiguousarray(np.stack(rows)))
+
+
+def unflatten_gates(flat, locations):
+    """S lists of 2^k x 2^k numpy arrays from the concatenated layout."""
+    a = flat.detach().cpu().numpy() if isinstance(flat, torch.Tensor) else np.asarray(flat)
+    out = []
+    for row in a.reshape(a.shape[0], -1):
+        gs, off = [], 0
+        for q in locations:
+            d = 2 ** len(tuple(q))
+            gs.append(row[off:off + d * d].reshape(d, d))
+            off += d * d
+        out.append(gs)
+    return out
 
 
 def _nqubits(target):
@@ -239,17 +289,29 @@ def costs(target, locations, gates, stream=None):
 
 
 class Plan:
-    """Device-resident multistart state (qf_plan_*)."""
+    """Device-resident multistart state (qf_plan_*).  ``locations`` holds
+    qubit pairs, or tuples of 2 or 3 qubits (qf_plan_create_k; gates then
+    use the concatenated layout (S, E), see flatten_gates)."""
 
     def __init__(self, n_qubits, locations, n_starts, precision=QF_C128):
-        self.locs = _locs(locations)
         self.n = int(n_qubits)
-        self.p = int(self.locs.shape[0])
         self.S = int(n_starts)
         h = ct.c_void_p()
-        check(_lib().qf_plan_create(self.n, self.p, _ptr(self.locs), self.S, int(precision),
-                                    ct.byref(h)))
+        self.k_path = not _is_pairs(locations)
+        if self.k_path:
+            self._larr, self.locations = _gate_locs(locations)
+            self.p = len(self.locations)
+            check(_lib().qf_plan_create_k(self.n, self.p, self._larr, self.S, int(precision),
+                                          ct.byref(h)))
+        else:
+            self.locs = _locs(locations)
+            self.p = int(self.locs.shape[0])
+            check(_lib().qf_plan_create(self.n, self.p, _ptr(self.locs), self.S, int(precision),
+                                        ct.byref(h)))
         self.h = h
+        e = ct.c_int64()
+        check(_lib().qf_plan_gate_entries(self.h, ct.byref(e)))
+        self.E = e.value
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
@@ -279,7 +341,10 @@ class Plan:
         return np.array(out[:])
 
     def gates(self, device="cpu"):
-        out = torch.empty((self.S, self.p, 4, 4), dtype=torch.complex128, device=device)
+        if self.k_path:
+            out = torch.empty((self.S, self.E), dtype=torch.complex128, device=device)
+        else:
+            out = torch.empty((self.S, self.p, 4, 4), dtype=torch.complex128, device=device)
         check(_lib().qf_plan_get_gates(self.h, _ptr(out)))
         return out
 
@@ -430,6 +495,102 @@ def partial_trace_after(T, a1, b1, L1, R1, a, b, stream=None):
                                         int(a), int(b), _ptr(P), _tensor_prec(T),
                                         _stream_handle(stream)))
     return P
+
+
+def instantiate_k(target, locations, starts, options=None, stream=None, **kw):
+    """Lock-step multistart Qfactor with 2- and 3-qubit gates
+    (qf_instantiate_k).  ``locations``: sequence of qubit tuples; ``starts``:
+    (S, E) complex128 in the concatenated layout or S lists of gate arrays.
+    Returns the dict of instantiate_ex with ``gates`` as S lists of arrays
+    and ``flat`` the (S, E) tensor."""
+    target = _c128(target, "target")
+    larr, locs = _gate_locs(locations)
+    if not isinstance(starts, torch.Tensor):
+        starts = flatten_gates(starts)
+    starts = _c128(starts, "starts")
+    if starts.dim() == 1:
+        starts = starts.unsqueeze(0)
+    n = _nqubits(target)
+    S = starts.shape[0]
+    if starts.shape[1] != gate_entries(locs):
+        raise ValueError("starts do not match the locations' gate sizes")
+    opts = options if options is not None else Options(**kw)
+    out = torch.empty_like(starts)
+    costs = (ct.c_double * S)()
+    res = nat.qf_result()
+    check(_lib().qf_instantiate_k(_ptr(target), n, len(locs), larr, S, _ptr(starts),
+                                  ct.byref(opts.c), _ptr(out), costs, ct.byref(res),
+                                  _stream_handle(stream)))
+    return {"gates": unflatten_gates(out, locs), "flat": out, "costs": np.array(costs[:]),
+            "best": res.best_start, "sweeps": res.sweeps, "c64_sweeps": res.c64_sweeps,
+            "reason": nat.REASONS.get(res.reason, str(res.reason)), "best_cost": res.best_cost}
+
+
+def apply_gate_k(T, qubits, L=None, R=None, stream=None):
+    """In place: T_s <- (L_s on qubits) T_s (R_s on qubits); L, R (S, d, d)."""
+    T = _dev(T, "T")
+    S, N = _tensor_sn(T)
+    n = int(N).bit_length() - 1
+    larr, _ = _gate_locs([qubits])
+    Lp = _ptr(_dev(_c128(L, "L"), "L")) if L is not None else None
+    Rp = _ptr(_dev(_c128(R, "R"), "R")) if R is not None else None
+    check(_lib().qf_apply_gate_k(_ptr(T), n, S, larr, Lp, Rp, _tensor_prec(T), _stream_handle(stream)))
+    return T
+
+
+def partial_trace_k(T, qubits, stream=None):
+    T = _dev(T, "T")
+    S, N = _tensor_sn(T)
+    n = int(N).bit_length() - 1
+    d = 2 ** len(tuple(qubits))
+    larr, _ = _gate_locs([qubits])
+    P = torch.empty((S, d, d), dtype=torch.complex128, device=T.device)
+    check(_lib().qf_partial_trace_k(_ptr(T), n, S, larr, _ptr(P), _tensor_prec(T),
+                                    _stream_handle(stream)))
+    return P
+
+
+def optimize_gates_k(E, u_old=None, beta=0.0, stream=None):
+    """OptimizeGate on (..., d, d) matrices, d = 4 or 8."""
+    E = _dev(_c128(E, "E"), "E")
+    d = E.shape[-1]
+    count = E.numel() // (d * d)
+    U = torch.empty_like(E)
+    sig = torch.empty(E.shape[:-2], dtype=torch.float64, device=E.device)
+    up = _ptr(_dev(_c128(u_old, "u_old"), "u_old")) if u_old is not None else None
+    check(_lib().qf_optimize_gates_k(_ptr(E), int(d), up, float(beta), count, _ptr(U), _ptr(sig),
+                                     _stream_handle(stream)))
+    return U, sig
+
+
+def init_tensor_k(target, locations, gates, dtype=torch.complex128, stream=None):
+    """InitCircuitTensor with 2- and 3-qubit gates; gates (S, E) or S lists."""
+    target = _dev(_c128(target, "target"), "target")
+    larr, locs = _gate_locs(locations)
+    if not isinstance(gates, torch.Tensor):
+        gates = flatten_gates(gates)
+    g = _c128(gates, "gates").to(target.device)
+    if g.dim() == 1:
+        g = g.unsqueeze(0)
+    n = _nqubits(target)
+    prec = QF_DF64 if dtype == "df64" else (QF_C128 if dtype == torch.complex128 else QF_C64)
+    T = _empty_tensor(g.shape[0], 1 << n, prec, target.device)
+    check(_lib().qf_init_tensor_k(_ptr(target), n, len(locs), larr, g.shape[0], _ptr(g), _ptr(T), prec,
+                                  _stream_handle(stream)))
+    return T
+
+
+def circuit_unitary_k(n_qubits, locations, gates, device="cuda", stream=None):
+    """C = G_0 ... G_{p-1} for 2- and 3-qubit gates (gates: E entries or a list)."""
+    larr, locs = _gate_locs(locations)
+    if not isinstance(gates, torch.Tensor):
+        gates = flatten_gates([gates])[0]
+    g = _c128(gates, "gates").reshape(-1).to(device)
+    N = 1 << int(n_qubits)
+    C = torch.empty((N, N), dtype=torch.complex128, device=device)
+    check(_lib().qf_circuit_unitary_k(int(n_qubits), len(locs), larr, _ptr(g), _ptr(C),
+                                      _stream_handle(stream)))
+    return C
 
 
 def partial_trace_noalloc(T, a, b, P=None, stream=None):

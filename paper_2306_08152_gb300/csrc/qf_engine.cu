@@ -97,6 +97,51 @@ int fetch_locations(const qf_loc* locs, int n, int p, std::vector<qf_loc>* out) 
   return QF_OK;
 }
 
+// A gate of the circuit: size k (2 or 3), its qubits in local-index order,
+// and the offset of its 4^k entries within one start's gate array.
+struct GateDesc {
+  int k;
+  int q[3];
+  long long off;
+};
+
+int descs_from_pairs(const std::vector<qf_loc>& locs, std::vector<GateDesc>* out, long long* gsz) {
+  out->resize(locs.size());
+  for (size_t i = 0; i < locs.size(); ++i) {
+    (*out)[i] = GateDesc{2, {locs[i].a, locs[i].b, -1}, (long long)i * 16};
+  }
+  *gsz = (long long)locs.size() * 16;
+  return QF_OK;
+}
+
+// Copy k-qubit locations (host or device) and validate them.
+int fetch_gate_locs(const qf_gate_loc* locs, int n, int p, std::vector<GateDesc>* out, long long* gsz) {
+  if (!locs) return set_error(QF_EINVAL, "locations is NULL");
+  std::vector<qf_gate_loc> h(p);
+  if (is_device_ptr(locs)) {
+    QF_CUDA(cudaMemcpy(h.data(), locs, sizeof(qf_gate_loc) * p, cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(h.data(), locs, sizeof(qf_gate_loc) * p);
+  }
+  out->resize(p);
+  long long off = 0;
+  for (int i = 0; i < p; ++i) {
+    const qf_gate_loc& l = h[i];
+    if (l.k != 2 && l.k != 3) return set_error(QF_EINVAL, "gate %d: k=%d must be 2 or 3", i, l.k);
+    for (int a = 0; a < l.k; ++a) {
+      if (l.q[a] < 0 || l.q[a] >= n)
+        return set_error(QF_EINVAL, "gate %d: qubit %d invalid for %d qubits", i, l.q[a], n);
+      for (int b = 0; b < a; ++b)
+        if (l.q[a] == l.q[b]) return set_error(QF_EINVAL, "gate %d: repeated qubit %d", i, l.q[a]);
+    }
+    if (l.k > n) return set_error(QF_EINVAL, "gate %d: k=%d > n_qubits=%d", i, l.k, n);
+    (*out)[i] = GateDesc{l.k, {l.q[0], l.q[1], l.k == 3 ? l.q[2] : -1}, off};
+    off += l.k == 3 ? 64 : 16;
+  }
+  *gsz = off;
+  return QF_OK;
+}
+
 int check_finite_host(const qf_c128* v, size_t count, const char* what) {
   for (size_t i = 0; i < count; ++i)
     if (!std::isfinite(v[i].re) || !std::isfinite(v[i].im))
@@ -164,8 +209,12 @@ int qf_internal_set_error(int code, const char* what, const char* detail) {
 struct qf_plan {
   int n = 0, p = 0, S = 0, prec = QF_C128;
   size_t N = 0, NN = 0;
-  std::vector<qf_loc> locs;
+  std::vector<qf_loc> locs;  // (q0, q1) of every gate
+  std::vector<GateDesc> gd;  // size, qubits and entry offset of every gate
+  long long gsz = 0;         // gate entries per start
+  bool mixed = false;        // some gate acts on three qubits
   DevBuf T, V, gates, LR, sigma, tr, status, part, counters;
+  DevBuf LR8, gdesc;         // three-qubit pass operators (start stride 128); gate table
   size_t T_capacity = 0;  // bytes
   cudaStream_t stream = nullptr;
   long long sweeps_since_load = 0;
@@ -245,25 +294,71 @@ int plan_pass(qf_plan* P, const Slice& sl, int a, int b, const double2* L, long 
   return QF_OK;
 }
 
+// The pass of a three-qubit gate: T <- (L on q) T (R on q), 8x8 operators.
+int plan_pass8(qf_plan* P, const Slice& sl, const int* q, const double2* L, long long Ls,
+               const double2* R, long long Rs) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (P->timing) {
+    if (P->events_used + 2 > P->events.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        QF_CUDA(cudaEventCreate(&e));
+        P->events.push_back(e);
+      }
+    }
+    e0 = P->events[P->events_used];
+    e1 = P->events[P->events_used + 1];
+    P->events_used += 2;
+    QF_CUDA(cudaEventRecord(e0, sl.st));
+  }
+  void* T = static_cast<char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
+  QF_CUDA(qf::launch_pass8(T, P->n, sl.Sg, q, L ? L + sl.s0 * Ls : nullptr, Ls,
+                           R ? R + sl.s0 * Rs : nullptr, Rs, kprec(P->prec), sl.st));
+  if (P->timing) {
+    QF_CUDA(cudaEventRecord(e1, sl.st));
+    P->pass_bytes += 2.0 * (double)sl.Sg * (double)P->NN * (double)elem_bytes(P->prec);
+  }
+  P->pass_launches++;
+  P->all_launches++;
+  return QF_OK;
+}
+
+// The fused pass of gate k with the operators its update left in LR / LR8.
+int plan_gate_pass(qf_plan* P, const Slice& sl, int k) {
+  if (P->gd[k].k == 3) {
+    const double2* L8 = P->LR8.as<double2>();
+    return plan_pass8(P, sl, P->gd[k].q, L8, 128, L8 + 64, 128);
+  }
+  const double2* LR = P->LR.as<double2>();
+  return plan_pass(P, sl, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32);
+}
+
+double2* gate_ptr(qf_plan* P, int s0, int k) {
+  return P->gates.as<double2>() + (size_t)s0 * P->gsz + P->gd[k].off;
+}
+
 // InitCircuitTensor (Alg. 1) for every start.
 int plan_build(qf_plan* P) {
   const int pr = kprec(P->prec);
   QF_CUDA(qf::launch_conj_transpose(P->V.as<double2>(), P->T.p, P->n, P->S, pr, P->stream));
   P->all_launches++;
-  if (qf::build_rows_supported(P->n, P->p, pr)) {
+  if (!P->mixed && qf::build_rows_supported(P->n, P->p, pr)) {
     std::vector<int> pa(P->p), pb(P->p);
     for (int k = 0; k < P->p; ++k) {
       pa[k] = qf::qubit_bit(P->n, P->locs[k].a);
       pb[k] = qf::qubit_bit(P->n, P->locs[k].b);
     }
     QF_CUDA(qf::launch_build_rows(P->T.p, P->n, P->S, P->p, pa.data(), pb.data(),
-                                  P->gates.as<double2>(), (long long)P->p * 16, P->stream));
+                                  P->gates.as<double2>(), P->gsz, P->stream));
     P->all_launches++;
     return QF_OK;
   }
   for (int k = 0; k < P->p; ++k) {
-    QF_TRY(plan_pass(P, all_starts(P), P->locs[k].a, P->locs[k].b, nullptr, 0,
-                     P->gates.as<double2>() + (size_t)k * 16, (long long)P->p * 16));
+    if (P->gd[k].k == 3)
+      QF_TRY(plan_pass8(P, all_starts(P), P->gd[k].q, nullptr, 0, gate_ptr(P, 0, k), P->gsz));
+    else
+      QF_TRY(plan_pass(P, all_starts(P), P->locs[k].a, P->locs[k].b, nullptr, 0, gate_ptr(P, 0, k),
+                       P->gsz));
   }
   return QF_OK;
 }
@@ -273,9 +368,18 @@ int plan_update(qf_plan* P, const Slice& sl, int k, int mode, double beta, doubl
   const int pr = kprec(P->prec);
   const int B = qf::env_ctas(P->n);
   const void* T = static_cast<const char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
+  if (P->gd[k].k == 3) {
+    QF_CUDA(qf::launch_update8(
+        T, P->n, sl.Sg, P->gd[k].q, gate_ptr(P, sl.s0, k), P->gsz, mode, beta,
+        P->LR8.as<double2>() + (size_t)sl.s0 * 128, env_out ? env_out + sl.s0 * env_stride : nullptr,
+        env_stride, P->sigma.as<double>() + sl.s0, P->status.as<int>(),
+        P->part.as<double>() + (size_t)sl.s0 * B * 128, P->counters.as<unsigned>() + sl.s0, pr,
+        sl.st));
+    P->all_launches++;
+    return QF_OK;
+  }
   QF_CUDA(qf::launch_update(
-      T, P->n, sl.Sg, P->locs[k].a, P->locs[k].b,
-      P->gates.as<double2>() + (size_t)sl.s0 * P->p * 16 + (size_t)k * 16, (long long)P->p * 16,
+      T, P->n, sl.Sg, P->locs[k].a, P->locs[k].b, gate_ptr(P, sl.s0, k), P->gsz,
       mode, beta, P->LR.as<double2>() + (size_t)sl.s0 * 32,
       env_out ? env_out + sl.s0 * env_stride : nullptr, env_stride,
       P->sigma.as<double>() + sl.s0, P->status.as<int>(),
@@ -293,7 +397,7 @@ int plan_update_look(qf_plan* P, const Slice& sl, int k1, int k2, int mode, doub
   const double2* LR = P->LR.as<double2>() + (size_t)sl.s0 * 32;
   QF_CUDA(qf::launch_update_lookahead(
       T, P->n, sl.Sg, P->locs[k1].a, P->locs[k1].b, LR, LR + 16, 32, P->locs[k2].a, P->locs[k2].b,
-      P->gates.as<double2>() + (size_t)sl.s0 * P->p * 16 + (size_t)k2 * 16, (long long)P->p * 16,
+      gate_ptr(P, sl.s0, k2), P->gsz,
       mode, beta, P->LR2.as<double2>() + (size_t)sl.s0 * 32, nullptr, 0,
       P->sigma.as<double>() + sl.s0, P->status.as<int>(),
       P->part.as<double>() + (size_t)sl.s0 * B * 32, P->counters.as<unsigned>() + sl.s0, pr, sl.st));
@@ -373,7 +477,7 @@ int plan_windows(qf_plan* P) {
 }
 
 bool plan_uses_lookahead(const qf_plan* P) {
-  return P->lookahead && P->prec == QF_C64 && P->n >= 8;
+  return P->lookahead && !P->mixed && P->prec == QF_C64 && P->n >= 8;
 }
 
 int plan_streams(qf_plan* P) {
@@ -412,15 +516,13 @@ int enqueue_window(qf_plan* P, const Slice& env_sl, const Slice& pass_sl, int h,
     return plan_pair_pass(P, pass_sl, P->geo_index[h * P->p + i]);
   }
   if (env_sl.st != pass_sl.st) return QF_OK;
-  const double2* LR = P->LR.as<double2>();
-  return plan_pass(P, pass_sl, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32);
+  return plan_gate_pass(P, pass_sl, k);
 }
 
 int enqueue_window_pass(qf_plan* P, const Slice& pass_sl, int h, int i, bool look) {
   if (look && P->win_first[h * P->p + i]) return plan_pair_pass(P, pass_sl, P->geo_index[h * P->p + i]);
   const int k = order_gate(P, h, i);
-  const double2* LR = P->LR.as<double2>();
-  return plan_pass(P, pass_sl, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32);
+  return plan_gate_pass(P, pass_sl, k);
 }
 
 int enqueue_sweep(qf_plan* P, double beta, cudaStream_t origin) {
@@ -460,16 +562,15 @@ int enqueue_sweep(qf_plan* P, double beta, cudaStream_t origin) {
     QF_CUDA(cudaStreamWaitEvent(origin, P->ev_join_pass, 0));
     return QF_OK;
   }
-  const double2* LR = P->LR.as<double2>();
   if (P->G == 1) {
     const Slice sl = all_starts(P, origin);
     for (int k = P->p - 1; k >= 0; --k) {
       QF_TRY(plan_update(P, sl, k, qf::kBackward, beta, nullptr, 0));
-      QF_TRY(plan_pass(P, sl, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
+      QF_TRY(plan_gate_pass(P, sl, k));
     }
     for (int k = 0; k < P->p; ++k) {
       QF_TRY(plan_update(P, sl, k, qf::kForward, beta, nullptr, 0));
-      QF_TRY(plan_pass(P, sl, P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
+      QF_TRY(plan_gate_pass(P, sl, k));
     }
     return QF_OK;
   }
@@ -488,7 +589,7 @@ int enqueue_sweep(qf_plan* P, double beta, cudaStream_t origin) {
       QF_TRY(plan_update(P, env_sl[g], k, backward ? qf::kBackward : qf::kForward, beta, nullptr, 0));
       QF_CUDA(cudaEventRecord(P->ev_env[g], P->s_env));
       QF_CUDA(cudaStreamWaitEvent(P->s_pass, P->ev_env[g], 0));
-      QF_TRY(plan_pass(P, pass_sl[g], P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
+      QF_TRY(plan_gate_pass(P, pass_sl[g], k));
       QF_CUDA(cudaEventRecord(P->ev_pass[g], P->s_pass));
     }
   }
@@ -560,9 +661,11 @@ int plan_costs_impl(qf_plan* P, double* costs, qf_c128* traces) {
   return QF_OK;
 }
 
-int plan_create_impl(int n, int p, const qf_loc* locs, int S, int prec, qf_plan** out) {
+int plan_create_desc(int n, const std::vector<GateDesc>& gd, long long gsz, int S, int prec,
+                     qf_plan** out) {
   if (!out) return set_error(QF_EINVAL, "out_plan is NULL");
   *out = nullptr;
+  const int p = (int)gd.size();
   QF_TRY(check_sizes(n, p));
   QF_TRY(check_prec(prec));
   if (S < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", S);
@@ -573,16 +676,33 @@ int plan_create_impl(int n, int p, const qf_loc* locs, int S, int prec, qf_plan*
   P->G = S >= 2 ? 2 : 1;
   P->N = (size_t)1 << n;
   P->NN = P->N * P->N;
-  int rc = fetch_locations(locs, n, p, &P->locs);
-  if (rc == QF_OK) rc = plan_ensure_T(P, prec);
+  P->gd = gd;
+  P->gsz = gsz;
+  P->locs.resize(p);
+  for (int k = 0; k < p; ++k) {
+    P->locs[k] = qf_loc{gd[k].q[0], gd[k].q[1]};
+    if (gd[k].k == 3) P->mixed = true;
+  }
+  const int B = qf::env_ctas(n);
+  int rc = plan_ensure_T(P, prec);
   if (rc == QF_OK) rc = P->V.alloc(P->NN * sizeof(double2));
-  if (rc == QF_OK) rc = P->gates.alloc((size_t)S * p * 16 * sizeof(double2));
+  if (rc == QF_OK) rc = P->gates.alloc((size_t)S * gsz * sizeof(double2));
   if (rc == QF_OK) rc = P->LR.alloc((size_t)S * 32 * sizeof(double2));
   if (rc == QF_OK) rc = P->sigma.alloc((size_t)S * sizeof(double));
   if (rc == QF_OK) rc = P->tr.alloc((size_t)S * sizeof(double2));
   if (rc == QF_OK) rc = P->status.alloc(sizeof(int));
-  if (rc == QF_OK) rc = P->part.alloc((size_t)S * qf::env_ctas(n) * 32 * sizeof(double));
+  if (rc == QF_OK) rc = P->part.alloc((size_t)S * B * (P->mixed ? 128 : 32) * sizeof(double));
   if (rc == QF_OK) rc = P->counters.alloc((size_t)S * sizeof(unsigned));
+  if (rc == QF_OK && P->mixed) {
+    rc = P->LR8.alloc((size_t)S * 128 * sizeof(double2));
+    // (k, entry offset) per gate, for the re-unitarisation kernel
+    std::vector<int2> tab(p);
+    for (int k = 0; k < p; ++k) tab[k] = make_int2(gd[k].k, (int)gd[k].off);
+    if (rc == QF_OK) rc = P->gdesc.alloc(sizeof(int2) * p);
+    if (rc == QF_OK && cudaMemcpy(P->gdesc.p, tab.data(), sizeof(int2) * p, cudaMemcpyHostToDevice) !=
+                           cudaSuccess)
+      rc = set_error(QF_ECUDA, "copying the gate table failed");
+  }
   if (rc == QF_OK && (cudaMemset(P->status.p, 0, sizeof(int)) != cudaSuccess ||
                       cudaMemset(P->counters.p, 0, (size_t)S * sizeof(unsigned)) != cudaSuccess))
     rc = set_error(QF_ECUDA, "cudaMemset of the plan's status words failed");
@@ -594,10 +714,22 @@ int plan_create_impl(int n, int p, const qf_loc* locs, int S, int prec, qf_plan*
   return QF_OK;
 }
 
+int plan_create_impl(int n, int p, const qf_loc* locs, int S, int prec, qf_plan** out) {
+  if (!out) return set_error(QF_EINVAL, "out_plan is NULL");
+  *out = nullptr;
+  QF_TRY(check_sizes(n, p));
+  std::vector<qf_loc> l;
+  QF_TRY(fetch_locations(locs, n, p, &l));
+  std::vector<GateDesc> gd;
+  long long gsz = 0;
+  QF_TRY(descs_from_pairs(l, &gd, &gsz));
+  return plan_create_desc(n, gd, gsz, S, prec, out);
+}
+
 int plan_load_impl(qf_plan* P, const qf_c128* target, const qf_c128* gates, cudaStream_t st) {
   P->stream = st;
   if (!target || !gates) return set_error(QF_EINVAL, "target or gates is NULL");
-  const size_t gcount = (size_t)P->S * P->p * 16;
+  const size_t gcount = (size_t)P->S * P->gsz;
   QF_CUDA(cudaMemcpyAsync(P->V.p, target, P->NN * sizeof(double2), cudaMemcpyDefault, st));
   QF_CUDA(cudaMemcpyAsync(P->gates.p, gates, gcount * sizeof(double2), cudaMemcpyDefault, st));
   QF_CUDA(cudaMemsetAsync(P->status.p, 0, sizeof(int), st));
@@ -611,7 +743,11 @@ int plan_load_impl(qf_plan* P, const qf_c128* target, const qf_c128* gates, cuda
 // The periodic reset (Sec. III-A2, reset_iter): re-unitarise every gate in
 // FP64, then rebuild every tensor from V and the gates.
 int plan_reset(qf_plan* P) {
-  QF_CUDA(qf::launch_reunitarize(P->gates.as<double2>(), P->S * P->p, P->stream));
+  if (P->mixed)
+    QF_CUDA(qf::launch_reunitarize_mixed(P->gates.as<double2>(), P->gsz, P->gdesc.as<int2>(), P->p,
+                                         P->S, P->stream));
+  else
+    QF_CUDA(qf::launch_reunitarize(P->gates.as<double2>(), P->S * P->p, P->stream));
   P->all_launches++;
   return plan_build(P);
 }
@@ -730,8 +866,7 @@ int qf_plan_costs(qf_plan* plan, double* out_costs, qf_c128* out_trace) {
 
 int qf_plan_get_gates(qf_plan* plan, qf_c128* out) {
   if (!plan) return set_error(QF_EINVAL, "plan is NULL");
-  QF_TRY(store_output(out, plan->gates.as<double2>(), (size_t)plan->S * plan->p * 16,
-                      plan->stream));
+  QF_TRY(store_output(out, plan->gates.as<double2>(), (size_t)plan->S * plan->gsz, plan->stream));
   QF_CUDA(cudaStreamSynchronize(plan->stream));
   return QF_OK;
 }
@@ -789,14 +924,18 @@ int qf_plan_status(qf_plan* plan) {
 // own plateau.
 constexpr double kStallSwitchCost = 1e-5;
 
-int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
-                      const qf_loc* locations, int n_starts, const qf_c128* initial_gates,
-                      const qf_options* opts, qf_c128* out_gates, double* out_costs,
-                      qf_result* out_result, void* stream) {
+}  // extern "C"
+
+namespace {
+
+int instantiate_core(const qf_c128* target, int n_qubits, const std::vector<GateDesc>& gd,
+                     long long gsz, int n_starts, const qf_c128* initial_gates,
+                     const qf_options* opts, qf_c128* out_gates, double* out_costs,
+                     qf_result* out_result, void* stream) {
   qf_options o;
   qf_options_default(&o);
   if (opts) o = *opts;
-  QF_TRY(check_sizes(n_qubits, n_gates));
+  QF_TRY(check_sizes(n_qubits, (int)gd.size()));
   if (n_starts < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", n_starts);
   if (o.max_sweeps < 1) return set_error(QF_EINVAL, "max_sweeps=%d must be >= 1", o.max_sweeps);
   if (o.precision != QF_C128 && o.precision != QF_C64 && o.precision != QF_C64_REFINE64 &&
@@ -806,7 +945,7 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
     return set_error(QF_EINVAL, "beta=%g outside [0, 1]", o.beta);
   if (!out_gates) return set_error(QF_EINVAL, "out_gates is NULL");
   cudaStream_t st = as_stream(stream);
-  const int S = n_starts, p = n_gates;
+  const int S = n_starts;
 
   PlanGuard g;
   const bool refine = o.precision == QF_C64_REFINE64 || o.precision == QF_C64_REFINE_DF;
@@ -815,7 +954,7 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
                         : o.precision == QF_C64                                   ? QF_C64
                                                                                   : QF_C128;
   const int tensor_prec = refine ? QF_C64 : fine_prec;
-  QF_TRY(plan_create_impl(n_qubits, p, locations, S, tensor_prec, &g.p));
+  QF_TRY(plan_create_desc(n_qubits, gd, gsz, S, tensor_prec, &g.p));
   qf_plan* P = g.p;
   if (refine) {
     // reserve the 16-byte tensor up front so the switch cannot fail late
@@ -905,7 +1044,7 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
   int best = 0;
   for (int s = 1; s < S; ++s)
     if (c[s] < c[best]) best = s;
-  QF_TRY(store_output(out_gates, P->gates.as<double2>(), (size_t)S * p * 16, st));
+  QF_TRY(store_output(out_gates, P->gates.as<double2>(), (size_t)S * gsz, st));
   QF_CUDA(cudaStreamSynchronize(st));
   if (out_costs)
     for (int s = 0; s < S; ++s) out_costs[s] = c[s];
@@ -916,6 +1055,52 @@ int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
     out_result->reason = reason;
     out_result->best_cost = c[best];
   }
+  return QF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qf_instantiate_ex(const qf_c128* target, int n_qubits, int n_gates,
+                      const qf_loc* locations, int n_starts, const qf_c128* initial_gates,
+                      const qf_options* opts, qf_c128* out_gates, double* out_costs,
+                      qf_result* out_result, void* stream) {
+  QF_TRY(check_sizes(n_qubits, n_gates));
+  std::vector<qf_loc> l;
+  QF_TRY(fetch_locations(locations, n_qubits, n_gates, &l));
+  std::vector<GateDesc> gd;
+  long long gsz = 0;
+  QF_TRY(descs_from_pairs(l, &gd, &gsz));
+  return instantiate_core(target, n_qubits, gd, gsz, n_starts, initial_gates, opts, out_gates,
+                          out_costs, out_result, stream);
+}
+
+int qf_instantiate_k(const qf_c128* target, int n_qubits, int n_gates,
+                     const qf_gate_loc* locations, int n_starts, const qf_c128* initial_gates,
+                     const qf_options* opts, qf_c128* out_gates, double* out_costs,
+                     qf_result* out_result, void* stream) {
+  QF_TRY(check_sizes(n_qubits, n_gates));
+  std::vector<GateDesc> gd;
+  long long gsz = 0;
+  QF_TRY(fetch_gate_locs(locations, n_qubits, n_gates, &gd, &gsz));
+  return instantiate_core(target, n_qubits, gd, gsz, n_starts, initial_gates, opts, out_gates,
+                          out_costs, out_result, stream);
+}
+
+int qf_plan_create_k(int n_qubits, int n_gates, const qf_gate_loc* locations, int n_starts,
+                     int precision, qf_plan** out_plan) {
+  if (out_plan) *out_plan = nullptr;
+  QF_TRY(check_sizes(n_qubits, n_gates));
+  std::vector<GateDesc> gd;
+  long long gsz = 0;
+  QF_TRY(fetch_gate_locs(locations, n_qubits, n_gates, &gd, &gsz));
+  return plan_create_desc(n_qubits, gd, gsz, n_starts, precision, out_plan);
+}
+
+int qf_plan_gate_entries(qf_plan* plan, int64_t* entries_per_start) {
+  if (!plan || !entries_per_start) return set_error(QF_EINVAL, "NULL argument");
+  *entries_per_start = plan->gsz;
   return QF_OK;
 }
 
@@ -1188,6 +1373,110 @@ int qf_trace(const void* T, int n_qubits, int n_starts, qf_c128* tr_out, int pre
   QF_CUDA(qf::launch_trace(T, n_qubits, n_starts, reinterpret_cast<double2*>(tr_out),
                            kprec(precision), as_stream(stream)));
   return QF_OK;
+}
+
+// ------------------------------------------------------ k-qubit steps
+
+int qf_apply_gate_k(void* T, int n_qubits, int n_starts, const qf_gate_loc* location,
+                    const qf_c128* L, const qf_c128* R, int precision, void* stream) {
+  QF_TRY(check_sizes(n_qubits, 1));
+  QF_TRY(check_prec(precision));
+  if (n_starts < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", n_starts);
+  if (!T) return set_error(QF_EINVAL, "T is NULL");
+  std::vector<GateDesc> gd;
+  long long gsz = 0;
+  QF_TRY(fetch_gate_locs(location, n_qubits, 1, &gd, &gsz));
+  const auto d = [](const qf_c128* x) { return reinterpret_cast<const double2*>(x); };
+  if (gd[0].k == 3)
+    QF_CUDA(qf::launch_pass8(T, n_qubits, n_starts, gd[0].q, d(L), 64, d(R), 64, kprec(precision),
+                             as_stream(stream)));
+  else
+    QF_CUDA(qf::launch_pass(T, n_qubits, n_starts, gd[0].q[0], gd[0].q[1], d(L), 16, d(R), 16,
+                            kprec(precision), as_stream(stream)));
+  return QF_OK;
+}
+
+int qf_partial_trace_k(const void* T, int n_qubits, int n_starts, const qf_gate_loc* location,
+                       qf_c128* P, int precision, void* stream) {
+  QF_TRY(check_sizes(n_qubits, 1));
+  QF_TRY(check_prec(precision));
+  if (n_starts < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", n_starts);
+  if (!T || !P) return set_error(QF_EINVAL, "NULL device pointer");
+  std::vector<GateDesc> gd;
+  long long gsz = 0;
+  QF_TRY(fetch_gate_locs(location, n_qubits, 1, &gd, &gsz));
+  if (gd[0].k == 2)
+    return qf_partial_trace(T, n_qubits, n_starts, gd[0].q[0], gd[0].q[1], P, precision, stream);
+  cudaStream_t st = as_stream(stream);
+  const size_t part_bytes = (size_t)n_starts * qf::env_ctas(n_qubits) * 128 * sizeof(double);
+  const size_t cnt_bytes = (size_t)n_starts * sizeof(unsigned);
+  void* scratch = nullptr;
+  QF_CUDA(cudaMallocAsync(&scratch, part_bytes + cnt_bytes, st));
+  unsigned* counters = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(scratch) + part_bytes);
+  cudaError_t e = cudaMemsetAsync(counters, 0, cnt_bytes, st);
+  if (e == cudaSuccess)
+    e = qf::launch_update8(T, n_qubits, n_starts, gd[0].q, nullptr, 0, qf::kTraceOnly, 0.0, nullptr,
+                           reinterpret_cast<double2*>(P), 64, nullptr, nullptr,
+                           reinterpret_cast<double*>(scratch), counters, kprec(precision), st);
+  const cudaError_t e2 = cudaFreeAsync(scratch, st);
+  if (e != cudaSuccess) return set_error(QF_ECUDA, "partial trace launch failed: %s", cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return set_error(QF_ECUDA, "cudaFreeAsync failed: %s", cudaGetErrorString(e2));
+  return QF_OK;
+}
+
+int qf_optimize_gates_k(const qf_c128* E, int dim, const qf_c128* u_old, double beta, int count,
+                        qf_c128* u_out, double* sigma_out, void* stream) {
+  if (dim != 4 && dim != 8) return set_error(QF_EINVAL, "dim=%d must be 4 or 8", dim);
+  if (dim == 4) return qf_optimize_gates(E, u_old, beta, count, u_out, sigma_out, stream);
+  if (count < 0) return set_error(QF_EINVAL, "count=%d < 0", count);
+  if (count == 0) return QF_OK;
+  if (!E || !u_out) return set_error(QF_EINVAL, "NULL device pointer");
+  if (beta != 0.0 && !u_old) return set_error(QF_EINVAL, "beta != 0 needs u_old");
+  if (!(beta >= 0.0 && beta <= 1.0)) return set_error(QF_EINVAL, "beta=%g outside [0, 1]", beta);
+  QF_CUDA(qf::launch_optimize8(reinterpret_cast<const double2*>(E),
+                               reinterpret_cast<const double2*>(u_old), beta, count,
+                               reinterpret_cast<double2*>(u_out), sigma_out, as_stream(stream)));
+  return QF_OK;
+}
+
+int qf_init_tensor_k(const qf_c128* target, int n_qubits, int n_gates,
+                     const qf_gate_loc* locations, int n_starts, const qf_c128* gates, void* T,
+                     int precision, void* stream) {
+  QF_TRY(check_sizes(n_qubits, n_gates));
+  QF_TRY(check_prec(precision));
+  if (n_starts < 1) return set_error(QF_EINVAL, "n_starts=%d must be >= 1", n_starts);
+  if (!target || !gates || !T) return set_error(QF_EINVAL, "NULL device pointer");
+  std::vector<GateDesc> gd;
+  long long gsz = 0;
+  QF_TRY(fetch_gate_locs(locations, n_qubits, n_gates, &gd, &gsz));
+  cudaStream_t st = as_stream(stream);
+  const int pr = kprec(precision);
+  const double2* g = reinterpret_cast<const double2*>(gates);
+  QF_CUDA(qf::launch_conj_transpose(reinterpret_cast<const double2*>(target), T, n_qubits, n_starts,
+                                    pr, st));
+  for (int k = 0; k < n_gates; ++k) {
+    if (gd[k].k == 3)
+      QF_CUDA(qf::launch_pass8(T, n_qubits, n_starts, gd[k].q, nullptr, 0, g + gd[k].off, gsz, pr, st));
+    else
+      QF_CUDA(qf::launch_pass(T, n_qubits, n_starts, gd[k].q[0], gd[k].q[1], nullptr, 0, g + gd[k].off,
+                              gsz, pr, st));
+  }
+  return QF_OK;
+}
+
+int qf_circuit_unitary_k(int n_qubits, int n_gates, const qf_gate_loc* locations,
+                         const qf_c128* gates, qf_c128* C_out, void* stream) {
+  QF_TRY(check_sizes(n_qubits, n_gates));
+  if (!gates || !C_out) return set_error(QF_EINVAL, "NULL device pointer");
+  const size_t N = (size_t)1 << n_qubits;
+  cudaStream_t st = as_stream(stream);
+  DevBuf I;
+  QF_TRY(I.alloc(N * N * sizeof(double2)));
+  QF_CUDA(qf::launch_set_identity(I.as<double2>(), n_qubits, st));
+  const int rc = qf_init_tensor_k(reinterpret_cast<const qf_c128*>(I.p), n_qubits, n_gates, locations,
+                                  1, gates, C_out, QF_C128, stream);
+  QF_CUDA(cudaStreamSynchronize(st));
+  return rc;
 }
 
 int qf_circuit_unitary(int n_qubits, int n_gates, const qf_loc* locations, const qf_c128* gates,

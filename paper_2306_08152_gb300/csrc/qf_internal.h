@@ -71,6 +71,24 @@ cudaError_t launch_pair_pass(void* T, int n, int S, const void* params, const do
                              const double2* R1, long long s1, const double2* L2,
                              const double2* R2, long long s2, cudaStream_t st);
 
+// Three-qubit gates (qf_kq.cu).  q: the gate's three qubits in local-index
+// order (q[0] is the most significant local bit).  Operators are 8x8 (64
+// FP64 complex values per start); LR has start stride 128 (L, then R); part
+// needs S * env_ctas(n) * 128 doubles.  Modes as for launch_update.
+cudaError_t launch_pass8(void* T, int n, int S, const int* q, const double2* L, long long Ls,
+                         const double2* R, long long Rs, int prec, cudaStream_t st);
+cudaError_t launch_update8(const void* T, int n, int S, const int* q, double2* gates_k,
+                           long long gstride, int mode, double beta, double2* LR, double2* out,
+                           long long out_stride, double* sigma_out, int* status, double* part,
+                           unsigned* counters, int prec, cudaStream_t st);
+cudaError_t launch_optimize8(const double2* E, const double2* u_old, double beta, int count,
+                             double2* u_out, double* sigma_out, cudaStream_t st);
+cudaError_t launch_reunitarize8(double2* gates, int count, cudaStream_t st);
+// Re-unitarise a mixed circuit: desc[k] = (size 2 or 3, entry offset) of
+// gate k; start s's gates begin at gates + s * gsz.
+cudaError_t launch_reunitarize_mixed(double2* gates, long long gsz, const int2* desc, int p, int S,
+                                     cudaStream_t st);
+
 // u_i = polar update of E_i (Eq. opt_u) for i < count.
 cudaError_t launch_optimize(const double2* E, const double2* u_old, double beta,
                             int count, double2* u_out, double* sigma_out,

@@ -1,0 +1,657 @@
+// Three-qubit gates (k = 3) for the QFactor sweep on sm_103a: the fused
+// pass, the environment with its 8x8 update, and the 8x8 polar.
+//
+// The paper states the method for two-qubit gates and notes that it extends
+// to k-qubit unitaries, whose environment is 2^k x 2^k (Sec. III).  A gate
+// on qubits (q0, q1, q2) touches bit positions p_i = n-1-q_i of the row and
+// column index; its local index is 4*bit(p0) + 2*bit(p1) + bit(p2).  The 64
+// entries that share every other row and column bit form an 8x8 block B,
+// and the fused update of Alg. 1 is B <- L B R, exactly as for 4x4 blocks.
+
+#include <string.h>
+
+#include "qf_device.cuh"
+#include "qf_internal.h"
+
+namespace qf {
+namespace {
+
+using namespace dev;
+
+// ------------------------------------------------------------ warp 8x8 math
+//
+// A warp holds an 8x8 complex matrix with lane l = 8*g + j owning the
+// elements (g, j) and (g + 4, j), g = 0..3, j = 0..7.
+
+struct L8 {
+  int l, g, j;
+  __device__ __forceinline__ L8() {
+    l = threadIdx.x & 31;
+    g = l >> 3;
+    j = l & 7;
+  }
+};
+
+__device__ __forceinline__ int src8(int row, int col) { return ((row & 3) << 3) | col; }
+
+// element (row, col) of the matrix (v0, v1) for every lane; `row` may differ
+// between lanes
+__device__ __forceinline__ double2 get8(double2 v0, double2 v1, int row, int col) {
+  const double2 a = shfl(v0, src8(row, col));
+  const double2 b = shfl(v1, src8(row, col));
+  return row < 4 ? a : b;
+}
+
+__device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// C = A B
+__device__ __forceinline__ void mm8(const L8& L, double2 a0, double2 a1, double2 b0, double2 b1,
+                                    double2& c0, double2& c1) {
+  double2 s0 = make_double2(0.0, 0.0), s1 = s0;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const double2 x0 = shfl(a0, src8(L.g, m)), x1 = shfl(a1, src8(L.g, m));  // A[g][m], A[g+4][m]
+    const double2 bm = m < 4 ? shfl(b0, src8(m, L.j)) : shfl(b1, src8(m, L.j));  // B[m][j]
+    s0 = cfma(x0, bm, s0);
+    s1 = cfma(x1, bm, s1);
+  }
+  c0 = s0;
+  c1 = s1;
+}
+
+// C = A B^dagger
+__device__ __forceinline__ void mm8_nd(const L8& L, double2 a0, double2 a1, double2 b0, double2 b1,
+                                       double2& c0, double2& c1) {
+  double2 s0 = make_double2(0.0, 0.0), s1 = s0;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const double2 x0 = shfl(a0, src8(L.g, m)), x1 = shfl(a1, src8(L.g, m));
+    const double2 bjm = get8(b0, b1, L.j, m);  // B[j][m]
+    const double2 cb = make_double2(bjm.x, -bjm.y);
+    s0 = cfma(x0, cb, s0);
+    s1 = cfma(x1, cb, s1);
+  }
+  c0 = s0;
+  c1 = s1;
+}
+
+// C = A^dagger B
+__device__ __forceinline__ void mm8_dn(const L8& L, double2 a0, double2 a1, double2 b0, double2 b1,
+                                       double2& c0, double2& c1) {
+  double2 s0 = make_double2(0.0, 0.0), s1 = s0;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    // A^dagger[i][m] = conj(A[m][i]) for i = g and g + 4
+    const double2 ami0 = m < 4 ? shfl(a0, src8(m, L.g)) : shfl(a1, src8(m, L.g));
+    const double2 ami1 = m < 4 ? shfl(a0, src8(m, L.g + 4)) : shfl(a1, src8(m, L.g + 4));
+    const double2 bm = m < 4 ? shfl(b0, src8(m, L.j)) : shfl(b1, src8(m, L.j));
+    s0 = cfma(make_double2(ami0.x, -ami0.y), bm, s0);
+    s1 = cfma(make_double2(ami1.x, -ami1.y), bm, s1);
+  }
+  c0 = s0;
+  c1 = s1;
+}
+
+// (v0, v1) <- its conjugate transpose
+__device__ __forceinline__ void dag8(const L8& L, double2& v0, double2& v1) {
+  const double2 t0 = get8(v0, v1, L.j, L.g), t1 = get8(v0, v1, L.j, L.g + 4);
+  v0 = make_double2(t0.x, -t0.y);
+  v1 = make_double2(t1.x, -t1.y);
+}
+
+__device__ __forceinline__ double wmaxd(double v) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, h));
+  return v;
+}
+__device__ __forceinline__ double colsum(double v) {  // over the 4 row groups
+  v += __shfl_xor_sync(kFull, v, 8);
+  v += __shfl_xor_sync(kFull, v, 16);
+  return v;
+}
+
+// Rare path: some singular value is (numerically) zero, so X needs an
+// orthonormal completion.  Lane 0 runs modified Gram-Schmidt in FP64 over
+// the columns of W in order of decreasing singular value, falling back to
+// standard basis vectors.  sm: 128 double2 of shared scratch for this warp.
+static __device__ __noinline__ void complete8(const L8& L, double2 w0, double2 w1, const double* sig,
+                                              double smax, double2* sm, double2& x0, double2& x1) {
+  sm[L.g * 8 + L.j] = w0;
+  sm[(L.g + 4) * 8 + L.j] = w1;
+  __syncwarp();
+  if (L.l == 0) {
+    int ord[8];
+    for (int a = 0; a < 8; ++a) ord[a] = a;
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 7 - a; ++b)
+        if (sig[ord[b]] < sig[ord[b + 1]]) {
+          const int t = ord[b];
+          ord[b] = ord[b + 1];
+          ord[b + 1] = t;
+        }
+    double2* X = sm + 64;
+    bool done[8];
+    for (int a = 0; a < 8; ++a) done[a] = false;
+    for (int e = 0; e < 64; ++e) X[e] = make_double2(0.0, 0.0);
+    for (int oi = 0; oi < 8; ++oi) {
+      const int k = ord[oi];
+      for (int att = 0; att < 9; ++att) {
+        double2 v[8];
+        if (att == 0) {
+          if (!(sig[k] > 1e-12 * smax)) continue;
+          for (int i = 0; i < 8; ++i) v[i] = make_double2(sm[i * 8 + k].x / sig[k], sm[i * 8 + k].y / sig[k]);
+        } else {
+          for (int i = 0; i < 8; ++i) v[i] = make_double2(i == att - 1 ? 1.0 : 0.0, 0.0);
+        }
+        for (int pass = 0; pass < 2; ++pass)  // twice is enough (Kahan)
+          for (int jj = 0; jj < 8; ++jj) {
+            if (!done[jj]) continue;
+            double2 d = make_double2(0.0, 0.0);
+            for (int i = 0; i < 8; ++i) d = cfma_cj(X[i * 8 + jj], v[i], d);
+            for (int i = 0; i < 8; ++i) {
+              const double2 pr = cmuld(d, X[i * 8 + jj]);
+              v[i].x -= pr.x;
+              v[i].y -= pr.y;
+            }
+          }
+        double nv = 0.0;
+        for (int i = 0; i < 8; ++i) nv += v[i].x * v[i].x + v[i].y * v[i].y;
+        nv = sqrt(nv);
+        if (nv > 0.3) {  // among e_0..e_7 one keeps a residual of at least 1/sqrt(8)
+          for (int i = 0; i < 8; ++i) X[i * 8 + k] = make_double2(v[i].x / nv, v[i].y / nv);
+          done[k] = true;
+          break;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  x0 = sm[64 + L.g * 8 + L.j];
+  x1 = sm[64 + (L.g + 4) * 8 + L.j];
+  __syncwarp();
+}
+
+// Warp 8x8 polar update (OptimizeGate, Sec. III-A1, Eq. opt_u): with
+// A = X D Y^dagger, u = Y X^dagger maximises Re Tr(A u).  One-sided Jacobi in
+// FP64 (rotations J with A J = W having orthogonal columns: Y = J, X = W's
+// normalised columns, D = their norms); each sweep pairs column j with
+// j ^ r for r = 1..7, four disjoint pairs per round.  *sig = sum(D).
+// Returns false for a non-finite A.
+static __device__ __noinline__ bool warp_polar8(double2 a0, double2 a1, double2* sm, double2* u0,
+                                                double2* u1, double* sig) {
+  const L8 L;
+  const bool fin = __all_sync(kFull, isfinite(a0.x) && isfinite(a0.y) && isfinite(a1.x) && isfinite(a1.y));
+  if (!fin) return false;
+  const double amax = wmaxd(fmax(fmax(fabs(a0.x), fabs(a0.y)), fmax(fabs(a1.x), fabs(a1.y))));
+  if (amax == 0.0) {  // A = 0: every unitary is optimal
+    *u0 = make_double2(L.g == L.j ? 1.0 : 0.0, 0.0);
+    *u1 = make_double2(L.g + 4 == L.j ? 1.0 : 0.0, 0.0);
+    *sig = 0.0;
+    return true;
+  }
+  const double sc = 1.0 / amax;
+  double2 w0 = make_double2(a0.x * sc, a0.y * sc), w1 = make_double2(a1.x * sc, a1.y * sc);
+  double2 y0 = make_double2(L.g == L.j ? 1.0 : 0.0, 0.0), y1 = make_double2(L.g + 4 == L.j ? 1.0 : 0.0, 0.0);
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    double off = 0.0;
+    for (int r = 1; r <= 7; ++r) {
+      const int q = L.j ^ r;
+      const bool isP = L.j < q;
+      const int src = L.l ^ r;
+      const double2 wq0 = shfl(w0, src), wq1 = shfl(w1, src);
+      const double2 yq0 = shfl(y0, src), yq1 = shfl(y1, src);
+      const double n2 = colsum(w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y);
+      const double n2q = __shfl_sync(kFull, n2, src);
+      const double2 cp0 = isP ? w0 : wq0, cq0 = isP ? wq0 : w0;
+      const double2 cp1 = isP ? w1 : wq1, cq1 = isP ? wq1 : w1;
+      // g = conj(W[:,p]) . W[:,q]
+      const double gx = colsum(cp0.x * cq0.x + cp0.y * cq0.y + cp1.x * cq1.x + cp1.y * cq1.y);
+      const double gy = colsum(cp0.x * cq0.y - cp0.y * cq0.x + cp1.x * cq1.y - cp1.y * cq1.x);
+      const double al = isP ? n2 : n2q, be = isP ? n2q : n2;
+      const double gm = hypot(gx, gy);
+      const double nrm = sqrt(al) * sqrt(be);
+      if (gm > 1e-15 * nrm && fmax(al, be) > 1e-200) {
+        off = fmax(off, gm / nrm);
+        const double zeta = 0.5 * (be - al) / gm;
+        const double t = copysign(1.0 / (fabs(zeta) + sqrt(1.0 + zeta * zeta)), zeta);
+        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        const double2 e = make_double2(gx / gm, -gy / gm);  // conj(g) / |g|
+        if (isP) {  // W[:,p] <- c W[:,p] - s e W[:,q]
+          const double2 e0 = cmuld(e, wq0), e1 = cmuld(e, wq1), f0 = cmuld(e, yq0), f1 = cmuld(e, yq1);
+          w0 = make_double2(c * w0.x - sn * e0.x, c * w0.y - sn * e0.y);
+          w1 = make_double2(c * w1.x - sn * e1.x, c * w1.y - sn * e1.y);
+          y0 = make_double2(c * y0.x - sn * f0.x, c * y0.y - sn * f0.y);
+          y1 = make_double2(c * y1.x - sn * f1.x, c * y1.y - sn * f1.y);
+        } else {  // W[:,q] <- s W[:,p] + c e W[:,q]
+          const double2 e0 = cmuld(e, w0), e1 = cmuld(e, w1), f0 = cmuld(e, y0), f1 = cmuld(e, y1);
+          w0 = make_double2(sn * wq0.x + c * e0.x, sn * wq0.y + c * e0.y);
+          w1 = make_double2(sn * wq1.x + c * e1.x, sn * wq1.y + c * e1.y);
+          y0 = make_double2(sn * yq0.x + c * f0.x, sn * yq0.y + c * f0.y);
+          y1 = make_double2(sn * yq1.x + c * f1.x, sn * yq1.y + c * f1.y);
+        }
+      }
+    }
+    if (wmaxd(off) < 1e-15) break;
+  }
+  const double sj = sqrt(colsum(w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y));
+  double s8[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s8[k] = __shfl_sync(kFull, sj, k);
+  double smax = 0.0, smin = s8[0], ssum = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    smax = fmax(smax, s8[k]);
+    smin = fmin(smin, s8[k]);
+    ssum += s8[k];
+  }
+  double2 x0, x1;
+  if (smin > 1e-10 * smax) {
+    x0 = make_double2(w0.x / sj, w0.y / sj);
+    x1 = make_double2(w1.x / sj, w1.y / sj);
+  } else {
+    complete8(L, w0, w1, s8, smax, sm, x0, x1);
+  }
+  mm8_nd(L, y0, y1, x0, x1, *u0, *u1);  // Y X^dagger
+  *sig = ssum * amax;
+  return __all_sync(kFull, isfinite(u0->x) && isfinite(u0->y) && isfinite(u1->x) && isfinite(u1->y));
+}
+
+// ------------------------------------------------------------------ pass
+//
+// B <- L B R on every 8x8 block.  A warp handles 4 blocks; lane 4x + b holds
+// row x of block b (consecutive blocks take consecutive column rest
+// indices, so a warp access covers 4 adjacent columns of 8 rows).  R acts
+// along the row in registers; the rows then go through a padded per-warp
+// shared buffer so that lane 4y + b takes column y for L, and writes it.
+
+constexpr int kPass8Threads = 256;
+constexpr int kBlkStride = 8 * 9 + 4;  // padded 8x8 block in the transpose buffer
+
+template <typename R, bool HL, bool HR>
+__global__ void __launch_bounds__(kPass8Threads)
+pass8_kernel(typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, int p2,
+             const double2* __restrict__ L, long long Ls, const double2* __restrict__ Rm,
+             long long Rs) {
+  typedef typename Cplx<R>::T C;
+  __shared__ C sL[64], sR[64];
+  __shared__ C buf[kPass8Threads / 32][4 * kBlkStride];
+  const int s = blockIdx.y;
+  if (threadIdx.x < 64) {
+    if (HL) sL[threadIdx.x] = cmake(L[s * Ls + threadIdx.x], R());
+    if (HR) sR[threadIdx.x] = cmake(Rm[s * Rs + threadIdx.x], R());
+  }
+  __syncthreads();
+  const unsigned N = 1u << n;
+  int q[3] = {p0, p1, p2};  // ascending for the deposit
+  if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
+  if (q[1] > q[2]) { const int t = q[1]; q[1] = q[2]; q[2] = t; }
+  if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
+  unsigned off[8];
+#pragma unroll
+  for (int x = 0; x < 8; ++x)
+    off[x] = (((unsigned)x >> 2) & 1u) << p0 | (((unsigned)x >> 1) & 1u) << p1 | ((unsigned)x & 1u) << p2;
+  const int lnc = n - 3;
+  const unsigned cmask = (1u << lnc) - 1u;
+  const unsigned nblk = 1u << (2 * lnc);
+  C* __restrict__ Ts = T + (size_t)s * N * N;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = lane & 3, x = lane >> 2;
+  C* wb = buf[w];
+  const unsigned warps = gridDim.x * (kPass8Threads / 32);
+  for (unsigned grp = blockIdx.x * (kPass8Threads / 32) + w; grp * 4u < nblk; grp += warps) {
+    const unsigned blk = grp * 4u + (unsigned)b;
+    const bool valid = blk < nblk;
+    const unsigned r0 = dep1(dep1(dep1(blk >> lnc, q[0]), q[1]), q[2]);
+    const unsigned c0 = dep1(dep1(dep1(blk & cmask, q[0]), q[1]), q[2]);
+    C row[8];
+    if (valid) {
+      const C* src = Ts + (size_t)(r0 | off[x]) * N + c0;
+#pragma unroll
+      for (int y = 0; y < 8; ++y) row[y] = src[off[y]];
+    } else {
+#pragma unroll
+      for (int y = 0; y < 8; ++y) row[y] = czero<C>();
+    }
+    if (HR) {  // row <- row R
+      C t[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        C acc = czero<C>();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc = cfma(row[k], sR[k * 8 + c], acc);
+        t[c] = cfinish(acc);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) row[c] = t[c];
+    }
+    if (HL) {
+#pragma unroll
+      for (int y = 0; y < 8; ++y) wb[b * kBlkStride + x * 9 + y] = row[y];
+      __syncwarp();
+      const int y = x;  // this lane now takes column y of block b
+      C col[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) col[k] = wb[b * kBlkStride + k * 9 + y];
+      __syncwarp();  // the buffer is rewritten by the next group
+      if (valid) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          C acc = czero<C>();
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc = cfma(sL[r * 8 + k], col[k], acc);
+          Ts[(size_t)(r0 | off[r]) * N + (c0 | off[y])] = cfinish(acc);
+        }
+      }
+    } else if (valid) {
+      C* dst = Ts + (size_t)(r0 | off[x]) * N + c0;
+#pragma unroll
+      for (int y = 0; y < 8; ++y) dst[off[y]] = row[y];
+    }
+  }
+}
+
+// ------------------------------------------------------------ environment
+//
+// P[x][y] = sum over the 2^(n-3) rests r of T[(r, x), (r, y)], from the
+// tensor before the gate's removal (E = P u^dagger backward, u^dagger P
+// forward), as for two-qubit gates.  Items are (rest, x); a thread sums its
+// items' 8 entries y in the tensor's accumulation precision, the warp folds
+// its 4 rests per x with two shuffles, the CTA adds its warps in order and
+// writes 128 partial sums; the last CTA of the start (atomic ticket) adds
+// the CTAs' partials in a fixed order and runs the 8x8 update on one warp.
+
+constexpr int kEnv8Threads = 256;
+
+template <typename R>
+__global__ void __launch_bounds__(kEnv8Threads)
+env8_kernel(const typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, int p2, int mode,
+            double2* __restrict__ gates_k, long long gstride, double beta, double2* __restrict__ LR,
+            double2* __restrict__ out, long long out_stride, double* __restrict__ sigma_out,
+            int* __restrict__ status, double* __restrict__ part, unsigned* __restrict__ counters) {
+  using CT = typename Cplx<R>::T;
+  using Ar = typename Acc<R>::T;
+  __shared__ double red[kEnv8Threads / 32][8][16];
+  __shared__ double2 sm[160];  // P, then the polar's scratch
+  __shared__ bool is_last;
+  const int s = blockIdx.y, B = gridDim.x, bb = blockIdx.x;
+  const unsigned N = 1u << n;
+  int q[3] = {p0, p1, p2};
+  if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
+  if (q[1] > q[2]) { const int t = q[1]; q[1] = q[2]; q[2] = t; }
+  if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
+  unsigned off[8];
+#pragma unroll
+  for (int x = 0; x < 8; ++x)
+    off[x] = (((unsigned)x >> 2) & 1u) << p0 | (((unsigned)x >> 1) & 1u) << p1 | ((unsigned)x & 1u) << p2;
+  const unsigned items = N;  // 2^(n-3) rests x 8 rows
+  const unsigned chunk = ((items / 8u + B - 1) / B) * 8u;  // whole rests per CTA
+  const unsigned i_beg = bb * chunk;
+  const unsigned i_end = min(items, i_beg + chunk);
+  const CT* Ts = T + (size_t)s * N * N;
+  Ar v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = Ar(0);
+  const int x = threadIdx.x & 7;  // blockDim and chunk are multiples of 8
+  for (unsigned it = i_beg + threadIdx.x; it < i_end; it += blockDim.x) {
+    const unsigned d = dep1(dep1(dep1(it >> 3, q[0]), q[1]), q[2]);
+    const CT* rowp = Ts + (size_t)(d | off[x]) * N + d;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+      const auto e = to_acc(rowp[off[y]]);
+      v[2 * y] += e.x;
+      v[2 * y + 1] += e.y;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    v[i] += __shfl_xor_sync(kFull, v[i], 8);
+    v[i] += __shfl_xor_sync(kFull, v[i], 16);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane < 8)
+#pragma unroll
+    for (int i = 0; i < 16; ++i) red[wid][lane][i] = (double)v[i];
+  __syncthreads();
+  if (threadIdx.x < 128) {
+    const int xx = threadIdx.x >> 4, c = threadIdx.x & 15;
+    double acc = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) acc += red[k][xx][c];
+    part[((size_t)s * B + bb) * 128 + threadIdx.x] = acc;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned ticket = atomicAdd(&counters[s], 1u);
+    is_last = (ticket == (unsigned)B - 1u);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  if (threadIdx.x < 128) {  // P[x][y] component c = 2y (+1 for the imaginary part)
+    double acc = 0.0;
+    for (int k = 0; k < B; ++k) acc += __ldcg(&part[((size_t)s * B + k) * 128 + threadIdx.x]);
+    reinterpret_cast<double*>(sm)[threadIdx.x] = acc;
+  }
+  if (threadIdx.x == 0) counters[s] = 0u;
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const L8 L;
+  const double2 P0 = sm[L.g * 8 + L.j], P1 = sm[(L.g + 4) * 8 + L.j];
+  __syncwarp();
+  if (mode == kTraceOnly) {
+    out[s * out_stride + L.g * 8 + L.j] = P0;
+    out[s * out_stride + (L.g + 4) * 8 + L.j] = P1;
+    return;
+  }
+  double2 u0 = gates_k[s * gstride + L.g * 8 + L.j], u1 = gates_k[s * gstride + (L.g + 4) * 8 + L.j];
+  double2 E0, E1;
+  if (mode == kForward)
+    mm8_dn(L, u0, u1, P0, P1, E0, E1);  // u^dagger P
+  else
+    mm8_nd(L, P0, P1, u0, u1, E0, E1);  // P u^dagger
+  if (out) {
+    out[s * out_stride + L.g * 8 + L.j] = E0;
+    out[s * out_stride + (L.g + 4) * 8 + L.j] = E1;
+  }
+  double2 ud0 = u0, ud1 = u1;
+  dag8(L, ud0, ud1);
+  double2* lr = LR + (size_t)s * 128;
+  if (mode == kEnvOnly) {
+    lr[L.g * 8 + L.j] = u0;
+    lr[(L.g + 4) * 8 + L.j] = u1;
+    lr[64 + L.g * 8 + L.j] = ud0;
+    lr[64 + (L.g + 4) * 8 + L.j] = ud1;
+    return;
+  }
+  double2 A0 = E0, A1 = E1;
+  if (beta != 0.0) {
+    A0 = make_double2((1.0 - beta) * E0.x + beta * ud0.x, (1.0 - beta) * E0.y + beta * ud0.y);
+    A1 = make_double2((1.0 - beta) * E1.x + beta * ud1.x, (1.0 - beta) * E1.y + beta * ud1.y);
+  }
+  double2 n0, n1;
+  double sg = 0.0;
+  if (!warp_polar8(A0, A1, sm, &n0, &n1, &sg)) {
+    if (L.l == 0) atomicExch(status, -4);
+    n0 = u0;  // keep the old gate: the tensor stays consistent
+    n1 = u1;
+    sg = 0.0;
+  }
+  gates_k[s * gstride + L.g * 8 + L.j] = n0;
+  gates_k[s * gstride + (L.g + 4) * 8 + L.j] = n1;
+  const bool bwd = mode == kBackward;
+  lr[L.g * 8 + L.j] = bwd ? n0 : ud0;
+  lr[(L.g + 4) * 8 + L.j] = bwd ? n1 : ud1;
+  lr[64 + L.g * 8 + L.j] = bwd ? ud0 : n0;
+  lr[64 + (L.g + 4) * 8 + L.j] = bwd ? ud1 : n1;
+  if (sigma_out && L.l == 0) sigma_out[s] = sg;
+}
+
+// One warp per 8x8 matrix.
+__global__ void __launch_bounds__(128) optimize8_kernel(const double2* __restrict__ E,
+                                                        const double2* __restrict__ u_old,
+                                                        double beta, int count,
+                                                        double2* __restrict__ u_out,
+                                                        double* __restrict__ sigma_out) {
+  __shared__ double2 sm[4][128];
+  const int wid = threadIdx.x >> 5;
+  const int m = blockIdx.x * 4 + wid;
+  if (m >= count) return;  // whole warps leave together
+  const L8 L;
+  const double2* e = E + (size_t)m * 64;
+  double2 a0 = e[L.g * 8 + L.j], a1 = e[(L.g + 4) * 8 + L.j];
+  if (beta != 0.0) {
+    double2 d0 = u_old[(size_t)m * 64 + L.g * 8 + L.j], d1 = u_old[(size_t)m * 64 + (L.g + 4) * 8 + L.j];
+    dag8(L, d0, d1);
+    a0 = make_double2((1.0 - beta) * a0.x + beta * d0.x, (1.0 - beta) * a0.y + beta * d0.y);
+    a1 = make_double2((1.0 - beta) * a1.x + beta * d1.x, (1.0 - beta) * a1.y + beta * d1.y);
+  }
+  double2 u0, u1;
+  double sg;
+  if (!warp_polar8(a0, a1, sm[wid], &u0, &u1, &sg)) {
+    u0 = u1 = make_double2(NAN, NAN);
+    sg = NAN;
+  }
+  u_out[(size_t)m * 64 + L.g * 8 + L.j] = u0;
+  u_out[(size_t)m * 64 + (L.g + 4) * 8 + L.j] = u1;
+  if (sigma_out && L.l == 0) sigma_out[m] = sg;
+}
+
+// Three FP64 Newton-Schulz steps u <- u (3I - u^dagger u) / 2 per 8x8 gate.
+__global__ void __launch_bounds__(128) reunitarize8_kernel(double2* __restrict__ gates, int count) {
+  const int m = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (m >= count) return;
+  const L8 L;
+  double2* gp = gates + (size_t)m * 64;
+  double2 u0 = gp[L.g * 8 + L.j], u1 = gp[(L.g + 4) * 8 + L.j];
+  for (int step = 0; step < 3; ++step) {
+    double2 P0, P1;
+    mm8_dn(L, u0, u1, u0, u1, P0, P1);
+    const double2 Q0 = make_double2((L.g == L.j ? 1.5 : 0.0) - 0.5 * P0.x, -0.5 * P0.y);
+    const double2 Q1 = make_double2((L.g + 4 == L.j ? 1.5 : 0.0) - 0.5 * P1.x, -0.5 * P1.y);
+    mm8(L, u0, u1, Q0, Q1, u0, u1);
+  }
+  gp[L.g * 8 + L.j] = u0;
+  gp[(L.g + 4) * 8 + L.j] = u1;
+}
+
+// Re-unitarisation of a circuit with 4x4 and 8x8 gates: warp m takes gate
+// m % p of start m / p; desc[k] = (size, entry offset); three FP64
+// Newton-Schulz steps each.
+__global__ void __launch_bounds__(128) reunitarize_mixed_kernel(double2* __restrict__ gates, long long gsz,
+                                                                const int2* __restrict__ desc, int p,
+                                                                int count) {
+  const int m = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (m >= count) return;  // whole warps leave together
+  const int s = m / p, k = m % p;
+  const int2 d = desc[k];
+  double2* gp = gates + (size_t)s * gsz + d.y;
+  if (d.x == 3) {
+    const L8 L;
+    double2 u0 = gp[L.g * 8 + L.j], u1 = gp[(L.g + 4) * 8 + L.j];
+    for (int step = 0; step < 3; ++step) {
+      double2 P0, P1;
+      mm8_dn(L, u0, u1, u0, u1, P0, P1);
+      const double2 Q0 = make_double2((L.g == L.j ? 1.5 : 0.0) - 0.5 * P0.x, -0.5 * P0.y);
+      const double2 Q1 = make_double2((L.g + 4 == L.j ? 1.5 : 0.0) - 0.5 * P1.x, -0.5 * P1.y);
+      mm8(L, u0, u1, Q0, Q1, u0, u1);
+    }
+    gp[L.g * 8 + L.j] = u0;
+    gp[(L.g + 4) * 8 + L.j] = u1;
+  } else {
+    const Lane L;
+    const int e = L.l & 15;
+    double2 u = gp[e];
+    for (int step = 0; step < 3; ++step) {
+      const double2 P = wmm_dn(L, u, u);
+      const double2 Q = make_double2((L.i == L.j ? 1.5 : 0.0) - 0.5 * P.x, -0.5 * P.y);
+      u = wmm(L, u, Q);
+    }
+    if (L.l < 16) gp[e] = u;
+  }
+}
+
+template <typename R, bool HL, bool HR>
+void pass8_launch(void* T, int n, int S, int p0, int p1, int p2, const double2* L, long long Ls,
+                  const double2* Rm, long long Rs, cudaStream_t st) {
+  typedef typename Cplx<R>::T C;
+  const long long groups = ((1ll << (2 * (n - 3))) + 3) / 4;
+  const long long want = (groups + 7) / 8;
+  long long cap = ((long long)sm_count() * 4 + S - 1) / S;
+  if (cap < 1) cap = 1;
+  dim3 grid((unsigned)(want < cap ? want : cap), S);
+  pass8_kernel<R, HL, HR><<<grid, kPass8Threads, 0, st>>>((C*)T, n, p0, p1, p2, L, Ls, Rm, Rs);
+}
+
+template <typename R>
+void pass8_ops(void* T, int n, int S, int p0, int p1, int p2, const double2* L, long long Ls,
+               const double2* Rm, long long Rs, cudaStream_t st) {
+  if (L && Rm)
+    pass8_launch<R, true, true>(T, n, S, p0, p1, p2, L, Ls, Rm, Rs, st);
+  else if (L)
+    pass8_launch<R, true, false>(T, n, S, p0, p1, p2, L, Ls, Rm, Rs, st);
+  else if (Rm)
+    pass8_launch<R, false, true>(T, n, S, p0, p1, p2, L, Ls, Rm, Rs, st);
+}
+
+}  // namespace
+
+// ================================================================ launchers
+
+cudaError_t launch_pass8(void* T, int n, int S, const int* q, const double2* L, long long Ls,
+                         const double2* R, long long Rs, int prec, cudaStream_t st) {
+  if (!L && !R) return cudaSuccess;
+  const int p0 = qubit_bit(n, q[0]), p1 = qubit_bit(n, q[1]), p2 = qubit_bit(n, q[2]);
+  if (prec == 0)
+    pass8_ops<double>(T, n, S, p0, p1, p2, L, Ls, R, Rs, st);
+  else if (prec == 2)
+    pass8_ops<DF>(T, n, S, p0, p1, p2, L, Ls, R, Rs, st);
+  else
+    pass8_ops<float>(T, n, S, p0, p1, p2, L, Ls, R, Rs, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update8(const void* T, int n, int S, const int* q, double2* gates_k,
+                           long long gstride, int mode, double beta, double2* LR, double2* out,
+                           long long out_stride, double* sigma_out, int* status, double* part,
+                           unsigned* counters, int prec, cudaStream_t st) {
+  const int p0 = qubit_bit(n, q[0]), p1 = qubit_bit(n, q[1]), p2 = qubit_bit(n, q[2]);
+  dim3 grid(env_ctas(n), S);
+  if (prec == 0)
+    env8_kernel<double><<<grid, kEnv8Threads, 0, st>>>((const double2*)T, n, p0, p1, p2, mode, gates_k,
+                                                       gstride, beta, LR, out, out_stride, sigma_out,
+                                                       status, part, counters);
+  else if (prec == 2)
+    env8_kernel<DF><<<grid, kEnv8Threads, 0, st>>>((const dfc*)T, n, p0, p1, p2, mode, gates_k, gstride,
+                                                   beta, LR, out, out_stride, sigma_out, status, part,
+                                                   counters);
+  else
+    env8_kernel<float><<<grid, kEnv8Threads, 0, st>>>((const float2*)T, n, p0, p1, p2, mode, gates_k,
+                                                      gstride, beta, LR, out, out_stride, sigma_out,
+                                                      status, part, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_optimize8(const double2* E, const double2* u_old, double beta, int count,
+                             double2* u_out, double* sigma_out, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  optimize8_kernel<<<(count + 3) / 4, 128, 0, st>>>(E, u_old, beta, count, u_out, sigma_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reunitarize_mixed(double2* gates, long long gsz, const int2* desc, int p, int S,
+                                     cudaStream_t st) {
+  const int count = p * S;
+  if (count <= 0) return cudaSuccess;
+  reunitarize_mixed_kernel<<<(count + 3) / 4, 128, 0, st>>>(gates, gsz, desc, p, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reunitarize8(double2* gates, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  reunitarize8_kernel<<<(count + 3) / 4, 128, 0, st>>>(gates, count);
+  return cudaGetLastError();
+}
+
+}  // namespace qf
