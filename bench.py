@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--batch-instances", type=int, default=4096)
     ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--no-lookahead", action="store_true")
+    ap.add_argument("--no-kqubit", action="store_true")
     return ap.parse_args()
 
 
@@ -491,6 +492,55 @@ def run_lookahead(args, qf, torch, dev, inst, V, starts, one_update_costs):
                                                                np.asarray(one_update_costs))))}
 
 
+def run_kqubit(args, qf, torch, dev):
+    """Three-qubit gates: 12 qubits, layers of gates on consecutive triples
+    (offsets 0, 1, 2 in turn, 20 gates), 8 starts, complex64 tensors, one
+    sweep per step; the 8x8 pass reads and writes the tensor once per update."""
+    n, S = 12, 8
+    locs = []
+    for layer in range(6):
+        o = layer % 3
+        locs += [(q, q + 1, q + 2) for q in range(o, n - 2, 3)]
+    gen = qi.rng(SEED + 33)
+    tgt = [qi.haar_unitary(8, gen) for _ in locs]
+    V = qf.circuit_unitary_k(n, locs, tgt, device=dev)
+    starts = qf.flatten_gates([[qi.haar_unitary(8, qi.rng(SEED + 34 + s)) for _ in locs]
+                               for s in range(S)]).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = qf.Plan(n, locs, S, qf.QF_C64)
+    plan.load(V, starts, stream=stream)
+    plan.sweep(2, reset_iter=0)
+    plan.costs()
+    plan.pass_stats()
+    plan.enable_pass_timing(True)
+    steps = 5
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.sweep(steps, reset_iter=0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pass_ms, launches, _, pbytes = plan.pass_stats()
+    costs = plan.costs()
+    plan.close()
+    peak, peak_kind = measured_peaks()
+    avg_s = (pass_ms / 1e3) / max(launches, 1)
+    alg = pbytes / max(launches, 1)
+    achieved = alg / avg_s / 1e9
+    updates = S * 2 * len(locs) * steps
+    return {"metric": "gate-updates/s at 12 qubits, three-qubit gates, complex64",
+            "unit": "gate-updates/s", "value": updates / (ms / 1e3), "ms_per_sweep": ms / steps,
+            "workload": f"12 qubits, {len(locs)} three-qubit gates on consecutive triples (6 layers, "
+                        "offsets 0/1/2), 8 starts, reachable Haar target, complex64 tensor, FP64 8x8 update",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "kernel": "pass8_kernel (B <- L B R on 8x8 blocks)",
+                         "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                         "alg_bytes_per_launch": alg, "avg_launch_ms": avg_s * 1e3,
+                         "pass_share_of_step": pass_ms / ms if ms > 0 else None},
+            "final_costs": [float(c) for c in costs]}
+
+
 def run_configs(args, qf, torch, dev):
     """Correctness and time per sweep of the smaller workloads:
     3-qubit alternating circuit (6 U(4) gates, 1 start, to 1e-10 or 500
@@ -706,6 +756,9 @@ def run_ours(args):
                        "allocation, H2D, InitCircuitTensor, one sweep, D2H"}
         del r
 
+    kqubit = None
+    if not args.no_kqubit and world == 1:
+        kqubit = run_kqubit(args, qf, torch, dev)
     lookahead = None
     if not args.no_lookahead and args.precision == "c64" and n >= 8 and world == 1:
         lookahead = run_lookahead(args, qf, torch, dev, inst, V, starts, costs)
@@ -738,7 +791,7 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(all_launches), "clocks": clock_info,
             "ms_per_step_graph": ms_graph,
-            "lookahead": lookahead, "c128": extra_c128, "df64": extra_df64, "batched": batched, "configs": configs,
+            "lookahead": lookahead, "kqubit": kqubit, "c128": extra_c128, "df64": extra_df64, "batched": batched, "configs": configs,
             "final_costs": [float(c) for c in costs],
         }
         print(json.dumps(line))
