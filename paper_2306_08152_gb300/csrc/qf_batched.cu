@@ -50,6 +50,7 @@ struct BatchParams {
   const int2* locs;
   const double2* targets;
   double2* gates;
+  float2* yprev;  // per gate entry: the last Jacobi rotation (warm start of the next update)
   double* cost_out;
   int* sweeps_out;
   int* c64_out;
@@ -66,9 +67,10 @@ struct BatchParams {
 
 // One out-of-line copy of the warp polar for the whole kernel: inlined at
 // every call site of both precisions the kernel outgrew the instruction cache.
-__device__ __noinline__ bool polar_once(double2 a, float2* scratch, double2* u_out, double* sig) {
+__device__ __noinline__ bool polar_once(double2 a, float2* scratch, double2* u_out, double* sig,
+                                        float2* y_io) {
   const Lane L;
-  return warp_polar(L, a, scratch, u_out, sig);
+  return warp_polar(L, a, scratch, u_out, sig, y_io);
 }
 
 template <typename R>
@@ -208,7 +210,8 @@ struct W {
 
   // One gate update: environment from the band, the FP64 warp polar, the
   // pass operators into shared memory, then the fused pass.
-  static __device__ __noinline__ void update(C* T, C* LRs, float2* scratch, double2* g, int2 lc,
+  static __device__ __noinline__ void update(C* T, C* LRs, float2* scratch, double2* g, float2* yp,
+                                             int2 lc,
                                              int n,
                                 bool forward, double beta, const Lane& L, int* bad) {
     const int pa = n - 1 - lc.x, pb = n - 1 - lc.y;
@@ -222,12 +225,15 @@ struct W {
       A = make_double2((1.0 - beta) * E.x + beta * ud.x, (1.0 - beta) * E.y + beta * ud.y);
     double2 un;
     double sg;
-    if (!polar_once(A, scratch, &un, &sg)) {
+    float2 y = yp[e];  // the gate's last Jacobi rotation: a warm start
+    if (!polar_once(A, scratch, &un, &sg, &y)) {
       *bad = 1;
       un = u;
+      y = make_float2(L.i == L.j ? 1.f : 0.f, 0.f);
     }
     if (L.l < 16) {
       g[e] = un;
+      yp[e] = y;
       LRs[e] = cmake(forward ? ud : un, R());
       LRs[16 + e] = cmake(forward ? un : ud, R());
     }
@@ -236,13 +242,13 @@ struct W {
   }
 
   // TwoSidedSweep (Alg. 1).
-  static __device__ __noinline__ void sweep(C* T, C* LRs, float2* scratch, double2* g,
+  static __device__ __noinline__ void sweep(C* T, C* LRs, float2* scratch, double2* g, float2* yp,
                                             const int2* locs,
                                int n, int p, double beta, const Lane& L, int* bad) {
     for (int k = p - 1; k >= 0; --k)
-      update(T, LRs, scratch, g + k * 16, locs[k], n, false, beta, L, bad);
+      update(T, LRs, scratch, g + k * 16, yp + k * 16, locs[k], n, false, beta, L, bad);
     for (int k = 0; k < p; ++k)
-      update(T, LRs, scratch, g + k * 16, locs[k], n, true, beta, L, bad);
+      update(T, LRs, scratch, g + k * 16, yp + k * 16, locs[k], n, true, beta, L, bad);
   }
 };
 
@@ -300,6 +306,10 @@ __global__ void batched_kernel(BatchParams bp) {
     const BatchInst in = bp.inst[i];
     const int n = in.n, p = in.p;
     double2* g = bp.gates + in.gate_off + (long long)s * p * 16;
+    float2* yp = bp.yprev + in.gate_off + (long long)s * p * 16;
+    if (L.l < 16)
+      for (int k = 0; k < p; ++k) yp[k * 16 + L.l] = make_float2(L.i == L.j ? 1.f : 0.f, 0.f);
+    __syncwarp();
     const double2* V = bp.targets + in.tgt_off;
     const int2* locs = bp.locs + in.loc_off;
     volatile int* conv = bp.conv_flag + i;
@@ -326,9 +336,9 @@ __global__ void batched_kernel(BatchParams bp) {
         break;
       }
       if (c64)
-        W<float>::sweep((float2*)Tbuf, LRf, scratch, g, locs, n, p, bp.beta, L, &bad);
+        W<float>::sweep((float2*)Tbuf, LRf, scratch, g, yp, locs, n, p, bp.beta, L, &bad);
       else
-        W<double>::sweep((double2*)Tbuf, LRd, scratch, g, locs, n, p, bp.beta, L, &bad);
+        W<double>::sweep((double2*)Tbuf, LRd, scratch, g, yp, locs, n, p, bp.beta, L, &bad);
       if (bp.reset_iter > 0 && it % bp.reset_iter == 0) {
         reunitarize(g, p, L);
         if (c64)
@@ -518,12 +528,13 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     return ((long long)inst[x].p << (2 * inst[x].n)) > ((long long)inst[y].p << (2 * inst[y].n));
   });
-  DevMem d_inst, d_order, d_locs, d_tgt, d_gates, d_cost, d_sw, d_c64, d_reason, d_flags;
+  DevMem d_inst, d_order, d_locs, d_tgt, d_gates, d_yprev, d_cost, d_sw, d_c64, d_reason, d_flags;
   if (d_inst.alloc(sizeof(BatchInst) * n_instances) != cudaSuccess ||
       d_order.alloc(sizeof(int) * n_instances) != cudaSuccess ||
       d_locs.alloc(sizeof(qf_loc) * loc_total) != cudaSuccess ||
       d_tgt.alloc(sizeof(double2) * tgt_total) != cudaSuccess ||
       d_gates.alloc(sizeof(double2) * gate_total) != cudaSuccess ||
+      d_yprev.alloc(sizeof(float2) * gate_total) != cudaSuccess ||
       d_cost.alloc(sizeof(double) * problems) != cudaSuccess ||
       d_sw.alloc(sizeof(int) * problems) != cudaSuccess ||
       d_c64.alloc(sizeof(int) * problems) != cudaSuccess ||
@@ -551,6 +562,7 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
   bp.locs = (const int2*)d_locs.p;
   bp.targets = (const double2*)d_tgt.p;
   bp.gates = (double2*)d_gates.p;
+  bp.yprev = (float2*)d_yprev.p;
   bp.cost_out = (double*)d_cost.p;
   bp.sweeps_out = (int*)d_sw.p;
   bp.c64_out = (int*)d_c64.p;

@@ -208,6 +208,40 @@ __device__ __forceinline__ C2 wmm_nd(const Lane& L, C2 a, C2 b) {
   for (int k = 0; k < 4; ++k) acc = cfma_cj(shfl(b, L.at(L.j, k)), shfl(a, L.at(L.i, k)), acc);
   return acc;
 }
+// FP64 versions: GB300 issues an FP64 warp instruction only about every
+// 33 ns per SM sub-partition, however many lanes are active, so the k sum
+// is split between the half-warps (k = 0, 1 on lanes 0-15, k = 2, 3 on lanes
+// 16-31) and the halves are added with one shuffle: 10 FP64 instructions
+// and two dependent multiply-adds per product instead of 16 and four.  Both
+// halves end with the same value (the two partial sums added in either
+// order), so lanes 16-31 still mirror lanes 0-15.
+__device__ __forceinline__ double2 half_sum(double2 acc) {
+  acc.x += __shfl_xor_sync(kFull, acc.x, 16);
+  acc.y += __shfl_xor_sync(kFull, acc.y, 16);
+  return acc;
+}
+template <>
+__device__ __forceinline__ double2 wmm<double2>(const Lane& L, double2 a, double2 b) {
+  const int k0 = (L.l >> 3) & 2;
+  double2 acc = cfma(shfl(a, L.at(L.i, k0)), shfl(b, L.at(k0, L.j)), czero<double2>());
+  acc = cfma(shfl(a, L.at(L.i, k0 + 1)), shfl(b, L.at(k0 + 1, L.j)), acc);
+  return half_sum(acc);
+}
+template <>
+__device__ __forceinline__ double2 wmm_dn<double2>(const Lane& L, double2 a, double2 b) {
+  const int k0 = (L.l >> 3) & 2;
+  double2 acc = cfma_cj(shfl(a, L.at(k0, L.i)), shfl(b, L.at(k0, L.j)), czero<double2>());
+  acc = cfma_cj(shfl(a, L.at(k0 + 1, L.i)), shfl(b, L.at(k0 + 1, L.j)), acc);
+  return half_sum(acc);
+}
+template <>
+__device__ __forceinline__ double2 wmm_nd<double2>(const Lane& L, double2 a, double2 b) {
+  const int k0 = (L.l >> 3) & 2;
+  double2 acc = cfma_cj(shfl(b, L.at(L.j, k0)), shfl(a, L.at(L.i, k0)), czero<double2>());
+  acc = cfma_cj(shfl(b, L.at(L.j, k0 + 1)), shfl(a, L.at(L.i, k0 + 1)), acc);
+  return half_sum(acc);
+}
+
 // A^dagger[i][j] = conj(A[j][i])
 template <typename C2>
 __device__ __forceinline__ C2 wdag(const Lane& L, C2 a) {

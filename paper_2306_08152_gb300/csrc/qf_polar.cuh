@@ -81,7 +81,13 @@ static __device__ __noinline__ float2 complete_left_vectors(const Lane& L, float
 // Warp-cooperative polar update.  Every lane passes element (L.i, L.j) of A
 // (FP64) and receives element (L.i, L.j) of u = argmax Re Tr(A u); *sig gets
 // the sum of singular values of A.  Returns false for a non-finite A.
-static __device__ __forceinline__ bool warp_polar(const Lane& L, double2 a, float2* sm, double2* u_out, double* sig) {
+//
+// y_io (optional, one element per lane): the Jacobi starts from A Y0 with
+// Y0 = *y_io instead of A (a warm start from the previous update of the same
+// gate, whose right singular vectors are close), and *y_io receives the
+// final rotation.  The FP64 refinement fixes the result whatever the start.
+static __device__ __forceinline__ bool warp_polar(const Lane& L, double2 a, float2* sm, double2* u_out, double* sig,
+                                                  float2* y_io = nullptr) {
   const bool fin = __all_sync(kFull, isfinite(a.x) && isfinite(a.y));
   if (!fin) return false;
   const float amax = warp_max(fmaxf(fabsf((float)a.x), fabsf((float)a.y)));
@@ -95,6 +101,10 @@ static __device__ __forceinline__ bool warp_polar(const Lane& L, double2 a, floa
   // ---- stage 1: one-sided Jacobi in FP32 (two disjoint column pairs per round)
   float2 w = make_float2((float)a.x * sc, (float)a.y * sc);
   float2 y = make_float2(L.i == L.j ? 1.f : 0.f, 0.f);
+  if (y_io) {  // W = A Y0
+    y = *y_io;
+    w = wmm(L, w, y);
+  }
   for (int sweep = 0; sweep < 12; ++sweep) {
     float off = 0.f;
 #pragma unroll
@@ -207,6 +217,7 @@ static __device__ __forceinline__ bool warp_polar(const Lane& L, double2 a, floa
     u = make_double2(u.x - 0.5 * (double)cor.x, u.y - 0.5 * (double)cor.y);
   }
   *u_out = u;
+  if (y_io) *y_io = y;
   return __all_sync(kFull, isfinite(u.x) && isfinite(u.y));
 }
 
