@@ -107,7 +107,9 @@ static __device__ __forceinline__ bool warp_polar(const Lane& L, double2 a, floa
   }
   for (int sweep = 0; sweep < 12; ++sweep) {
     float off = 0.f;
-#pragma unroll
+    // kept rolled: the batched kernel runs one copy of this code per warp
+    // and its instruction fetch, not the loop overhead, is what costs
+#pragma unroll 1
     for (int r = 1; r <= 3; ++r) {
       const int q = L.j ^ r;
       const bool isP = L.j < q;
