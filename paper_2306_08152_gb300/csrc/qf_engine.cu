@@ -266,8 +266,11 @@ struct Slice {
 Slice all_starts(qf_plan* P, cudaStream_t st) { return Slice{0, P->S, st}; }
 Slice all_starts(qf_plan* P) { return all_starts(P, P->stream); }
 
-int plan_pass(qf_plan* P, const Slice& sl, int a, int b, const double2* L, long long Ls,
-              const double2* R, long long Rs) {
+// Enqueue one pass launch over the slice's tensors; with pass timing on it is
+// bracketed by a pair of events and its algorithmic bytes (one read and one
+// write of every entry it covers) are counted.
+template <typename Launch>
+int timed_pass(qf_plan* P, const Slice& sl, Launch launch) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (P->timing) {
     if (P->events_used + 2 > P->events.size()) {
@@ -283,8 +286,7 @@ int plan_pass(qf_plan* P, const Slice& sl, int a, int b, const double2* L, long 
     QF_CUDA(cudaEventRecord(e0, sl.st));
   }
   void* T = static_cast<char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
-  QF_CUDA(qf::launch_pass(T, P->n, sl.Sg, a, b, L ? L + sl.s0 * Ls : nullptr, Ls,
-                          R ? R + sl.s0 * Rs : nullptr, Rs, kprec(P->prec), sl.st));
+  QF_CUDA(launch(T));
   if (P->timing) {
     QF_CUDA(cudaEventRecord(e1, sl.st));
     P->pass_bytes += 2.0 * (double)sl.Sg * (double)P->NN * (double)elem_bytes(P->prec);
@@ -294,33 +296,21 @@ int plan_pass(qf_plan* P, const Slice& sl, int a, int b, const double2* L, long 
   return QF_OK;
 }
 
+int plan_pass(qf_plan* P, const Slice& sl, int a, int b, const double2* L, long long Ls,
+              const double2* R, long long Rs) {
+  return timed_pass(P, sl, [&](void* T) {
+    return qf::launch_pass(T, P->n, sl.Sg, a, b, L ? L + sl.s0 * Ls : nullptr, Ls,
+                           R ? R + sl.s0 * Rs : nullptr, Rs, kprec(P->prec), sl.st);
+  });
+}
+
 // The pass of a three-qubit gate: T <- (L on q) T (R on q), 8x8 operators.
 int plan_pass8(qf_plan* P, const Slice& sl, const int* q, const double2* L, long long Ls,
                const double2* R, long long Rs) {
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (P->timing) {
-    if (P->events_used + 2 > P->events.size()) {
-      for (int i = 0; i < 64; ++i) {
-        cudaEvent_t e;
-        QF_CUDA(cudaEventCreate(&e));
-        P->events.push_back(e);
-      }
-    }
-    e0 = P->events[P->events_used];
-    e1 = P->events[P->events_used + 1];
-    P->events_used += 2;
-    QF_CUDA(cudaEventRecord(e0, sl.st));
-  }
-  void* T = static_cast<char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
-  QF_CUDA(qf::launch_pass8(T, P->n, sl.Sg, q, L ? L + sl.s0 * Ls : nullptr, Ls,
-                           R ? R + sl.s0 * Rs : nullptr, Rs, kprec(P->prec), sl.st));
-  if (P->timing) {
-    QF_CUDA(cudaEventRecord(e1, sl.st));
-    P->pass_bytes += 2.0 * (double)sl.Sg * (double)P->NN * (double)elem_bytes(P->prec);
-  }
-  P->pass_launches++;
-  P->all_launches++;
-  return QF_OK;
+  return timed_pass(P, sl, [&](void* T) {
+    return qf::launch_pass8(T, P->n, sl.Sg, q, L ? L + sl.s0 * Ls : nullptr, Ls,
+                            R ? R + sl.s0 * Rs : nullptr, Rs, kprec(P->prec), sl.st);
+  });
 }
 
 // The fused pass of gate k with the operators its update left in LR / LR8.
@@ -407,32 +397,12 @@ int plan_update_look(qf_plan* P, const Slice& sl, int k1, int k2, int mode, doub
 
 // The pass of a look-ahead window: both updates' operators in one pass.
 int plan_pair_pass(qf_plan* P, const Slice& sl, int slot) {
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (P->timing) {
-    if (P->events_used + 2 > P->events.size()) {
-      for (int i = 0; i < 64; ++i) {
-        cudaEvent_t e;
-        QF_CUDA(cudaEventCreate(&e));
-        P->events.push_back(e);
-      }
-    }
-    e0 = P->events[P->events_used];
-    e1 = P->events[P->events_used + 1];
-    P->events_used += 2;
-    QF_CUDA(cudaEventRecord(e0, sl.st));
-  }
-  void* T = static_cast<char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
   const double2* LR = P->LR.as<double2>() + (size_t)sl.s0 * 32;
   const double2* LR2 = P->LR2.as<double2>() + (size_t)sl.s0 * 32;
   const void* pp = P->pair_params.data() + (size_t)slot * qf::pair_params_bytes();
-  QF_CUDA(qf::launch_pair_pass(T, P->n, sl.Sg, pp, LR, LR + 16, 32, LR2, LR2 + 16, 32, sl.st));
-  if (P->timing) {
-    QF_CUDA(cudaEventRecord(e1, sl.st));
-    P->pass_bytes += 2.0 * (double)sl.Sg * (double)P->NN * (double)elem_bytes(P->prec);
-  }
-  P->pass_launches++;
-  P->all_launches++;
-  return QF_OK;
+  return timed_pass(P, sl, [&](void* T) {
+    return qf::launch_pair_pass(T, P->n, sl.Sg, pp, LR, LR + 16, 32, LR2, LR2 + 16, 32, sl.st);
+  });
 }
 
 // Gate order of half-sweep h (0 = backward k = p-1..0, 1 = forward k = 0..p-1).
