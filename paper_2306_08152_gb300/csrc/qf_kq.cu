@@ -173,11 +173,82 @@ static __device__ __noinline__ void complete8(const L8& L, double2 w0, double2 w
   __syncwarp();
 }
 
+// One-sided Jacobi sweeps on the lane-distributed 8x8 pair (W, Y): each
+// sweep pairs column j with j ^ r for r = 1..7 (four disjoint pairs per
+// round) and rotates W[:,p], W[:,q] (and Y's) so that they become
+// orthogonal.  Stops when the largest |g_pq| / (|W_p| |W_q|) is below tol
+// or after max_sweeps.  R is float or double.
+template <typename R, typename C2>
+__device__ __forceinline__ void jacobi8(const L8& L, C2& w0, C2& w1, C2& y0, C2& y1, R tol,
+                                        int max_sweeps) {
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    R off = R(0);
+#pragma unroll 1
+    for (int r = 1; r <= 7; ++r) {
+      const int q = L.j ^ r;
+      const bool isP = L.j < q;
+      const int src = L.l ^ r;
+      const C2 wq0 = shfl(w0, src), wq1 = shfl(w1, src);
+      const C2 yq0 = shfl(y0, src), yq1 = shfl(y1, src);
+      R n2 = w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y;
+      n2 += __shfl_xor_sync(kFull, n2, 8);
+      n2 += __shfl_xor_sync(kFull, n2, 16);
+      const R n2q = __shfl_sync(kFull, n2, src);
+      const C2 cp0 = isP ? w0 : wq0, cq0 = isP ? wq0 : w0;
+      const C2 cp1 = isP ? w1 : wq1, cq1 = isP ? wq1 : w1;
+      // g = conj(W[:,p]) . W[:,q]
+      R gx = cp0.x * cq0.x + cp0.y * cq0.y + cp1.x * cq1.x + cp1.y * cq1.y;
+      R gy = cp0.x * cq0.y - cp0.y * cq0.x + cp1.x * cq1.y - cp1.y * cq1.x;
+      gx += __shfl_xor_sync(kFull, gx, 8);
+      gx += __shfl_xor_sync(kFull, gx, 16);
+      gy += __shfl_xor_sync(kFull, gy, 8);
+      gy += __shfl_xor_sync(kFull, gy, 16);
+      const R al = isP ? n2 : n2q, be = isP ? n2q : n2;
+      // |g| with a scaled hypot: g can lie far below sqrt of the smallest normal
+      const R gm0 = fmax(fabs(gx), fabs(gy));
+      const R nrm = sqrt(al) * sqrt(be);
+      const R tiny = sizeof(R) == 4 ? R(1e-12) : R(1e-200);
+      if (gm0 > tol * R(0.01) * nrm && fmax(al, be) > tiny && gm0 > R(0)) {
+        const R gxs = gx / gm0, gys = gy / gm0;
+        const R hs = sqrt(gxs * gxs + gys * gys);
+        const R gm = gm0 * hs;
+        off = fmax(off, gm / nrm);
+        const R zeta = R(0.5) * (be - al) / gm;
+        const R t = copysign(R(1) / (fabs(zeta) + sqrt(R(1) + zeta * zeta)), zeta);
+        const R c = R(1) / sqrt(R(1) + t * t), sn = c * t;
+        C2 e;  // conj(g) / |g|
+        e.x = gxs / hs;
+        e.y = -gys / hs;
+        if (isP) {  // W[:,p] <- c W[:,p] - s e W[:,q]
+          const C2 e0 = cmul(e, wq0), e1 = cmul(e, wq1), f0 = cmul(e, yq0), f1 = cmul(e, yq1);
+          w0.x = c * w0.x - sn * e0.x; w0.y = c * w0.y - sn * e0.y;
+          w1.x = c * w1.x - sn * e1.x; w1.y = c * w1.y - sn * e1.y;
+          y0.x = c * y0.x - sn * f0.x; y0.y = c * y0.y - sn * f0.y;
+          y1.x = c * y1.x - sn * f1.x; y1.y = c * y1.y - sn * f1.y;
+        } else {  // W[:,q] <- s W[:,p] + c e W[:,q]
+          const C2 e0 = cmul(e, w0), e1 = cmul(e, w1), f0 = cmul(e, y0), f1 = cmul(e, y1);
+          w0.x = sn * wq0.x + c * e0.x; w0.y = sn * wq0.y + c * e0.y;
+          w1.x = sn * wq1.x + c * e1.x; w1.y = sn * wq1.y + c * e1.y;
+          y0.x = sn * yq0.x + c * f0.x; y0.y = sn * yq0.y + c * f0.y;
+          y1.x = sn * yq1.x + c * f1.x; y1.y = sn * yq1.y + c * f1.y;
+        }
+      }
+    }
+    R m = off;
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, h));
+    if (m < tol) break;
+  }
+}
+
 // Warp 8x8 polar update (OptimizeGate, Sec. III-A1, Eq. opt_u): with
-// A = X D Y^dagger, u = Y X^dagger maximises Re Tr(A u).  One-sided Jacobi in
-// FP64 (rotations J with A J = W having orthogonal columns: Y = J, X = W's
-// normalised columns, D = their norms); each sweep pairs column j with
-// j ^ r for r = 1..7, four disjoint pairs per round.  *sig = sum(D).
+// A = X D Y^dagger, u = Y X^dagger maximises Re Tr(A u).  One-sided Jacobi
+// (rotations J with A J = W having orthogonal columns: Y = J, X = W's
+// normalised columns, D = their norms), first in FP32 from A to an
+// off-diagonal measure of 1e-6, then in FP64 from W = A Y32 (Y32 made
+// unitary to FP64 rounding first), where a couple of sweeps reach 1e-15:
+// the FP32 stage carries most of the rotations at 1/64 of the FP64 cost on
+// GB300.  *sig = sum(D).
 // Returns false for a non-finite A.
 static __device__ __noinline__ bool warp_polar8(double2 a0, double2 a1, double2* sm, double2* u0,
                                                 double2* u1, double* sig) {
@@ -192,49 +263,26 @@ static __device__ __noinline__ bool warp_polar8(double2 a0, double2 a1, double2*
     return true;
   }
   const double sc = 1.0 / amax;
-  double2 w0 = make_double2(a0.x * sc, a0.y * sc), w1 = make_double2(a1.x * sc, a1.y * sc);
-  double2 y0 = make_double2(L.g == L.j ? 1.0 : 0.0, 0.0), y1 = make_double2(L.g + 4 == L.j ? 1.0 : 0.0, 0.0);
-  for (int sweep = 0; sweep < 20; ++sweep) {
-    double off = 0.0;
-    for (int r = 1; r <= 7; ++r) {
-      const int q = L.j ^ r;
-      const bool isP = L.j < q;
-      const int src = L.l ^ r;
-      const double2 wq0 = shfl(w0, src), wq1 = shfl(w1, src);
-      const double2 yq0 = shfl(y0, src), yq1 = shfl(y1, src);
-      const double n2 = colsum(w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y);
-      const double n2q = __shfl_sync(kFull, n2, src);
-      const double2 cp0 = isP ? w0 : wq0, cq0 = isP ? wq0 : w0;
-      const double2 cp1 = isP ? w1 : wq1, cq1 = isP ? wq1 : w1;
-      // g = conj(W[:,p]) . W[:,q]
-      const double gx = colsum(cp0.x * cq0.x + cp0.y * cq0.y + cp1.x * cq1.x + cp1.y * cq1.y);
-      const double gy = colsum(cp0.x * cq0.y - cp0.y * cq0.x + cp1.x * cq1.y - cp1.y * cq1.x);
-      const double al = isP ? n2 : n2q, be = isP ? n2q : n2;
-      const double gm = hypot(gx, gy);
-      const double nrm = sqrt(al) * sqrt(be);
-      if (gm > 1e-15 * nrm && fmax(al, be) > 1e-200) {
-        off = fmax(off, gm / nrm);
-        const double zeta = 0.5 * (be - al) / gm;
-        const double t = copysign(1.0 / (fabs(zeta) + sqrt(1.0 + zeta * zeta)), zeta);
-        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-        const double2 e = make_double2(gx / gm, -gy / gm);  // conj(g) / |g|
-        if (isP) {  // W[:,p] <- c W[:,p] - s e W[:,q]
-          const double2 e0 = cmuld(e, wq0), e1 = cmuld(e, wq1), f0 = cmuld(e, yq0), f1 = cmuld(e, yq1);
-          w0 = make_double2(c * w0.x - sn * e0.x, c * w0.y - sn * e0.y);
-          w1 = make_double2(c * w1.x - sn * e1.x, c * w1.y - sn * e1.y);
-          y0 = make_double2(c * y0.x - sn * f0.x, c * y0.y - sn * f0.y);
-          y1 = make_double2(c * y1.x - sn * f1.x, c * y1.y - sn * f1.y);
-        } else {  // W[:,q] <- s W[:,p] + c e W[:,q]
-          const double2 e0 = cmuld(e, w0), e1 = cmuld(e, w1), f0 = cmuld(e, y0), f1 = cmuld(e, y1);
-          w0 = make_double2(sn * wq0.x + c * e0.x, sn * wq0.y + c * e0.y);
-          w1 = make_double2(sn * wq1.x + c * e1.x, sn * wq1.y + c * e1.y);
-          y0 = make_double2(sn * yq0.x + c * f0.x, sn * yq0.y + c * f0.y);
-          y1 = make_double2(sn * yq1.x + c * f1.x, sn * yq1.y + c * f1.y);
-        }
-      }
-    }
-    if (wmaxd(off) < 1e-15) break;
+  const double2 as0 = make_double2(a0.x * sc, a0.y * sc), as1 = make_double2(a1.x * sc, a1.y * sc);
+  // stage 1: FP32
+  float2 fw0 = make_float2((float)as0.x, (float)as0.y), fw1 = make_float2((float)as1.x, (float)as1.y);
+  float2 fy0 = make_float2(L.g == L.j ? 1.f : 0.f, 0.f), fy1 = make_float2(L.g + 4 == L.j ? 1.f : 0.f, 0.f);
+  jacobi8<float>(L, fw0, fw1, fy0, fy1, 1e-6f, 15);
+  // stage 2: FP64.  Y32 is unitary only to FP32 rounding: two Newton-Schulz
+  // steps Y <- Y (3I - Y^dagger Y) / 2 in FP64 make it unitary to FP64
+  // rounding (the error squares each step), so W = A Y has A's singular
+  // values; then FP64 sweeps from W
+  double2 y0 = to_d2(fy0), y1 = to_d2(fy1);
+  for (int step = 0; step < 2; ++step) {
+    double2 P0, P1;
+    mm8_dn(L, y0, y1, y0, y1, P0, P1);
+    const double2 Q0 = make_double2((L.g == L.j ? 1.5 : 0.0) - 0.5 * P0.x, -0.5 * P0.y);
+    const double2 Q1 = make_double2((L.g + 4 == L.j ? 1.5 : 0.0) - 0.5 * P1.x, -0.5 * P1.y);
+    mm8(L, y0, y1, Q0, Q1, y0, y1);
   }
+  double2 w0, w1;
+  mm8(L, as0, as1, y0, y1, w0, w1);
+  jacobi8<double>(L, w0, w1, y0, y1, 1e-15, 8);
   const double sj = sqrt(colsum(w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y));
   double s8[8];
 #pragma unroll
