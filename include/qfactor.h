@@ -335,8 +335,9 @@ int qf_plan_load(qf_plan* plan, const qf_c128* target, const qf_c128* gates,
  * never).  With two or more starts the starts form two groups whose
  * environment kernels and passes run on two internal streams, so that one
  * group's gate update overlaps the other group's pass.  Without pass timing,
- * a sweep is captured once as a CUDA graph (per beta and precision) and
- * replayed.  Enqueue only. */
+ * from the plan's second sweep on, a sweep is captured once as a CUDA graph
+ * (per beta and precision) and replayed (the first sweep runs as live
+ * launches, so one-sweep uses pay no capture).  Enqueue only. */
 int qf_plan_sweep(qf_plan* plan, int n_sweeps, int reset_iter, double beta);
 
 /* Rebuild every tensor from the target and the current gates, in

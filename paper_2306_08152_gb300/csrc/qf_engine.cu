@@ -237,6 +237,7 @@ struct qf_plan {
   bool graph_look = false;
   long long graph_pass_launches = 0, graph_all_launches = 0;  // per replay
   bool use_graph = true;
+  long long sweeps_enqueued = 0;  // a plan's first sweep runs live (no capture cost for one-sweep uses)
   // look-ahead: consecutive updates on disjoint pairs share one pass
   bool lookahead = false;
   DevBuf LR2;                      // the second update's pass operators
@@ -574,7 +575,9 @@ int enqueue_sweep(qf_plan* P, double beta, cudaStream_t origin) {
 // events), otherwise the sweep is captured once as a CUDA graph per (beta,
 // precision) and replayed.
 int plan_sweep_once(qf_plan* P, double beta) {
-  if (P->timing || !P->use_graph) return enqueue_sweep(P, beta, P->stream);
+  // the first sweep of a plan runs as live launches: capturing and
+  // instantiating the graph costs more than it saves for a single sweep
+  if (P->timing || !P->use_graph || P->sweeps_enqueued++ == 0) return enqueue_sweep(P, beta, P->stream);
   const bool look = plan_uses_lookahead(P);
   if (!P->graph || P->graph_beta != beta || P->graph_prec != P->prec || P->graph_look != look) {
     if (P->graph) {
