@@ -241,12 +241,83 @@ __device__ __forceinline__ void jacobi8(const L8& L, C2& w0, C2& w1, C2& y0, C2&
   }
 }
 
+// 1/sqrt(q) for a positive normal double q by Newton's iteration
+// r <- r (3 - q r^2) / 2 from an FP32 seed.  q = m 4^k with m in [1, 4), so
+// the seed rsqrtf(m) 2^-k neither under- nor overflows in FP32; its relative
+// error (~1e-7) squares with each step, so two steps reach FP64 rounding.
+__device__ __forceinline__ double rsqrt_d(double q) {
+  const int k = (((__double2hiint(q) >> 20) & 0x7ff) - 1023) >> 1;  // floor(log2(q) / 2)
+  const double m = q * __hiloint2double((1023 - 2 * k) << 20, 0);
+  double r = (double)rsqrtf((float)m) * __hiloint2double((1023 - k) << 20, 0);
+  r = r * (1.5 - 0.5 * q * r * r);
+  r = r * (1.5 - 0.5 * q * r * r);
+  return r;
+}
+
+// FP64 polishing sweeps after the FP32 stage, in which every column pair is
+// already orthogonal to ~1e-6.  The inner products g = W_p^dagger W_q,
+// |W_p|^2 and |W_q|^2 are FP64 sums; the rotation angle t = tan(theta) is
+// taken in FP32 from zeta = (|W_q|^2 - |W_p|^2) / (2|g|) (an angle accurate
+// to FP32 still shrinks g by ~1e-7 per sweep); the rotation applied is
+// unitary to FP64 rounding: c = 1/sqrt(1 + t^2) and e = conj(g)/|g| by
+// rsqrt_d, s = c t.  No FP64 division or square root (long instruction
+// sequences on the FP64 pipe).  Stops once every pair has
+// |g| <= tol |W_p| |W_q| (tested as g^2 <= tol^2 |W_p|^2 |W_q|^2).
+__device__ __forceinline__ void polish8(const L8& L, double2& w0, double2& w1, double2& y0, double2& y1,
+                                        double tol, int max_sweeps) {
+  const double tol2 = tol * tol;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    bool open = false;
+#pragma unroll 1
+    for (int r = 1; r <= 7; ++r) {
+      const int q = L.j ^ r;
+      const bool isP = L.j < q;
+      const int src = L.l ^ r;
+      const double2 wq0 = shfl(w0, src), wq1 = shfl(w1, src);
+      const double2 yq0 = shfl(y0, src), yq1 = shfl(y1, src);
+      const double n2 = colsum(w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y);
+      const double n2q = __shfl_sync(kFull, n2, src);
+      const double2 cp0 = isP ? w0 : wq0, cq0 = isP ? wq0 : w0;
+      const double2 cp1 = isP ? w1 : wq1, cq1 = isP ? wq1 : w1;
+      const double gx = colsum(cp0.x * cq0.x + cp0.y * cq0.y + cp1.x * cq1.x + cp1.y * cq1.y);
+      const double gy = colsum(cp0.x * cq0.y - cp0.y * cq0.x + cp1.x * cq1.y - cp1.y * cq1.x);
+      const double al = isP ? n2 : n2q, be = isP ? n2q : n2;
+      const double g2 = gx * gx + gy * gy, ab = al * be;
+      open |= g2 > tol2 * ab;
+      // rotate where |g| is above FP64 rounding of |W_p| |W_q| (and normal)
+      if (g2 > 1e-4 * tol2 * ab && g2 > 1e-300) {
+        const double rg = rsqrt_d(g2);
+        const float z = (float)(0.5 * (be - al) * rg), az = fabsf(z);
+        const float tf = copysignf(az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(1.f + az * az)), z);
+        const double t = (double)tf;
+        const double c = rsqrt_d(1.0 + t * t), sn = c * t;
+        const double2 e = make_double2(gx * rg, -gy * rg);  // conj(g) / |g|
+        if (isP) {  // W[:,p] <- c W[:,p] - s e W[:,q]
+          const double2 e0 = cmuld(e, wq0), e1 = cmuld(e, wq1), f0 = cmuld(e, yq0), f1 = cmuld(e, yq1);
+          w0 = make_double2(c * w0.x - sn * e0.x, c * w0.y - sn * e0.y);
+          w1 = make_double2(c * w1.x - sn * e1.x, c * w1.y - sn * e1.y);
+          y0 = make_double2(c * y0.x - sn * f0.x, c * y0.y - sn * f0.y);
+          y1 = make_double2(c * y1.x - sn * f1.x, c * y1.y - sn * f1.y);
+        } else {  // W[:,q] <- s W[:,p] + c e W[:,q]
+          const double2 e0 = cmuld(e, w0), e1 = cmuld(e, w1), f0 = cmuld(e, y0), f1 = cmuld(e, y1);
+          w0 = make_double2(sn * wq0.x + c * e0.x, sn * wq0.y + c * e0.y);
+          w1 = make_double2(sn * wq1.x + c * e1.x, sn * wq1.y + c * e1.y);
+          y0 = make_double2(sn * yq0.x + c * f0.x, sn * yq0.y + c * f0.y);
+          y1 = make_double2(sn * yq1.x + c * f1.x, sn * yq1.y + c * f1.y);
+        }
+      }
+    }
+    if (!__any_sync(kFull, open)) break;
+  }
+}
+
 // Warp 8x8 polar update (OptimizeGate, Sec. III-A1, Eq. opt_u): with
 // A = X D Y^dagger, u = Y X^dagger maximises Re Tr(A u).  One-sided Jacobi
 // (rotations J with A J = W having orthogonal columns: Y = J, X = W's
 // normalised columns, D = their norms), first in FP32 from A to an
 // off-diagonal measure of 1e-6, then in FP64 from W = A Y32 (Y32 made
-// unitary to FP64 rounding first), where a couple of sweeps reach 1e-15:
+// unitary to FP64 rounding first), where a couple of polishing sweeps
+// (angles from FP32, exactly unitary FP64 rotations) reach 1e-14:
 // the FP32 stage carries most of the rotations at 1/64 of the FP64 cost on
 // GB300.  *sig = sum(D).
 // Returns false for a non-finite A.
@@ -282,7 +353,7 @@ static __device__ __noinline__ bool warp_polar8(double2 a0, double2 a1, double2*
   }
   double2 w0, w1;
   mm8(L, as0, as1, y0, y1, w0, w1);
-  jacobi8<double>(L, w0, w1, y0, y1, 1e-15, 8);
+  polish8(L, w0, w1, y0, y1, 1e-15, 8);
   const double sj = sqrt(colsum(w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y));
   double s8[8];
 #pragma unroll
