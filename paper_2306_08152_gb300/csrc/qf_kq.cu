@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include "qf_device.cuh"
+#include "qf_f32x2.cuh"
 #include "qf_internal.h"
 
 namespace qf {
@@ -471,6 +472,136 @@ pass8_kernel(typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, int p2,
   }
 }
 
+// complex64 version for the FP32 pipe.  The old layout spends one broadcast
+// shared load of an operator entry per complex multiply-add, which puts the
+// shared-memory pipe near its limit; here a lane takes row x of two blocks
+// (b and b + 4 of an 8-block group), so every operator entry loaded serves
+// two rows.  The R stage writes each output column straight to the
+// transpose buffer and the L stage each output row straight to global
+// memory, so a lane holds only its two input rows (80 registers: three
+// CTAs of eight warps per SM).  Without L the lane reads its own rows back
+// from the buffer.  (Loading the next group's rows ahead of the arithmetic
+// needs 123 registers, two CTAs per SM, and ran slower.)
+constexpr int kPass8fBlocks = 8;  // blocks per warp and group
+
+__device__ __forceinline__ unsigned off8(int v, int p0, int p1, int p2) {
+  return (((unsigned)v >> 2) & 1u) << p0 | (((unsigned)v >> 1) & 1u) << p1 | ((unsigned)v & 1u) << p2;
+}
+
+struct Grp8 {  // one block of a group: its row and column rest offsets
+  unsigned r0, c0;
+  bool valid;
+};
+
+constexpr int kPass8fCtasPerSm = 3;
+
+template <bool HL, bool HR>
+__global__ void __launch_bounds__(kPass8Threads, kPass8fCtasPerSm)
+pass8f_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const double2* __restrict__ L,
+              long long Ls, const double2* __restrict__ Rm, long long Rs) {
+  __shared__ float2 sL[64], sR[64];
+  __shared__ float2 buf[kPass8Threads / 32][kPass8fBlocks * kBlkStride];
+  const int s = blockIdx.y;
+  if (threadIdx.x < 64) {
+    if (HL) sL[threadIdx.x] = cmake(L[s * Ls + threadIdx.x], 0.f);
+    if (HR) sR[threadIdx.x] = cmake(Rm[s * Rs + threadIdx.x], 0.f);
+  }
+  __syncthreads();
+  const unsigned N = 1u << n;
+  int q[3] = {p0, p1, p2};  // ascending for the deposit
+  if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
+  if (q[1] > q[2]) { const int t = q[1]; q[1] = q[2]; q[2] = t; }
+  if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
+  const unsigned m0 = 1u << p0, m1 = 1u << p1, m2 = 1u << p2;
+  // offset of local index v (a compile-time constant at every use)
+  auto off = [&](int v) { return ((v & 4) ? m0 : 0u) | ((v & 2) ? m1 : 0u) | ((v & 1) ? m2 : 0u); };
+  const int lnc = n - 3;
+  const unsigned cmask = (1u << lnc) - 1u;
+  const unsigned nblk = 1u << (2 * lnc);
+  float2* __restrict__ Ts = T + (size_t)s * N * N;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = lane & 3, x = lane >> 2;
+  const unsigned offx = off8(x, p0, p1, p2);  // offset of this lane's row (R stage) / column (L stage)
+  float2* wb = buf[w];
+  const unsigned warps = gridDim.x * (kPass8Threads / 32);
+  auto locate = [&](unsigned grp, int h) {
+    const unsigned blk = grp * kPass8fBlocks + (unsigned)(b + 4 * h);
+    Grp8 g;
+    g.valid = blk < nblk;
+    g.r0 = dep1(dep1(dep1(blk >> lnc, q[0]), q[1]), q[2]);
+    g.c0 = dep1(dep1(dep1(blk & cmask, q[0]), q[1]), q[2]);
+    return g;
+  };
+  auto load = [&](const Grp8& g, float2* row) {
+    if (g.valid) {
+      const float2* src = Ts + (size_t)(g.r0 | offx) * N + g.c0;
+#pragma unroll
+      for (int y = 0; y < 8; ++y) row[y] = src[off(y)];
+    } else {
+#pragma unroll
+      for (int y = 0; y < 8; ++y) row[y] = make_float2(0.f, 0.f);
+    }
+  };
+  unsigned grp = blockIdx.x * (kPass8Threads / 32) + w;
+  for (; grp * kPass8fBlocks < nblk; grp += warps) {
+    const Grp8 cg[2] = {locate(grp, 0), locate(grp, 1)};
+    float2 row[2][8];
+    load(cg[0], row[0]);
+    load(cg[1], row[1]);
+    // R stage (or the plain row) into the transpose buffer, column by column
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      float2 a0 = row[0][c], a1 = row[1][c];
+      if (HR) {
+        a0 = a1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float2 r = sR[k * 8 + c];
+          a0 = cfma(row[0][k], r, a0);
+          a1 = cfma(row[1][k], r, a1);
+        }
+      }
+      wb[b * kBlkStride + x * 9 + c] = a0;
+      wb[(b + 4) * kBlkStride + x * 9 + c] = a1;
+    }
+    __syncwarp();
+    if (HL) {  // L stage: this lane takes column x of blocks b and b + 4
+      float2 col[2][8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        col[0][k] = wb[b * kBlkStride + k * 9 + x];
+        col[1][k] = wb[(b + 4) * kBlkStride + k * 9 + x];
+      }
+      __syncwarp();  // the buffer is rewritten by the next group
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float2 l = sL[r * 8 + k];
+          a0 = cfma(l, col[0][k], a0);
+          a1 = cfma(l, col[1][k], a1);
+        }
+        if (cg[0].valid) Ts[(size_t)(cg[0].r0 | off(r)) * N + (cg[0].c0 | offx)] = a0;
+        if (cg[1].valid) Ts[(size_t)(cg[1].r0 | off(r)) * N + (cg[1].c0 | offx)] = a1;
+      }
+    } else {  // R only: the lane reads its own output rows back and writes them
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float2 o[8];
+#pragma unroll
+        for (int y = 0; y < 8; ++y) o[y] = wb[(b + 4 * h) * kBlkStride + x * 9 + y];
+        if (cg[h].valid) {
+          float2* dst = Ts + (size_t)(cg[h].r0 | offx) * N + cg[h].c0;
+#pragma unroll
+          for (int y = 0; y < 8; ++y) dst[off(y)] = o[y];
+        }
+      }
+      __syncwarp();  // the buffer is rewritten by the next group
+    }
+  }
+}
+
 // ------------------------------------------------------------ environment
 //
 // P[x][y] = sum over the 2^(n-3) rests r of T[(r, x), (r, y)], from the
@@ -700,7 +831,15 @@ void pass8_launch(void* T, int n, int S, int p0, int p1, int p2, const double2* 
   long long cap = ((long long)sm_count() * 4 + S - 1) / S;
   if (cap < 1) cap = 1;
   dim3 grid((unsigned)(want < cap ? want : cap), S);
-  pass8_kernel<R, HL, HR><<<grid, kPass8Threads, 0, st>>>((C*)T, n, p0, p1, p2, L, Ls, Rm, Rs);
+  if (sizeof(R) == sizeof(float)) {
+    const long long fgroups = ((1ll << (2 * (n - 3))) + kPass8fBlocks - 1) / kPass8fBlocks;
+    const long long fwant = (fgroups + 7) / 8;
+    long long fcap = ((long long)sm_count() * kPass8fCtasPerSm + S - 1) / S;
+    if (fcap < 1) fcap = 1;
+    dim3 fgrid((unsigned)(fwant < fcap ? fwant : fcap), S);
+    pass8f_kernel<HL, HR><<<fgrid, kPass8Threads, 0, st>>>((float2*)T, n, p0, p1, p2, L, Ls, Rm, Rs);
+  } else
+    pass8_kernel<R, HL, HR><<<grid, kPass8Threads, 0, st>>>((C*)T, n, p0, p1, p2, L, Ls, Rm, Rs);
 }
 
 template <typename R>
