@@ -11,7 +11,6 @@
 #include <string.h>
 
 #include "qf_device.cuh"
-#include "qf_f32x2.cuh"
 #include "qf_internal.h"
 
 namespace qf {
