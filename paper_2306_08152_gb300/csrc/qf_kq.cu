@@ -601,6 +601,104 @@ pass8f_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const doubl
   }
 }
 
+// complex64 pass for gates whose bits are all >= 4 (so n >= 7): the low four
+// column bits are then rest bits, and 16 consecutive rest columns are 16
+// adjacent entries (128 bytes).  A warp takes 16 such blocks (lane b) with
+// the same rest row, and a lane the rows x = xh, xh + 2, xh + 4, xh + 6
+// (xh = lane / 16), so every warp load or store covers two whole 128-byte
+// lines, and every broadcast operator entry serves four rows.  The R stage
+// writes each output column to the transpose buffer (or, without L, to
+// global memory); the L stage reads columns y = xh + 2j back and writes each
+// output row to global memory.  The buffer pads each block to 65 slots, so
+// both the column writes and the column reads of a warp hit every bank pair
+// exactly twice.  (Used with L; the R-only pass goes to pass8f_kernel.)
+constexpr int kPass8aThreads = 128;
+constexpr int kPass8aCtasPerSm = 4;
+constexpr int kBlkA = 65;
+
+template <bool HR>
+__global__ void __launch_bounds__(kPass8aThreads, kPass8aCtasPerSm)
+pass8a_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const double2* __restrict__ L,
+              long long Ls, const double2* __restrict__ Rm, long long Rs) {
+  __shared__ float2 sL[64], sR[64];
+  __shared__ float2 buf[kPass8aThreads / 32][16 * kBlkA];
+  const int s = blockIdx.y;
+  if (threadIdx.x < 64) {
+    sL[threadIdx.x] = cmake(L[s * Ls + threadIdx.x], 0.f);
+    if (HR) sR[threadIdx.x] = cmake(Rm[s * Rs + threadIdx.x], 0.f);
+  }
+  __syncthreads();
+  const unsigned N = 1u << n;
+  int q[3] = {p0, p1, p2};  // ascending for the deposit
+  if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
+  if (q[1] > q[2]) { const int t = q[1]; q[1] = q[2]; q[2] = t; }
+  if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
+  const unsigned m0 = 1u << p0, m1 = 1u << p1, m2 = 1u << p2;
+  auto off = [&](int v) { return ((v & 4) ? m0 : 0u) | ((v & 2) ? m1 : 0u) | ((v & 1) ? m2 : 0u); };
+  const int cgb = n - 7;  // bits of the 16-column group index within a rest row
+  const unsigned ngrp = 1u << (2 * (n - 3) - 4);
+  float2* __restrict__ Ts = T + (size_t)s * N * N;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = lane & 15, xh = lane >> 4;
+  const unsigned ox = xh ? m2 : 0u;  // off(xh + 2i) = ox | off(2i)
+  float2* wb = buf[w] + b * kBlkA;
+  for (unsigned g = blockIdx.x * (kPass8aThreads / 32) + w; g < ngrp;
+       g += gridDim.x * (kPass8aThreads / 32)) {
+    const unsigned rr = g >> cgb, cc = ((g & ((1u << cgb) - 1u)) << 4) | (unsigned)b;
+    const unsigned r0 = dep1(dep1(dep1(rr, q[0]), q[1]), q[2]);
+    const unsigned c0 = dep1(dep1(dep1(cc, q[0]), q[1]), q[2]);
+    float2 v[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int y = 0; y < 8; ++y) v[i][y] = Ts[(size_t)(r0 | ox | off(2 * i)) * N + (c0 | off(y))];
+    if (HR) {  // rolled by two: the fully unrolled group body overflows the instruction cache
+#pragma unroll 2
+      for (int c = 0; c < 8; ++c) {
+        float2 a[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float2 r = sR[k * 8 + c];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = cfma(v[i][k], r, a[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) wb[(xh + 2 * i) * 8 + c] = a[i];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) wb[(xh + 2 * i) * 8 + c] = v[i][c];
+    }
+    {
+      __syncwarp();
+      float2 col[4][8];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) col[j][k] = wb[k * 8 + xh + 2 * j];
+      __syncwarp();  // the buffer is rewritten by the next group
+#pragma unroll 2
+      for (int r = 0; r < 8; ++r) {
+        float2 a[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float2 l = sL[r * 8 + k];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) a[j] = cfma(l, col[j][k], a[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Ts[(size_t)(r0 | off(r)) * N + (c0 | ox | off(2 * j))] = a[j];
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------ environment
 //
 // P[x][y] = sum over the 2^(n-3) rests r of T[(r, x), (r, y)], from the
@@ -830,7 +928,14 @@ void pass8_launch(void* T, int n, int S, int p0, int p1, int p2, const double2* 
   long long cap = ((long long)sm_count() * 4 + S - 1) / S;
   if (cap < 1) cap = 1;
   dim3 grid((unsigned)(want < cap ? want : cap), S);
-  if (sizeof(R) == sizeof(float)) {
+  if (sizeof(R) == sizeof(float) && HL && p0 >= 4 && p1 >= 4 && p2 >= 4) {
+    const long long agroups = 1ll << (2 * (n - 3) - 4);
+    const long long awant = (agroups + 3) / 4;
+    long long acap = ((long long)sm_count() * kPass8aCtasPerSm + S - 1) / S;
+    if (acap < 1) acap = 1;
+    dim3 agrid((unsigned)(awant < acap ? awant : acap), S);
+    pass8a_kernel<HR><<<agrid, kPass8aThreads, 0, st>>>((float2*)T, n, p0, p1, p2, L, Ls, Rm, Rs);
+  } else if (sizeof(R) == sizeof(float)) {
     const long long fgroups = ((1ll << (2 * (n - 3))) + kPass8fBlocks - 1) / kPass8fBlocks;
     const long long fwant = (fgroups + 7) / 8;
     long long fcap = ((long long)sm_count() * kPass8fCtasPerSm + S - 1) / S;
