@@ -354,6 +354,30 @@ int plan_build(qf_plan* P) {
   return QF_OK;
 }
 
+// Kernel nodes captured into a graph do not take the capturing stream's
+// priority; give the kernel just captured on st (an environment kernel) that
+// priority explicitly, so that a replayed sweep keeps the overlap of one
+// group's environment with the other group's pass.
+int mark_stream_priority(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  QF_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return QF_OK;
+  int prio = 0;
+  QF_CUDA(cudaStreamGetPriority(st, &prio));
+  cudaLaunchAttributeValue v;
+  memset(&v, 0, sizeof(v));
+  v.priority = prio;
+  for (size_t i = 0; i < nd; ++i) {
+    cudaGraphNodeType t;
+    QF_CUDA(cudaGraphNodeGetType(deps[i], &t));
+    if (t == cudaGraphNodeTypeKernel)
+      QF_CUDA(cudaGraphKernelNodeSetAttribute(deps[i], cudaLaunchAttributePriority, &v));
+  }
+  return QF_OK;
+}
+
 int plan_update(qf_plan* P, const Slice& sl, int k, int mode, double beta, double2* env_out,
                 long long env_stride) {
   const int pr = kprec(P->prec);
@@ -367,7 +391,7 @@ int plan_update(qf_plan* P, const Slice& sl, int k, int mode, double beta, doubl
         P->part.as<double>() + (size_t)sl.s0 * B * 128, P->counters.as<unsigned>() + sl.s0, pr,
         sl.st));
     P->all_launches++;
-    return QF_OK;
+    return mark_stream_priority(sl.st);
   }
   QF_CUDA(qf::launch_update(
       T, P->n, sl.Sg, P->locs[k].a, P->locs[k].b, gate_ptr(P, sl.s0, k), P->gsz,
@@ -376,7 +400,7 @@ int plan_update(qf_plan* P, const Slice& sl, int k, int mode, double beta, doubl
       P->sigma.as<double>() + sl.s0, P->status.as<int>(),
       P->part.as<double>() + (size_t)sl.s0 * B * 32, P->counters.as<unsigned>() + sl.s0, pr, sl.st));
   P->all_launches++;
-  return QF_OK;
+  return mark_stream_priority(sl.st);
 }
 
 // Look-ahead update of gate k2, whose environment sees the pending update of
@@ -393,7 +417,7 @@ int plan_update_look(qf_plan* P, const Slice& sl, int k1, int k2, int mode, doub
       P->sigma.as<double>() + sl.s0, P->status.as<int>(),
       P->part.as<double>() + (size_t)sl.s0 * B * 32, P->counters.as<unsigned>() + sl.s0, pr, sl.st));
   P->all_launches++;
-  return QF_OK;
+  return mark_stream_priority(sl.st);
 }
 
 // The pass of a look-ahead window: both updates' operators in one pass.
@@ -453,8 +477,13 @@ bool plan_uses_lookahead(const qf_plan* P) {
 
 int plan_streams(qf_plan* P) {
   if (P->s_env) return QF_OK;
-  QF_CUDA(cudaStreamCreateWithFlags(&P->s_env, cudaStreamNonBlocking));
-  QF_CUDA(cudaStreamCreateWithFlags(&P->s_pass, cudaStreamNonBlocking));
+  // the environment stream has the higher priority: its CTAs take the SM
+  // slots that the running pass's CTAs free, so that a pass that fills every
+  // SM does not hold the other group's environment back until it ends
+  int lo = 0, hi = 0;
+  QF_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  QF_CUDA(cudaStreamCreateWithPriority(&P->s_env, cudaStreamNonBlocking, hi));
+  QF_CUDA(cudaStreamCreateWithPriority(&P->s_pass, cudaStreamNonBlocking, lo));
   QF_CUDA(cudaStreamCreateWithFlags(&P->s_cap, cudaStreamNonBlocking));
   cudaEvent_t* evs[] = {&P->ev_fork, &P->ev_join_env, &P->ev_join_pass, &P->ev_env[0],
                         &P->ev_env[1], &P->ev_pass[0], &P->ev_pass[1]};
@@ -598,7 +627,8 @@ int plan_sweep_once(qf_plan* P, double beta) {
       return rc;
     }
     if (e != cudaSuccess) return set_error(QF_ECUDA, "sweep capture failed: %s", cudaGetErrorString(e));
-    const cudaError_t ei = cudaGraphInstantiate(&P->graph, g, 0);
+    // the environment kernels carry a higher node priority (mark_stream_priority)
+    const cudaError_t ei = cudaGraphInstantiate(&P->graph, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (ei != cudaSuccess)
       return set_error(QF_ECUDA, "sweep graph instantiation failed: %s", cudaGetErrorString(ei));

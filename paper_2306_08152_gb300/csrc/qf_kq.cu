@@ -709,7 +709,7 @@ pass8a_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const doubl
 // writes 128 partial sums; the last CTA of the start (atomic ticket) adds
 // the CTAs' partials in a fixed order and runs the 8x8 update on one warp.
 
-constexpr int kEnv8Threads = 256;
+constexpr int kEnv8Threads = 128;
 
 template <typename R>
 __global__ void __launch_bounds__(kEnv8Threads)
@@ -919,6 +919,11 @@ __global__ void __launch_bounds__(128) reunitarize_mixed_kernel(double2* __restr
   }
 }
 
+// Grids of the complex64 passes: kPass8Waves times the resident CTAs, so
+// that CTAs retire throughout the pass and a higher-priority environment
+// kernel of the other start group finds SM room while the pass runs.
+constexpr int kPass8Waves = 8;
+
 template <typename R, bool HL, bool HR>
 void pass8_launch(void* T, int n, int S, int p0, int p1, int p2, const double2* L, long long Ls,
                   const double2* Rm, long long Rs, cudaStream_t st) {
@@ -931,14 +936,14 @@ void pass8_launch(void* T, int n, int S, int p0, int p1, int p2, const double2* 
   if (sizeof(R) == sizeof(float) && HL && p0 >= 4 && p1 >= 4 && p2 >= 4) {
     const long long agroups = 1ll << (2 * (n - 3) - 4);
     const long long awant = (agroups + 3) / 4;
-    long long acap = ((long long)sm_count() * kPass8aCtasPerSm + S - 1) / S;
+    long long acap = ((long long)sm_count() * kPass8aCtasPerSm * kPass8Waves + S - 1) / S;
     if (acap < 1) acap = 1;
     dim3 agrid((unsigned)(awant < acap ? awant : acap), S);
     pass8a_kernel<HR><<<agrid, kPass8aThreads, 0, st>>>((float2*)T, n, p0, p1, p2, L, Ls, Rm, Rs);
   } else if (sizeof(R) == sizeof(float)) {
     const long long fgroups = ((1ll << (2 * (n - 3))) + kPass8fBlocks - 1) / kPass8fBlocks;
     const long long fwant = (fgroups + 7) / 8;
-    long long fcap = ((long long)sm_count() * kPass8fCtasPerSm + S - 1) / S;
+    long long fcap = ((long long)sm_count() * kPass8fCtasPerSm * kPass8Waves + S - 1) / S;
     if (fcap < 1) fcap = 1;
     dim3 fgrid((unsigned)(fwant < fcap ? fwant : fcap), S);
     pass8f_kernel<HL, HR><<<fgrid, kPass8Threads, 0, st>>>((float2*)T, n, p0, p1, p2, L, Ls, Rm, Rs);
