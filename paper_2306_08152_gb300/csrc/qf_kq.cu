@@ -601,17 +601,20 @@ pass8f_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const doubl
   }
 }
 
-// complex64 pass for gates whose bits are all >= 4 (so n >= 7): the low four
-// column bits are then rest bits, and 16 consecutive rest columns are 16
-// adjacent entries (128 bytes).  A warp takes 16 such blocks (lane b) with
-// the same rest row, and a lane the rows x = xh, xh + 2, xh + 4, xh + 6
-// (xh = lane / 16), so every warp load or store covers two whole 128-byte
-// lines, and every broadcast operator entry serves four rows.  The R stage
-// writes each output column to the transpose buffer (or, without L, to
-// global memory); the L stage reads columns y = xh + 2j back and writes each
-// output row to global memory.  The buffer pads each block to 65 slots, so
-// both the column writes and the column reads of a warp hit every bank pair
-// exactly twice.  (Used with L; the R-only pass goes to pass8f_kernel.)
+// complex64 pass for n >= 7, used when every gate bit is >= 2.  A warp
+// takes 16 blocks (lane b) with the same rest row and 16 consecutive rest
+// columns, and a lane the rows x = xh, xh + 2, xh + 4, xh + 6 (xh = lane /
+// 16).  With every gate bit >= 4 the low four column bits are rest bits, so
+// the 16 columns a warp access takes in one row are 16 adjacent entries (a
+// whole 128-byte line); with the lowest gate bit at 2 or 3 they fall in runs
+// of 4 or 8 adjacent entries.  (Gates on bit 0 or 1 leave runs of one or two
+// entries, where pass8f_kernel's layout is faster.)  Every broadcast
+// operator entry serves four rows.  The R stage (the identity without R)
+// writes each output column to the transpose buffer; the L stage reads
+// columns y = xh + 2j back and writes each output row to global memory.
+// The buffer pads each block to 65 slots, so both the column writes and the
+// column reads of a warp hit every bank pair exactly twice.  (Used with L;
+// the R-only pass goes to pass8f_kernel.)
 constexpr int kPass8aThreads = 128;
 constexpr int kPass8aCtasPerSm = 4;
 constexpr int kBlkA = 65;
@@ -933,7 +936,7 @@ void pass8_launch(void* T, int n, int S, int p0, int p1, int p2, const double2* 
   long long cap = ((long long)sm_count() * 4 + S - 1) / S;
   if (cap < 1) cap = 1;
   dim3 grid((unsigned)(want < cap ? want : cap), S);
-  if (sizeof(R) == sizeof(float) && HL && p0 >= 4 && p1 >= 4 && p2 >= 4) {
+  if (sizeof(R) == sizeof(float) && HL && n >= 7 && p0 >= 2 && p1 >= 2 && p2 >= 2) {
     const long long agroups = 1ll << (2 * (n - 3) - 4);
     const long long awant = (agroups + 3) / 4;
     long long acap = ((long long)sm_count() * kPass8aCtasPerSm * kPass8Waves + S - 1) / S;
