@@ -389,6 +389,62 @@ int qf_plan_create_k(int n_qubits, int n_gates, const qf_gate_loc* locations,
 int qf_plan_gate_entries(qf_plan* plan, int64_t* entries_per_start);
 
 /* ------------------------------------------------------------------------
+ * Specialised gate sets (Sec. III-A, "Specializing gate sets").  A circuit
+ * may mix general unitaries with parameterised gates G(theta), whose
+ * update is the closed-form theta' = argmax Re Tr(A G(theta)) (A = E, or
+ * (1 - beta) E + beta u^dagger with damping) instead of the SVD:
+ *   QF_GATE_RZ   Rz(theta) = diag(1, e^{i theta}) on q[0];
+ *                theta' = -arg A1[1][1]
+ *   QF_GATE_GPI  GPI(phi) = [[0, e^{-i phi}], [e^{i phi}, 0]] on q[0];
+ *                phi' = -arg(A1[0][1] + conj A1[1][0])
+ *   QF_GATE_MS   Moelmer-Soerensen MS(phi0, phi1) on (q[0], q[1]):
+ *                (1/sqrt 2) [[1,0,0,-i e^{-i(phi0+phi1)}],
+ *                            [0,1,-i e^{-i(phi0-phi1)},0],
+ *                            [0,-i e^{i(phi0-phi1)},1,0],
+ *                            [-i e^{i(phi0+phi1)},0,0,1]];
+ *                phi0 + phi1 = -arg z_a, phi0 - phi1 = -arg z_b with
+ *                z_a = -i (A[0][3] - conj A[3][0]), z_b = -i (A[1][2] - conj A[2][1])
+ *   QF_GATE_U4, QF_GATE_U8  general unitaries on 2 or 3 qubits (SVD update).
+ * An angle whose modulus is zero keeps its old value.  RZ and GPI run as
+ * G (x) I in a 4x4 slot on (q[0], q[1]) (local index 2 bit(q[0]) +
+ * bit(q[1])), q[1] being any other qubit, or, for q[1] < 0, q[0] + 1
+ * (q[0] - 1 for the last qubit); A1[x][y] = sum_r A[2x+r][2y+r] is the
+ * one-qubit environment.  Every gate takes a slot of E entries as in
+ * qf_plan_create_k (16, or 64 for QF_GATE_U8), and two parameters per
+ * (start, gate) (theta in the first for RZ and GPI; none used for general
+ * gates), start stride 2 n_gates.
+ * ---------------------------------------------------------------------- */
+#define QF_GATE_U4 0
+#define QF_GATE_U8 1
+#define QF_GATE_RZ 2
+#define QF_GATE_GPI 3
+#define QF_GATE_MS 4
+
+typedef struct {
+    int32_t kind;  /* QF_GATE_* */
+    int32_t q[3];  /* qubits (q[1] of RZ/GPI: the slot's partner qubit, < 0 automatic) */
+} qf_gate_spec;
+
+/* A resident plan for a circuit of specialised and general gates (as
+ * qf_plan_create_k).  The look-ahead flag is ignored for these plans.
+ * Errors: QF_EINVAL for an unknown kind, repeated or out-of-range qubits. */
+int qf_plan_create_spec(int n_qubits, int n_gates, const qf_gate_spec* gates,
+                        int n_starts, int precision, qf_plan** out_plan);
+
+/* Load the target (N x N), the general gates' matrices (n_starts x E
+ * entries, the slots of parameterised gates ignored; NULL if the circuit
+ * has no general gate) and the parameters (n_starts x n_gates x 2 doubles),
+ * all host-or-device; the parameterised gates' matrices are built from the
+ * parameters on the device, then every tensor is built (InitCircuitTensor).
+ * Non-finite inputs raise the plan status.  Enqueue only. */
+int qf_plan_load_spec(qf_plan* plan, const qf_c128* target, const qf_c128* gates,
+                      const double* params, void* stream);
+
+/* The current parameters, n_starts x n_gates x 2 doubles (host or device).
+ * Synchronises. */
+int qf_plan_get_params(qf_plan* plan, double* out_params);
+
+/* ------------------------------------------------------------------------
  * Single steps of the sweep (Alg. 1), on device arrays, enqueue only.
  * ---------------------------------------------------------------------- */
 

@@ -64,6 +64,17 @@ class qf_gate_loc(ct.Structure):
     _fields_ = [("k", ct.c_int32), ("q", ct.c_int32 * 3)]
 
 
+class qf_gate_spec(ct.Structure):
+    _fields_ = [("kind", ct.c_int32), ("q", ct.c_int32 * 3)]
+
+
+QF_GATE_U4 = 0
+QF_GATE_U8 = 1
+QF_GATE_RZ = 2
+QF_GATE_GPI = 3
+QF_GATE_MS = 4
+
+
 class qf_batch_stats(ct.Structure):
     _fields_ = [
         ("warps_per_cta", ct.c_int32),
@@ -120,6 +131,9 @@ SIGNATURES = {
                              ct.POINTER(qf_result), P]),
     "qf_plan_create_k": (I, [I, I, P, I, I, ct.POINTER(P)]),
     "qf_plan_gate_entries": (I, [P, I64P]),
+    "qf_plan_create_spec": (I, [I, I, P, I, I, ct.POINTER(P)]),
+    "qf_plan_load_spec": (I, [P, P, P, P, P]),
+    "qf_plan_get_params": (I, [P, P]),
     "qf_apply_gate_k": (I, [P, I, I, P, P, P, I, P]),
     "qf_partial_trace_k": (I, [P, I, I, P, P, I, P]),
     "qf_optimize_gates_k": (I, [P, I, P, D, I, P, P, P]),

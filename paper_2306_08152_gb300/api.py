@@ -22,6 +22,7 @@ __all__ = [
     "partial_trace", "partial_trace_noalloc", "apply_two_pairs", "partial_trace_after", "convert_tensor",
     "instantiate_k", "apply_gate_k", "partial_trace_k", "optimize_gates_k", "init_tensor_k",
     "circuit_unitary_k", "flatten_gates", "unflatten_gates", "gate_entries", "optimize_gates", "reunitarize_gates", "trace", "circuit_unitary",
+    "gate_specs", "spec_slots",
 ]
 
 QF_C128 = nat.QF_C128
@@ -86,6 +87,48 @@ def _gate_locs(locations):
         for j, x in enumerate(q):
             arr[i].q[j] = x
     return arr, locs
+
+
+_SPEC_KINDS = {"u4": nat.QF_GATE_U4, "u8": nat.QF_GATE_U8, "rz": nat.QF_GATE_RZ,
+               "gpi": nat.QF_GATE_GPI, "ms": nat.QF_GATE_MS}
+
+
+def _is_specs(locations):
+    """True for a sequence of (kind, qubit, ...) tuples with a string kind."""
+    return (not isinstance(locations, (torch.Tensor, np.ndarray)) and len(locations) > 0
+            and all(isinstance(g, (tuple, list)) and isinstance(g[0], str) for g in locations))
+
+
+def gate_specs(specs):
+    """ctypes array of qf_gate_spec from (kind, q0[, q1[, q2]]) tuples, kind
+    one of "u4", "u8", "rz", "gpi", "ms" (Sec. III-A, specialised gate sets);
+    "rz"/"gpi" take an optional partner qubit for their 4x4 slot."""
+    arr = (nat.qf_gate_spec * len(specs))()
+    for i, g in enumerate(specs):
+        kind = g[0].lower()
+        if kind not in _SPEC_KINDS:
+            raise ValueError(f"unknown gate kind {g[0]!r}")
+        arr[i].kind = _SPEC_KINDS[kind]
+        q = [int(x) for x in g[1:]] + [-1] * (4 - len(g))
+        for j in range(3):
+            arr[i].q[j] = q[j]
+    return arr
+
+
+def spec_slots(specs, n_qubits):
+    """The qubits of each gate's matrix slot: (a, b) for 4x4 slots (rz/gpi
+    with their partner qubit, automatic: q0 + 1, or q0 - 1 for the last
+    qubit), (a, b, c) for "u8"."""
+    out = []
+    for g in specs:
+        kind = g[0].lower()
+        q = [int(x) for x in g[1:]]
+        if kind in ("rz", "gpi"):
+            partner = q[1] if len(q) > 1 and q[1] >= 0 else (q[0] + 1 if q[0] + 1 < n_qubits else q[0] - 1)
+            out.append((q[0], partner))
+        else:
+            out.append(tuple(q))
+    return out
 
 
 def gate_entries(locations):
@@ -297,8 +340,15 @@ class Plan:
         self.n = int(n_qubits)
         self.S = int(n_starts)
         h = ct.c_void_p()
-        self.k_path = not _is_pairs(locations)
-        if self.k_path:
+        self.spec = _is_specs(locations)
+        self.k_path = self.spec or not _is_pairs(locations)
+        if self.spec:
+            self.specs = [tuple(g) for g in locations]
+            self._sarr = gate_specs(self.specs)
+            self.p = len(self.specs)
+            check(_lib().qf_plan_create_spec(self.n, self.p, self._sarr, self.S, int(precision),
+                                             ct.byref(h)))
+        elif self.k_path:
             self._larr, self.locations = _gate_locs(locations)
             self.p = len(self.locations)
             check(_lib().qf_plan_create_k(self.n, self.p, self._larr, self.S, int(precision),
@@ -328,6 +378,25 @@ class Plan:
         self._t = _c128(target, "target")
         self._g = _c128(gates, "gates")
         check(_lib().qf_plan_load(self.h, _ptr(self._t), _ptr(self._g), _stream_handle(stream)))
+
+    def load_params(self, target, params, gates=None, stream=None):
+        """Specialised-gate plans: load the target, the parameters (S, p, 2)
+        float64 and, for circuits with general gates, their matrices in the
+        concatenated layout (S, E)."""
+        self._t = _c128(target, "target")
+        pr = params if isinstance(params, torch.Tensor) else torch.as_tensor(np.asarray(params, dtype=np.float64))
+        if pr.dtype != torch.float64:
+            raise TypeError("params must be float64")
+        self._p = pr.contiguous()
+        self._g = _c128(gates, "gates") if gates is not None else None
+        check(_lib().qf_plan_load_spec(self.h, _ptr(self._t), _ptr(self._g) if self._g is not None else None,
+                                       _ptr(self._p), _stream_handle(stream)))
+
+    def params(self, device="cpu"):
+        """Specialised-gate plans: the current parameters, (S, p, 2) float64."""
+        out = torch.empty((self.S, self.p, 2), dtype=torch.float64, device=device)
+        check(_lib().qf_plan_get_params(self.h, _ptr(out)))
+        return out
 
     def sweep(self, n_sweeps=1, reset_iter=40, beta=0.0):
         check(_lib().qf_plan_sweep(self.h, int(n_sweeps), int(reset_iter), float(beta)))

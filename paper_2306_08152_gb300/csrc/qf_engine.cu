@@ -103,6 +103,7 @@ struct GateDesc {
   int k;
   int q[3];
   long long off;
+  int kind = qf::kGateGeneral;  // parameterised kinds occupy a 4x4 slot (k = 2)
 };
 
 int descs_from_pairs(const std::vector<qf_loc>& locs, std::vector<GateDesc>* out, long long* gsz) {
@@ -111,6 +112,48 @@ int descs_from_pairs(const std::vector<qf_loc>& locs, std::vector<GateDesc>* out
     (*out)[i] = GateDesc{2, {locs[i].a, locs[i].b, -1}, (long long)i * 16};
   }
   *gsz = (long long)locs.size() * 16;
+  return QF_OK;
+}
+
+// Copy gate specifications (host or device) and validate them.  RZ and GPI
+// act on q[0]; their 4x4 slot pairs it with q[1] (any other qubit), or, for
+// q[1] < 0, with q[0] + 1 (q[0] - 1 for the last qubit).
+int fetch_gate_specs(const qf_gate_spec* specs, int n, int p, std::vector<GateDesc>* out,
+                     long long* gsz) {
+  if (!specs) return set_error(QF_EINVAL, "gate specifications are NULL");
+  std::vector<qf_gate_spec> h(p);
+  if (is_device_ptr(specs)) {
+    QF_CUDA(cudaMemcpy(h.data(), specs, sizeof(qf_gate_spec) * p, cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(h.data(), specs, sizeof(qf_gate_spec) * p);
+  }
+  out->resize(p);
+  long long off = 0;
+  for (int i = 0; i < p; ++i) {
+    const qf_gate_spec& g = h[i];
+    int k = 2, kind = qf::kGateGeneral, q[3] = {g.q[0], g.q[1], -1};
+    switch (g.kind) {
+      case QF_GATE_U4: break;
+      case QF_GATE_U8: k = 3; q[2] = g.q[2]; break;
+      case QF_GATE_MS: kind = qf::kGateMs; break;
+      case QF_GATE_RZ:
+      case QF_GATE_GPI:
+        kind = g.kind == QF_GATE_RZ ? qf::kGateRz : qf::kGateGpi;
+        if (q[1] < 0) q[1] = q[0] + 1 < n ? q[0] + 1 : q[0] - 1;
+        break;
+      default: return set_error(QF_EINVAL, "gate %d: unknown kind %d", i, g.kind);
+    }
+    if (k > n) return set_error(QF_EINVAL, "gate %d: %d qubits > n_qubits=%d", i, k, n);
+    for (int a = 0; a < k; ++a) {
+      if (q[a] < 0 || q[a] >= n)
+        return set_error(QF_EINVAL, "gate %d: qubit %d invalid for %d qubits", i, q[a], n);
+      for (int b = 0; b < a; ++b)
+        if (q[a] == q[b]) return set_error(QF_EINVAL, "gate %d: repeated qubit %d", i, q[a]);
+    }
+    (*out)[i] = GateDesc{k, {q[0], q[1], q[2]}, off, kind};
+    off += k == 3 ? 64 : 16;
+  }
+  *gsz = off;
   return QF_OK;
 }
 
@@ -215,6 +258,10 @@ struct qf_plan {
   bool mixed = false;        // some gate acts on three qubits
   DevBuf T, V, gates, LR, sigma, tr, status, part, counters;
   DevBuf LR8, gdesc;         // three-qubit pass operators (start stride 128); gate table
+  // parameterised gates: (kind, entry offset) per gate and 2 parameters per
+  // (start, gate), start stride 2p
+  bool spec = false;
+  DevBuf ptab, params;
   size_t T_capacity = 0;  // bytes
   cudaStream_t stream = nullptr;
   long long sweeps_since_load = 0;
@@ -393,12 +440,16 @@ int plan_update(qf_plan* P, const Slice& sl, int k, int mode, double beta, doubl
     P->all_launches++;
     return mark_stream_priority(sl.st);
   }
+  const int kind = P->gd[k].kind;
+  double* prm = kind == qf::kGateGeneral ? nullptr
+                                         : P->params.as<double>() + (size_t)sl.s0 * 2 * P->p + 2 * k;
   QF_CUDA(qf::launch_update(
       T, P->n, sl.Sg, P->locs[k].a, P->locs[k].b, gate_ptr(P, sl.s0, k), P->gsz,
       mode, beta, P->LR.as<double2>() + (size_t)sl.s0 * 32,
       env_out ? env_out + sl.s0 * env_stride : nullptr, env_stride,
       P->sigma.as<double>() + sl.s0, P->status.as<int>(),
-      P->part.as<double>() + (size_t)sl.s0 * B * 32, P->counters.as<unsigned>() + sl.s0, pr, sl.st));
+      P->part.as<double>() + (size_t)sl.s0 * B * 32, P->counters.as<unsigned>() + sl.s0, pr, sl.st,
+      kind, prm, 2LL * P->p));
   P->all_launches++;
   return mark_stream_priority(sl.st);
 }
@@ -472,7 +523,7 @@ int plan_windows(qf_plan* P) {
 }
 
 bool plan_uses_lookahead(const qf_plan* P) {
-  return P->lookahead && !P->mixed && P->prec == QF_C64 && P->n >= 8;
+  return P->lookahead && !P->mixed && !P->spec && P->prec == QF_C64 && P->n >= 8;
 }
 
 int plan_streams(qf_plan* P) {
@@ -752,6 +803,11 @@ int plan_reset(qf_plan* P) {
   else
     QF_CUDA(qf::launch_reunitarize(P->gates.as<double2>(), P->S * P->p, P->stream));
   P->all_launches++;
+  if (P->spec) {  // parameterised gates: exactly G(theta) again
+    QF_CUDA(qf::launch_param_gates(P->gates.as<double2>(), P->gsz, P->ptab.as<int2>(),
+                                   P->params.as<double>(), 2LL * P->p, P->p, P->S, P->stream));
+    P->all_launches++;
+  }
   return plan_build(P);
 }
 
@@ -1099,6 +1155,70 @@ int qf_plan_create_k(int n_qubits, int n_gates, const qf_gate_loc* locations, in
   long long gsz = 0;
   QF_TRY(fetch_gate_locs(locations, n_qubits, n_gates, &gd, &gsz));
   return plan_create_desc(n_qubits, gd, gsz, n_starts, precision, out_plan);
+}
+
+int qf_plan_create_spec(int n_qubits, int n_gates, const qf_gate_spec* gates, int n_starts,
+                        int precision, qf_plan** out_plan) {
+  if (out_plan) *out_plan = nullptr;
+  QF_TRY(check_sizes(n_qubits, n_gates));
+  std::vector<GateDesc> gd;
+  long long gsz = 0;
+  QF_TRY(fetch_gate_specs(gates, n_qubits, n_gates, &gd, &gsz));
+  qf_plan* P = nullptr;
+  QF_TRY(plan_create_desc(n_qubits, gd, gsz, n_starts, precision, &P));
+  std::vector<int2> tab(n_gates);
+  for (int k = 0; k < n_gates; ++k) tab[k] = make_int2(gd[k].kind, (int)gd[k].off);
+  int rc = P->ptab.alloc(sizeof(int2) * n_gates);
+  if (rc == QF_OK) rc = P->params.alloc(sizeof(double) * 2 * n_gates * (size_t)n_starts);
+  if (rc == QF_OK &&
+      (cudaMemcpy(P->ptab.p, tab.data(), sizeof(int2) * n_gates, cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemset(P->params.p, 0, sizeof(double) * 2 * n_gates * (size_t)n_starts) != cudaSuccess))
+    rc = set_error(QF_ECUDA, "copying the gate kinds failed");
+  if (rc != QF_OK) {
+    qf_plan_destroy(P);
+    return rc;
+  }
+  P->spec = true;
+  *out_plan = P;
+  return QF_OK;
+}
+
+int qf_plan_load_spec(qf_plan* plan, const qf_c128* target, const qf_c128* gates,
+                      const double* params, void* stream) {
+  if (!plan) return set_error(QF_EINVAL, "plan is NULL");
+  if (!plan->spec) return set_error(QF_EINVAL, "the plan was not made by qf_plan_create_spec");
+  if (!target || !params) return set_error(QF_EINVAL, "target or params is NULL");
+  bool general = false;
+  for (const GateDesc& g : plan->gd) general |= g.kind == qf::kGateGeneral;
+  if (general && !gates) return set_error(QF_EINVAL, "gates is NULL but the circuit has general gates");
+  qf_plan* P = plan;
+  const cudaStream_t st = as_stream(stream);
+  P->stream = st;
+  const size_t gcount = (size_t)P->S * P->gsz;
+  const size_t pcount = (size_t)P->S * 2 * P->p;
+  QF_CUDA(cudaMemcpyAsync(P->V.p, target, P->NN * sizeof(double2), cudaMemcpyDefault, st));
+  if (gates)
+    QF_CUDA(cudaMemcpyAsync(P->gates.p, gates, gcount * sizeof(double2), cudaMemcpyDefault, st));
+  else
+    QF_CUDA(cudaMemsetAsync(P->gates.p, 0, gcount * sizeof(double2), st));
+  QF_CUDA(cudaMemcpyAsync(P->params.p, params, pcount * sizeof(double), cudaMemcpyDefault, st));
+  QF_CUDA(cudaMemsetAsync(P->status.p, 0, sizeof(int), st));
+  QF_CUDA(qf::launch_check_finite(P->params.as<double>(), pcount, P->status.as<int>(), st));
+  QF_CUDA(qf::launch_param_gates(P->gates.as<double2>(), P->gsz, P->ptab.as<int2>(), P->params.as<double>(),
+                                 2LL * P->p, P->p, P->S, st));
+  QF_CUDA(qf::launch_check_finite(P->V.as<double>(), P->NN * 2, P->status.as<int>(), st));
+  QF_CUDA(qf::launch_check_finite(P->gates.as<double>(), gcount * 2, P->status.as<int>(), st));
+  P->sweeps_since_load = 0;
+  return plan_build(P);
+}
+
+int qf_plan_get_params(qf_plan* plan, double* out_params) {
+  if (!plan) return set_error(QF_EINVAL, "plan is NULL");
+  if (!plan->spec) return set_error(QF_EINVAL, "the plan was not made by qf_plan_create_spec");
+  QF_TRY(store_output(reinterpret_cast<qf_c128*>(out_params), plan->params.as<double2>(),
+                      (size_t)plan->S * plan->p, plan->stream));
+  QF_CUDA(cudaStreamSynchronize(plan->stream));
+  return QF_OK;
 }
 
 int qf_plan_gate_entries(qf_plan* plan, int64_t* entries_per_start) {

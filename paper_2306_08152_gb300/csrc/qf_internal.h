@@ -15,6 +15,18 @@ enum UpdateMode {
   kTraceOnly = 3,  // P written out
 };
 
+// Gate kinds of the 4x4 update (Sec. III-A, "Specializing gate sets").
+// kGateGeneral is a general unitary (the SVD update); the others are
+// parameterised gates whose update is the closed-form argmax of
+// Re Tr(E G(theta)).  A one-qubit kind acts as G (x) I on its qubit and a
+// partner qubit (local index 2 bit(qubit) + bit(partner)).
+enum GateKind {
+  kGateGeneral = 0,
+  kGateRz = 2,   // diag(1, e^{i theta})
+  kGateGpi = 3,  // [[0, e^{-i phi}], [e^{i phi}, 0]]
+  kGateMs = 4,   // Moelmer-Soerensen MS(phi0, phi1)
+};
+
 // Bit position of qubit q in an n-bit row or column index (qubit 0 = MSB).
 inline int qubit_bit(int n, int q) { return n - 1 - q; }
 
@@ -38,12 +50,23 @@ int env_ctas(int n);
 // receives the singular-value sum.  part (S * env_ctas(n) * 32 doubles) and
 // counters (S unsigned: zero before the first launch, left zero after each
 // launch) are scratch owned by the caller.
+// kind selects the update (GateKind); a parameterised kind reads its old
+// parameters from and writes the new ones to prm + s * prm_stride (2
+// doubles), and sigma_out receives the maximised Re Tr(A G).
 cudaError_t launch_update(const void* T, int n, int S, int a, int b,
                           double2* gates_k, long long gstride, int mode,
                           double beta, double2* LR, double2* out,
                           long long out_stride, double* sigma_out, int* status,
                           double* part, unsigned* counters, int prec,
-                          cudaStream_t st);
+                          cudaStream_t st, int kind = kGateGeneral,
+                          double* prm = nullptr, long long prm_stride = 0);
+
+// The 4x4 matrices of the parameterised gates: for every start s and gate
+// g with tab[g].x != kGateGeneral, gates[s * gsz + tab[g].y ...] (16
+// entries) <- G(params[s * prm_stride + 2 g ...]).  Other gates untouched.
+cudaError_t launch_param_gates(double2* gates, long long gsz, const int2* tab,
+                               const double* params, long long prm_stride, int p,
+                               int S, cudaStream_t st);
 
 // launch_update for a gate on (a, b) whose environment is taken from a tensor
 // that still lacks the pending update of the preceding gate on the disjoint

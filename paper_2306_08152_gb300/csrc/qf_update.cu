@@ -20,6 +20,90 @@ using namespace dev;
 
 constexpr int kEnvThreads = 256;
 
+// ------------------------------------------- parameterised gate updates
+//
+// Sec. III-A ("Specializing gate sets"): for a parameterised gate G(theta)
+// the update is theta' = argmax Re Tr(A G(theta)) (A = E, or the damped
+// (1 - beta) E + beta u^dagger), in closed form.  With A the 4x4 matrix of
+// the gate's slot and, for one-qubit kinds, A1[x][y] = sum_r A[2x+r][2y+r]:
+//   Rz:  Re Tr = Re A1[0][0] + Re(e^{i theta} z), z = A1[1][1];
+//   GPI: Re Tr = Re(e^{i phi} z), z = A1[0][1] + conj A1[1][0];
+//   MS:  sqrt 2 Re Tr = Re Tr A + Re(e^{i a} z_a) + Re(e^{i b} z_b),
+//        a = phi0 + phi1, b = phi0 - phi1,
+//        z_a = -i (A[0][3] - conj A[3][0]), z_b = -i (A[1][2] - conj A[2][1]);
+// each angle is -arg of its z (kept where z = 0: every angle is optimal).
+
+// Entry e = 4 i + j of the 4x4 slot matrix of gate kind with parameters
+// (p0, p1); one-qubit kinds are G (x) I.
+__device__ __forceinline__ double2 param_gate_entry(int kind, double p0, double p1, int e) {
+  const int i = e >> 2, j = e & 3;
+  if (kind == kGateMs) {
+    const double h = 0.70710678118654752440;  // 1 / sqrt 2
+    if (i == j) return make_double2(h, 0.0);
+    if (i + j != 3) return make_double2(0.0, 0.0);
+    // -i e^{i t} = (sin t, -cos t) with t = -a, -b, b, a for i = 0, 1, 2, 3
+    const double t = (i == 0) ? -(p0 + p1) : (i == 1) ? -(p0 - p1) : (i == 2) ? (p0 - p1) : (p0 + p1);
+    double sn, cs;
+    sincos(t, &sn, &cs);
+    return make_double2(h * sn, -h * cs);
+  }
+  if ((i & 1) != (j & 1)) return make_double2(0.0, 0.0);
+  const int x = i >> 1, y = j >> 1;
+  double sn, cs;
+  if (kind == kGateRz) {
+    if (x != y) return make_double2(0.0, 0.0);
+    if (x == 0) return make_double2(1.0, 0.0);
+    sincos(p0, &sn, &cs);
+    return make_double2(cs, sn);
+  }
+  // GPI: [[0, e^{-i phi}], [e^{i phi}, 0]]
+  if (x == y) return make_double2(0.0, 0.0);
+  sincos(p0, &sn, &cs);
+  return make_double2(cs, x == 0 ? -sn : sn);
+}
+
+// The warp's closed-form update: lane e (mod 16) holds A[e]; returns the new
+// slot matrix's entry e and the maximum in *sg; prm (2 doubles) holds the
+// old parameters and receives the new ones.  false (prm untouched) if the
+// maximiser is not finite.
+__device__ __noinline__ bool param_update(int kind, double2 A, double* prm, double2* un, double* sg) {
+  const int l = threadIdx.x & 31, e = l & 15;
+  double2 a[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) a[j] = shfl(A, j);
+  const double o0 = prm[0], o1 = prm[1];
+  __syncwarp();
+  double p0 = o0, p1 = o1, best;
+  if (kind == kGateMs) {
+    const double2 wa = make_double2(a[3].x - a[12].x, a[3].y + a[12].y);  // A03 - conj A30
+    const double2 wb = make_double2(a[6].x - a[9].x, a[6].y + a[9].y);    // A12 - conj A21
+    const double2 za = make_double2(wa.y, -wa.x), zb = make_double2(wb.y, -wb.x);  // -i w
+    double ta = o0 + o1, tb = o0 - o1;
+    if (za.x != 0.0 || za.y != 0.0) ta = atan2(-za.y, za.x);
+    if (zb.x != 0.0 || zb.y != 0.0) tb = atan2(-zb.y, zb.x);
+    p0 = 0.5 * (ta + tb);
+    p1 = 0.5 * (ta - tb);
+    best = (a[0].x + a[5].x + a[10].x + a[15].x + hypot(za.x, za.y) + hypot(zb.x, zb.y)) *
+           0.70710678118654752440;
+  } else if (kind == kGateRz) {
+    const double2 z = make_double2(a[10].x + a[15].x, a[10].y + a[15].y);
+    if (z.x != 0.0 || z.y != 0.0) p0 = atan2(-z.y, z.x);
+    best = a[0].x + a[5].x + hypot(z.x, z.y);
+  } else {  // GPI
+    const double2 z = make_double2(a[2].x + a[7].x + a[8].x + a[13].x, a[2].y + a[7].y - a[8].y - a[13].y);
+    if (z.x != 0.0 || z.y != 0.0) p0 = atan2(-z.y, z.x);
+    best = hypot(z.x, z.y);
+  }
+  if (!isfinite(p0) || !isfinite(p1)) return false;
+  if (l == 0) {
+    prm[0] = p0;
+    prm[1] = p1;
+  }
+  *un = param_gate_entry(kind, p0, p1, e);
+  *sg = best;
+  return true;
+}
+
 // ----------------------------------------------------- environment kernel
 //
 // Grid (B, S): CTA b of start s sums the band entries of rests
@@ -43,7 +127,8 @@ __global__ void __launch_bounds__(kEnvThreads) env_kernel(
     int mode, double2* __restrict__ gates_k, long long gstride, double beta,
     double2* __restrict__ LR, double2* __restrict__ out, long long out_stride,
     double* __restrict__ sigma_out, int* __restrict__ status, double* __restrict__ part,
-    unsigned* __restrict__ counters, LookGeom lg) {
+    unsigned* __restrict__ counters, LookGeom lg, int kind, double* __restrict__ prm,
+    long long prm_stride) {
   using CT = typename Cplx<R>::T;   // tensor entry
   using Ar = typename Acc<R>::T;    // accumulation real (FP32 for complex64, else FP64)
   using AT = typename Cplx<Ar>::T;
@@ -171,7 +256,9 @@ __global__ void __launch_bounds__(kEnvThreads) env_kernel(
     A = make_double2((1.0 - beta) * E.x + beta * ud.x, (1.0 - beta) * E.y + beta * ud.y);
   double2 un;
   double sg = 0.0;
-  if (!warp_polar(L, A, scratch, &un, &sg)) {
+  const bool ok = kind == kGateGeneral ? warp_polar(L, A, scratch, &un, &sg)
+                                       : param_update(kind, A, prm + s * prm_stride, &un, &sg);
+  if (!ok) {
     if (L.l == 0) atomicExch(status, -4);
     un = u;  // keep the old gate: the tensor stays consistent
     sg = 0.0;
@@ -187,6 +274,21 @@ __global__ void __launch_bounds__(kEnvThreads) env_kernel(
     }
   }
   if (sigma_out && L.l == 0) sigma_out[s] = sg;
+}
+
+// The slot matrices of the parameterised gates from their parameters, one
+// thread per entry.
+__global__ void param_gates_kernel(double2* __restrict__ gates, long long gsz, const int2* __restrict__ tab,
+                                   const double* __restrict__ params, long long prm_stride, int p, int S) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)S * p * 16) return;
+  const int e = (int)(idx & 15);
+  const long long sg = idx >> 4;
+  const int g = (int)(sg % p), s = (int)(sg / p);
+  const int2 t = tab[g];
+  if (t.x == kGateGeneral) return;
+  const double* pr = params + s * prm_stride + 2 * g;
+  gates[s * gsz + t.y + e] = param_gate_entry(t.x, pr[0], pr[1], e);
 }
 
 // One warp per matrix.
@@ -298,15 +400,15 @@ cudaError_t launch_update_lookahead(const void* T, int n, int S, int a1, int b1,
   if (prec == 0)
     env_kernel<double, true><<<grid, kEnvThreads, 0, st>>>(
         (const double2*)T, n, 0, 0, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
-        sigma_out, status, part, counters, lg);
+        sigma_out, status, part, counters, lg, kGateGeneral, nullptr, 0);
   else if (prec == 2)
     env_kernel<DF, true><<<grid, kEnvThreads, 0, st>>>(
         (const dfc*)T, n, 0, 0, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
-        sigma_out, status, part, counters, lg);
+        sigma_out, status, part, counters, lg, kGateGeneral, nullptr, 0);
   else
     env_kernel<float, true><<<grid, kEnvThreads, 0, st>>>(
         (const float2*)T, n, 0, 0, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
-        sigma_out, status, part, counters, lg);
+        sigma_out, status, part, counters, lg, kGateGeneral, nullptr, 0);
   return cudaGetLastError();
 }
 
@@ -321,22 +423,32 @@ int env_ctas(int n) {
 cudaError_t launch_update(const void* T, int n, int S, int a, int b, double2* gates_k,
                           long long gstride, int mode, double beta, double2* LR, double2* out,
                           long long out_stride, double* sigma_out, int* status, double* part,
-                          unsigned* counters, int prec, cudaStream_t st) {
+                          unsigned* counters, int prec, cudaStream_t st, int kind, double* prm,
+                          long long prm_stride) {
   const int pa = qubit_bit(n, a), pb = qubit_bit(n, b);
   const int plo = pa < pb ? pa : pb, phi = pa < pb ? pb : pa;
   dim3 grid(env_ctas(n), S);
   if (prec == 0)
     env_kernel<double, false><<<grid, kEnvThreads, 0, st>>>(
         (const double2*)T, n, plo, phi, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
-        sigma_out, status, part, counters, LookGeom{});
+        sigma_out, status, part, counters, LookGeom{}, kind, prm, prm_stride);
   else if (prec == 2)
     env_kernel<DF, false><<<grid, kEnvThreads, 0, st>>>(
         (const dfc*)T, n, plo, phi, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
-        sigma_out, status, part, counters, LookGeom{});
+        sigma_out, status, part, counters, LookGeom{}, kind, prm, prm_stride);
   else
     env_kernel<float, false><<<grid, kEnvThreads, 0, st>>>(
         (const float2*)T, n, plo, phi, pa, pb, mode, gates_k, gstride, beta, LR, out, out_stride,
-        sigma_out, status, part, counters, LookGeom{});
+        sigma_out, status, part, counters, LookGeom{}, kind, prm, prm_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_param_gates(double2* gates, long long gsz, const int2* tab, const double* params,
+                               long long prm_stride, int p, int S, cudaStream_t st) {
+  const long long count = (long long)S * p * 16;
+  if (count <= 0) return cudaSuccess;
+  param_gates_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(gates, gsz, tab, params, prm_stride,
+                                                                      p, S);
   return cudaGetLastError();
 }
 
