@@ -425,6 +425,19 @@ typedef struct {
     int32_t q[3];  /* qubits (q[1] of RZ/GPI: the slot's partner qubit, < 0 automatic) */
 } qf_gate_spec;
 
+/* qf_instantiate_ex for a circuit of specialised and general gates: the
+ * same stopping rules, multistart and precision phases.  initial_gates:
+ * host-or-device n_starts x E entries, the general gates' matrices (the
+ * parameterised slots ignored; NULL if every gate is parameterised);
+ * initial_params / out_params: host-or-device n_starts x n_gates x 2
+ * doubles; out_gates receives every slot matrix (n_starts x E).  Errors as
+ * qf_instantiate_ex and qf_plan_create_spec. */
+int qf_instantiate_spec(const qf_c128* target, int n_qubits, int n_gates,
+                        const qf_gate_spec* gates, int n_starts,
+                        const qf_c128* initial_gates, const double* initial_params,
+                        const qf_options* opts, qf_c128* out_gates, double* out_params,
+                        double* out_costs, qf_result* out_result, void* stream);
+
 /* A resident plan for a circuit of specialised and general gates (as
  * qf_plan_create_k).  The look-ahead flag is ignored for these plans.
  * Errors: QF_EINVAL for an unknown kind, repeated or out-of-range qubits. */

@@ -132,6 +132,8 @@ SIGNATURES = {
     "qf_plan_create_k": (I, [I, I, P, I, I, ct.POINTER(P)]),
     "qf_plan_gate_entries": (I, [P, I64P]),
     "qf_plan_create_spec": (I, [I, I, P, I, I, ct.POINTER(P)]),
+    "qf_instantiate_spec": (I, [P, I, I, P, I, P, P, ct.POINTER(qf_options), P, P, DP,
+                                ct.POINTER(qf_result), P]),
     "qf_plan_load_spec": (I, [P, P, P, P, P]),
     "qf_plan_get_params": (I, [P, P]),
     "qf_apply_gate_k": (I, [P, I, I, P, P, P, I, P]),

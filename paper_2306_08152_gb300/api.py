@@ -22,7 +22,7 @@ __all__ = [
     "partial_trace", "partial_trace_noalloc", "apply_two_pairs", "partial_trace_after", "convert_tensor",
     "instantiate_k", "apply_gate_k", "partial_trace_k", "optimize_gates_k", "init_tensor_k",
     "circuit_unitary_k", "flatten_gates", "unflatten_gates", "gate_entries", "optimize_gates", "reunitarize_gates", "trace", "circuit_unitary",
-    "gate_specs", "spec_slots",
+    "gate_specs", "spec_slots", "instantiate_spec",
 ]
 
 QF_C128 = nat.QF_C128
@@ -592,6 +592,39 @@ def instantiate_k(target, locations, starts, options=None, stream=None, **kw):
                                   _stream_handle(stream)))
     return {"gates": unflatten_gates(out, locs), "flat": out, "costs": np.array(costs[:]),
             "best": res.best_start, "sweeps": res.sweeps, "c64_sweeps": res.c64_sweeps,
+            "reason": nat.REASONS.get(res.reason, str(res.reason)), "best_cost": res.best_cost}
+
+
+def instantiate_spec(target, specs, params, gates=None, options=None, stream=None, **kw):
+    """Lock-step multistart Qfactor over a circuit of specialised gates
+    (rz, gpi, ms) and general unitaries (u4, u8) (qf_instantiate_spec).
+    ``params``: (S, p, 2) float64 start angles; ``gates``: (S, E) complex128
+    start matrices of the general gates (None if there are none).  Returns
+    the dict of instantiate_ex with ``params`` (S, p, 2) and ``flat`` the
+    (S, E) slot matrices."""
+    target = _c128(target, "target")
+    specs = [tuple(g) for g in specs]
+    sarr = gate_specs(specs)
+    n = _nqubits(target)
+    pr = params if isinstance(params, torch.Tensor) else torch.as_tensor(np.asarray(params, dtype=np.float64))
+    if pr.dtype != torch.float64 or pr.dim() != 3 or pr.shape[1:] != (len(specs), 2):
+        raise ValueError("params must be float64 of shape (S, n_gates, 2)")
+    pr = pr.contiguous()
+    S = pr.shape[0]
+    E = sum(64 if g[0].lower() == "u8" else 16 for g in specs)
+    g = _c128(gates, "gates") if gates is not None else None
+    if g is not None and tuple(g.shape) != (S, E):
+        raise ValueError(f"gates must be (S, {E})")
+    opts = options if options is not None else Options(**kw)
+    out = torch.empty((S, E), dtype=torch.complex128, device=pr.device)
+    out_p = torch.empty_like(pr)
+    costs = (ct.c_double * S)()
+    res = nat.qf_result()
+    check(_lib().qf_instantiate_spec(_ptr(target), n, len(specs), sarr, S,
+                                     _ptr(g) if g is not None else None, _ptr(pr), ct.byref(opts.c),
+                                     _ptr(out), _ptr(out_p), costs, ct.byref(res), _stream_handle(stream)))
+    return {"params": out_p, "flat": out, "costs": np.array(costs[:]), "best": res.best_start,
+            "sweeps": res.sweeps, "c64_sweeps": res.c64_sweeps,
             "reason": nat.REASONS.get(res.reason, str(res.reason)), "best_cost": res.best_cost}
 
 

@@ -716,7 +716,7 @@ int plan_costs_impl(qf_plan* P, double* costs, qf_c128* traces) {
 }
 
 int plan_create_desc(int n, const std::vector<GateDesc>& gd, long long gsz, int S, int prec,
-                     qf_plan** out) {
+                     qf_plan** out, bool with_params = false) {
   if (!out) return set_error(QF_EINVAL, "out_plan is NULL");
   *out = nullptr;
   const int p = (int)gd.size();
@@ -757,6 +757,19 @@ int plan_create_desc(int n, const std::vector<GateDesc>& gd, long long gsz, int 
                            cudaSuccess)
       rc = set_error(QF_ECUDA, "copying the gate table failed");
   }
+  P->spec = with_params;
+  for (int k = 0; k < p; ++k) P->spec |= gd[k].kind != qf::kGateGeneral;
+  if (rc == QF_OK && P->spec) {
+    // parameterised gates: (kind, entry offset) per gate, 2 parameters per (start, gate)
+    std::vector<int2> tab(p);
+    for (int k = 0; k < p; ++k) tab[k] = make_int2(gd[k].kind, (int)gd[k].off);
+    rc = P->ptab.alloc(sizeof(int2) * p);
+    if (rc == QF_OK) rc = P->params.alloc(sizeof(double) * 2 * p * (size_t)S);
+    if (rc == QF_OK &&
+        (cudaMemcpy(P->ptab.p, tab.data(), sizeof(int2) * p, cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemset(P->params.p, 0, sizeof(double) * 2 * p * (size_t)S) != cudaSuccess))
+      rc = set_error(QF_ECUDA, "copying the gate kinds failed");
+  }
   if (rc == QF_OK && (cudaMemset(P->status.p, 0, sizeof(int)) != cudaSuccess ||
                       cudaMemset(P->counters.p, 0, (size_t)S * sizeof(unsigned)) != cudaSuccess))
     rc = set_error(QF_ECUDA, "cudaMemset of the plan's status words failed");
@@ -788,6 +801,35 @@ int plan_load_impl(qf_plan* P, const qf_c128* target, const qf_c128* gates, cuda
   QF_CUDA(cudaMemcpyAsync(P->gates.p, gates, gcount * sizeof(double2), cudaMemcpyDefault, st));
   QF_CUDA(cudaMemsetAsync(P->status.p, 0, sizeof(int), st));
   // non-finite inputs raise the status word (read at the next status check)
+  QF_CUDA(qf::launch_check_finite(P->V.as<double>(), P->NN * 2, P->status.as<int>(), st));
+  QF_CUDA(qf::launch_check_finite(P->gates.as<double>(), gcount * 2, P->status.as<int>(), st));
+  P->sweeps_since_load = 0;
+  return plan_build(P);
+}
+
+// Load for plans with parameterised gates: the general gates' matrices (the
+// parameterised slots are ignored; gates may be NULL when every gate is
+// parameterised), the parameters, then the parameterised slots built from
+// them, then the tensors.
+int plan_load_spec_impl(qf_plan* P, const qf_c128* target, const qf_c128* gates, const double* params,
+                        cudaStream_t st) {
+  if (!target || !params) return set_error(QF_EINVAL, "target or params is NULL");
+  bool general = false;
+  for (const GateDesc& g : P->gd) general |= g.kind == qf::kGateGeneral;
+  if (general && !gates) return set_error(QF_EINVAL, "gates is NULL but the circuit has general gates");
+  P->stream = st;
+  const size_t gcount = (size_t)P->S * P->gsz;
+  const size_t pcount = (size_t)P->S * 2 * P->p;
+  QF_CUDA(cudaMemcpyAsync(P->V.p, target, P->NN * sizeof(double2), cudaMemcpyDefault, st));
+  if (gates)
+    QF_CUDA(cudaMemcpyAsync(P->gates.p, gates, gcount * sizeof(double2), cudaMemcpyDefault, st));
+  else
+    QF_CUDA(cudaMemsetAsync(P->gates.p, 0, gcount * sizeof(double2), st));
+  QF_CUDA(cudaMemcpyAsync(P->params.p, params, pcount * sizeof(double), cudaMemcpyDefault, st));
+  QF_CUDA(cudaMemsetAsync(P->status.p, 0, sizeof(int), st));
+  QF_CUDA(qf::launch_check_finite(P->params.as<double>(), pcount, P->status.as<int>(), st));
+  QF_CUDA(qf::launch_param_gates(P->gates.as<double2>(), P->gsz, P->ptab.as<int2>(), P->params.as<double>(),
+                                 2LL * P->p, P->p, P->S, st));
   QF_CUDA(qf::launch_check_finite(P->V.as<double>(), P->NN * 2, P->status.as<int>(), st));
   QF_CUDA(qf::launch_check_finite(P->gates.as<double>(), gcount * 2, P->status.as<int>(), st));
   P->sweeps_since_load = 0;
@@ -990,7 +1032,8 @@ namespace {
 int instantiate_core(const qf_c128* target, int n_qubits, const std::vector<GateDesc>& gd,
                      long long gsz, int n_starts, const qf_c128* initial_gates,
                      const qf_options* opts, qf_c128* out_gates, double* out_costs,
-                     qf_result* out_result, void* stream) {
+                     qf_result* out_result, void* stream, const double* initial_params = nullptr,
+                     double* out_params = nullptr) {
   qf_options o;
   qf_options_default(&o);
   if (opts) o = *opts;
@@ -1020,7 +1063,10 @@ int instantiate_core(const qf_c128* target, int n_qubits, const std::vector<Gate
     QF_TRY(plan_ensure_T(P, fine_prec));
     P->prec = QF_C64;
   }
-  QF_TRY(plan_load_impl(P, target, initial_gates, st));
+  if (P->spec)
+    QF_TRY(plan_load_spec_impl(P, target, initial_gates, initial_params, st));
+  else
+    QF_TRY(plan_load_impl(P, target, initial_gates, st));
 
   std::vector<std::vector<double>> hist(S);
   std::vector<double> c(S);
@@ -1104,6 +1150,9 @@ int instantiate_core(const qf_c128* target, int n_qubits, const std::vector<Gate
   for (int s = 1; s < S; ++s)
     if (c[s] < c[best]) best = s;
   QF_TRY(store_output(out_gates, P->gates.as<double2>(), (size_t)S * gsz, st));
+  if (P->spec && out_params)
+    QF_TRY(store_output(reinterpret_cast<qf_c128*>(out_params), P->params.as<double2>(),
+                        (size_t)S * P->p, st));
   QF_CUDA(cudaStreamSynchronize(st));
   if (out_costs)
     for (int s = 0; s < S; ++s) out_costs[s] = c[s];
@@ -1157,6 +1206,29 @@ int qf_plan_create_k(int n_qubits, int n_gates, const qf_gate_loc* locations, in
   return plan_create_desc(n_qubits, gd, gsz, n_starts, precision, out_plan);
 }
 
+int qf_instantiate_spec(const qf_c128* target, int n_qubits, int n_gates, const qf_gate_spec* gates,
+                        int n_starts, const qf_c128* initial_gates, const double* initial_params,
+                        const qf_options* opts, qf_c128* out_gates, double* out_params,
+                        double* out_costs, qf_result* out_result, void* stream) {
+  QF_TRY(check_sizes(n_qubits, n_gates));
+  if (!initial_params || !out_params) return set_error(QF_EINVAL, "initial_params or out_params is NULL");
+  std::vector<GateDesc> gd;
+  long long gsz = 0;
+  QF_TRY(fetch_gate_specs(gates, n_qubits, n_gates, &gd, &gsz));
+  bool param = false;
+  for (const GateDesc& g : gd) param |= g.kind != qf::kGateGeneral;
+  if (!param) {  // all general: the parameters pass through
+    QF_TRY(instantiate_core(target, n_qubits, gd, gsz, n_starts, initial_gates, opts, out_gates,
+                            out_costs, out_result, stream));
+    if (out_params != initial_params)
+      QF_CUDA(cudaMemcpy(out_params, initial_params, sizeof(double) * 2 * n_gates * (size_t)n_starts,
+                         cudaMemcpyDefault));
+    return QF_OK;
+  }
+  return instantiate_core(target, n_qubits, gd, gsz, n_starts, initial_gates, opts, out_gates, out_costs,
+                          out_result, stream, initial_params, out_params);
+}
+
 int qf_plan_create_spec(int n_qubits, int n_gates, const qf_gate_spec* gates, int n_starts,
                         int precision, qf_plan** out_plan) {
   if (out_plan) *out_plan = nullptr;
@@ -1164,52 +1236,15 @@ int qf_plan_create_spec(int n_qubits, int n_gates, const qf_gate_spec* gates, in
   std::vector<GateDesc> gd;
   long long gsz = 0;
   QF_TRY(fetch_gate_specs(gates, n_qubits, n_gates, &gd, &gsz));
-  qf_plan* P = nullptr;
-  QF_TRY(plan_create_desc(n_qubits, gd, gsz, n_starts, precision, &P));
-  std::vector<int2> tab(n_gates);
-  for (int k = 0; k < n_gates; ++k) tab[k] = make_int2(gd[k].kind, (int)gd[k].off);
-  int rc = P->ptab.alloc(sizeof(int2) * n_gates);
-  if (rc == QF_OK) rc = P->params.alloc(sizeof(double) * 2 * n_gates * (size_t)n_starts);
-  if (rc == QF_OK &&
-      (cudaMemcpy(P->ptab.p, tab.data(), sizeof(int2) * n_gates, cudaMemcpyHostToDevice) != cudaSuccess ||
-       cudaMemset(P->params.p, 0, sizeof(double) * 2 * n_gates * (size_t)n_starts) != cudaSuccess))
-    rc = set_error(QF_ECUDA, "copying the gate kinds failed");
-  if (rc != QF_OK) {
-    qf_plan_destroy(P);
-    return rc;
-  }
-  P->spec = true;
-  *out_plan = P;
-  return QF_OK;
+  // parameter buffers even for an all-general circuit, so the parameter calls stay valid
+  return plan_create_desc(n_qubits, gd, gsz, n_starts, precision, out_plan, true);
 }
 
 int qf_plan_load_spec(qf_plan* plan, const qf_c128* target, const qf_c128* gates,
                       const double* params, void* stream) {
   if (!plan) return set_error(QF_EINVAL, "plan is NULL");
   if (!plan->spec) return set_error(QF_EINVAL, "the plan was not made by qf_plan_create_spec");
-  if (!target || !params) return set_error(QF_EINVAL, "target or params is NULL");
-  bool general = false;
-  for (const GateDesc& g : plan->gd) general |= g.kind == qf::kGateGeneral;
-  if (general && !gates) return set_error(QF_EINVAL, "gates is NULL but the circuit has general gates");
-  qf_plan* P = plan;
-  const cudaStream_t st = as_stream(stream);
-  P->stream = st;
-  const size_t gcount = (size_t)P->S * P->gsz;
-  const size_t pcount = (size_t)P->S * 2 * P->p;
-  QF_CUDA(cudaMemcpyAsync(P->V.p, target, P->NN * sizeof(double2), cudaMemcpyDefault, st));
-  if (gates)
-    QF_CUDA(cudaMemcpyAsync(P->gates.p, gates, gcount * sizeof(double2), cudaMemcpyDefault, st));
-  else
-    QF_CUDA(cudaMemsetAsync(P->gates.p, 0, gcount * sizeof(double2), st));
-  QF_CUDA(cudaMemcpyAsync(P->params.p, params, pcount * sizeof(double), cudaMemcpyDefault, st));
-  QF_CUDA(cudaMemsetAsync(P->status.p, 0, sizeof(int), st));
-  QF_CUDA(qf::launch_check_finite(P->params.as<double>(), pcount, P->status.as<int>(), st));
-  QF_CUDA(qf::launch_param_gates(P->gates.as<double2>(), P->gsz, P->ptab.as<int2>(), P->params.as<double>(),
-                                 2LL * P->p, P->p, P->S, st));
-  QF_CUDA(qf::launch_check_finite(P->V.as<double>(), P->NN * 2, P->status.as<int>(), st));
-  QF_CUDA(qf::launch_check_finite(P->gates.as<double>(), gcount * 2, P->status.as<int>(), st));
-  P->sweeps_since_load = 0;
-  return plan_build(P);
+  return plan_load_spec_impl(plan, target, gates, params, as_stream(stream));
 }
 
 int qf_plan_get_params(qf_plan* plan, double* out_params) {

@@ -161,3 +161,42 @@ def test_lookahead_flag_is_ignored_and_invalid_specs_rejected(qf):
         plan.load_params(torch.eye(8, dtype=torch.complex128).cuda(),
                          torch.zeros((1, 2, 2), dtype=torch.float64).cuda())
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["c128", "c64refine"])
+def test_instantiate_spec_reaches_tolerance(qf, precision):
+    """A reachable circuit of GPI, MS, Rz and one general gate, from starts
+    near the target's angles (the angle landscape has local optima): the
+    run converges to 1e-10, and the oracle's cost of the returned angles and
+    gate agrees."""
+    n = 3
+    specs = [("gpi", 0), ("gpi", 1), ("ms", 0, 1), ("rz", 2), ("ms", 1, 2), ("u4", 0, 2), ("gpi", 2, 0)]
+    kinds = [KIND[sp[0]] for sp in specs]
+    olocs = _oracle_locs(specs)
+    g = qi.rng(13300)
+    tgt = _start(specs, g)
+    V = osp.circuit_unitary_spec(kinds, olocs, tgt, n)
+    S = 4
+    params = np.zeros((S, len(specs), 2))
+    mats = []
+    for s in range(S):
+        row = []
+        for i, (sp, x) in enumerate(zip(specs, tgt)):
+            if sp[0] == "u4":
+                row.append(qi.haar_unitary(4, qi.rng(13310 + s)))
+            else:
+                params[s, i, :len(x)] = np.asarray(x) + 0.3 * qi.rng(13320 + s).standard_normal(len(x))
+                row.append(np.zeros((4, 4)))
+        mats.append(row)
+    prec = qf.QF_C128 if precision == "c128" else qf.QF_C64_REFINE64
+    res = qf.instantiate_spec(torch.from_numpy(V).cuda(), specs, torch.from_numpy(params).cuda(),
+                              qf.flatten_gates(mats).cuda(), dist_tol=1e-10, max_sweeps=400, precision=prec)
+    assert res["best_cost"] <= 1e-10, res["costs"]
+    b = res["best"]
+    slots = qf.spec_slots(specs, n)
+    gates = qf.unflatten_gates(res["flat"], slots)[b]
+    pb = res["params"][b].cpu().numpy()
+    st = [gates[i] if sp[0] == "u4" else list(pb[i, :osp.NPARAM[KIND[sp[0]]]]) for i, sp in enumerate(specs)]
+    C = osp.circuit_unitary_spec(kinds, olocs, st, n)
+    c_ref = 1.0 - abs(np.trace(V.conj().T @ C)) / 2**n
+    assert c_ref <= 2e-10 and abs(c_ref - res["best_cost"]) <= 1e-10
