@@ -868,9 +868,12 @@ namespace {
 // Packed f32x2 FMAs as in the pair pass; the row is XOR-swizzled in shared
 // memory (bits 4..7 of a column into bits 0..3), which keeps the 16 lanes of
 // a half-warp on distinct banks when the gate bits are the lowest ones.
-// Used for complex64, where the per-gate passes are bound by HBM.
+// Used for complex64, where the per-gate passes are bound by HBM.  128
+// threads and 4 CTAs per SM (128 registers, ~50 KB of shared memory each at
+// 12 qubits): 256-thread CTAs took 138 registers and fit once per SM
+// (9.1 ms against 7.2 ms for 8 starts at 12 qubits and 66 gates).
 
-constexpr int kBuildThreads = 256;
+constexpr int kBuildThreads = 128;  // 4 CTAs per SM (registers and shared memory)
 constexpr int kBuildMaxSteps = 960;
 
 struct BuildParams {
@@ -883,7 +886,7 @@ struct BuildParams {
 
 __device__ __forceinline__ unsigned bswz(unsigned c) { return c ^ ((c >> 4) & 15u); }
 
-__global__ void __launch_bounds__(kBuildThreads)
+__global__ void __launch_bounds__(kBuildThreads, 4)
 build_rows_kernel(float2* __restrict__ T, const __grid_constant__ BuildParams bp,
                   const double2* __restrict__ gates, long long gstride, int p) {
   extern __shared__ __align__(16) unsigned char build_smem[];
