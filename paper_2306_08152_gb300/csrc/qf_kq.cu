@@ -10,6 +10,8 @@
 
 #include <string.h>
 
+#include <type_traits>
+
 #include "qf_device.cuh"
 #include "qf_internal.h"
 
@@ -384,6 +386,8 @@ static __device__ __noinline__ bool warp_polar8(double2 a0, double2 a1, double2*
 // indices, so a warp access covers 4 adjacent columns of 8 rows).  R acts
 // along the row in registers; the rows then go through a padded per-warp
 // shared buffer so that lane 4y + b takes column y for L, and writes it.
+// Used for complex128 and df64, whose arithmetic bounds the pass; complex64
+// takes pass8a_kernel or pass8f_kernel (below).
 
 constexpr int kPass8Threads = 256;
 constexpr int kBlkStride = 8 * 9 + 4;  // padded 8x8 block in the transpose buffer
@@ -936,20 +940,22 @@ void pass8_launch(void* T, int n, int S, int p0, int p1, int p2, const double2* 
   long long cap = ((long long)sm_count() * 4 + S - 1) / S;
   if (cap < 1) cap = 1;
   dim3 grid((unsigned)(want < cap ? want : cap), S);
-  if (sizeof(R) == sizeof(float) && HL && n >= 7 && p0 >= 2 && p1 >= 2 && p2 >= 2) {
-    const long long agroups = 1ll << (2 * (n - 3) - 4);
-    const long long awant = (agroups + 3) / 4;
-    long long acap = ((long long)sm_count() * kPass8aCtasPerSm * kPass8Waves + S - 1) / S;
-    if (acap < 1) acap = 1;
-    dim3 agrid((unsigned)(awant < acap ? awant : acap), S);
-    pass8a_kernel<HR><<<agrid, kPass8aThreads, 0, st>>>((float2*)T, n, p0, p1, p2, L, Ls, Rm, Rs);
-  } else if (sizeof(R) == sizeof(float)) {
-    const long long fgroups = ((1ll << (2 * (n - 3))) + kPass8fBlocks - 1) / kPass8fBlocks;
-    const long long fwant = (fgroups + 7) / 8;
-    long long fcap = ((long long)sm_count() * kPass8fCtasPerSm * kPass8Waves + S - 1) / S;
-    if (fcap < 1) fcap = 1;
-    dim3 fgrid((unsigned)(fwant < fcap ? fwant : fcap), S);
-    pass8f_kernel<HL, HR><<<fgrid, kPass8Threads, 0, st>>>((float2*)T, n, p0, p1, p2, L, Ls, Rm, Rs);
+  if constexpr (std::is_same<R, float>::value) {
+    if (HL && n >= 7 && p0 >= 2 && p1 >= 2 && p2 >= 2) {
+      const long long agroups = 1ll << (2 * (n - 3) - 4);
+      const long long awant = (agroups + 3) / 4;
+      long long acap = ((long long)sm_count() * kPass8aCtasPerSm * kPass8Waves + S - 1) / S;
+      if (acap < 1) acap = 1;
+      dim3 agrid((unsigned)(awant < acap ? awant : acap), S);
+      pass8a_kernel<HR><<<agrid, kPass8aThreads, 0, st>>>((float2*)T, n, p0, p1, p2, L, Ls, Rm, Rs);
+    } else {
+      const long long fgroups = ((1ll << (2 * (n - 3))) + kPass8fBlocks - 1) / kPass8fBlocks;
+      const long long fwant = (fgroups + 7) / 8;
+      long long fcap = ((long long)sm_count() * kPass8fCtasPerSm * kPass8Waves + S - 1) / S;
+      if (fcap < 1) fcap = 1;
+      dim3 fgrid((unsigned)(fwant < fcap ? fwant : fcap), S);
+      pass8f_kernel<HL, HR><<<fgrid, kPass8Threads, 0, st>>>((float2*)T, n, p0, p1, p2, L, Ls, Rm, Rs);
+    }
   } else
     pass8_kernel<R, HL, HR><<<grid, kPass8Threads, 0, st>>>((C*)T, n, p0, p1, p2, L, Ls, Rm, Rs);
 }
