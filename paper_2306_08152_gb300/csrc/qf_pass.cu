@@ -176,8 +176,11 @@ pass_half_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, i
   const unsigned units = 2u << (2 * lnc);  // two lanes per block: a multiple of 32 (n >= 4)
   C* __restrict__ Ts = T + (size_t)s * N * N;
   const unsigned o1 = 1u << pb, o2 = 1u << pa;
-  const unsigned off[4] = {0u, o1, o2, o1 | o2};
+  const unsigned off[4] = {0u, o1, o2, o1 | o2};  // constant indices only
   const int h = threadIdx.x & 1;  // the row pair {2h, 2h+1}
+  // off[2h + i] without a lane-dependent index (which would put the arrays
+  // in local memory)
+  const unsigned oh = h ? o2 : 0u;
 
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < units;
        t += gridDim.x * blockDim.x) {
@@ -187,7 +190,7 @@ pass_half_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, i
     C e[2][4];  // rows 2h, 2h+1
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-      const unsigned rb = (r0 | off[2 * h + i]) * N;
+      const unsigned rb = (r0 | oh | (i ? o1 : 0u)) * N;
 #pragma unroll
       for (int y = 0; y < 4; ++y) e[i][y] = Ts[rb + (c0 | off[y])];
     }
@@ -208,15 +211,16 @@ pass_half_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, i
     if (HL) {
       // exchange: the even lane gives columns 2-3 of its rows and takes
       // columns 0-1 of rows 2-3; the odd lane the mirror image
-      C col[4][2];  // all four rows of columns {2h', 2h'+1}, h' = h
+      C col[4][2];  // all four rows of columns {2h, 2h+1}
 #pragma unroll
       for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          const C give = e[i][2 * (1 - h) + j];
+          const C give = h ? e[i][j] : e[i][2 + j];
+          const C keep = h ? e[i][2 + j] : e[i][j];
           const C got = shfl(give, (int)(threadIdx.x & 31) ^ 1);
-          col[2 * h + i][j] = e[i][2 * h + j];
-          col[2 * (1 - h) + i][j] = got;
+          col[i][j] = h ? got : keep;      // row i
+          col[2 + i][j] = h ? keep : got;  // row 2 + i
         }
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
@@ -229,12 +233,12 @@ pass_half_kernel(typename Cplx<R>::T* __restrict__ T, int n, int plo, int phi, i
           t4[x] = cfinish(acc);
         }
 #pragma unroll
-        for (int x = 0; x < 4; ++x) Ts[(r0 | off[x]) * N + (c0 | off[2 * h + j])] = t4[x];
+        for (int x = 0; x < 4; ++x) Ts[(r0 | off[x]) * N + (c0 | oh | (j ? o1 : 0u))] = t4[x];
       }
     } else {
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
-        const unsigned rb = (r0 | off[2 * h + i]) * N;
+        const unsigned rb = (r0 | oh | (i ? o1 : 0u)) * N;
 #pragma unroll
         for (int y = 0; y < 4; ++y) Ts[rb + (c0 | off[y])] = e[i][y];
       }
