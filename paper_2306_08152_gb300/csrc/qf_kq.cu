@@ -389,6 +389,11 @@ static __device__ __noinline__ bool warp_polar8(double2 a0, double2 a1, double2*
 // Used for complex128 and df64, whose arithmetic bounds the pass; complex64
 // takes pass8a_kernel or pass8f_kernel (below).
 
+// Offset of local index v of a gate on bit positions (p0, p1, p2).
+__device__ __forceinline__ unsigned off8(int v, int p0, int p1, int p2) {
+  return (((unsigned)v >> 2) & 1u) << p0 | (((unsigned)v >> 1) & 1u) << p1 | ((unsigned)v & 1u) << p2;
+}
+
 constexpr int kPass8Threads = 256;
 constexpr int kBlkStride = 8 * 9 + 4;  // padded 8x8 block in the transpose buffer
 
@@ -411,16 +416,16 @@ pass8_kernel(typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, int p2,
   if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
   if (q[1] > q[2]) { const int t = q[1]; q[1] = q[2]; q[2] = t; }
   if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
-  unsigned off[8];
+  unsigned off[8];  // constant indices only (a lane-dependent index would move it to local memory)
 #pragma unroll
-  for (int x = 0; x < 8; ++x)
-    off[x] = (((unsigned)x >> 2) & 1u) << p0 | (((unsigned)x >> 1) & 1u) << p1 | ((unsigned)x & 1u) << p2;
+  for (int x = 0; x < 8; ++x) off[x] = off8(x, p0, p1, p2);
   const int lnc = n - 3;
   const unsigned cmask = (1u << lnc) - 1u;
   const unsigned nblk = 1u << (2 * lnc);
   C* __restrict__ Ts = T + (size_t)s * N * N;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int b = lane & 3, x = lane >> 2;
+  const unsigned offx = off8(x, p0, p1, p2);
   C* wb = buf[w];
   const unsigned warps = gridDim.x * (kPass8Threads / 32);
   for (unsigned grp = blockIdx.x * (kPass8Threads / 32) + w; grp * 4u < nblk; grp += warps) {
@@ -430,7 +435,7 @@ pass8_kernel(typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, int p2,
     const unsigned c0 = dep1(dep1(dep1(blk & cmask, q[0]), q[1]), q[2]);
     C row[8];
     if (valid) {
-      const C* src = Ts + (size_t)(r0 | off[x]) * N + c0;
+      const C* src = Ts + (size_t)(r0 | offx) * N + c0;
 #pragma unroll
       for (int y = 0; y < 8; ++y) row[y] = src[off[y]];
     } else {
@@ -464,11 +469,11 @@ pass8_kernel(typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, int p2,
           C acc = czero<C>();
 #pragma unroll
           for (int k = 0; k < 8; ++k) acc = cfma(sL[r * 8 + k], col[k], acc);
-          Ts[(size_t)(r0 | off[r]) * N + (c0 | off[y])] = cfinish(acc);
+          Ts[(size_t)(r0 | off[r]) * N + (c0 | offx)] = cfinish(acc);
         }
       }
     } else if (valid) {
-      C* dst = Ts + (size_t)(r0 | off[x]) * N + c0;
+      C* dst = Ts + (size_t)(r0 | offx) * N + c0;
 #pragma unroll
       for (int y = 0; y < 8; ++y) dst[off[y]] = row[y];
     }
@@ -486,10 +491,6 @@ pass8_kernel(typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, int p2,
 // from the buffer.  (Loading the next group's rows ahead of the arithmetic
 // needs 123 registers, two CTAs per SM, and ran slower.)
 constexpr int kPass8fBlocks = 8;  // blocks per warp and group
-
-__device__ __forceinline__ unsigned off8(int v, int p0, int p1, int p2) {
-  return (((unsigned)v >> 2) & 1u) << p0 | (((unsigned)v >> 1) & 1u) << p1 | ((unsigned)v & 1u) << p2;
-}
 
 struct Grp8 {  // one block of a group: its row and column rest offsets
   unsigned r0, c0;
@@ -735,10 +736,9 @@ env8_kernel(const typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, in
   if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
   if (q[1] > q[2]) { const int t = q[1]; q[1] = q[2]; q[2] = t; }
   if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
-  unsigned off[8];
+  unsigned off[8];  // constant indices only
 #pragma unroll
-  for (int x = 0; x < 8; ++x)
-    off[x] = (((unsigned)x >> 2) & 1u) << p0 | (((unsigned)x >> 1) & 1u) << p1 | ((unsigned)x & 1u) << p2;
+  for (int x = 0; x < 8; ++x) off[x] = off8(x, p0, p1, p2);
   const unsigned items = N;  // 2^(n-3) rests x 8 rows
   const unsigned chunk = ((items / 8u + B - 1) / B) * 8u;  // whole rests per CTA
   const unsigned i_beg = bb * chunk;
@@ -748,9 +748,10 @@ env8_kernel(const typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, in
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = Ar(0);
   const int x = threadIdx.x & 7;  // blockDim and chunk are multiples of 8
+  const unsigned offx = off8(x, p0, p1, p2);
   for (unsigned it = i_beg + threadIdx.x; it < i_end; it += blockDim.x) {
     const unsigned d = dep1(dep1(dep1(it >> 3, q[0]), q[1]), q[2]);
-    const CT* rowp = Ts + (size_t)(d | off[x]) * N + d;
+    const CT* rowp = Ts + (size_t)(d | offx) * N + d;
 #pragma unroll
     for (int y = 0; y < 8; ++y) {
       const auto e = to_acc(rowp[off[y]]);
