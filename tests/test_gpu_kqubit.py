@@ -44,12 +44,14 @@ def _triples(n, g, count):
 
 
 @pytest.mark.parametrize("n,dtype", [(3, torch.complex128), (4, torch.complex128), (6, torch.complex128),
-                                     (9, torch.complex128), (6, torch.complex64), (7, torch.complex64),
-                                     (10, torch.complex64), (11, torch.complex64)])
+                                     (9, torch.complex128), (3, torch.complex64), (4, torch.complex64),
+                                     (6, torch.complex64), (7, torch.complex64), (10, torch.complex64),
+                                     (11, torch.complex64)])
 def test_apply_gate_k3_matches_oracle(qf, n, dtype):
-    """Complex64 covers both pass kernels: gates whose bits are all >= 4 (the
+    """Complex64 covers both pass kernels: gates whose bits are all >= 2 (the
     coalesced kernel; n = 7 is its smallest case, one 16-column group per
-    rest row) and the rest."""
+    rest row) and the rest (n = 3: a single block, so most of a warp's
+    eight-block group is empty)."""
     g = qi.rng(10000 + n)
     S = 2
     T0 = _rand_T(S, n, g)
