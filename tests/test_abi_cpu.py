@@ -135,3 +135,40 @@ def test_invalid_options_are_rejected(lib):
         rc = lib.qf_instantiate_ex(V.ctypes.data, 3, 1, locs.ctypes.data, 1, g.ctypes.data,
                                    ct.byref(bad), out.ctypes.data, None, None, None)
         assert rc == nat.QF_EINVAL, field
+
+
+@pytest.mark.parametrize("spec,msg", [((2, 1, 1), b"repeated"), ((4, 0, 0), b"repeated"),
+                                      ((7, 0, 1), b"unknown kind"), ((3, 5, -1), b"invalid"),
+                                      ((1, 0, 1, 2), b"qubits >")])
+def test_invalid_gate_specs_are_rejected(lib, spec, msg):
+    """Specialised-gate plans (Sec. III-A): unknown kinds, repeated or
+    out-of-range qubits and too-large gates fail before any CUDA call."""
+    from paper_2306_08152_gb300 import _native as nat
+
+    arr = (nat.qf_gate_spec * 1)()
+    arr[0].kind = spec[0]
+    q = list(spec[1:]) + [-1] * (4 - len(spec))
+    for j in range(3):
+        arr[0].q[j] = q[j]
+    h = ct.c_void_p()
+    rc = lib.qf_plan_create_spec(2, 1, arr, 1, nat.QF_C128, ct.byref(h))
+    assert rc == nat.QF_EINVAL
+    assert msg in lib.qf_last_error(), lib.qf_last_error()
+    assert not h.value
+    assert lib.qf_plan_load_spec(None, None, None, None, None) == nat.QF_EINVAL
+    assert lib.qf_plan_get_params(None, None) == nat.QF_EINVAL
+
+
+def test_spec_helpers_match_the_slot_rule():
+    import paper_2306_08152_gb300 as qf
+    from paper_2306_08152_gb300 import _native as nat
+
+    specs = [("rz", 2), ("gpi", 0, 3), ("ms", 1, 2), ("u4", 0, 1), ("u8", 0, 1, 2), ("GPI", 1)]
+    arr = qf.gate_specs(specs)
+    assert [arr[i].kind for i in range(len(specs))] == [nat.QF_GATE_RZ, nat.QF_GATE_GPI, nat.QF_GATE_MS,
+                                                        nat.QF_GATE_U4, nat.QF_GATE_U8, nat.QF_GATE_GPI]
+    assert list(arr[0].q) == [2, -1, -1] and list(arr[4].q) == [0, 1, 2]
+    # automatic partner: the next qubit, or the previous one for the last qubit
+    assert qf.spec_slots(specs, 3) == [(2, 1), (0, 3), (1, 2), (0, 1), (0, 1, 2), (1, 2)]
+    with pytest.raises(ValueError):
+        qf.gate_specs([("cx", 0, 1)])
