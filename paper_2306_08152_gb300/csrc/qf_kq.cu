@@ -707,6 +707,176 @@ pass8a_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const doubl
   }
 }
 
+// complex64 pass for gates with every bit <= 5 and one at bit 0 or 1 (n >=
+// 6), where the layouts above touch 8-16 lines per warp access.  A warp
+// takes a tile of the 8 row variants of one rest row and 64 adjacent
+// columns (8 blocks: the tile holds every column variant of 8 rest
+// columns), loads and stores it with 16-byte accesses of whole lines (lane
+// l: columns 2l, 2l+1), and moves it through shared memory:
+//   R stage  lane (j, xa) = (l & 7, l >> 3) takes rows xa and xa + 4 of
+//            block j, in place;
+//   L stage  lane l takes columns 2l and 2l+1 of every row and writes the
+//            output rows to global memory.
+// Each broadcast operator entry serves two rows or two columns.  The
+// shared tile is XOR-swizzled per launch: slot(x, c) = 64x + (c & 48) +
+// ((c & 15) ^ phi), phi = Px(x & 3) ^ Qh(c >> 4), with (P, Q) GF(2)-linear
+// and chosen on the host so that every warp access above (fixed y in the R
+// stage, fixed row in the others) hits each 8-byte bank pair exactly twice
+// (pass8c_swizzle).
+constexpr int kPass8cThreads = 128;
+constexpr int kPass8cCtasPerSm = 4;
+
+template <bool HR>
+__global__ void __launch_bounds__(kPass8cThreads, kPass8cCtasPerSm)
+pass8c_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const double2* __restrict__ L,
+              long long Ls, const double2* __restrict__ Rm, long long Rs, unsigned phx, unsigned phh) {
+  __shared__ float2 sL[64], sR[64];
+  __shared__ float2 buf[kPass8cThreads / 32][512];
+  const int s = blockIdx.y;
+  if (threadIdx.x < 64) {
+    sL[threadIdx.x] = cmake(L[s * Ls + threadIdx.x], 0.f);
+    if (HR) sR[threadIdx.x] = cmake(Rm[s * Rs + threadIdx.x], 0.f);
+  }
+  __syncthreads();
+  const unsigned N = 1u << n;
+  int q[3] = {p0, p1, p2};  // ascending for the deposit
+  if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
+  if (q[1] > q[2]) { const int t = q[1]; q[1] = q[2]; q[2] = t; }
+  if (q[0] > q[1]) { const int t = q[0]; q[0] = q[1]; q[1] = t; }
+  const unsigned m0 = 1u << p0, m1 = 1u << p1, m2 = 1u << p2;
+  auto off = [&](int v) { return ((v & 4) ? m0 : 0u) | ((v & 2) ? m1 : 0u) | ((v & 1) ? m2 : 0u); };
+  auto slot = [&](int x, unsigned c) {
+    const unsigned phi = ((phx >> (4 * (x & 3))) ^ (phh >> (4 * (c >> 4)))) & 15u;
+    return x * 64 + (int)(c & 48u) + (int)((c & 15u) ^ phi);
+  };
+  const int ctb = n - 6;  // bits of the 64-column tile index
+  const unsigned ntiles = 1u << (2 * n - 9);
+  float2* __restrict__ Ts = T + (size_t)s * N * N;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float2* tb = buf[w];
+  const int j = lane & 7, xa = lane >> 3;
+  const unsigned cj = dep1(dep1(dep1((unsigned)j, q[0]), q[1]), q[2]);  // block j's rest bits
+  for (unsigned g = blockIdx.x * (kPass8cThreads / 32) + w; g < ntiles;
+       g += gridDim.x * (kPass8cThreads / 32)) {
+    const unsigned rr = g >> ctb, t = g & ((1u << ctb) - 1u);
+    const unsigned r0 = dep1(dep1(dep1(rr, q[0]), q[1]), q[2]);
+    const size_t cb = (size_t)t * 64 + 2 * lane;
+    {  // load: rows x, columns 2 lane and 2 lane + 1
+      float4 v[8];
+#pragma unroll
+      for (int x = 0; x < 8; ++x) v[x] = *reinterpret_cast<const float4*>(Ts + (size_t)(r0 | off(x)) * N + cb);
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        tb[slot(x, 2u * lane)] = make_float2(v[x].x, v[x].y);
+        tb[slot(x, 2u * lane + 1u)] = make_float2(v[x].z, v[x].w);
+      }
+    }
+    __syncwarp();
+    if (HR) {  // rows xa and xa + 4 of block j <- row R; every slot here is this lane's
+      float2 ia[8], ib[8];
+#pragma unroll
+      for (int y = 0; y < 8; ++y) {
+        const unsigned c = cj | off(y);
+        ia[y] = tb[slot(xa, c)];
+        ib[y] = tb[slot(xa + 4, c)];
+      }
+#pragma unroll 2
+      for (int c = 0; c < 8; ++c) {
+        float2 a = make_float2(0.f, 0.f), b = a;
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          const float2 r = sR[y * 8 + c];
+          a = cfma(ia[y], r, a);
+          b = cfma(ib[y], r, b);
+        }
+        const unsigned cc = cj | off(c);
+        tb[slot(xa, cc)] = a;
+        tb[slot(xa + 4, cc)] = b;
+      }
+      __syncwarp();
+    }
+    float2 ce[8], co[8];  // columns 2 lane and 2 lane + 1 of every row
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      ce[k] = tb[slot(k, 2u * lane)];
+      co[k] = tb[slot(k, 2u * lane + 1u)];
+    }
+    __syncwarp();  // the buffer is rewritten by the next tile
+#pragma unroll 2
+    for (int r = 0; r < 8; ++r) {
+      float2 a = make_float2(0.f, 0.f), b = a;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float2 l = sL[r * 8 + k];
+        a = cfma(l, ce[k], a);
+        b = cfma(l, co[k], b);
+      }
+      *reinterpret_cast<float4*>(Ts + (size_t)(r0 | off(r)) * N + cb) = make_float4(a.x, a.y, b.x, b.y);
+    }
+  }
+}
+
+// The swizzle of pass8c_kernel for gate bits (p0, p1, p2), all <= 5: the
+// first (P, Q) in a fixed order such that (a) some column-tile bit (c >> 4)
+// flips bank bit 0, which spreads a row's even (or odd) columns over all 16
+// banks, and (b) the map from (block j, row xa & 3) to banks in the R stage
+// has rank 4 over GF(2), i.e. hits each bank exactly twice.  Returned as
+// nibble tables: phx = Px(x) for x = 0..3, phh = Qh(h) for h = 0..3.
+bool pass8c_swizzle(int p0, int p1, int p2, unsigned* phx, unsigned* phh) {
+  int rest[3], nr = 0;
+  for (int b = 0; b < 6; ++b)
+    if (b != p0 && b != p1 && b != p2 && nr < 3) rest[nr++] = b;
+  if (nr != 3) return false;
+  for (unsigned P0 = 0; P0 < 16; ++P0)
+    for (unsigned P1 = 0; P1 < 16; ++P1)
+      for (unsigned Q0 = 0; Q0 < 16; ++Q0)
+        for (unsigned Q1 = 0; Q1 < 16; ++Q1) {
+          if (!((Q0 | Q1) & 1u)) continue;
+          const unsigned Qc[2] = {Q0, Q1};
+          unsigned cols[5];
+          for (int i = 0; i < 3; ++i) cols[i] = rest[i] < 4 ? 1u << rest[i] : Qc[rest[i] - 4];
+          cols[3] = P0;
+          cols[4] = P1;
+          unsigned basis[4];
+          int rank = 0;
+          for (int i = 0; i < 5; ++i) {
+            unsigned v = cols[i];
+            for (int k = 0; k < rank; ++k) v = (v ^ basis[k]) < v ? v ^ basis[k] : v;
+            if (v) basis[rank++] = v;
+          }
+          if (rank != 4) continue;
+          *phx = 0u;
+          *phh = 0u;
+          for (unsigned x = 0; x < 4; ++x)
+            *phx |= (((x & 1u) ? P0 : 0u) ^ ((x & 2u) ? P1 : 0u)) << (4 * x);
+          for (unsigned h = 0; h < 4; ++h)
+            *phh |= (((h & 1u) ? Q0 : 0u) ^ ((h & 2u) ? Q1 : 0u)) << (4 * h);
+          return true;
+        }
+  return false;
+}
+
+// pass8c_swizzle for every bit triple, computed once; false if a bit is
+// above 5 (or the triple has no swizzle, which the search does not meet).
+bool pass8c_tables(int p0, int p1, int p2, unsigned* phx, unsigned* phh) {
+  struct Tab {
+    unsigned x[6][6][6], h[6][6][6];
+    bool ok[6][6][6];
+  };
+  static const Tab tab = [] {
+    Tab t{};
+    for (int a = 0; a < 6; ++a)
+      for (int b = 0; b < 6; ++b)
+        for (int c = 0; c < 6; ++c)
+          t.ok[a][b][c] = a != b && a != c && b != c && pass8c_swizzle(a, b, c, &t.x[a][b][c], &t.h[a][b][c]);
+    return t;
+  }();
+  if (p0 < 0 || p1 < 0 || p2 < 0 || p0 > 5 || p1 > 5 || p2 > 5 || !tab.ok[p0][p1][p2]) return false;
+  *phx = tab.x[p0][p1][p2];
+  *phh = tab.h[p0][p1][p2];
+  return true;
+}
+
 // ------------------------------------------------------------ environment
 //
 // P[x][y] = sum over the 2^(n-3) rests r of T[(r, x), (r, y)], from the
@@ -942,6 +1112,7 @@ void pass8_launch(void* T, int n, int S, int p0, int p1, int p2, const double2* 
   if (cap < 1) cap = 1;
   dim3 grid((unsigned)(want < cap ? want : cap), S);
   if constexpr (std::is_same<R, float>::value) {
+    unsigned phx = 0, phh = 0;
     if (HL && n >= 7 && p0 >= 2 && p1 >= 2 && p2 >= 2) {
       const long long agroups = 1ll << (2 * (n - 3) - 4);
       const long long awant = (agroups + 3) / 4;
@@ -949,6 +1120,13 @@ void pass8_launch(void* T, int n, int S, int p0, int p1, int p2, const double2* 
       if (acap < 1) acap = 1;
       dim3 agrid((unsigned)(awant < acap ? awant : acap), S);
       pass8a_kernel<HR><<<agrid, kPass8aThreads, 0, st>>>((float2*)T, n, p0, p1, p2, L, Ls, Rm, Rs);
+    } else if (HL && n >= 6 && pass8c_tables(p0, p1, p2, &phx, &phh)) {
+      const long long ctiles = 1ll << (2 * n - 9);
+      const long long cwant = (ctiles + 3) / 4;
+      long long ccap = ((long long)sm_count() * kPass8cCtasPerSm * kPass8Waves + S - 1) / S;
+      if (ccap < 1) ccap = 1;
+      dim3 cgrid((unsigned)(cwant < ccap ? cwant : ccap), S);
+      pass8c_kernel<HR><<<cgrid, kPass8cThreads, 0, st>>>((float2*)T, n, p0, p1, p2, L, Ls, Rm, Rs, phx, phh);
     } else {
       const long long fgroups = ((1ll << (2 * (n - 3))) + kPass8fBlocks - 1) / kPass8fBlocks;
       const long long fwant = (fgroups + 7) / 8;
