@@ -613,8 +613,8 @@ pass8f_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const doubl
 // the 16 columns a warp access takes in one row are 16 adjacent entries (a
 // whole 128-byte line); with the lowest gate bit at 2 or 3 they fall in runs
 // of 4 or 8 adjacent entries.  (Gates on bit 0 or 1 leave runs of one or two
-// entries, where pass8f_kernel's layout is faster.)  Every broadcast
-// operator entry serves four rows.  The R stage (the identity without R)
+// entries; those take pass8c_kernel, or pass8f_kernel with a bit above 5.)
+// Every broadcast operator entry serves four rows.  The R stage (the identity without R)
 // writes each output column to the transpose buffer; the L stage reads
 // columns y = xh + 2j back and writes each output row to global memory.
 // The buffer pads each block to 65 slots, so both the column writes and the
