@@ -707,8 +707,9 @@ pass8a_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const doubl
   }
 }
 
-// complex64 pass for gates with every bit <= 5 and one at bit 0 or 1 (n >=
-// 6), where the layouts above touch 8-16 lines per warp access.  A warp
+// complex64 pass for gates with every bit <= 5 (n >= 6) that pass8a_kernel
+// does not take: a bit at 0 or 1, where the layouts above touch 8-16 lines
+// per warp access, or n = 6.  A warp
 // takes a tile of the 8 row variants of one rest row and 64 adjacent
 // columns (8 blocks: the tile holds every column variant of 8 rest
 // columns), loads and stores it with 16-byte accesses of whole lines (lane
