@@ -62,8 +62,9 @@ typedef struct { int32_t a, b; } qf_loc;     /* gate location: qubits a != b  */
 /* Circuit-tensor precision. */
 #define QF_C128          0   /* complex128 tensor, FP64 arithmetic throughout */
 #define QF_C64           1   /* complex64 tensor, FP32 gate application; the
-                                partial trace accumulates and the 4x4 update
-                                runs in FP64 */
+                                partial trace sums in FP32 within each CTA's
+                                slice of the band and in FP64 across CTAs;
+                                the 4x4 update runs in FP64 */
 #define QF_C64_REFINE64  2   /* bulk sweeps in QF_C64, then the tensor is
                                 rebuilt in QF_C128 for the final sweeps    */
 #define QF_DF64          3   /* double-FP32 complex tensor: each real part is
@@ -504,7 +505,9 @@ int qf_partial_trace_after(const void* T, int n_qubits, int n_starts, int a1,
                            int b, qf_c128* P, int precision, void* stream);
 
 /* Step a3, CalcEnvMat (Alg. 1): P_s = partial trace of T_s over every qubit
- * except (a, b), accumulated in FP64.  P: device n_starts x 16. */
+ * except (a, b).  QF_C128 and QF_DF64 tensors are summed in FP64; QF_C64
+ * tensors in FP32 within each CTA's slice of the band (error about 1e-6 of
+ * the summed magnitudes) and in FP64 across CTAs.  P: device n_starts x 16. */
 int qf_partial_trace(const void* T, int n_qubits, int n_starts, int a, int b,
                      qf_c128* P, int precision, void* stream);
 

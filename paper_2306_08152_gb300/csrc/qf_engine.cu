@@ -247,6 +247,10 @@ int qf_internal_set_error(int code, const char* what, const char* detail) {
   return set_error(code, "%s", what);
 }
 
+int qf_internal_check_sizes(int n_qubits, int n_gates) { return check_sizes(n_qubits, n_gates); }
+int qf_internal_check_prec(int precision) { return check_prec(precision); }
+int qf_internal_kernel_prec(int precision) { return kprec(precision); }
+
 // ============================================================ the plan
 
 struct qf_plan {

@@ -158,3 +158,13 @@ int sm_count();
 // return `code`; the message is "<what>: <detail>" (detail may be "").
 __attribute__((visibility("hidden"))) int qf_internal_set_error(int code, const char* what,
                                                                 const char* detail);
+
+// The argument checks of the exported entry points, for other translation
+// units: the qubit count within [QF_MIN_QUBITS, QF_MAX_QUBITS] and n_gates
+// >= 1; a tensor precision of QF_C128, QF_C64 or QF_DF64.  Each records a
+// message and returns QF_EINVAL on failure, QF_OK otherwise.
+__attribute__((visibility("hidden"))) int qf_internal_check_sizes(int n_qubits, int n_gates);
+__attribute__((visibility("hidden"))) int qf_internal_check_prec(int precision);
+// Tensor precision (QF_C128, QF_C64, QF_DF64) -> the kernels' precision code
+// (0 complex128, 1 complex64, 2 double-FP32).
+__attribute__((visibility("hidden"))) int qf_internal_kernel_prec(int precision);

@@ -56,10 +56,10 @@ int scratch_address(void** out) {
 
 extern "C" int qf_partial_trace_noalloc(const void* T, int n_qubits, int n_starts, int a, int b,
                                         qf_c128* P, int precision, void* stream) {
-  if (n_qubits < QF_MIN_QUBITS || n_qubits > QF_MAX_QUBITS)
-    return qf_internal_set_error(QF_EINVAL, "n_qubits outside the supported range", "");
-  if (precision != QF_C128 && precision != QF_C64 && precision != QF_DF64)
-    return qf_internal_set_error(QF_EINVAL, "precision must be QF_C128, QF_C64 or QF_DF64", "");
+  int rc = qf_internal_check_sizes(n_qubits, 1);
+  if (rc != QF_OK) return rc;
+  rc = qf_internal_check_prec(precision);
+  if (rc != QF_OK) return rc;
   if (n_starts < 1) return qf_internal_set_error(QF_EINVAL, "n_starts must be >= 1", "");
   if (!T || !P) return qf_internal_set_error(QF_EINVAL, "NULL device pointer", "");
   if (a < 0 || a >= n_qubits || b < 0 || b >= n_qubits || a == b)
@@ -74,7 +74,7 @@ extern "C" int qf_partial_trace_noalloc(const void* T, int n_qubits, int n_start
         "use qf_partial_trace or fewer starts per call",
         "");
   void* base = nullptr;
-  int rc = scratch_address(&base);
+  rc = scratch_address(&base);
   if (rc != QF_OK) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   unsigned* counters = reinterpret_cast<unsigned*>(static_cast<char*>(base) + cnt_off);
@@ -86,7 +86,7 @@ extern "C" int qf_partial_trace_noalloc(const void* T, int n_qubits, int n_start
                                  cudaGetErrorString(e));
   e = qf::launch_update(T, n_qubits, n_starts, a, b, nullptr, 0, qf::kTraceOnly, 0.0, nullptr,
                         reinterpret_cast<double2*>(P), 16, nullptr, nullptr,
-                        static_cast<double*>(base), counters, precision == QF_C128 ? 0 : precision == QF_DF64 ? 2 : 1, st);
+                        static_cast<double*>(base), counters, qf_internal_kernel_prec(precision), st);
   if (e != cudaSuccess)
     return qf_internal_set_error(QF_ECUDA, "partial trace launch failed", cudaGetErrorString(e));
   return QF_OK;

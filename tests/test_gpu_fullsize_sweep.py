@@ -1,0 +1,203 @@
+"""Whole-sweep parity at the benchmarked sizes (11 and 12 qubits) against the
+FP64 oracle's TwoSidedSweep (Alg. 1), through the resident plan exactly as
+the benchmark drives it: the starts split into two groups whose environment
+kernels and passes run on two internal streams, the plan's first sweep runs
+as live launches and the second as a replay of the captured CUDA graph.
+
+From 11 qubits the environment kernel splits each start's band over several
+CTAs (2 at 11 qubits, 4 at 12, 8 at 13): every CTA writes its partial sums,
+the last CTA to finish (atomic ticket) adds them in a fixed order and runs
+the FP64 4x4 update in its epilogue.  Smaller circuits use one CTA per start,
+so only these sizes check that path inside a whole sweep.
+
+Sampled starts: the first and the last of the launch (one per start group).
+Tolerances: complex128 and double-FP32 tensors, costs 1e-10 and gates 1e-9
+(the spec bars for complex128 results); complex64 tensors, the cost
+and gate errors against the FP64 oracle are printed and bounded by 1e-7 and
+1e-4 (FP32 tensor arithmetic over 132-264 passes; measured on a GB300: at
+most 7e-9 and 4e-6 after two sweeps).
+
+The oracle takes about 17 s per 12-qubit sweep of one start on 16 host
+cores, so its results are computed once per module and shared by every
+precision and by the look-ahead sweep (which visits the gates in the same
+order and differs only by rounding).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+import oracle.kqubit as ok
+import qf_inputs as qi
+
+pytestmark = pytest.mark.gpu
+
+SWEEPS = 2
+C64_COST_TOL = 1e-7
+C64_GATE_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def qf():
+    import paper_2306_08152_gb300 as qf
+
+    qf._native.load()
+    return qf
+
+
+def _oracle_trajectory(V, gates, locs, n, sweeps):
+    """Oracle costs and gates after every sweep (no reset within `sweeps`)."""
+    T = orc.init_circuit_tensor(V, gates, locs, n)
+    g = gates
+    out = []
+    for _ in range(sweeps):
+        T, g = orc.two_sided_sweep(T, g, locs, n)
+        out.append((orc.trace_cost(T, n), g.copy()))
+    return out
+
+
+class _Problem:
+    def __init__(self, n, S, seed, sampled):
+        self.n = n
+        self.locs = qi.brickwork_locations(n, 12)
+        self.inst = qi.make_problem(n, self.locs, S, seed=seed)
+        # reachable target, as in the benchmark
+        self.V = orc.circuit_unitary(self.inst.target_gates, self.locs, n)
+        self.sampled = sampled
+        self.ref = {s: _oracle_trajectory(self.V, self.inst.starts[s], self.locs, n, SWEEPS)
+                    for s in sampled}
+
+
+@pytest.fixture(scope="module")
+def p12():
+    # the benchmark's launch configuration: 12 qubits, 66 gates, 8 starts
+    return _Problem(12, 8, 2024, (0, 7))
+
+
+@pytest.fixture(scope="module")
+def p11():
+    return _Problem(11, 2, 1111, (0, 1))
+
+
+def _run_plan(qf, prob, precision, lookahead=False):
+    """Sweep a plan SWEEPS times; return (costs, gates) after every sweep."""
+    plan = qf.Plan(prob.n, prob.locs, prob.inst.n_starts, precision)
+    if lookahead:
+        assert plan.set_lookahead(True) == len(prob.locs)  # brickwork: every pair is disjoint
+    plan.load(torch.from_numpy(prob.V).cuda(), torch.from_numpy(prob.inst.starts).cuda())
+    out = []
+    for _ in range(SWEEPS):
+        plan.sweep(1, reset_iter=0)  # sweep 1 live, sweep 2 a graph replay
+        out.append((plan.costs(), plan.gates().numpy()))
+    assert plan.status() == 0
+    plan.close()
+    return out
+
+
+def _check(prob, got, cost_tol, gate_tol, label):
+    for it in range(SWEEPS):
+        costs, gates = got[it]
+        for s in prob.sampled:
+            c_ref, g_ref = prob.ref[s][it]
+            dc = abs(costs[s] - c_ref)
+            dg = float(np.max(np.abs(gates[s] - g_ref)))
+            print(f"{label} n={prob.n} sweep {it + 1} start {s}: cost {costs[s]:.12e} "
+                  f"|dcost| {dc:.2e} max|dgate| {dg:.2e}")
+            assert dc <= cost_tol, (label, it, s, costs[s], c_ref)
+            assert dg <= gate_tol, (label, it, s, dg)
+
+
+def test_sweeps_12q_c128_match_oracle(qf, p12):
+    _check(p12, _run_plan(qf, p12, qf.QF_C128), 1e-10, 1e-9, "c128")
+
+
+def test_sweeps_12q_c64_track_oracle(qf, p12):
+    _check(p12, _run_plan(qf, p12, qf.QF_C64), C64_COST_TOL, C64_GATE_TOL, "c64")
+
+
+def test_lookahead_sweeps_12q_track_oracle(qf, p12):
+    _check(p12, _run_plan(qf, p12, qf.QF_C64, lookahead=True), C64_COST_TOL, C64_GATE_TOL,
+           "c64 look-ahead")
+
+
+def test_sweeps_11q_c128_match_oracle(qf, p11):
+    _check(p11, _run_plan(qf, p11, qf.QF_C128), 1e-10, 1e-9, "c128")
+
+
+def test_sweeps_11q_df64_match_oracle(qf, p11):
+    _check(p11, _run_plan(qf, p11, qf.QF_DF64), 1e-10, 1e-9, "df64")
+
+
+def test_lookahead_sweeps_11q_track_oracle(qf, p11):
+    _check(p11, _run_plan(qf, p11, qf.QF_C64, lookahead=True), C64_COST_TOL, C64_GATE_TOL,
+           "c64 look-ahead")
+
+
+def test_mixed_k3_sweeps_11q_c128_match_oracle(qf):
+    """Two- and three-qubit gates at 11 qubits (the 8x8 environment kernel
+    splits each start's band over several CTAs too), two start groups, the
+    second sweep a graph replay; k-qubit oracle."""
+    n, S = 11, 2
+    g = qi.rng(11300)
+    locs = [(0, 1, 2), (3, 4), (5, 6, 7), (8, 9, 10), (2, 3), (4, 5, 6), (7, 8), (9, 10),
+            (10, 0, 5), (1, 2)]
+    tgt = [qi.haar_unitary(2 ** len(q), g) for q in locs]
+    V = ok.circuit_unitary_k(tgt, locs, n)
+    starts = [[qi.haar_unitary(2 ** len(q), g) for q in locs] for _ in range(S)]
+    plan = qf.Plan(n, locs, S, qf.QF_C128)
+    plan.load(torch.from_numpy(V).cuda(), qf.flatten_gates(starts).cuda())
+    got = []
+    for _ in range(SWEEPS):
+        plan.sweep(1, reset_iter=0)
+        got.append((plan.costs(), qf.unflatten_gates(plan.gates(), locs)))
+    assert plan.status() == 0
+    plan.close()
+    for s in range(S):
+        T = ok.init_circuit_tensor_k(V, starts[s], locs, n)
+        gref = starts[s]
+        for it in range(SWEEPS):
+            T, gref = ok.two_sided_sweep_k(T, gref, locs, n)
+            c_ref = ok.trace_cost(T, n)
+            costs, gates = got[it]
+            print(f"k3 n={n} sweep {it + 1} start {s}: |dcost| {abs(costs[s] - c_ref):.2e}")
+            assert abs(costs[s] - c_ref) <= 1e-10, (it, s, costs[s], c_ref)
+            for a, b in zip(gates[s], gref):
+                assert np.max(np.abs(a - b)) <= 1e-9, (it, s)
+
+
+def _rand_T(S, n, g, dtype):
+    N = 2**n
+    fdt = np.float32 if dtype == torch.complex64 else np.float64
+    re = g.standard_normal((S, N, N), dtype=fdt)
+    im = g.standard_normal((S, N, N), dtype=fdt)
+    T = np.empty((S, N, N), dtype=np.complex64 if dtype == torch.complex64 else np.complex128)
+    T.real = re
+    T.imag = im
+    return T
+
+
+def _pairs(n):
+    # lowest and highest bits (qubit n-1 is bit 0, qubit 0 the top bit),
+    # both orders, one pair far apart and one in the middle
+    return [(0, 1), (n - 1, n - 2), (n - 2, n - 1), (0, n - 1), (n - 1, 0), (n // 2, n // 2 - 1)]
+
+
+@pytest.mark.parametrize("n,S,dtype", [(11, 3, torch.complex128), (11, 3, torch.complex64),
+                                       (12, 2, torch.complex128), (12, 3, torch.complex64),
+                                       (13, 1, torch.complex128), (13, 2, torch.complex64)])
+def test_partial_trace_multi_cta_matches_oracle(qf, n, S, dtype):
+    """CalcEnvMat (Alg. 1) at sizes where every start's band is split over
+    2 (11 qubits), 4 (12) or 8 (13) CTAs."""
+    g = qi.rng(11000 + n)
+    T0 = _rand_T(S, n, g, dtype)
+    T = torch.from_numpy(T0).cuda()
+    for a, b in _pairs(n):
+        P = qf.partial_trace(T, a, b).cpu().numpy()
+        for s in range(S):
+            Ts = T0[s].astype(np.complex128)
+            ref = orc.calc_env_mat(Ts, a, b, n)
+            if dtype == torch.complex128:
+                assert np.max(np.abs(P[s] - ref)) <= 1e-12 * np.max(np.abs(ref)), (a, b, s)
+            else:  # FP32 band sums within a CTA: 1e-6 of the sum of magnitudes
+                bound = 1e-6 * orc.calc_env_mat(np.abs(Ts).astype(np.complex128), a, b, n).real
+                assert np.all(np.abs(P[s] - ref) <= bound), (a, b, s)

@@ -1,0 +1,170 @@
+"""OptimizeGate (Sec. III-A1, Eq. opt_u) on ill-conditioned and degenerate
+environments, against the FP64 oracle (LAPACK SVD).
+
+For a nonsingular complex E the optimal gate u = Y X^dagger (E = X D Y^dagger)
+is unique: it is the unitary polar factor of E^dagger.  It is also
+ill-conditioned when E nearly loses rank: a perturbation dE moves it by at
+most 2 ||dE|| / (s_min(E) + s_min(E + dE)) (R.-C. Li's bound for the unitary
+polar factor of a complex matrix, Frobenius norm).  Both the GPU and LAPACK
+compute the factor of E plus a backward error of a few units of FP64 rounding
+times ||E||, so the two may differ by
+
+    bound = C * eps * s_max / s_min,     eps = 2^-52,
+
+with C = 100 for 4x4 and 8x8 matrices (a few rounding errors per entry,
+two sides, Frobenius norms), and never by more than 1e-11 for a
+well-conditioned E.  Independently of that bound, every result must attain
+the optimum: Re Tr(E u) = sum of singular values to 1e-12 relative, the
+returned sum likewise, and u must be unitary to 1e-13.
+
+Spectra: graded (s_min / s_max = 1e-3 .. 1e-12, geometric and with a single
+small value), near-degenerate and exactly degenerate singular values, global
+complex phases and scales far from 1.  The same environments are also fed
+through whole sweeps of the resident plan and of the batched kernel (whose
+Jacobi starts warm from the previous update's rotation): a three-qubit
+circuit with one gate on (0, 1) and the target V = W^dagger,
+W = U1 (x) |0><0| + U2 (x) |1><1|, has the environment E = U1 + U2 at every
+update, with singular values |1 + e^{i theta_k}| set by the eigenphases of
+U1^dagger U2.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+import oracle.kqubit as ok
+import qf_inputs as qi
+
+pytestmark = pytest.mark.gpu
+
+EPS = 2.0**-52
+C_BOUND = 100.0
+
+
+@pytest.fixture(scope="module")
+def qf():
+    import paper_2306_08152_gb300 as qf
+
+    qf._native.load()
+    return qf
+
+
+def _bound(sig):
+    sig = np.asarray(sig, dtype=float)
+    return max(C_BOUND * EPS * sig.max() / sig.min(), 1e-11)
+
+
+def _spectra(d):
+    out = []
+    for r in (1e-3, 1e-6, 1e-9, 1e-12):
+        out.append(r ** (np.arange(d) / (d - 1)))             # geometric grading
+        out.append(np.r_[np.linspace(1.0, 0.5, d - 1), r])   # one small value
+    out.append(np.r_[1.0, 1.0 + 1e-9, np.full(d - 2, 0.3) * (1 + 1e-12 * np.arange(d - 2))])
+    out.append(np.ones(d))                                   # exactly degenerate: u = unique
+    out.append(np.r_[np.full(d // 2, 2.0), np.full(d // 2, 1e-3)])
+    return out
+
+
+def _cases(d, seed):
+    g = qi.rng(seed)
+    Es, sigs = [], []
+    for sig in _spectra(d):
+        for scale in (1.0, 1e-150, 1e120):
+            X = qi.haar_unitary(d, g)
+            Y = qi.haar_unitary(d, g)
+            ph = np.exp(1j * g.uniform(0, 2 * np.pi))
+            Es.append(scale * ph * (X * sig[None, :]) @ Y.conj().T)
+            sigs.append(scale * np.sort(sig)[::-1])
+    return np.stack(Es), sigs
+
+
+def _check(U, S, Es, sigs, label):
+    d = Es.shape[-1]
+    worst = 0.0
+    for i, E in enumerate(Es):
+        u_ref, s_ref = orc.optimize_gate(E) if d == 4 else ok.optimize_gate_k(E)
+        s_true = float(np.sum(sigs[i]))
+        assert abs(s_ref - s_true) <= 1e-12 * s_true  # the oracle itself
+        assert np.max(np.abs(U[i].conj().T @ U[i] - np.eye(d))) <= 1e-13, (label, i)
+        attained = np.trace(E @ U[i])
+        assert abs(attained.real - s_true) <= 1e-12 * s_true, (label, i, attained, s_true)
+        assert abs(attained.imag) <= 1e-12 * s_true, (label, i)
+        assert abs(S[i] - s_true) <= 1e-12 * s_true, (label, i, S[i], s_true)
+        err = float(np.max(np.abs(U[i] - u_ref)))
+        b = _bound(sigs[i])
+        worst = max(worst, err / b)
+        assert err <= b, (label, i, err, b, sigs[i])
+    print(f"{label}: worst |u - u_oracle| / bound = {worst:.3f}")
+
+
+def test_optimize_gates_4x4_ill_conditioned(qf):
+    Es, sigs = _cases(4, 12000)
+    U, S = qf.optimize_gates(torch.from_numpy(Es).cuda())
+    _check(U.cpu().numpy(), S.cpu().numpy(), Es, sigs, "4x4")
+
+
+def test_optimize_gates_8x8_ill_conditioned(qf):
+    Es, sigs = _cases(8, 12001)
+    U, S = qf.optimize_gates_k(torch.from_numpy(Es).cuda())
+    _check(U.cpu().numpy(), S.cpu().numpy(), Es, sigs, "8x8")
+
+
+# ---------------------------------------------------------------- in sweeps
+
+SWEEP_SPECTRA = [(2.0, 1.0, 1e-3, 1e-6), (2.0, 1.5, 1e-9, 1e-12), (1.9, 1e-6, 1e-6, 1e-9),
+                 (2.0, 2.0, 2.0, 1e-10)]
+
+
+def _controlled_problem(sig, g):
+    """n = 3, one gate on (0, 1); E = U1 + U2 has singular values sig."""
+    U1 = qi.haar_unitary(4, g)
+    Z = qi.haar_unitary(4, g)
+    theta = np.pi - 2.0 * np.arcsin(np.asarray(sig) / 2.0)  # |1 + e^{i theta}| = sig
+    Q = (Z * np.exp(1j * theta)[None, :]) @ Z.conj().T
+    U2 = U1 @ Q
+    W = np.kron(U1, np.diag([1.0, 0.0])) + np.kron(U2, np.diag([0.0, 1.0]))
+    V = W.conj().T
+    E = U1 + U2
+    # the rounded E's own singular values (within ~eps * s_max of sig) set the bound
+    sv = np.linalg.svd(E, compute_uv=False)
+    assert np.allclose(np.sort(sv), np.sort(sig), rtol=0, atol=1e-14)
+    locs = np.array([[0, 1]], dtype=np.int32)
+    assert np.allclose(orc.calc_env_mat(V.conj().T, 0, 1, 3), E, atol=1e-14)
+    return V, locs, E, sv
+
+
+def test_ill_conditioned_environments_in_plan_sweeps(qf):
+    g = qi.rng(12100)
+    for sig in SWEEP_SPECTRA:
+        V, locs, E, sv = _controlled_problem(sig, g)
+        u_ref, s_ref = orc.optimize_gate(E)
+        starts = np.stack([qi.haar_gates(1, g) for _ in range(2)])
+        plan = qf.Plan(3, locs, 2, qf.QF_C128)
+        plan.load(torch.from_numpy(V).cuda(), torch.from_numpy(starts).cuda())
+        plan.sweep(3, reset_iter=0)
+        costs, G = plan.costs(), plan.gates().numpy()
+        plan.close()
+        for s in range(2):
+            assert abs(costs[s] - (1.0 - s_ref / 8.0)) <= 1e-13, (sig, s)
+            assert np.max(np.abs(G[s, 0] - u_ref)) <= _bound(sv), (sig, s)
+
+
+def test_ill_conditioned_environments_in_batched_kernel(qf):
+    """The batched kernel starts each update's Jacobi from the previous
+    update's rotation of the same gate; three sweeps = six updates of the
+    same environment per start."""
+    g = qi.rng(12200)
+    insts, refs = [], []
+    for sig in SWEEP_SPECTRA:
+        V, locs, E, sv = _controlled_problem(sig, g)
+        starts = np.stack([qi.haar_gates(1, g) for _ in range(2)])
+        insts.append((V, locs, starts))
+        refs.append((orc.optimize_gate(E), sv))
+    # complex128 tensors: a complex64 tensor's environment carries FP32
+    # rounding, which the polar factor amplifies by 1/s_min
+    res = qf.instantiate_batched(insts, dist_tol=0.0, max_sweeps=3, reset_iter=0, precision=qf.QF_C128)
+    for i, ((u_ref, s_ref), sv) in enumerate(refs):
+        for s in range(2):
+            assert abs(res["costs"][i, s] - (1.0 - s_ref / 8.0)) <= 1e-13, (sv, s)
+            err = np.max(np.abs(res["gates"][i][s, 0] - u_ref))
+            assert err <= _bound(sv), (sv, s, err)
