@@ -35,6 +35,7 @@ N_QUBITS = 12
 LAYERS = 12
 STARTS = 8
 SEED = 2024
+RESET_ITER = 40  # Sec. III-A2 reset_iter
 METRIC = "gate-updates/s at 12 qubits (% HBM roofline)"
 UNIT = "gate-updates/s"
 
@@ -59,6 +60,7 @@ def parse():
     ap.add_argument("--no-lookahead", action="store_true")
     ap.add_argument("--no-kqubit", action="store_true")
     ap.add_argument("--no-spec", action="store_true")
+    ap.add_argument("--oracle-1core", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -78,7 +80,9 @@ def config_dict(args, inst):
         "starts_per_gpu": inst.n_starts,
         "precision": args.precision,
         "updates_per_step_per_gpu": inst.n_starts * 2 * inst.p,
-        "step": "one TwoSidedSweep of every start (rebuild every 40 sweeps)",
+        "step": "one TwoSidedSweep of every start; after every 40th sweep of the plan the gates "
+                "are re-unitarised and the tensors rebuilt (the timed region starts at such a sweep, "
+                "so it holds ceil(steps/40) rebuilds)",
         "l2": "no flush: the circuit tensors (%.2f GB) exceed L2" % (
             inst.n_starts * 4**inst.n * (8 if args.precision == "c64" else 16) / 1e9),
         "parallelism": "replicas (independent starts per GPU)",
@@ -177,6 +181,41 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+_ALU_PEAKS = {}
+
+
+def measured_alu_peaks(torch, dev):
+    """Dense FP64 and FP32 throughput of this GPU, measured in this run: the
+    best of 5 cuBLAS DGEMM (4096^3) and SGEMM (8192^3, TF32 off) products,
+    2 n^3 flops each, CUDA events.  Denominators for the complex128 pass
+    (bound by the FP64 pipe) and the double-FP32 pass (FP32 pipe)."""
+    if _ALU_PEAKS:
+        return _ALU_PEAKS
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for key, dt, m in (("fp64_gflops", torch.float64, 4096), ("fp32_gflops", torch.float32, 8192)):
+            a = torch.randn(m, m, dtype=dt, device=dev)
+            b = torch.randn(m, m, dtype=dt, device=dev)
+            c = a @ b
+            best = float("inf")
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            _ALU_PEAKS[key] = 2.0 * m**3 / (best / 1e3) / 1e9
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    _ALU_PEAKS["how"] = ("cuBLAS DGEMM 4096^3 and SGEMM 8192^3 (TF32 off) through torch.matmul, "
+                         "best of 5, 2 n^3 flops, CUDA events, in this run")
+    return _ALU_PEAKS
+
+
 def kernel_traffic(precision, starts, n):
     """DRAM bytes per pass launch from a committed ncu summary, if it was
     taken on the current kernel source; else None."""
@@ -199,16 +238,21 @@ def kernel_traffic(precision, starts, n):
     return entry["dram_bytes"] * scale
 
 
-def oracle_sample(inst, seconds, max_updates=None):
-    """Time the oracle's gate updates (Alg. 1 TwoSidedSweep backward steps)
-    on start 0 of the workload.  Setup (the target and the initial circuit
-    tensor, built by the oracle) is untimed."""
+def oracle_setup(inst):
+    """The oracle's circuit tensor of start 0 (untimed setup of a sample)."""
     import oracle as orc
 
-    n, locs = inst.n, inst.locs
-    V = orc.circuit_unitary(inst.target_gates, locs, n)
-    T = orc.init_circuit_tensor(V, inst.starts[0], locs, n)
-    gates = inst.starts[0].copy()
+    V = orc.circuit_unitary(inst.target_gates, inst.locs, inst.n)
+    return orc.init_circuit_tensor(V, inst.starts[0], inst.locs, inst.n)
+
+
+def oracle_updates(T, gates, locs, n, seconds, max_updates=None):
+    """Time the oracle's gate updates (Alg. 1 TwoSidedSweep backward steps,
+    ApplyRight, CalcEnvMat, OptimizeGate, ApplyLeft) from tensor T for about
+    `seconds`; returns (updates, wall s, CPU s)."""
+    import oracle as orc
+
+    gates = gates.copy()
     p = len(locs)
     done = 0
     w0 = time.perf_counter()
@@ -229,6 +273,39 @@ def oracle_sample(inst, seconds, max_updates=None):
     wall = time.perf_counter() - w0
     cpu = time.process_time() - c0
     return done, wall, cpu
+
+
+def oracle_sample(inst, seconds, max_updates=None):
+    """The oracle's gate updates on start 0 of the workload, on every host
+    core NumPy uses."""
+    T = oracle_setup(inst)
+    return oracle_updates(T, inst.starts[0], inst.locs, inst.n, seconds, max_updates), T
+
+
+def oracle_single_core(inst, T, seconds):
+    """The same oracle updates in a child process pinned to one host core
+    with one BLAS/OpenMP thread (the tensor is handed over in a file, so the
+    child only times updates)."""
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "oracle_state.npz")
+        np.savez(path, T=T, gates=inst.starts[0], locs=inst.locs, n=inst.n)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-1core", path,
+               "--cpu-seconds", str(seconds)]
+        res = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    if res.returncode != 0:
+        return {"error": res.stderr.strip().splitlines()[-1] if res.stderr.strip() else "failed"}
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_1core(args):
+    """Child of oracle_single_core: pin to one core, time the updates."""
+    cpus = sorted(os.sched_getaffinity(0))
+    os.sched_setaffinity(0, {cpus[-1]})
+    st = np.load(args.oracle_1core)
+    done, wall, cpu = oracle_updates(st["T"], st["gates"], st["locs"], int(st["n"]), args.cpu_seconds)
+    print(json.dumps({"updates": done, "wall_s": wall, "cpu_s": cpu, "core": cpus[-1]}))
+    return 0
 
 
 # ------------------------------------------------------------------ reference arm
@@ -325,8 +402,18 @@ def run_batched(args, qf, torch, dev):
     wall = time.perf_counter() - t0
     best = res["costs"][np.arange(len(probs)), res["best"]]
     ok = int((best <= 1e-10).sum())
+    # the same instances with complex128 tensors throughout (no complex64
+    # phase): do the complex64 sweeps lose successes?
+    qf.instantiate_batched(probs[:64], precision=qf.QF_C128, **opts)  # tuning
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res128 = qf.instantiate_batched(probs, precision=qf.QF_C128, **opts)
+    wall128 = time.perf_counter() - t0
+    best128 = res128["costs"][np.arange(len(probs)), res128["best"]]
+    ok128 = int((best128 <= 1e-10).sum())
+    both = int(((best <= 1e-10) & (best128 <= 1e-10)).sum())
     # plain FP64 per-instance path on a sample
-    sample = probs[: max(1, min(8, len(probs)))]
+    sample = probs[: max(1, min(64, len(probs)))]
     t1 = time.perf_counter()
     ok_plain = 0
     for V, L, G in sample:
@@ -341,6 +428,12 @@ def run_batched(args, qf, torch, dev):
         "precision": "complex64 sweeps, FP64 4x4 updates, complex128 refinement",
         "workload": f"{len(probs)} reachable instances, 3/4/5 qubits 2:1:1, 5-40 U(4) gates on random "
                     "adjacent pairs, 4 Haar starts, tol 1e-10, <=500 sweeps",
+        "success_c128": {"success": ok128, "value": ok128 / wall128, "wall_s": wall128,
+                         "kernel_ms": res128["kernel_ms"], "sweeps": res128["total_sweeps"],
+                         "success_in_both": both,
+                         "note": "the same instances, starts and options with complex128 tensors "
+                                 "throughout the batched kernel"},
+        "success_plain_sample_c64refine": int((best[: len(sample)] <= 1e-10).sum()),
         "plain_fp64_per_instance": {"value": ok_plain / wall_plain, "unit": "instantiations/s",
                                     "success": ok_plain, "sample": len(sample), "wall_s": wall_plain,
                                     "path": "qf_instantiate_ex per instance, complex128, 4 starts"},
@@ -370,11 +463,13 @@ def run_c128(args, qf, torch, dev, inst, V, starts):
     updates = inst.n_starts * 2 * inst.p * steps
     flops = pbytes / max(launches, 1) / 32 * 64  # 16-byte entries, read + write
     achieved = flops / ((pass_ms / 1e3) / max(launches, 1)) / 1e9
+    peaks = measured_alu_peaks(torch, dev)
     return {"metric": "gate-updates/s at 12 qubits, complex128", "unit": "gate-updates/s",
             "value": updates / (ms / 1e3), "ms_per_sweep": ms / steps, "dtype": "c128",
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": 1250.0, "unit": "GFLOP/s",
-                         "frac": achieved / 1250.0,
-                         "peak_source": "nominal FP64 1.25 TFLOP/s (fma_chain probe measured 1.20)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fp64_gflops"],
+                         "unit": "GFLOP/s", "frac": achieved / peaks["fp64_gflops"],
+                         "peak_source": "measured FP64: " + peaks["how"],
+                         "nominal_peak": 1250.0, "frac_of_nominal": achieved / 1250.0,
                          "flops_per_launch": flops}}
 
 
@@ -414,6 +509,7 @@ def run_df64(args, qf, torch, dev, inst, V, starts):
     avg_s = (pass_ms / 1e3) / max(launches, 1)
     achieved = ops / avg_s / 1e9
     peak, _ = measured_peaks()
+    peaks = measured_alu_peaks(torch, dev)
     return {"metric": "gate-updates/s at 12 qubits, df64 (double-FP32 complex tensor)",
             "unit": "gate-updates/s", "value": updates / (ms / 1e3), "ms_per_sweep": ms / steps,
             "dtype": "df64",
@@ -421,6 +517,8 @@ def run_df64(args, qf, torch, dev, inst, V, starts):
                          "unit": "Gop/s", "frac": achieved / FP32_PIPE_GOPS,
                          "peak_source": "FP32 pipe from unit counts and clock: 152 SMs x 128 lanes "
                                         "x 2.07 GHz, one operation per lane per cycle",
+                         "measured_sgemm_gflops": peaks["fp32_gflops"],
+                         "frac_of_measured_sgemm_flops": 2 * achieved / peaks["fp32_gflops"],
                          "ops_per_entry": DF64_OPS_PER_ENTRY, "avg_launch_ms": avg_s * 1e3,
                          "hbm_gbs": pbytes / max(launches, 1) / avg_s / 1e9,
                          "hbm_frac": pbytes / max(launches, 1) / avg_s / 1e9 / peak},
@@ -618,6 +716,16 @@ def run_spec(args, qf, torch, dev):
             "final_costs": [float(c) for c in costs]}
 
 
+def config_oracle_costs():
+    """The FP64 oracle's final costs on the 3- and 6-qubit workloads, stored
+    by tests/golden/make_config_costs.py (read here, not recomputed)."""
+    path = os.path.join(ROOT, "tests", "golden", "config_oracle_costs.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        return json.load(f)
+
+
 def run_configs(args, qf, torch, dev):
     """Correctness and time per sweep of the smaller workloads:
     3-qubit alternating circuit (6 U(4) gates, 1 start, to 1e-10 or 500
@@ -636,8 +744,10 @@ def run_configs(args, qf, torch, dev):
     t = time.perf_counter()
     r = qf.instantiate_ex(V, locs, torch.from_numpy(inst.starts).to(dev), dist_tol=1e-10, max_sweeps=500)
     w = time.perf_counter() - t
+    gold = config_oracle_costs()
     out["3q_6gates"] = {"cost": r["best_cost"], "sweeps": r["sweeps"], "reason": r["reason"],
-                        "ms_per_sweep": 1e3 * w / max(r["sweeps"], 1), "path": "qf_instantiate_ex, complex128"}
+                        "ms_per_sweep": 1e3 * w / max(r["sweeps"], 1), "path": "qf_instantiate_ex, complex128",
+                        "oracle": gold.get("3q_6gates", {}).get("start0")}
 
     # 6 qubits, brickwork of 30 gates, 16 starts
     locs = qi.brickwork_locations(6, 12)
@@ -660,6 +770,16 @@ def run_configs(args, qf, torch, dev):
                            "reason": r["reason"], "s": w, "ms_per_sweep": 1e3 * w / max(r["sweeps"], 1)},
                 "batched": {"best_cost": float(rb["costs"][0].min()), "max_sweeps": int(rb["sweeps"].max()),
                             "s": wb, "kernel_ms": rb["kernel_ms"]}}
+    # starts 0 and 1 alone, next to the oracle's final cost for the same start
+    per_start = {}
+    for tname, V in (("haar", Vh), ("reachable", Vr)):
+        for st in (0, 1):
+            r = qf.instantiate_ex(V, locs, starts[st:st + 1], dist_tol=1e-10, max_sweeps=500,
+                                  precision=qf.QF_C128)
+            per_start[f"{tname}/start{st}"] = {
+                "gpu_c128": {"cost": r["best_cost"], "sweeps": r["sweeps"]},
+                "oracle": gold.get("6q_30gates", {}).get(tname, {}).get(f"start{st}")}
+    rows["per_start_vs_oracle"] = per_start
     out["6q_30gates_16starts"] = rows
 
     # 8 qubits, 56 gates, 32 gate sets: differentiable cost (forward + backward)
@@ -740,6 +860,14 @@ def run_ours(args):
     plan.load(V, starts, stream=stream)
     for _ in range(args.warmup):
         plan.sweep(1, reset_iter=40)
+    # untimed sweeps up to the next rebuild sweep: the first timed sweep is
+    # a multiple of RESET_ITER, so every RESET_ITER timed sweeps hold one
+    # re-unitarisation and rebuild
+    align = (RESET_ITER - 1 - args.warmup) % RESET_ITER
+    for _ in range(align):
+        plan.sweep(1, reset_iter=RESET_ITER)
+    first_timed = args.warmup + align + 1
+    rebuilds_timed = sum(1 for k in range(first_timed, first_timed + args.steps) if k % RESET_ITER == 0)
     plan.costs()
     plan.pass_stats()  # reset counters
 
@@ -754,7 +882,7 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        plan.sweep(1, reset_iter=40)
+        plan.sweep(1, reset_iter=RESET_ITER)
     e1.record(stream)
     torch.cuda.synchronize()
     clock_info = clocks.stop()
@@ -858,11 +986,19 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        done, wall, cput = oracle_sample(inst, args.cpu_seconds)
+        (done, wall, cput), T0 = oracle_sample(inst, args.cpu_seconds)
+        one = oracle_single_core(inst, T0, args.cpu_seconds)
+        del T0
+        single = ({"value": one["updates"] / one["wall_s"], "unit": UNIT, "cores": 1,
+                   "sample": f"{one['updates']} gate updates, {one['wall_s']:.1f} s wall, one process "
+                             f"pinned to core {one['core']} with one BLAS/OpenMP thread"}
+                  if "updates" in one else one)
         cpu = {"value": done / wall, "unit": UNIT, "cores": round(cput / wall, 2), "kind": "oracle",
                "sample": f"{done} gate updates (ApplyRight, CalcEnvMat, OptimizeGate, ApplyLeft) "
                          f"of the FP64 NumPy oracle on start 0 of the same {n}-qubit workload, "
-                         f"{wall:.1f} s wall; cores = CPU time / wall time"}
+                         f"{wall:.1f} s wall; cores = CPU time / wall time",
+               "single_core": single, "nproc": os.cpu_count(),
+               "cores_available": len(os.sched_getaffinity(0))}
 
     if rank == 0:
         line = {
@@ -870,7 +1006,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "c64" if args.precision == "c64" else "c128",
-            "data": "synthetic", "config": config_dict(args, inst),
+            "data": "synthetic", "config": dict(config_dict(args, inst),
+                                                rebuilds_in_timed_region=rebuilds_timed,
+                                                first_timed_sweep=first_timed),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(all_launches), "clocks": clock_info,
             "ms_per_step_live": ms_live,
@@ -889,6 +1027,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.oracle_1core:
+        return run_oracle_1core(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
