@@ -248,6 +248,21 @@ __device__ __forceinline__ C2 wdag(const Lane& L, C2 a) {
   return cconj(shfl(a, L.at(L.j, L.i)));
 }
 
+// 1/sqrt(q) for a positive normal double q by Newton's iteration
+// r <- r (3 - q r^2) / 2 from an FP32 seed.  q = m 4^k with m in [1, 4), so
+// the seed rsqrtf(m) 2^-k neither under- nor overflows in FP32; its relative
+// error (~1e-7) squares with each step, so two steps reach FP64 rounding.
+// No FP64 division or square root (long instruction sequences on the FP64
+// pipe).
+__device__ __forceinline__ double rsqrt_d(double q) {
+  const int k = (((__double2hiint(q) >> 20) & 0x7ff) - 1023) >> 1;  // floor(log2(q) / 2)
+  const double m = q * __hiloint2double((1023 - 2 * k) << 20, 0);
+  double r = (double)rsqrtf((float)m) * __hiloint2double((1023 - k) << 20, 0);
+  r = r * (1.5 - 0.5 * q * r * r);
+  r = r * (1.5 - 0.5 * q * r * r);
+  return r;
+}
+
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int h = 16; h >= 1; h >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, h));

@@ -114,10 +114,11 @@ __device__ __forceinline__ double colsum(double v) {  // over the 4 row groups
   return v;
 }
 
-// Rare path: some singular value is (numerically) zero, so X needs an
-// orthonormal completion.  Lane 0 runs modified Gram-Schmidt in FP64 over
-// the columns of W in order of decreasing singular value, falling back to
-// standard basis vectors.  sm: 128 double2 of shared scratch for this warp.
+// Rare path: some singular value is below 1e-3 of the largest, so X is built
+// by modified Gram-Schmidt in FP64 (lane 0) over the columns of W in order
+// of decreasing singular value (columns below 1e-13 of the largest are
+// numerically zero), falling back to standard basis vectors for an
+// orthonormal completion.  sm: 128 double2 of shared scratch for this warp.
 static __device__ __noinline__ void complete8(const L8& L, double2 w0, double2 w1, const double* sig,
                                               double smax, double2* sm, double2& x0, double2& x1) {
   sm[L.g * 8 + L.j] = w0;
@@ -142,7 +143,7 @@ static __device__ __noinline__ void complete8(const L8& L, double2 w0, double2 w
       for (int att = 0; att < 9; ++att) {
         double2 v[8];
         if (att == 0) {
-          if (!(sig[k] > 1e-12 * smax)) continue;
+          if (!(sig[k] > 1e-13 * smax)) continue;  // numerically zero: complete instead
           for (int i = 0; i < 8; ++i) v[i] = make_double2(sm[i * 8 + k].x / sig[k], sm[i * 8 + k].y / sig[k]);
         } else {
           for (int i = 0; i < 8; ++i) v[i] = make_double2(i == att - 1 ? 1.0 : 0.0, 0.0);
@@ -241,19 +242,6 @@ __device__ __forceinline__ void jacobi8(const L8& L, C2& w0, C2& w1, C2& y0, C2&
     for (int h = 16; h >= 1; h >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, h));
     if (m < tol) break;
   }
-}
-
-// 1/sqrt(q) for a positive normal double q by Newton's iteration
-// r <- r (3 - q r^2) / 2 from an FP32 seed.  q = m 4^k with m in [1, 4), so
-// the seed rsqrtf(m) 2^-k neither under- nor overflows in FP32; its relative
-// error (~1e-7) squares with each step, so two steps reach FP64 rounding.
-__device__ __forceinline__ double rsqrt_d(double q) {
-  const int k = (((__double2hiint(q) >> 20) & 0x7ff) - 1023) >> 1;  // floor(log2(q) / 2)
-  const double m = q * __hiloint2double((1023 - 2 * k) << 20, 0);
-  double r = (double)rsqrtf((float)m) * __hiloint2double((1023 - k) << 20, 0);
-  r = r * (1.5 - 0.5 * q * r * r);
-  r = r * (1.5 - 0.5 * q * r * r);
-  return r;
 }
 
 // FP64 polishing sweeps after the FP32 stage, in which every column pair is
@@ -368,10 +356,14 @@ static __device__ __noinline__ bool warp_polar8(double2 a0, double2 a1, double2*
     ssum += s8[k];
   }
   double2 x0, x1;
-  if (smin > 1e-10 * smax) {
+  if (smin > 1e-3 * smax) {
     x0 = make_double2(w0.x / sj, w0.y / sj);
     x1 = make_double2(w1.x / sj, w1.y / sj);
   } else {
+    // A close to singular (rare): a column of small norm s has its direction
+    // only to ~eps s_max / s, so X is re-orthonormalised (Gram-Schmidt, in
+    // order of decreasing s) rather than normalised, keeping u unitary to
+    // FP64 rounding; columns below 1e-13 s_max are completed
     complete8(L, w0, w1, s8, smax, sm, x0, x1);
   }
   mm8_nd(L, y0, y1, x0, x1, *u0, *u1);  // Y X^dagger
