@@ -90,7 +90,7 @@ typedef struct { int32_t a, b; } qf_loc;     /* gate location: qubits a != b  */
  * Hyperparameters of Sec. III-A2.  qf_options_default() fills: dist_tol 1e-10,
  * max_sweeps 500, min_sweeps 0, reset_iter 40, diff_tol_a 0, diff_tol_r 0,
  * long_diff_count 0, long_diff_r 0.1, beta 0, precision QF_C128,
- * switch_tol 1e-6, max_c64_sweeps 1000.
+ * switch_tol 1e-6, max_c64_sweeps 1000, cost_history NULL.
  *   dist_tol      stop once a start's cost is <= dist_tol.
  *   max_sweeps    upper bound on two-sided sweeps (all phases together).
  *   min_sweeps    no stopping test before this many sweeps.
@@ -112,6 +112,16 @@ typedef struct { int32_t a, b; } qf_loc;     /* gate location: qubits a != b  */
  *                 stays in c64), or after max_c64_sweeps.  The plateau rules
  *                 apply in both phases.  Reported costs are always FP64
  *                 traces.
+ *   cost_history  optional (NULL = off), host-or-device: the cost of every
+ *                 start after every sweep (Alg. 1: the cost the stopping
+ *                 rules of Sec. III-A2 test), row-major [start][sweep],
+ *                 max_sweeps + 1 doubles per start (qf_instantiate_batched:
+ *                 [instance][start][sweep]).  Entry 0 is the initial
+ *                 circuit's cost, entry i the cost after sweep i: an FP64
+ *                 trace of the tensor in the precision of that sweep (of the
+ *                 rebuilt QF_C128/QF_DF64 tensor at the sweep that leaves the
+ *                 complex64 phase).  Entries after a start's last sweep are
+ *                 NaN.
  */
 typedef struct {
     double dist_tol;
@@ -126,6 +136,7 @@ typedef struct {
     int32_t precision;
     int32_t max_c64_sweeps;
     double switch_tol;
+    double* cost_history;
 } qf_options;
 
 /* Result summary of an instantiation. */

@@ -47,6 +47,7 @@ class qf_options(ct.Structure):
         ("precision", ct.c_int32),
         ("max_c64_sweeps", ct.c_int32),
         ("switch_tol", ct.c_double),
+        ("cost_history", ct.c_void_p),
     ]
 
 

@@ -198,10 +198,21 @@ def instantiate(target, locations, initial_gates, tol=1e-10, max_sweeps=500, str
     return out, cost.value, sweeps.value
 
 
-def instantiate_ex(target, locations, starts, options=None, stream=None, **kw):
+def _history_buffer(opts, rows):
+    """A host buffer for qf_options.cost_history (rows x (max_sweeps + 1)
+    doubles), set in a copy of the options; returns (options, buffer)."""
+    o = nat.qf_options.from_buffer_copy(opts.c)
+    h = np.empty((rows, int(o.max_sweeps) + 1), dtype=np.float64)
+    o.cost_history = h.ctypes.data
+    return o, h
+
+
+def instantiate_ex(target, locations, starts, options=None, stream=None, history=False, **kw):
     """Lock-step multistart Qfactor (qf_instantiate_ex).  ``starts`` has
     shape (S, p, 4, 4).  Returns a dict with gates, costs, best, sweeps,
-    c64_sweeps, reason and best_cost."""
+    c64_sweeps, reason and best_cost; with ``history=True`` also "history",
+    the cost of every start after every sweep (S, max_sweeps + 1), NaN after
+    the last sweep."""
     target = _c128(target, "target")
     starts = _c128(starts, "starts")
     locs = _locs(locations)
@@ -210,15 +221,19 @@ def instantiate_ex(target, locations, starts, options=None, stream=None, **kw):
     if p != locs.shape[0]:
         raise ValueError("starts and locations disagree on the gate count")
     opts = options if options is not None else Options(**kw)
+    oc, hist = _history_buffer(opts, S) if history else (opts.c, None)
     out = torch.empty_like(starts)
     costs = (ct.c_double * S)()
     res = nat.qf_result()
     check(_lib().qf_instantiate_ex(_ptr(target), n, p, _ptr(locs), S, _ptr(starts),
-                                   ct.byref(opts.c), _ptr(out), costs, ct.byref(res),
+                                   ct.byref(oc), _ptr(out), costs, ct.byref(res),
                                    _stream_handle(stream)))
-    return {"gates": out, "costs": np.array(costs[:]), "best": res.best_start,
-            "sweeps": res.sweeps, "c64_sweeps": res.c64_sweeps,
-            "reason": nat.REASONS.get(res.reason, str(res.reason)), "best_cost": res.best_cost}
+    r = {"gates": out, "costs": np.array(costs[:]), "best": res.best_start,
+         "sweeps": res.sweeps, "c64_sweeps": res.c64_sweeps,
+         "reason": nat.REASONS.get(res.reason, str(res.reason)), "best_cost": res.best_cost}
+    if history:
+        r["history"] = hist
+    return r
 
 
 def cost_and_env(target, locations, gates, stream=None):
@@ -244,12 +259,14 @@ def cost_and_env(target, locations, gates, stream=None):
     return c, envs, trs
 
 
-def instantiate_batched(instances, options=None, stream=None, **kw):
+def instantiate_batched(instances, options=None, stream=None, history=False, **kw):
     """Many small instantiations in one persistent launch
     (qf_instantiate_batched).  ``instances`` is a sequence of
     (target (N,N), locations (p,2), starts (S,p,4,4)) with the same S; arrays
     may be numpy or CPU tensors.  Returns a dict with per-(instance, start)
-    costs and sweeps, per-instance best start, the gates and launch stats."""
+    costs and sweeps, per-instance best start, the gates and launch stats;
+    with ``history=True`` also "history" (I, S, max_sweeps + 1), the cost
+    after every sweep, NaN after a start's last sweep."""
     targets, locs, starts, nq, ng = [], [], [], [], []
     S = None
     for V, L, G in instances:
@@ -277,9 +294,10 @@ def instantiate_batched(instances, options=None, stream=None, **kw):
     best = np.empty(I, dtype=np.int32)
     stats = nat.qf_batch_stats()
     opts = options if options is not None else Options(**kw)
+    oc, hist = _history_buffer(opts, I * S) if history else (opts.c, None)
     check(_lib().qf_instantiate_batched(
         I, ct.c_void_p(nq.ctypes.data), ct.c_void_p(ng.ctypes.data), ct.c_void_p(lc.ctypes.data),
-        ct.c_void_p(tg.ctypes.data), S, ct.c_void_p(st.ctypes.data), ct.byref(opts.c),
+        ct.c_void_p(tg.ctypes.data), S, ct.c_void_p(st.ctypes.data), ct.byref(oc),
         ct.c_void_p(out.ctypes.data), costs.ctypes.data_as(ct.POINTER(ct.c_double)),
         ct.c_void_p(sweeps.ctypes.data), ct.c_void_p(best.ctypes.data), ct.byref(stats),
         _stream_handle(stream)))
@@ -288,10 +306,13 @@ def instantiate_batched(instances, options=None, stream=None, **kw):
         k = S * ng[i] * 16
         gates.append(out[off:off + k].reshape(S, ng[i], 4, 4))
         off += k
-    return {"costs": costs.reshape(I, S), "sweeps": sweeps.reshape(I, S), "best": best,
-            "gates": gates, "warps_per_cta": stats.warps_per_cta, "ctas": stats.ctas,
-            "kernel_ms": stats.kernel_ms, "total_sweeps": stats.total_sweeps,
-            "total_c64_sweeps": stats.total_c64_sweeps}
+    r = {"costs": costs.reshape(I, S), "sweeps": sweeps.reshape(I, S), "best": best,
+         "gates": gates, "warps_per_cta": stats.warps_per_cta, "ctas": stats.ctas,
+         "kernel_ms": stats.kernel_ms, "total_sweeps": stats.total_sweeps,
+         "total_c64_sweeps": stats.total_c64_sweeps}
+    if history:
+        r["history"] = hist.reshape(I, S, -1)
+    return r
 
 
 def cost_grad(target, locations, gates, stream=None):

@@ -24,6 +24,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "qf_device.cuh"
 #include "qf_internal.h"
 #include "qf_polar.cuh"
@@ -61,6 +63,8 @@ struct BatchParams {
   unsigned* work;
   double dist_tol, diff_a, diff_r, long_r, beta, switch_tol;
   int max_sweeps, min_sweeps, reset_iter, long_L, precision, max_c64;
+  double* hist;    // optional cost history [instance][start][sweep], row hist_row
+  int hist_row;
   int tmax_bytes;  // tensor capacity of a warp slice (complex128, largest n)
   int warp_bytes;  // whole warp slice
 };
@@ -323,8 +327,10 @@ __global__ void batched_kernel(BatchParams bp) {
     else
       W<double>::build((double2*)Tbuf, LRd, V, g, locs, n, p, L);
     double c = c64 ? W<float>::cost((float2*)Tbuf, n) : W<double>::cost((double2*)Tbuf, n);
+    double* hist = bp.hist ? bp.hist + ((long long)i * bp.S + s) * bp.hist_row : nullptr;
     int len = 0;
     if (L.l == 0) ring[0] = c;
+    if (hist && L.l == 0) hist[0] = c;
     len = 1;
     __syncwarp();
     int it = 0, c64_sw = 0, reason = QF_STOP_MAX_SWEEPS;
@@ -363,6 +369,7 @@ __global__ void batched_kernel(BatchParams bp) {
           c64 = false;
         } else {
           if (L.l == 0) ring[len % kRing] = c;
+          if (hist && L.l == 0) hist[it] = c;
           ++len;
           __syncwarp();
           if (it >= bp.min_sweeps && !plateaued && plateau_test(ring, len, it, bp)) {
@@ -378,6 +385,7 @@ __global__ void batched_kernel(BatchParams bp) {
         }
       }
       if (L.l == 0) ring[len % kRing] = c;
+      if (hist && L.l == 0) hist[it] = c;
       ++len;
       __syncwarp();
       if (it >= bp.min_sweeps) {
@@ -528,7 +536,22 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     return ((long long)inst[x].p << (2 * inst[x].n)) > ((long long)inst[y].p << (2 * inst[y].n));
   });
-  DevMem d_inst, d_order, d_locs, d_tgt, d_gates, d_yprev, d_cost, d_sw, d_c64, d_reason, d_flags;
+  DevMem d_inst, d_order, d_locs, d_tgt, d_gates, d_yprev, d_cost, d_sw, d_c64, d_reason, d_flags,
+      d_hist;
+  const size_t hist_row = (size_t)o.max_sweeps + 1;
+  const size_t hist_bytes = sizeof(double) * (size_t)problems * hist_row;
+  double* hist_dev = nullptr;  // where the kernel writes the cost history
+  if (o.cost_history) {
+    if (is_dev(o.cost_history)) {
+      hist_dev = o.cost_history;
+    } else {
+      if (d_hist.alloc(hist_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return qf_internal_set_error(QF_ENOMEM, "device allocation for the cost history failed", "");
+      }
+      hist_dev = (double*)d_hist.p;
+    }
+  }
   if (d_inst.alloc(sizeof(BatchInst) * n_instances) != cudaSuccess ||
       d_order.alloc(sizeof(int) * n_instances) != cudaSuccess ||
       d_locs.alloc(sizeof(qf_loc) * loc_total) != cudaSuccess ||
@@ -584,6 +607,8 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
   bp.long_L = o.long_diff_count;
   bp.precision = o.precision;
   bp.max_c64 = o.max_c64_sweeps;
+  bp.hist = hist_dev;
+  bp.hist_row = (int)hist_row;
   bp.tmax_bytes = (1 << (2 * nmax)) * 16;
   bp.warp_bytes = ((bp.tmax_bytes + 768 + kRing * 8) + 255) & ~255;
   const size_t flag_bytes = sizeof(int) * (2 * (size_t)n_instances + 2);
@@ -607,6 +632,7 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
     float best_ms = 1e30f;
     BatchParams tp = bp;
     tp.max_sweeps = 2;
+    tp.hist = nullptr;
     tp.n_inst = (int)std::min<long long>(n_instances, std::max<long long>(1, 4096 / n_starts));
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -636,6 +662,10 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
   }
 
   // the run: reset, then one persistent launch, captured as a CUDA graph
+  nvtxRangePushA("qf batched run");
+  struct PopAtExit {
+    ~PopAtExit() { nvtxRangePop(); }
+  } pop_at_exit;
   e = cudaMemcpyAsync(d_gates.p, initial_gates, sizeof(double2) * gate_total, cudaMemcpyDefault, st);
   if (e != cudaSuccess)
     return qf_internal_set_error(QF_ECUDA, "copying the initial gates failed", cudaGetErrorString(e));
@@ -648,6 +678,8 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
   e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaError_t e1 = cudaMemsetAsync(d_flags.p, 0, flag_bytes, cap);
+    // all-ones bytes are a NaN: entries after a start's last sweep
+    if (e1 == cudaSuccess && hist_dev) e1 = cudaMemsetAsync(hist_dev, 0xff, hist_bytes, cap);
     cudaError_t e2 = e1 == cudaSuccess ? launch_batch(bp, wpc, smem_optin, cap, &ctas) : e1;
     e = cudaStreamEndCapture(cap, &graph);
     if (e == cudaSuccess) e = e2;
@@ -682,6 +714,8 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
     e = cudaMemcpy(hc64.data(), d_c64.p, sizeof(int) * problems, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess)
     e = cudaMemcpy(out_gates, d_gates.p, sizeof(double2) * gate_total, cudaMemcpyDefault);
+  if (e == cudaSuccess && hist_dev && hist_dev != o.cost_history)
+    e = cudaMemcpy(o.cost_history, hist_dev, hist_bytes, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess)
     return qf_internal_set_error(QF_ECUDA, "copying the batch results failed", cudaGetErrorString(e));
   if (out_sweeps)

@@ -19,12 +19,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "qf_internal.h"
 #include "qfactor.h"
 
 namespace {
 
 thread_local std::string g_last_error;
+
+// NVTX range for profilers (nsys, ncu --nvtx): one per sweep and per phase
+// of an instantiation; free when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 int set_error(int code, const char* fmt, ...) {
   char buf[512];
@@ -859,9 +870,13 @@ int plan_reset(qf_plan* P) {
 
 int plan_sweep_impl(qf_plan* P, int n_sweeps, int reset_iter, double beta) {
   for (int i = 0; i < n_sweeps; ++i) {
+    NvtxRange r("qf sweep");
     QF_TRY(plan_sweep_once(P, beta));
     P->sweeps_since_load++;
-    if (reset_iter > 0 && P->sweeps_since_load % reset_iter == 0) QF_TRY(plan_reset(P));
+    if (reset_iter > 0 && P->sweeps_since_load % reset_iter == 0) {
+      NvtxRange rr("qf reset");
+      QF_TRY(plan_reset(P));
+    }
   }
   return QF_OK;
 }
@@ -903,7 +918,7 @@ extern "C" {
 
 const char* qf_last_error(void) { return g_last_error.c_str(); }
 
-int qf_version(void) { return 100; }
+int qf_version(void) { return 200; }
 
 int qf_options_default(qf_options* o) {
   if (!o) return set_error(QF_EINVAL, "opts is NULL");
@@ -919,6 +934,7 @@ int qf_options_default(qf_options* o) {
   o->precision = QF_C128;
   o->max_c64_sweeps = 1000;
   o->switch_tol = 1e-6;
+  o->cost_history = nullptr;
   return QF_OK;
 }
 
@@ -1080,7 +1096,9 @@ int instantiate_core(const qf_c128* target, int n_qubits, const std::vector<Gate
   std::vector<char> plateaued(S, 0);
   bool c64_phase = refine;
   int reason = QF_STOP_MAX_SWEEPS, it = 0, c64_sweeps = 0;
+  nvtxRangePushA(c64_phase ? "qf bulk complex64 phase" : "qf sweeps");
   for (it = 1; it <= o.max_sweeps; ++it) {
+    NvtxRange sweep_range("qf sweep");
     QF_TRY(plan_sweep_once(P, o.beta));
     P->sweeps_since_load++;
     if (o.reset_iter > 0 && P->sweeps_since_load % o.reset_iter == 0) QF_TRY(plan_reset(P));
@@ -1103,6 +1121,9 @@ int instantiate_core(const qf_c128* target, int n_qubits, const std::vector<Gate
       if (best <= o.switch_tol || (stalled && best <= kStallSwitchCost) ||
           c64_sweeps >= o.max_c64_sweeps) {
         // rebuild every tensor in the fine precision from V and the FP64 gates
+        nvtxRangePop();
+        NvtxRange sw("qf switch to the fine precision");
+        nvtxRangePushA("qf refinement phase");
         P->prec = fine_prec;
         QF_TRY(plan_build(P));
         QF_TRY(plan_costs_impl(P, c.data(), nullptr));
@@ -1144,11 +1165,20 @@ int instantiate_core(const qf_c128* target, int n_qubits, const std::vector<Gate
       }
     }
   }
+  nvtxRangePop();
   if (it > o.max_sweeps) it = o.max_sweeps;
   if (c64_phase) {  // report FP64 traces of fine tensors: rebuild once
     P->prec = fine_prec;
     QF_TRY(plan_build(P));
     QF_TRY(plan_costs_impl(P, c.data(), nullptr));
+  }
+  if (o.cost_history) {  // [start][sweep], NaN after a start's last sweep
+    const size_t row = (size_t)o.max_sweeps + 1;
+    std::vector<double> h((size_t)S * row, std::nan(""));
+    for (int s = 0; s < S; ++s)
+      for (size_t i = 0; i < hist[s].size() && i < row; ++i) h[s * row + i] = hist[s][i];
+    QF_CUDA(cudaMemcpyAsync(o.cost_history, h.data(), h.size() * sizeof(double), cudaMemcpyDefault, st));
+    QF_CUDA(cudaStreamSynchronize(st));  // h is released at the end of this block
   }
   int best = 0;
   for (int s = 1; s < S; ++s)

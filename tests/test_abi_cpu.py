@@ -61,16 +61,42 @@ def test_options_defaults(lib):
     assert lib.qf_options_default(ct.byref(o)) == 0
     assert o.dist_tol == 1e-10 and o.max_sweeps == 500 and o.reset_iter == 40
     assert o.beta == 0.0 and o.precision == nat.QF_C128
+    assert o.cost_history is None
     assert lib.qf_options_default(None) == nat.QF_EINVAL
     assert b"NULL" in lib.qf_last_error()
     assert lib.qf_version() >= 100
 
 
-def test_struct_layouts_match_header(lib):
+def test_struct_layouts_match_header(lib, tmp_path):
+    """The ctypes structures have the header's sizes and field offsets (a C
+    program built from include/qfactor.h prints them)."""
+    import shutil
+    import subprocess
+
     from paper_2306_08152_gb300 import _native as nat
 
-    assert ct.sizeof(nat.qf_options) == 72
-    assert ct.sizeof(nat.qf_result) == 24
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = {"qf_options": nat.qf_options, "qf_result": nat.qf_result,
+               "qf_batch_stats": nat.qf_batch_stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "qfactor.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ct.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
+    assert ct.sizeof(nat.qf_options) == 80 and ct.sizeof(nat.qf_result) == 24
 
 
 def _call_instantiate(lib, n, p, locs):
