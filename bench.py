@@ -652,6 +652,74 @@ def run_kqubit(args, qf, torch, dev):
             "final_costs": [float(c) for c in costs]}
 
 
+# FP32 FMA operations per tensor entry of a complex64 16x16 pass (both
+# operators): 2 x 16 complex multiply-adds of 4 FMAs.
+K4_FMA_PER_ENTRY = 2 * 16 * 4
+
+
+def run_k4(args, qf, torch, dev):
+    """Four-qubit gates: 12 qubits, layers of gates on consecutive quadruples
+    (offsets 0 and 2 in turn, 15 gates), 8 starts, complex64 tensors, one
+    sweep per step; the 16x16 pass reads and writes the tensor once per
+    update but does 128 FP32 FMAs per entry, so the FP32 pipe bounds it."""
+    n, S = 12, 8
+    locs = []
+    for layer in range(6):
+        o = 0 if layer % 2 == 0 else 2
+        locs += [(q, q + 1, q + 2, q + 3) for q in range(o, n - 3, 4)]
+    gen = qi.rng(SEED + 44)
+    tgt = [qi.haar_unitary(16, gen) for _ in locs]
+    V = qf.circuit_unitary_k(n, locs, tgt, device=dev)
+    starts = qf.flatten_gates([[qi.haar_unitary(16, qi.rng(SEED + 45 + s)) for _ in locs]
+                               for s in range(S)]).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = qf.Plan(n, locs, S, qf.QF_C64)
+    plan.load(V, starts, stream=stream)
+    plan.sweep(2, reset_iter=0)  # the second sweep captures the graph
+    plan.costs()
+    steps = 3
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.sweep(steps, reset_iter=0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = e0.elapsed_time(e1)
+    plan.pass_stats()
+    plan.enable_pass_timing(True)
+    e0.record(stream)
+    plan.sweep(steps, reset_iter=0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pass_ms, launches, _, pbytes = plan.pass_stats()
+    costs = plan.costs()
+    if plan.status() != 0:
+        raise RuntimeError("device status reports a non-finite update")
+    plan.close()
+    peak, peak_kind = measured_peaks()
+    peaks = measured_alu_peaks(torch, dev)
+    avg_s = (pass_ms / 1e3) / max(launches, 1)
+    alg = pbytes / max(launches, 1)
+    entries = alg / 16  # 8-byte entries, read + write
+    fma_ops = entries * K4_FMA_PER_ENTRY / avg_s / 1e9
+    fma_peak = peaks["fp32_gflops"] / 2  # measured SGEMM flops, an FMA counted twice
+    updates = S * 2 * len(locs) * steps
+    return {"metric": "gate-updates/s at 12 qubits, four-qubit gates, complex64",
+            "unit": "gate-updates/s", "value": updates / (ms_graph / 1e3),
+            "ms_per_sweep": ms_graph / steps, "ms_per_sweep_live": ms / steps,
+            "workload": f"12 qubits, {len(locs)} four-qubit gates on consecutive quadruples (6 layers, "
+                        "offsets 0/2), 8 starts, reachable Haar target, complex64 tensor, FP64 16x16 update",
+            "roofline": {"bound": "alu", "achieved": fma_ops, "peak": fma_peak, "unit": "G FMA/s",
+                         "frac": fma_ops / fma_peak,
+                         "kernel": "pass16_kernel (B <- L B R on 16x16 blocks, 128 FP32 FMAs per entry)",
+                         "peak_source": "measured FP32: " + peaks["how"] + "; FMAs = flops / 2",
+                         "hbm_gbs": alg / avg_s / 1e9, "hbm_frac": alg / avg_s / 1e9 / peak,
+                         "alg_bytes_per_launch": alg, "avg_launch_ms": avg_s * 1e3,
+                         "pass_share_of_step": pass_ms / ms if ms > 0 else None},
+            "final_costs": [float(c) for c in costs]}
+
+
 def run_spec(args, qf, torch, dev):
     """Specialised gate set (a trapped-ion native set: GPI and Rz on every
     qubit, Moelmer-Soerensen on brickwork pairs): 12 qubits, 8 starts,
@@ -964,9 +1032,10 @@ def run_ours(args):
                        "allocation, H2D, InitCircuitTensor, one sweep, D2H"}
         del r
 
-    kqubit = None
+    kqubit = k4 = None
     if not args.no_kqubit and world == 1:
         kqubit = run_kqubit(args, qf, torch, dev)
+        k4 = run_k4(args, qf, torch, dev)
     spec = None
     if not args.no_spec and world == 1:
         spec = run_spec(args, qf, torch, dev)
@@ -1014,7 +1083,7 @@ def run_ours(args):
             "ms_per_step_live": ms_live,
             "timing": "value: CUDA-graph replay of each sweep (qf_plan_sweep); roofline: the same "
                       "sweeps as live launches with CUDA events around every pass",
-            "lookahead": lookahead, "kqubit": kqubit, "spec": spec, "c128": extra_c128, "df64": extra_df64, "batched": batched, "configs": configs,
+            "lookahead": lookahead, "kqubit": kqubit, "k4": k4, "spec": spec, "c128": extra_c128, "df64": extra_df64, "batched": batched, "configs": configs,
             "final_costs": [float(c) for c in costs],
         }
         print(json.dumps(line))

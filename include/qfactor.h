@@ -263,9 +263,9 @@ int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
                            qf_batch_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------
- * Gates on more than two qubits (the paper's method extends to k-qubit
- * unitaries with a 2^k x 2^k environment, Sec. III).  Supported: k = 2 and
- * k = 3, mixed freely in one circuit.
+ * Gates on more than two qubits (the paper treats a multi-qubit unitary as
+ * one variable with a 2^k x 2^k environment, Sec. III and Sec. VI).
+ * Supported: k = 2, 3 and 4, mixed freely in one circuit.
  *
  * A gate on k qubits (q[0], ..., q[k-1]) acts on the local index
  * sum_i bit(q[i]) 2^(k-1-i) (k = 2: 2*bit(q[0]) + bit(q[1]), as qf_loc).
@@ -274,17 +274,18 @@ int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
  * entries and start s's begin at s*E.
  * ---------------------------------------------------------------------- */
 typedef struct {
-    int32_t k;     /* 2 or 3 */
-    int32_t q[3];  /* qubits in local-index order; q[2] unused for k = 2 */
+    int32_t k;     /* 2, 3 or 4 */
+    int32_t q[4];  /* qubits in local-index order; q[k..3] unused */
 } qf_gate_loc;
 
-/* qf_instantiate_ex for a circuit of 2- and 3-qubit gates.  locations:
+/* qf_instantiate_ex for a circuit of 2-, 3- and 4-qubit gates.  locations:
  * host-or-device, n_gates entries; initial_gates and out_gates:
  * host-or-device, n_starts x E entries (see above).  The three-qubit
- * updates use the 8x8 FP64 polar (one-sided Jacobi on one warp); the
- * look-ahead and the one-pass InitCircuitTensor apply to two-qubit-only
- * circuits.  Errors as qf_instantiate_ex, QF_EINVAL for k outside {2, 3},
- * repeated or out-of-range qubits. */
+ * updates use the 8x8 FP64 polar (one-sided Jacobi on one warp), the
+ * four-qubit updates the 16x16 FP64 polar (one-sided Jacobi on one CTA of
+ * 256 threads); the look-ahead and the one-pass InitCircuitTensor apply to
+ * two-qubit-only circuits.  Errors as qf_instantiate_ex, QF_EINVAL for k
+ * outside {2, 3, 4}, k > n_qubits, repeated or out-of-range qubits. */
 int qf_instantiate_k(const qf_c128* target, int n_qubits, int n_gates,
                      const qf_gate_loc* locations, int n_starts,
                      const qf_c128* initial_gates, const qf_options* opts,
@@ -296,9 +297,9 @@ int qf_instantiate_k(const qf_c128* target, int n_qubits, int n_gates,
  *                       n_starts x 4^k (either may be NULL for identity).
  *   qf_partial_trace_k  P_s = partial trace of T_s over every qubit not in
  *                       q (CalcEnvMat, Alg. 1); P device n_starts x 4^k.
- *                       k = 3 allocates its scratch stream-ordered.
+ *                       k = 3 and 4 allocate their scratch stream-ordered.
  *   qf_optimize_gates_k OptimizeGate (Eq. opt_u) on `count` dim x dim
- *                       matrices, dim 4 or 8 (see qf_optimize_gates).
+ *                       matrices, dim 4, 8 or 16 (see qf_optimize_gates).
  *   qf_init_tensor_k    InitCircuitTensor with k-qubit gates (gates device,
  *                       n_starts x E).
  *   qf_circuit_unitary_k C = G_0 ... G_{p-1} (complex128, device N x N;

@@ -20,7 +20,7 @@ Conventions (identical to the two-qubit oracle for k = 2):
     Tr(E_k u_k); the update is u' = Y X^dagger from E = X D Y^dagger (Eq. opt_u).
 
 Parity pins (tests/test_oracle_pins_k.py): dense basis-loop operators for
-n <= 5 with 1-, 2- and 3-qubit gates, agreement with the two-qubit oracle at
+n <= 5 with 1-, 2-, 3- and 4-qubit gates, agreement with the two-qubit oracle at
 k = 2, finite differences of Tr(V^dagger C), the identity Tr(E_k u_k) =
 Tr(V^dagger C), the closed-form single-gate fits (n = k: one update reaches
 cost 0; n = k + 1 with a product target: cost 1 - |Tr g|/2), local

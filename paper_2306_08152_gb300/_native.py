@@ -62,7 +62,7 @@ class qf_result(ct.Structure):
 
 
 class qf_gate_loc(ct.Structure):
-    _fields_ = [("k", ct.c_int32), ("q", ct.c_int32 * 3)]
+    _fields_ = [("k", ct.c_int32), ("q", ct.c_int32 * 4)]
 
 
 class qf_gate_spec(ct.Structure):

@@ -76,13 +76,13 @@ def _is_pairs(locations):
 
 
 def _gate_locs(locations):
-    """ctypes array of qf_gate_loc from a sequence of qubit tuples (2 or 3)."""
+    """ctypes array of qf_gate_loc from a sequence of qubit tuples (2, 3 or 4)."""
     locs = [tuple(int(x) for x in q) for q in (locations.tolist() if hasattr(locations, "tolist")
                                                 else locations)]
     arr = (nat.qf_gate_loc * len(locs))()
     for i, q in enumerate(locs):
-        if len(q) not in (2, 3):
-            raise ValueError("a location has 2 or 3 qubits")
+        if len(q) not in (2, 3, 4):
+            raise ValueError("a location has 2, 3 or 4 qubits")
         arr[i].k = len(q)
         for j, x in enumerate(q):
             arr[i].q[j] = x
@@ -588,7 +588,7 @@ def partial_trace_after(T, a1, b1, L1, R1, a, b, stream=None):
 
 
 def instantiate_k(target, locations, starts, options=None, stream=None, **kw):
-    """Lock-step multistart Qfactor with 2- and 3-qubit gates
+    """Lock-step multistart Qfactor with 2-, 3- and 4-qubit gates
     (qf_instantiate_k).  ``locations``: sequence of qubit tuples; ``starts``:
     (S, E) complex128 in the concatenated layout or S lists of gate arrays.
     Returns the dict of instantiate_ex with ``gates`` as S lists of arrays
@@ -674,7 +674,7 @@ def partial_trace_k(T, qubits, stream=None):
 
 
 def optimize_gates_k(E, u_old=None, beta=0.0, stream=None):
-    """OptimizeGate on (..., d, d) matrices, d = 4 or 8."""
+    """OptimizeGate on (..., d, d) matrices, d = 4, 8 or 16."""
     E = _dev(_c128(E, "E"), "E")
     d = E.shape[-1]
     count = E.numel() // (d * d)

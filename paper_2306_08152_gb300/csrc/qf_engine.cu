@@ -112,7 +112,7 @@ int fetch_locations(const qf_loc* locs, int n, int p, std::vector<qf_loc>* out) 
 // and the offset of its 4^k entries within one start's gate array.
 struct GateDesc {
   int k;
-  int q[3];
+  int q[4];
   long long off;
   int kind = qf::kGateGeneral;  // parameterised kinds occupy a 4x4 slot (k = 2)
 };
@@ -120,7 +120,7 @@ struct GateDesc {
 int descs_from_pairs(const std::vector<qf_loc>& locs, std::vector<GateDesc>* out, long long* gsz) {
   out->resize(locs.size());
   for (size_t i = 0; i < locs.size(); ++i) {
-    (*out)[i] = GateDesc{2, {locs[i].a, locs[i].b, -1}, (long long)i * 16};
+    (*out)[i] = GateDesc{2, {locs[i].a, locs[i].b, -1, -1}, (long long)i * 16};
   }
   *gsz = (long long)locs.size() * 16;
   return QF_OK;
@@ -161,7 +161,7 @@ int fetch_gate_specs(const qf_gate_spec* specs, int n, int p, std::vector<GateDe
       for (int b = 0; b < a; ++b)
         if (q[a] == q[b]) return set_error(QF_EINVAL, "gate %d: repeated qubit %d", i, q[a]);
     }
-    (*out)[i] = GateDesc{k, {q[0], q[1], q[2]}, off, kind};
+    (*out)[i] = GateDesc{k, {q[0], q[1], q[2], -1}, off, kind};
     off += k == 3 ? 64 : 16;
   }
   *gsz = off;
@@ -181,7 +181,7 @@ int fetch_gate_locs(const qf_gate_loc* locs, int n, int p, std::vector<GateDesc>
   long long off = 0;
   for (int i = 0; i < p; ++i) {
     const qf_gate_loc& l = h[i];
-    if (l.k != 2 && l.k != 3) return set_error(QF_EINVAL, "gate %d: k=%d must be 2 or 3", i, l.k);
+    if (l.k < 2 || l.k > 4) return set_error(QF_EINVAL, "gate %d: k=%d must be 2, 3 or 4", i, l.k);
     for (int a = 0; a < l.k; ++a) {
       if (l.q[a] < 0 || l.q[a] >= n)
         return set_error(QF_EINVAL, "gate %d: qubit %d invalid for %d qubits", i, l.q[a], n);
@@ -189,8 +189,8 @@ int fetch_gate_locs(const qf_gate_loc* locs, int n, int p, std::vector<GateDesc>
         if (l.q[a] == l.q[b]) return set_error(QF_EINVAL, "gate %d: repeated qubit %d", i, l.q[a]);
     }
     if (l.k > n) return set_error(QF_EINVAL, "gate %d: k=%d > n_qubits=%d", i, l.k, n);
-    (*out)[i] = GateDesc{l.k, {l.q[0], l.q[1], l.k == 3 ? l.q[2] : -1}, off};
-    off += l.k == 3 ? 64 : 16;
+    (*out)[i] = GateDesc{l.k, {l.q[0], l.q[1], l.k >= 3 ? l.q[2] : -1, l.k == 4 ? l.q[3] : -1}, off};
+    off += 1ll << (2 * l.k);
   }
   *gsz = off;
   return QF_OK;
@@ -273,6 +273,8 @@ struct qf_plan {
   bool mixed = false;        // some gate acts on three qubits
   DevBuf T, V, gates, LR, sigma, tr, status, part, counters;
   DevBuf LR8, gdesc;         // three-qubit pass operators (start stride 128); gate table
+  bool has16 = false;        // some gate acts on four qubits
+  DevBuf LR16;               // four-qubit pass operators (start stride 512)
   // parameterised gates: (kind, entry offset) per gate and 2 parameters per
   // (start, gate), start stride 2p
   bool spec = false;
@@ -376,8 +378,21 @@ int plan_pass8(qf_plan* P, const Slice& sl, const int* q, const double2* L, long
   });
 }
 
-// The fused pass of gate k with the operators its update left in LR / LR8.
+// The pass of a four-qubit gate: T <- (L on q) T (R on q), 16x16 operators.
+int plan_pass16(qf_plan* P, const Slice& sl, const int* q, const double2* L, long long Ls,
+                const double2* R, long long Rs) {
+  return timed_pass(P, sl, [&](void* T) {
+    return qf::launch_pass16(T, P->n, sl.Sg, q, L ? L + sl.s0 * Ls : nullptr, Ls,
+                             R ? R + sl.s0 * Rs : nullptr, Rs, kprec(P->prec), sl.st);
+  });
+}
+
+// The fused pass of gate k with the operators its update left in LR / LR8 / LR16.
 int plan_gate_pass(qf_plan* P, const Slice& sl, int k) {
+  if (P->gd[k].k == 4) {
+    const double2* L16 = P->LR16.as<double2>();
+    return plan_pass16(P, sl, P->gd[k].q, L16, 512, L16 + 256, 512);
+  }
   if (P->gd[k].k == 3) {
     const double2* L8 = P->LR8.as<double2>();
     return plan_pass8(P, sl, P->gd[k].q, L8, 128, L8 + 64, 128);
@@ -407,7 +422,9 @@ int plan_build(qf_plan* P) {
     return QF_OK;
   }
   for (int k = 0; k < P->p; ++k) {
-    if (P->gd[k].k == 3)
+    if (P->gd[k].k == 4)
+      QF_TRY(plan_pass16(P, all_starts(P), P->gd[k].q, nullptr, 0, gate_ptr(P, 0, k), P->gsz));
+    else if (P->gd[k].k == 3)
       QF_TRY(plan_pass8(P, all_starts(P), P->gd[k].q, nullptr, 0, gate_ptr(P, 0, k), P->gsz));
     else
       QF_TRY(plan_pass(P, all_starts(P), P->locs[k].a, P->locs[k].b, nullptr, 0, gate_ptr(P, 0, k),
@@ -445,6 +462,16 @@ int plan_update(qf_plan* P, const Slice& sl, int k, int mode, double beta, doubl
   const int pr = kprec(P->prec);
   const int B = qf::env_ctas(P->n);
   const void* T = static_cast<const char*>(P->T.p) + (size_t)sl.s0 * P->NN * elem_bytes(P->prec);
+  if (P->gd[k].k == 4) {
+    QF_CUDA(qf::launch_update16(
+        T, P->n, sl.Sg, P->gd[k].q, gate_ptr(P, sl.s0, k), P->gsz, mode, beta,
+        P->LR16.as<double2>() + (size_t)sl.s0 * 512, env_out ? env_out + sl.s0 * env_stride : nullptr,
+        env_stride, P->sigma.as<double>() + sl.s0, P->status.as<int>(),
+        P->part.as<double>() + (size_t)sl.s0 * B * 512, P->counters.as<unsigned>() + sl.s0, pr,
+        sl.st));
+    P->all_launches++;
+    return mark_stream_priority(sl.st);
+  }
   if (P->gd[k].k == 3) {
     QF_CUDA(qf::launch_update8(
         T, P->n, sl.Sg, P->gd[k].q, gate_ptr(P, sl.s0, k), P->gsz, mode, beta,
@@ -750,8 +777,11 @@ int plan_create_desc(int n, const std::vector<GateDesc>& gd, long long gsz, int 
   P->locs.resize(p);
   for (int k = 0; k < p; ++k) {
     P->locs[k] = qf_loc{gd[k].q[0], gd[k].q[1]};
-    if (gd[k].k == 3) P->mixed = true;
+    if (gd[k].k >= 3) P->mixed = true;
+    if (gd[k].k == 4) P->has16 = true;
   }
+  // partial sums per environment CTA: 16, 64 or 256 complex values
+  const int part_per_cta = P->has16 ? 512 : P->mixed ? 128 : 32;
   const int B = qf::env_ctas(n);
   int rc = plan_ensure_T(P, prec);
   if (rc == QF_OK) rc = P->V.alloc(P->NN * sizeof(double2));
@@ -760,8 +790,9 @@ int plan_create_desc(int n, const std::vector<GateDesc>& gd, long long gsz, int 
   if (rc == QF_OK) rc = P->sigma.alloc((size_t)S * sizeof(double));
   if (rc == QF_OK) rc = P->tr.alloc((size_t)S * sizeof(double2));
   if (rc == QF_OK) rc = P->status.alloc(sizeof(int));
-  if (rc == QF_OK) rc = P->part.alloc((size_t)S * B * (P->mixed ? 128 : 32) * sizeof(double));
+  if (rc == QF_OK) rc = P->part.alloc((size_t)S * B * part_per_cta * sizeof(double));
   if (rc == QF_OK) rc = P->counters.alloc((size_t)S * sizeof(unsigned));
+  if (rc == QF_OK && P->has16) rc = P->LR16.alloc((size_t)S * 512 * sizeof(double2));
   if (rc == QF_OK && P->mixed) {
     rc = P->LR8.alloc((size_t)S * 128 * sizeof(double2));
     // (k, entry offset) per gate, for the re-unitarisation kernel
@@ -860,6 +891,11 @@ int plan_reset(qf_plan* P) {
   else
     QF_CUDA(qf::launch_reunitarize(P->gates.as<double2>(), P->S * P->p, P->stream));
   P->all_launches++;
+  if (P->has16) {  // the mixed kernel leaves 16x16 gates to this one
+    QF_CUDA(qf::launch_reunitarize16(P->gates.as<double2>(), P->gsz, P->gdesc.as<int2>(), P->p, P->S,
+                                     P->stream));
+    P->all_launches++;
+  }
   if (P->spec) {  // parameterised gates: exactly G(theta) again
     QF_CUDA(qf::launch_param_gates(P->gates.as<double2>(), P->gsz, P->ptab.as<int2>(),
                                    P->params.as<double>(), 2LL * P->p, P->p, P->S, P->stream));
@@ -1579,7 +1615,10 @@ int qf_apply_gate_k(void* T, int n_qubits, int n_starts, const qf_gate_loc* loca
   long long gsz = 0;
   QF_TRY(fetch_gate_locs(location, n_qubits, 1, &gd, &gsz));
   const auto d = [](const qf_c128* x) { return reinterpret_cast<const double2*>(x); };
-  if (gd[0].k == 3)
+  if (gd[0].k == 4)
+    QF_CUDA(qf::launch_pass16(T, n_qubits, n_starts, gd[0].q, d(L), 256, d(R), 256, kprec(precision),
+                              as_stream(stream)));
+  else if (gd[0].k == 3)
     QF_CUDA(qf::launch_pass8(T, n_qubits, n_starts, gd[0].q, d(L), 64, d(R), 64, kprec(precision),
                              as_stream(stream)));
   else
@@ -1600,13 +1639,18 @@ int qf_partial_trace_k(const void* T, int n_qubits, int n_starts, const qf_gate_
   if (gd[0].k == 2)
     return qf_partial_trace(T, n_qubits, n_starts, gd[0].q[0], gd[0].q[1], P, precision, stream);
   cudaStream_t st = as_stream(stream);
-  const size_t part_bytes = (size_t)n_starts * qf::env_ctas(n_qubits) * 128 * sizeof(double);
+  const int per_cta = gd[0].k == 4 ? 512 : 128;
+  const size_t part_bytes = (size_t)n_starts * qf::env_ctas(n_qubits) * per_cta * sizeof(double);
   const size_t cnt_bytes = (size_t)n_starts * sizeof(unsigned);
   void* scratch = nullptr;
   QF_CUDA(cudaMallocAsync(&scratch, part_bytes + cnt_bytes, st));
   unsigned* counters = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(scratch) + part_bytes);
   cudaError_t e = cudaMemsetAsync(counters, 0, cnt_bytes, st);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && gd[0].k == 4)
+    e = qf::launch_update16(T, n_qubits, n_starts, gd[0].q, nullptr, 0, qf::kTraceOnly, 0.0, nullptr,
+                            reinterpret_cast<double2*>(P), 256, nullptr, nullptr,
+                            reinterpret_cast<double*>(scratch), counters, kprec(precision), st);
+  else if (e == cudaSuccess)
     e = qf::launch_update8(T, n_qubits, n_starts, gd[0].q, nullptr, 0, qf::kTraceOnly, 0.0, nullptr,
                            reinterpret_cast<double2*>(P), 64, nullptr, nullptr,
                            reinterpret_cast<double*>(scratch), counters, kprec(precision), st);
@@ -1618,13 +1662,19 @@ int qf_partial_trace_k(const void* T, int n_qubits, int n_starts, const qf_gate_
 
 int qf_optimize_gates_k(const qf_c128* E, int dim, const qf_c128* u_old, double beta, int count,
                         qf_c128* u_out, double* sigma_out, void* stream) {
-  if (dim != 4 && dim != 8) return set_error(QF_EINVAL, "dim=%d must be 4 or 8", dim);
+  if (dim != 4 && dim != 8 && dim != 16) return set_error(QF_EINVAL, "dim=%d must be 4, 8 or 16", dim);
   if (dim == 4) return qf_optimize_gates(E, u_old, beta, count, u_out, sigma_out, stream);
   if (count < 0) return set_error(QF_EINVAL, "count=%d < 0", count);
   if (count == 0) return QF_OK;
   if (!E || !u_out) return set_error(QF_EINVAL, "NULL device pointer");
   if (beta != 0.0 && !u_old) return set_error(QF_EINVAL, "beta != 0 needs u_old");
   if (!(beta >= 0.0 && beta <= 1.0)) return set_error(QF_EINVAL, "beta=%g outside [0, 1]", beta);
+  if (dim == 16) {
+    QF_CUDA(qf::launch_optimize16(reinterpret_cast<const double2*>(E),
+                                  reinterpret_cast<const double2*>(u_old), beta, count,
+                                  reinterpret_cast<double2*>(u_out), sigma_out, as_stream(stream)));
+    return QF_OK;
+  }
   QF_CUDA(qf::launch_optimize8(reinterpret_cast<const double2*>(E),
                                reinterpret_cast<const double2*>(u_old), beta, count,
                                reinterpret_cast<double2*>(u_out), sigma_out, as_stream(stream)));
@@ -1647,7 +1697,9 @@ int qf_init_tensor_k(const qf_c128* target, int n_qubits, int n_gates,
   QF_CUDA(qf::launch_conj_transpose(reinterpret_cast<const double2*>(target), T, n_qubits, n_starts,
                                     pr, st));
   for (int k = 0; k < n_gates; ++k) {
-    if (gd[k].k == 3)
+    if (gd[k].k == 4)
+      QF_CUDA(qf::launch_pass16(T, n_qubits, n_starts, gd[k].q, nullptr, 0, g + gd[k].off, gsz, pr, st));
+    else if (gd[k].k == 3)
       QF_CUDA(qf::launch_pass8(T, n_qubits, n_starts, gd[k].q, nullptr, 0, g + gd[k].off, gsz, pr, st));
     else
       QF_CUDA(qf::launch_pass(T, n_qubits, n_starts, gd[k].q[0], gd[k].q[1], nullptr, 0, g + gd[k].off,

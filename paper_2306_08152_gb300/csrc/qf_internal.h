@@ -107,8 +107,26 @@ cudaError_t launch_update8(const void* T, int n, int S, const int* q, double2* g
 cudaError_t launch_optimize8(const double2* E, const double2* u_old, double beta, int count,
                              double2* u_out, double* sigma_out, cudaStream_t st);
 cudaError_t launch_reunitarize8(double2* gates, int count, cudaStream_t st);
-// Re-unitarise a mixed circuit: desc[k] = (size 2 or 3, entry offset) of
-// gate k; start s's gates begin at gates + s * gsz.
+// Four-qubit gates (qf_k4.cu): q holds the gate's four qubits in
+// local-index order.  Operators are 16x16 (256 FP64 complex values per
+// start); LR has start stride 512 (L, then R); part needs
+// S * env_ctas(n) * 512 doubles.  Modes as for launch_update; the update
+// runs on one CTA of 256 threads per start.
+cudaError_t launch_pass16(void* T, int n, int S, const int* q, const double2* L, long long Ls,
+                          const double2* R, long long Rs, int prec, cudaStream_t st);
+cudaError_t launch_update16(const void* T, int n, int S, const int* q, double2* gates_k,
+                            long long gstride, int mode, double beta, double2* LR, double2* out,
+                            long long out_stride, double* sigma_out, int* status, double* part,
+                            unsigned* counters, int prec, cudaStream_t st);
+cudaError_t launch_optimize16(const double2* E, const double2* u_old, double beta, int count,
+                              double2* u_out, double* sigma_out, cudaStream_t st);
+// Three FP64 Newton-Schulz steps on every gate of size 4 in desc (others
+// untouched).
+cudaError_t launch_reunitarize16(double2* gates, long long gsz, const int2* desc, int p, int S,
+                                 cudaStream_t st);
+// Re-unitarise a mixed circuit: desc[k] = (size 2, 3 or 4, entry offset) of
+// gate k; start s's gates begin at gates + s * gsz.  Gates of size 4 are left
+// to launch_reunitarize16.
 cudaError_t launch_reunitarize_mixed(double2* gates, long long gsz, const int2* desc, int p, int S,
                                      cudaStream_t st);
 

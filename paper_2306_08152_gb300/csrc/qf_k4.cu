@@ -1,0 +1,663 @@
+// Four-qubit gates (the paper's method with a 16 x 16 unitary as one
+// variable, Sec. III and Sec. VI): the fused 16x16 pass, the band partial
+// trace over the other qubits, and the 16x16 FP64 update (OptimizeGate,
+// Eq. opt_u) on one CTA.
+//
+// A gate on qubits (q[0], q[1], q[2], q[3]) acts on the local index
+// sum_i bit(q[i]) 2^(3-i) (q[0] is the most significant local bit).  Its
+// operators are 16x16 row-major (256 FP64 complex values); a start's pass
+// operators L, R sit at LR + s*512 (L first).
+//
+// The 16x16 update runs on a whole CTA of 256 threads (thread t holds
+// element (t / 16, t % 16) of every shared matrix): one-sided Jacobi in FP32
+// (eight disjoint column pairs per round, one warp per pair: lanes 0-15 hold
+// the pair's rows of W, lanes 16-31 those of Y), then from W = A Y (Y made
+// unitary in FP64) FP64 sweeps with angles from FP32 and exactly unitary
+// FP64 rotations, X = W's normalised columns (re-orthonormalised by FP64
+// Gram-Schmidt when a singular value is below 1e-3 of the largest, and
+// completed below 1e-13), u = Y X^dagger.  The per-element FP64 work is
+// spread over eight warps because GB300 issues FP64 at 1/64 of its FP32 rate.
+
+#include <cuda_runtime.h>
+
+#include "qf_device.cuh"
+#include "qf_internal.h"
+
+namespace qf {
+namespace {
+
+using namespace dev;
+
+constexpr int kCta16 = 256;  // threads of every 16x16 kernel that runs the update
+
+// Offset of local index v of a gate on bit positions p[0..3] (p[0]: the
+// local index's most significant bit).
+__device__ __forceinline__ unsigned off16(int v, const int* p) {
+  return (((unsigned)v >> 3) & 1u) << p[0] | (((unsigned)v >> 2) & 1u) << p[1] |
+         (((unsigned)v >> 1) & 1u) << p[2] | ((unsigned)v & 1u) << p[3];
+}
+
+// Insert zero bits at the four (ascending) positions qs[0..3].
+__device__ __forceinline__ unsigned dep4(unsigned x, const int* qs) {
+  return dep1(dep1(dep1(dep1(x, qs[0]), qs[1]), qs[2]), qs[3]);
+}
+
+__device__ __forceinline__ void sort4(const int* p, int* qs) {
+  for (int i = 0; i < 4; ++i) qs[i] = p[i];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 3 - a; ++b)
+      if (qs[b] > qs[b + 1]) {
+        const int t = qs[b];
+        qs[b] = qs[b + 1];
+        qs[b + 1] = t;
+      }
+}
+
+// ------------------------------------------------------ CTA 16x16 products
+// C = op(A) op(B) on shared 16x16 FP64 matrices, one element per thread
+// (t = 16 i + j); C must not alias A or B.  Ends with a barrier.
+enum MmOp { kMmNN = 0, kMmND = 1, kMmDN = 2 };  // A B, A B^dagger, A^dagger B
+
+template <int OP>
+__device__ __forceinline__ void cta_mm(const double2* A, const double2* B, double2* C) {
+  const int t = threadIdx.x, i = t >> 4, j = t & 15;
+  double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 4
+  for (int k = 0; k < 16; ++k) {
+    if (OP == kMmNN) {
+      acc = cfma(A[i * 16 + k], B[k * 16 + j], acc);
+    } else if (OP == kMmND) {  // A[i][k] conj(B[j][k])
+      acc = cfma_cj(B[j * 16 + k], A[i * 16 + k], acc);
+    } else {  // conj(A[k][i]) B[k][j]
+      acc = cfma_cj(A[k * 16 + i], B[k * 16 + j], acc);
+    }
+  }
+  C[t] = acc;
+  __syncthreads();
+}
+
+// Two FP64 Newton-Schulz steps M <- M (3I - M^dagger M) / 2 on shared M
+// (tmp, tmp2: shared scratch).
+__device__ __forceinline__ void cta_newton_schulz(double2* M, double2* tmp, double2* tmp2, int steps) {
+  const int t = threadIdx.x, i = t >> 4, j = t & 15;
+  for (int s = 0; s < steps; ++s) {
+    cta_mm<kMmDN>(M, M, tmp);
+    tmp[t] = make_double2((i == j ? 1.5 : 0.0) - 0.5 * tmp[t].x, -0.5 * tmp[t].y);
+    __syncthreads();
+    cta_mm<kMmNN>(M, tmp, tmp2);
+    M[t] = tmp2[t];
+    __syncthreads();
+  }
+}
+
+// The column pair of warp w in Jacobi round r = 1..15: (p, p ^ r), p < p ^ r;
+// the eight pairs of a round are disjoint.
+__device__ __forceinline__ int pair_col(int r, int w) {
+  const int hb = 31 - __clz(r);
+  return ((w >> hb) << (hb + 1)) | (w & ((1 << hb) - 1));
+}
+
+// ------------------------------------------------------ CTA 16x16 polar
+// Shared workspace of the 16x16 update (29 KB).
+struct Polar16Smem {
+  double2 a[256];  // A, scaled in place by a power of two
+  double2 w[256];  // W = A Y
+  double2 y[256];  // Y
+  double2 x[256];  // X, then the result u
+  double2 t1[256], t2[256];
+  float2 fw[256], fy[256];  // the FP32 stage's W and Y
+  double s[16];             // column norms (singular values)
+  unsigned emax;
+  float off[2];
+};
+
+__device__ __forceinline__ unsigned expo_field(double v) {
+  return (unsigned)(__double2hiint(v) >> 20) & 0x7ffu;
+}
+
+// Largest exponent field of the shared matrix a (every thread gets it).
+__device__ __forceinline__ unsigned cta_max_exponent(Polar16Smem& S) {
+  const int t = threadIdx.x;
+  if (t == 0) S.emax = 0u;
+  __syncthreads();
+  const double2 v = S.a[t];
+  const unsigned e = __reduce_max_sync(kFull, max(expo_field(v.x), expo_field(v.y)));
+  if ((t & 31) == 0) atomicMax(&S.emax, e);
+  __syncthreads();
+  return S.emax;
+}
+
+// One-sided Jacobi round r on the lane-split pair (W, Y) in FP32: warp w
+// rotates columns (p, p ^ r); lanes 0-15 hold rows of W, lanes 16-31 rows
+// of Y.  Returns the pair's off-diagonal measure |g| / (|W_p| |W_q|).
+__device__ __forceinline__ float jacobi16_round_f(Polar16Smem& S, int r) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int p = pair_col(r, w), q = p ^ r, row = lane & 15;
+  const bool isW = lane < 16;
+  float2* M = isW ? S.fw : S.fy;
+  const float2 xp = M[row * 16 + p], xq = M[row * 16 + q];
+  float al = isW ? xp.x * xp.x + xp.y * xp.y : 0.f;
+  float be = isW ? xq.x * xq.x + xq.y * xq.y : 0.f;
+  float gx = isW ? xp.x * xq.x + xp.y * xq.y : 0.f;  // conj(W[i][p]) W[i][q]
+  float gy = isW ? xp.x * xq.y - xp.y * xq.x : 0.f;
+#pragma unroll
+  for (int h = 1; h < 16; h <<= 1) {
+    al += __shfl_xor_sync(kFull, al, h);
+    be += __shfl_xor_sync(kFull, be, h);
+    gx += __shfl_xor_sync(kFull, gx, h);
+    gy += __shfl_xor_sync(kFull, gy, h);
+  }
+  al = __shfl_sync(kFull, al, 0);
+  be = __shfl_sync(kFull, be, 0);
+  gx = __shfl_sync(kFull, gx, 0);
+  gy = __shfl_sync(kFull, gy, 0);
+  const float gm = fmaxf(fabsf(gx), fabsf(gy));
+  const float nrm = sqrtf(al) * sqrtf(be);
+  float off = 0.f;
+  // columns below 1e-6 of A's largest entry are noise in FP32: the FP64
+  // stage resolves them
+  if (gm > 1e-7f * nrm && fmaxf(al, be) > 1e-12f && gm > 0.f) {
+    const float gxs = __fdividef(gx, gm), gys = __fdividef(gy, gm);
+    const float rr = rsqrtf(gxs * gxs + gys * gys);
+    const float ag = gm * (gxs * gxs + gys * gys) * rr;
+    off = __fdividef(ag, nrm);
+    const float zeta = 0.5f * __fdividef(be - al, ag);
+    const float az = fabsf(zeta);
+    const float tt = az > 1e18f ? __fdividef(0.5f, zeta)
+                                : copysignf(__fdividef(1.f, az + sqrtf(1.f + az * az)), zeta);
+    const float c = rsqrtf(1.f + tt * tt), sn = c * tt;
+    const float2 e = make_float2(gxs * rr, -gys * rr);  // conj(g) / |g|
+    const float2 ex = cmul(e, xq);
+    M[row * 16 + p] = make_float2(c * xp.x - sn * ex.x, c * xp.y - sn * ex.y);
+    M[row * 16 + q] = make_float2(sn * xp.x + c * ex.x, sn * xp.y + c * ex.y);
+  }
+  return off;
+}
+
+// The same round in FP64 (after the FP32 stage): FP64 inner products, an
+// FP32 rotation angle, a rotation unitary to FP64 rounding (rsqrt_d, no
+// FP64 division or square root).  Returns whether the pair is still above
+// |g| <= tol |W_p| |W_q|.
+__device__ __forceinline__ bool jacobi16_round_d(Polar16Smem& S, int r, double tol2) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int p = pair_col(r, w), q = p ^ r, row = lane & 15;
+  const bool isW = lane < 16;
+  double2* M = isW ? S.w : S.y;
+  const double2 xp = M[row * 16 + p], xq = M[row * 16 + q];
+  double al = isW ? xp.x * xp.x + xp.y * xp.y : 0.0;
+  double be = isW ? xq.x * xq.x + xq.y * xq.y : 0.0;
+  double gx = isW ? xp.x * xq.x + xp.y * xq.y : 0.0;
+  double gy = isW ? xp.x * xq.y - xp.y * xq.x : 0.0;
+#pragma unroll
+  for (int h = 1; h < 16; h <<= 1) {
+    al += __shfl_xor_sync(kFull, al, h);
+    be += __shfl_xor_sync(kFull, be, h);
+    gx += __shfl_xor_sync(kFull, gx, h);
+    gy += __shfl_xor_sync(kFull, gy, h);
+  }
+  al = __shfl_sync(kFull, al, 0);
+  be = __shfl_sync(kFull, be, 0);
+  gx = __shfl_sync(kFull, gx, 0);
+  gy = __shfl_sync(kFull, gy, 0);
+  const double g2 = gx * gx + gy * gy, ab = al * be;
+  // rotate where |g| is above FP64 rounding of |W_p| |W_q| (and normal)
+  if (g2 > 1e-4 * tol2 * ab && g2 > 1e-300) {
+    const double rg = rsqrt_d(g2);
+    const float z = (float)(0.5 * (be - al) * rg), az = fabsf(z);
+    const float tf = copysignf(az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(1.f + az * az)), z);
+    const double tt = (double)tf;
+    const double c = rsqrt_d(1.0 + tt * tt), sn = c * tt;
+    const double2 e = make_double2(gx * rg, -gy * rg);  // conj(g) / |g|
+    const double2 ex = cmul(e, xq);
+    M[row * 16 + p] = make_double2(c * xp.x - sn * ex.x, c * xp.y - sn * ex.y);
+    M[row * 16 + q] = make_double2(sn * xp.x + c * ex.x, sn * xp.y + c * ex.y);
+  }
+  return g2 > tol2 * ab;
+}
+
+// X for a nearly singular A (warp 0; lane i < 16 holds row i): the columns
+// of W in order of decreasing norm, normalised and orthogonalised (twice,
+// Kahan) against those before; columns below 1e-13 of the largest norm are
+// numerically zero and completed with standard basis vectors.
+__device__ void gram_schmidt16(Polar16Smem& S, double smax) {
+  const int lane = threadIdx.x & 31;
+  int ord[16];
+  for (int k = 0; k < 16; ++k) ord[k] = k;
+  for (int a = 0; a < 16; ++a)
+    for (int b = a + 1; b < 16; ++b)
+      if (S.s[ord[b]] > S.s[ord[a]]) {
+        const int tmp = ord[a];
+        ord[a] = ord[b];
+        ord[b] = tmp;
+      }
+  unsigned done = 0u;
+  for (int oi = 0; oi < 16; ++oi) {
+    const int k = ord[oi];
+    for (int att = 0; att <= 16; ++att) {
+      double2 v = make_double2(0.0, 0.0);
+      if (att == 0) {
+        if (!(S.s[k] > 1e-13 * smax)) continue;
+        if (lane < 16) {
+          const double inv = 1.0 / S.s[k];
+          v = make_double2(S.w[lane * 16 + k].x * inv, S.w[lane * 16 + k].y * inv);
+        }
+      } else if (lane == att - 1) {
+        v = make_double2(1.0, 0.0);
+      }
+      for (int pass = 0; pass < 2; ++pass)
+        for (int jj = 0; jj < 16; ++jj) {
+          if (!(done & (1u << jj))) continue;
+          const double2 xj = lane < 16 ? S.x[lane * 16 + jj] : make_double2(0.0, 0.0);
+          double2 d = cfma_cj(xj, v, make_double2(0.0, 0.0));
+#pragma unroll
+          for (int h = 16; h >= 1; h >>= 1) {
+            d.x += __shfl_xor_sync(kFull, d.x, h);
+            d.y += __shfl_xor_sync(kFull, d.y, h);
+          }
+          const double2 pr = cmul(d, xj);
+          v.x -= pr.x;
+          v.y -= pr.y;
+        }
+      double nv = v.x * v.x + v.y * v.y;
+#pragma unroll
+      for (int h = 16; h >= 1; h >>= 1) nv += __shfl_xor_sync(kFull, nv, h);
+      nv = sqrt(nv);
+      // among e_0..e_15 one keeps a residual of at least 1/4
+      if (nv > 0.24) {
+        if (lane < 16) S.x[lane * 16 + k] = make_double2(v.x / nv, v.y / nv);
+        done |= 1u << k;
+        break;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// OptimizeGate on a CTA of kCta16 threads: A in S.a (FP64, destroyed) ->
+// u = Y X^dagger in S.x with A = X D Y^dagger, *sig = sum(D).  Returns false
+// for a non-finite A.  Every thread must call it.
+__device__ bool cta_polar16(Polar16Smem& S, double* sig) {
+  const int t = threadIdx.x, i = t >> 4, j = t & 15;
+  {
+    const double2 a = S.a[t];
+    if (__syncthreads_or(!(isfinite(a.x) && isfinite(a.y)))) return false;
+  }
+  // exact power-of-two scaling: the largest entry in [1, 4)
+  unsigned em = cta_max_exponent(S);
+  double pre = 1.0;
+  if (em == 0u) {
+    const double2 a = S.a[t];
+    if (__syncthreads_and(a.x == 0.0 && a.y == 0.0)) {  // A = 0: every unitary is optimal
+      S.x[t] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      *sig = 0.0;
+      __syncthreads();
+      return true;
+    }
+    pre = __hiloint2double((1023 + 600) << 20, 0);  // 2^600: subnormal entries only
+    S.a[t] = make_double2(a.x * pre, a.y * pre);
+    em = cta_max_exponent(S);
+  }
+  if (em > 2045u) em = 2045u;
+  const double sc = __hiloint2double((int)(2046u - em) << 20, 0);  // 2^(1023 - em)
+  const double unscale =
+      __hiloint2double((int)em << 20, 0) * (pre == 1.0 ? 1.0 : __hiloint2double((1023 - 600) << 20, 0));
+  {
+    const double2 a = S.a[t];
+    S.a[t] = make_double2(a.x * sc, a.y * sc);
+    S.fw[t] = make_float2((float)(a.x * sc), (float)(a.y * sc));
+    S.fy[t] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  // stage 1: FP32 one-sided Jacobi to an off-diagonal measure of 1e-6
+  for (int sweep = 0; sweep < 15; ++sweep) {
+    if (t == 0) S.off[sweep & 1] = 0.f;
+    __syncthreads();
+    float off = 0.f;
+    for (int r = 1; r <= 15; ++r) {
+      off = fmaxf(off, jacobi16_round_f(S, r));
+      __syncthreads();
+    }
+    if ((t & 31) == 0) atomicMax(reinterpret_cast<int*>(&S.off[sweep & 1]), __float_as_int(off));
+    __syncthreads();
+    if (S.off[sweep & 1] < 1e-6f) break;
+  }
+  // stage 2: Y unitary in FP64, W = A Y, FP64 sweeps to 1e-15
+  S.y[t] = to_d2(S.fy[t]);
+  __syncthreads();
+  cta_newton_schulz(S.y, S.t1, S.t2, 2);
+  cta_mm<kMmNN>(S.a, S.y, S.w);
+  const double tol2 = 1e-30;
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    bool open = false;
+    for (int r = 1; r <= 15; ++r) {
+      open |= jacobi16_round_d(S, r, tol2);
+      __syncthreads();
+    }
+    if (!__syncthreads_or(open)) break;
+  }
+  if (t < 16) {
+    double s2 = 0.0;
+    for (int r = 0; r < 16; ++r) s2 += S.w[r * 16 + t].x * S.w[r * 16 + t].x + S.w[r * 16 + t].y * S.w[r * 16 + t].y;
+    S.s[t] = sqrt(s2);
+  }
+  __syncthreads();
+  double smax = 0.0, smin = S.s[0], ssum = 0.0;
+  for (int k = 0; k < 16; ++k) {
+    smax = fmax(smax, S.s[k]);
+    smin = fmin(smin, S.s[k]);
+    ssum += S.s[k];
+  }
+  if (smin > 1e-3 * smax) {
+    const double inv = 1.0 / S.s[j];
+    S.x[t] = make_double2(S.w[t].x * inv, S.w[t].y * inv);
+  } else if (t < 32) {  // rare: re-orthonormalise, complete the null space
+    gram_schmidt16(S, smax);
+  }
+  __syncthreads();
+  cta_mm<kMmND>(S.y, S.x, S.t1);  // u = Y X^dagger
+  const double2 u = S.t1[t];
+  S.x[t] = u;
+  *sig = ssum * unscale;
+  return __syncthreads_and(isfinite(u.x) && isfinite(u.y));
+}
+
+// ------------------------------------------------------------ environment
+//
+// P[x][y] = sum over the 2^(n-4) rests r of T[(r, x), (r, y)], taken from
+// the tensor before the gate's removal (E = P u^dagger backward,
+// u^dagger P forward, as for two-qubit gates).  Grid (B, S): thread
+// t = 16 x + y of CTA b sums entry (x, y) over its CTA's slice of rests in
+// the tensor's accumulation precision and writes it; the last CTA of the
+// start (atomic ticket) adds the B partials in a fixed order and runs the
+// 16x16 update.
+
+template <typename R>
+__global__ void __launch_bounds__(kCta16)
+env16_kernel(const typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, int p2, int p3,
+             int mode, double2* __restrict__ gates_k, long long gstride, double beta,
+             double2* __restrict__ LR, double2* __restrict__ out, long long out_stride,
+             double* __restrict__ sigma_out, int* __restrict__ status, double* __restrict__ part,
+             unsigned* __restrict__ counters) {
+  using CT = typename Cplx<R>::T;
+  using Ar = typename Acc<R>::T;
+  __shared__ Polar16Smem S;
+  __shared__ bool is_last;
+  const int s = blockIdx.y, B = gridDim.x, bb = blockIdx.x, t = threadIdx.x;
+  const int i = t >> 4, j = t & 15;
+  const int p[4] = {p0, p1, p2, p3};
+  int qs[4];
+  sort4(p, qs);
+  const unsigned N = 1u << n;
+  const unsigned nr = 1u << (n - 4);
+  const unsigned chunk = (nr + B - 1) / B;
+  const unsigned r_beg = bb * chunk, r_end = min(nr, r_beg + chunk);
+  const CT* Ts = T + (size_t)s * N * N;
+  const unsigned ox = off16(i, p), oy = off16(j, p);
+  Ar vx = Ar(0), vy = Ar(0);
+  for (unsigned r = r_beg; r < r_end; ++r) {
+    const unsigned d = dep4(r, qs);
+    const auto e = to_acc(Ts[(size_t)(d | ox) * N + (d | oy)]);
+    vx += e.x;
+    vy += e.y;
+  }
+  part[((size_t)s * B + bb) * 512 + 2 * t] = (double)vx;
+  part[((size_t)s * B + bb) * 512 + 2 * t + 1] = (double)vy;
+  __threadfence();
+  __syncthreads();
+  if (t == 0) {
+    const unsigned ticket = atomicAdd(&counters[s], 1u);
+    is_last = (ticket == (unsigned)B - 1u);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double2 P = make_double2(0.0, 0.0);
+  for (int k = 0; k < B; ++k) {
+    P.x += __ldcg(&part[((size_t)s * B + k) * 512 + 2 * t]);
+    P.y += __ldcg(&part[((size_t)s * B + k) * 512 + 2 * t + 1]);
+  }
+  if (t == 0) counters[s] = 0u;
+  if (mode == kTraceOnly) {
+    out[s * out_stride + t] = P;
+    return;
+  }
+  S.t1[t] = P;
+  const double2 u = gates_k[s * gstride + t];
+  S.t2[t] = u;
+  __syncthreads();
+  const double2 ud = cconj(S.t2[j * 16 + i]);  // u^dagger[i][j]
+  if (mode == kForward)
+    cta_mm<kMmDN>(S.t2, S.t1, S.a);  // u^dagger P
+  else
+    cta_mm<kMmND>(S.t1, S.t2, S.a);  // P u^dagger
+  const double2 E = S.a[t];
+  if (out) out[s * out_stride + t] = E;
+  double2* lr = LR + (size_t)s * 512;
+  if (mode == kEnvOnly) {
+    lr[t] = u;
+    lr[256 + t] = ud;
+    return;
+  }
+  if (beta != 0.0) S.a[t] = make_double2((1.0 - beta) * E.x + beta * ud.x, (1.0 - beta) * E.y + beta * ud.y);
+  __syncthreads();
+  double sg = 0.0;
+  double2 un;
+  if (cta_polar16(S, &sg)) {
+    un = S.x[t];
+  } else {
+    if (t == 0) atomicExch(status, -4);
+    un = u;  // keep the old gate: the tensor stays consistent
+    sg = 0.0;
+  }
+  gates_k[s * gstride + t] = un;
+  const bool bwd = mode == kBackward;
+  lr[t] = bwd ? un : ud;
+  lr[256 + t] = bwd ? ud : un;
+  if (sigma_out && t == 0) sigma_out[s] = sg;
+}
+
+// One CTA per 16x16 matrix (qf_optimize_gates_k with dim 16).
+__global__ void __launch_bounds__(kCta16) optimize16_kernel(const double2* __restrict__ E,
+                                                            const double2* __restrict__ u_old,
+                                                            double beta, double2* __restrict__ u_out,
+                                                            double* __restrict__ sigma_out) {
+  __shared__ Polar16Smem S;
+  const int m = blockIdx.x, t = threadIdx.x, i = t >> 4, j = t & 15;
+  double2 a = E[(size_t)m * 256 + t];
+  if (beta != 0.0) {
+    const double2 d = cconj(u_old[(size_t)m * 256 + j * 16 + i]);
+    a = make_double2((1.0 - beta) * a.x + beta * d.x, (1.0 - beta) * a.y + beta * d.y);
+  }
+  S.a[t] = a;
+  __syncthreads();
+  double sg = 0.0;
+  const bool ok = cta_polar16(S, &sg);
+  u_out[(size_t)m * 256 + t] = ok ? S.x[t] : make_double2(NAN, NAN);
+  if (sigma_out && t == 0) sigma_out[m] = ok ? sg : NAN;
+}
+
+// Re-unitarisation (reset_iter): three FP64 Newton-Schulz steps on every
+// 16x16 gate of a circuit; CTA m takes gate m % p of start m / p and leaves
+// gates of other sizes alone (desc[k] = (size, entry offset)).
+__global__ void __launch_bounds__(kCta16) reunitarize16_kernel(double2* __restrict__ gates, long long gsz,
+                                                               const int2* __restrict__ desc, int p) {
+  __shared__ double2 M[256], t1[256], t2[256];
+  const int m = blockIdx.x, s = m / p, k = m % p;
+  const int2 d = desc[k];
+  if (d.x != 4) return;  // the whole CTA leaves together
+  double2* gp = gates + (size_t)s * gsz + d.y;
+  M[threadIdx.x] = gp[threadIdx.x];
+  __syncthreads();
+  cta_newton_schulz(M, t1, t2, 3);
+  gp[threadIdx.x] = M[threadIdx.x];
+}
+
+// ------------------------------------------------------------------ pass
+//
+// B <- L B R on every 16x16 block (Alg. 1 ApplyRight and ApplyLeft on four
+// qubits, fused): 32 complex multiply-adds per entry against one read and
+// one write.  A warp takes two blocks per group, lane 16 b + x holding row x
+// of block b (consecutive blocks take consecutive column rests).  R acts
+// along the row in registers and each output entry goes to a padded
+// per-warp transpose buffer; the lane then takes column x of its block,
+// applies L and writes the output entries of that column.  Every complex
+// multiply-add takes one operator entry from shared memory (a broadcast).
+
+constexpr int kPass16Threads = 128;
+constexpr int kBlk16 = 16 * 17;  // padded 16x16 block in the transpose buffer
+
+template <typename R, bool HL, bool HR>
+__global__ void __launch_bounds__(kPass16Threads)
+pass16_kernel(typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, int p2, int p3,
+              const double2* __restrict__ L, long long Ls, const double2* __restrict__ Rm,
+              long long Rs) {
+  typedef typename Cplx<R>::T C;
+  __shared__ C sL[256], sR[256];
+  __shared__ C buf[kPass16Threads / 32][2 * kBlk16];
+  const int s = blockIdx.y;
+  for (int e = threadIdx.x; e < 256; e += kPass16Threads) {
+    if (HL) sL[e] = cmake(L[s * Ls + e], R());
+    if (HR) sR[e] = cmake(Rm[s * Rs + e], R());
+  }
+  __syncthreads();
+  const int p[4] = {p0, p1, p2, p3};
+  int qs[4];
+  sort4(p, qs);
+  unsigned off[16];  // constant indices only
+#pragma unroll
+  for (int v = 0; v < 16; ++v) off[v] = off16(v, p);
+  const unsigned N = 1u << n;
+  const int lnc = n - 4;
+  const unsigned cmask = (1u << lnc) - 1u;
+  const unsigned nblk = 1u << (2 * lnc);
+  C* __restrict__ Ts = T + (size_t)s * N * N;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = lane >> 4, x = lane & 15;
+  const unsigned offx = off16(x, p);
+  C* wb = buf[w] + b * kBlk16;
+  const unsigned warps = gridDim.x * (kPass16Threads / 32);
+  for (unsigned grp = blockIdx.x * (kPass16Threads / 32) + w; grp * 2u < nblk; grp += warps) {
+    const unsigned blk = grp * 2u + (unsigned)b;
+    const bool valid = blk < nblk;
+    const unsigned r0 = dep4(blk >> lnc, qs), c0 = dep4(blk & cmask, qs);
+    C row[16];
+    if (valid) {
+      const C* src = Ts + (size_t)(r0 | offx) * N + c0;
+#pragma unroll
+      for (int y = 0; y < 16; ++y) row[y] = src[off[y]];
+    } else {
+#pragma unroll
+      for (int y = 0; y < 16; ++y) row[y] = czero<C>();
+    }
+    if (HR) {  // row <- row R
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        C acc = czero<C>();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc = cfma(row[k], sR[k * 16 + c], acc);
+        acc = cfinish(acc);
+        if (HL)
+          wb[x * 17 + c] = acc;
+        else if (valid)
+          Ts[(size_t)(r0 | offx) * N + (c0 | off[c])] = acc;
+      }
+    } else if (HL) {
+#pragma unroll
+      for (int y = 0; y < 16; ++y) wb[x * 17 + y] = row[y];
+    }
+    if (HL) {
+      __syncwarp();
+      C col[16];  // column x of the block
+#pragma unroll
+      for (int k = 0; k < 16; ++k) col[k] = wb[k * 17 + x];
+      __syncwarp();  // the buffer is rewritten by the next group
+      if (valid) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          C acc = czero<C>();
+#pragma unroll
+          for (int k = 0; k < 16; ++k) acc = cfma(sL[r * 16 + k], col[k], acc);
+          Ts[(size_t)(r0 | off[r]) * N + (c0 | offx)] = cfinish(acc);
+        }
+      }
+    }
+  }
+}
+
+template <typename R, bool HL, bool HR>
+void pass16_launch(void* T, int n, int S, const int* p, const double2* L, long long Ls,
+                   const double2* Rm, long long Rs, cudaStream_t st) {
+  typedef typename Cplx<R>::T C;
+  const long long groups = ((1ll << (2 * (n - 4))) + 1) / 2;
+  const long long want = (groups + 3) / 4;
+  long long cap = ((long long)sm_count() * 8 + S - 1) / S;
+  if (cap < 1) cap = 1;
+  dim3 grid((unsigned)(want < cap ? want : cap), S);
+  pass16_kernel<R, HL, HR><<<grid, kPass16Threads, 0, st>>>((C*)T, n, p[0], p[1], p[2], p[3], L, Ls, Rm, Rs);
+}
+
+template <typename R>
+void pass16_ops(void* T, int n, int S, const int* p, const double2* L, long long Ls,
+                const double2* Rm, long long Rs, cudaStream_t st) {
+  if (L && Rm)
+    pass16_launch<R, true, true>(T, n, S, p, L, Ls, Rm, Rs, st);
+  else if (L)
+    pass16_launch<R, true, false>(T, n, S, p, L, Ls, Rm, Rs, st);
+  else if (Rm)
+    pass16_launch<R, false, true>(T, n, S, p, L, Ls, Rm, Rs, st);
+}
+
+}  // namespace
+
+// ================================================================ launchers
+
+cudaError_t launch_pass16(void* T, int n, int S, const int* q, const double2* L, long long Ls,
+                          const double2* R, long long Rs, int prec, cudaStream_t st) {
+  if (!L && !R) return cudaSuccess;
+  const int p[4] = {qubit_bit(n, q[0]), qubit_bit(n, q[1]), qubit_bit(n, q[2]), qubit_bit(n, q[3])};
+  if (prec == 0)
+    pass16_ops<double>(T, n, S, p, L, Ls, R, Rs, st);
+  else if (prec == 2)
+    pass16_ops<DF>(T, n, S, p, L, Ls, R, Rs, st);
+  else
+    pass16_ops<float>(T, n, S, p, L, Ls, R, Rs, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update16(const void* T, int n, int S, const int* q, double2* gates_k,
+                            long long gstride, int mode, double beta, double2* LR, double2* out,
+                            long long out_stride, double* sigma_out, int* status, double* part,
+                            unsigned* counters, int prec, cudaStream_t st) {
+  const int p0 = qubit_bit(n, q[0]), p1 = qubit_bit(n, q[1]), p2 = qubit_bit(n, q[2]),
+            p3 = qubit_bit(n, q[3]);
+  dim3 grid(env_ctas(n), S);
+  if (prec == 0)
+    env16_kernel<double><<<grid, kCta16, 0, st>>>((const double2*)T, n, p0, p1, p2, p3, mode, gates_k,
+                                                  gstride, beta, LR, out, out_stride, sigma_out, status,
+                                                  part, counters);
+  else if (prec == 2)
+    env16_kernel<DF><<<grid, kCta16, 0, st>>>((const dfc*)T, n, p0, p1, p2, p3, mode, gates_k, gstride,
+                                              beta, LR, out, out_stride, sigma_out, status, part,
+                                              counters);
+  else
+    env16_kernel<float><<<grid, kCta16, 0, st>>>((const float2*)T, n, p0, p1, p2, p3, mode, gates_k,
+                                                 gstride, beta, LR, out, out_stride, sigma_out, status,
+                                                 part, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_optimize16(const double2* E, const double2* u_old, double beta, int count,
+                              double2* u_out, double* sigma_out, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  optimize16_kernel<<<count, kCta16, 0, st>>>(E, u_old, beta, u_out, sigma_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reunitarize16(double2* gates, long long gsz, const int2* desc, int p, int S,
+                                 cudaStream_t st) {
+  if (p * S <= 0) return cudaSuccess;
+  reunitarize16_kernel<<<p * S, kCta16, 0, st>>>(gates, gsz, desc, p);
+  return cudaGetLastError();
+}
+
+}  // namespace qf

@@ -1064,6 +1064,7 @@ __global__ void __launch_bounds__(128) reunitarize_mixed_kernel(double2* __restr
   if (m >= count) return;  // whole warps leave together
   const int s = m / p, k = m % p;
   const int2 d = desc[k];
+  if (d.x == 4) return;  // 16x16 gates: reunitarize16_kernel
   double2* gp = gates + (size_t)s * gsz + d.y;
   if (d.x == 3) {
     const L8 L;

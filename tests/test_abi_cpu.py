@@ -78,7 +78,8 @@ def test_struct_layouts_match_header(lib, tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("gcc not available")
     structs = {"qf_options": nat.qf_options, "qf_result": nat.qf_result,
-               "qf_batch_stats": nat.qf_batch_stats}
+               "qf_batch_stats": nat.qf_batch_stats, "qf_gate_loc": nat.qf_gate_loc,
+               "qf_gate_spec": nat.qf_gate_spec}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "qfactor.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')

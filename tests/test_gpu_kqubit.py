@@ -209,4 +209,4 @@ def test_invalid_k_locations_are_rejected(qf):
     with pytest.raises(QFactorError):
         qf.instantiate_k(V, [(0, 1, 4)], [[np.eye(8)]])
     with pytest.raises(ValueError):
-        qf.instantiate_k(V, [(0, 1, 2, 3)], [[np.eye(16)]])
+        qf.instantiate_k(V, [(0, 1, 2, 3, 4)], [[np.eye(32)]])

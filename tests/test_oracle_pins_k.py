@@ -2,7 +2,7 @@
 other than itself: explicit basis-loop operators and partial traces,
 finite differences, the trace identity, closed-form single-gate fits,
 local optimality and monotonicity (Sec. III, Alg. 1, Eq. opt_u).  Gates of
-1, 2 and 3 qubits, in every qubit order."""
+1, 2, 3 and 4 qubits, in every qubit order."""
 import numpy as np
 import pytest
 
@@ -33,7 +33,9 @@ def test_dense_helper_k_matches_kron_for_adjacent_qubits():
 def test_apply_right_left_k_match_dense(n):
     g = qi.rng(9100 + n)
     T = qi.haar_unitary(2**n, g) + 0.3 * qi.haar_unitary(2**n, g)
-    for k in (1, 2, 3):
+    for k in (1, 2, 3, 4):
+        if k > n:
+            continue
         for _ in range(4):
             q = tuple(int(x) for x in g.choice(n, k, replace=False))
             u = qi.haar_unitary(2**k, g)
@@ -46,7 +48,9 @@ def test_apply_right_left_k_match_dense(n):
 def test_partial_trace_k_matches_dense(n):
     g = qi.rng(9200 + n)
     M = g.standard_normal((2**n, 2**n)) + 1j * g.standard_normal((2**n, 2**n))
-    for k in (1, 2, 3):
+    for k in (1, 2, 3, 4):
+        if k > n:
+            continue
         for _ in range(3):
             q = tuple(int(x) for x in g.choice(n, k, replace=False))
             np.testing.assert_allclose(ok.calc_env_mat_k(M, q, n), dr.dense_partial_trace_k(M, q, n),
@@ -78,13 +82,13 @@ def test_environments_k_match_dense_and_trace_identity(n):
     assert abs(cost - (1 - abs(t) / 2**n)) <= 1e-15
 
 
-def test_environment_k_is_the_gradient_of_the_trace():
+@pytest.mark.parametrize("n,ks", [(4, (2, 3)), (5, (2, 4))])
+def test_environment_k_is_the_gradient_of_the_trace(n, ks):
     """Tr(V^dagger C) is linear in each gate, so a central difference in
     entry (i, j) of u_k equals E_k[j, i] up to rounding."""
-    n = 4
-    g = qi.rng(9500)
-    gates, locs = _mixed_structure(n, 5, g, ks=(2, 3))
-    V = qi.haar_unitary(16, g)
+    g = qi.rng(9500 + n)
+    gates, locs = _mixed_structure(n, 5, g, ks=ks)
+    V = qi.haar_unitary(2**n, g)
     _, envs, _ = ok.cost_and_env_k(V, gates, locs, n)
     h = 1e-6
     for k in range(len(gates)):
@@ -101,39 +105,43 @@ def test_environment_k_is_the_gradient_of_the_trace():
                 assert abs(fd - envs[k][j, i]) <= 1e-8, (k, i, j)
 
 
-def test_single_three_qubit_gate_fits_its_target_in_one_update():
-    """n = 3, one gate on all qubits: the environment of u from T = V^dagger u
+@pytest.mark.parametrize("n,orders", [(3, [(0, 1, 2), (2, 0, 1)]), (4, [(0, 1, 2, 3), (3, 1, 0, 2)])])
+def test_single_gate_on_every_qubit_fits_its_target_in_one_update(n, orders):
+    """One gate on all n qubits: the environment of u from T = V^dagger u
     after removal is V^dagger, and the update returns u' = V, cost 0."""
-    g = qi.rng(9600)
-    V = qi.haar_unitary(8, g)
-    for q in [(0, 1, 2), (2, 0, 1)]:
-        u0 = qi.haar_unitary(8, g)
-        T = ok.init_circuit_tensor_k(V, [u0], [q], 3)
-        T, gates = ok.two_sided_sweep_k(T, [u0], [q], 3)
+    g = qi.rng(9600 + n)
+    V = qi.haar_unitary(2**n, g)
+    for q in orders:
+        u0 = qi.haar_unitary(2**n, g)
+        T = ok.init_circuit_tensor_k(V, [u0], [q], n)
+        T, gates = ok.two_sided_sweep_k(T, [u0], [q], n)
         # the gate on permuted qubits equals V in the permuted local basis
-        np.testing.assert_allclose(dr.full_operator_k(gates[0], q, 3), V, atol=1e-12)
-        assert ok.trace_cost(T, 3) <= 1e-14
+        np.testing.assert_allclose(dr.full_operator_k(gates[0], q, n), V, atol=1e-12)
+        assert ok.trace_cost(T, n) <= 1e-14
 
 
-def test_product_target_closed_form_cost():
-    """n = 4, one gate on (0, 1, 2) and V = w (x) h with h on qubit 3: the
-    update reaches w up to a phase and the cost 1 - |Tr h| / 2."""
-    g = qi.rng(9700)
-    w = qi.haar_unitary(8, g)
+@pytest.mark.parametrize("k", [3, 4])
+def test_product_target_closed_form_cost(k):
+    """n = k + 1, one gate on qubits 0..k-1 and V = w (x) h with h on qubit
+    k: the update reaches w up to a phase and the cost 1 - |Tr h| / 2."""
+    g = qi.rng(9700 + k)
+    d = 2**k
+    w = qi.haar_unitary(d, g)
     h = qi.haar_unitary(2, g)
     V = np.kron(w, h)
-    u0 = qi.haar_unitary(8, g)
-    T = ok.init_circuit_tensor_k(V, [u0], [(0, 1, 2)], 4)
-    T, gates = ok.two_sided_sweep_k(T, [u0], [(0, 1, 2)], 4)
-    assert abs(ok.trace_cost(T, 4) - (1 - abs(np.trace(h)) / 2)) <= 1e-13
-    ph = np.trace(w.conj().T @ gates[0]) / 8
+    q = tuple(range(k))
+    u0 = qi.haar_unitary(d, g)
+    T = ok.init_circuit_tensor_k(V, [u0], [q], k + 1)
+    T, gates = ok.two_sided_sweep_k(T, [u0], [q], k + 1)
+    assert abs(ok.trace_cost(T, k + 1) - (1 - abs(np.trace(h)) / 2)) <= 1e-13
+    ph = np.trace(w.conj().T @ gates[0]) / d
     np.testing.assert_allclose(gates[0], ph * w, atol=1e-12)
     assert abs(abs(ph) - 1) <= 1e-12
 
 
 def test_update_k_is_locally_optimal_and_unitary():
     g = qi.rng(9800)
-    for d in (2, 8):
+    for d in (2, 8, 16):
         E = g.standard_normal((d, d)) + 1j * g.standard_normal((d, d))
         u, s = ok.optimize_gate_k(E)
         assert abs(np.trace(E @ u) - s) <= 1e-12
@@ -175,4 +183,22 @@ def test_reachable_three_qubit_gate_circuit_converges():
     assert res["costs"].min() <= 1e-12, res["costs"]
     C = ok.circuit_unitary_k(res["gates"][res["best"]], locs, n)
     ph = np.trace(V.conj().T @ C) / 16
+    np.testing.assert_allclose(C, ph * V, atol=1e-5)
+
+
+def test_reachable_four_qubit_gate_circuit_converges():
+    """Four-qubit gates on (0,1,2,3) and (1,2,3,4) with two-qubit gates
+    between, target reachable from the same structure: some start reaches
+    cost < 1e-12 and its circuit equals V up to a global phase."""
+    n = 5
+    locs = [(0, 1, 2, 3), (3, 4), (1, 2, 3, 4), (0, 1)]
+    g = qi.rng(9960)
+    tgt = [qi.haar_unitary(2 ** len(q), g) for q in locs]
+    V = ok.circuit_unitary_k(tgt, locs, n)
+    starts = [[qi.haar_unitary(2 ** len(q), qi.rng(9961 + s * 10 + i)) for i, q in enumerate(locs)]
+              for s in range(4)]
+    res = ok.qfactor_multistart_k(V, starts, locs, n, dist_tol=1e-12, max_iter=300)
+    assert res["costs"].min() <= 1e-12, res["costs"]
+    C = ok.circuit_unitary_k(res["gates"][res["best"]], locs, n)
+    ph = np.trace(V.conj().T @ C) / 32
     np.testing.assert_allclose(C, ph * V, atol=1e-5)
