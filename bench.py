@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-kqubit", action="store_true")
     ap.add_argument("--no-spec", action="store_true")
     ap.add_argument("--oracle-1core", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--profile-case", choices=["k4", "k3", "pair", "pass"], default=None,
+                    help="run one small case of a kernel family for a profiler capture (12 qubits, "
+                         "2 starts, complex64, one live sweep after one warm-up sweep) and exit")
     return ap.parse_args()
 
 
@@ -1094,10 +1097,62 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """A small case of one kernel family for ncu captures: 12 qubits, 2
+    starts (the tensors, 268 MB in complex64, exceed L2), complex64, a
+    warm-up sweep and one live sweep (no graph).  k4: four-qubit gates on
+    consecutive quadruples (pass16c_kernel, env16_kernel); k3: three-qubit
+    gates on consecutive triples (pass8a/pass8c/pass8f kernels); pair: the
+    look-ahead brickwork (pass_pair_kernel); pass: the plain brickwork
+    (pass_block/window/lane kernels)."""
+    import torch
+
+    import paper_2306_08152_gb300 as qf
+
+    qf._native.load()
+    dev = torch.device("cuda", 0)
+    n, S = 12, 2
+    if args.profile_case == "k4":
+        locs = []
+        for layer in range(6):
+            o = 0 if layer % 2 == 0 else 2
+            locs += [(q, q + 1, q + 2, q + 3) for q in range(o, n - 3, 4)]
+    elif args.profile_case == "k3":
+        locs = []
+        for layer in range(6):
+            o = layer % 3
+            locs += [(q, q + 1, q + 2) for q in range(o, n - 2, 3)]
+    else:
+        locs = [tuple(int(x) for x in q) for q in qi.brickwork_locations(n, LAYERS)]
+    gen = qi.rng(SEED + 55)
+    tgt = [qi.haar_unitary(2 ** len(q), gen) for q in locs]
+    V = qf.circuit_unitary_k(n, locs, tgt, device=dev)
+    starts = qf.flatten_gates([[qi.haar_unitary(2 ** len(q), qi.rng(SEED + 56 + s)) for q in locs]
+                               for s in range(S)]).to(dev)
+    plan = qf.Plan(n, locs, S, qf.QF_C64)
+    if args.profile_case == "pair":
+        plan.set_lookahead(True)
+    plan.enable_pass_timing(True)  # live launches
+    plan.load(V, starts)
+    plan.sweep(1, reset_iter=0)
+    plan.pass_stats()
+    plan.sweep(1, reset_iter=0)
+    ms, launches, all_launches, pbytes = plan.pass_stats()
+    costs = plan.costs()
+    plan.close()
+    print(json.dumps({"case": args.profile_case, "n_qubits": n, "starts": S, "gates": len(locs),
+                      "pass_ms": ms, "pass_launches": launches, "launches": all_launches,
+                      "pass_gbs": pbytes / (ms / 1e3) / 1e9 if ms > 0 else None,
+                      "costs": [float(c) for c in costs]}))
+    return 0
+
+
 def main():
     args = parse()
     if args.oracle_1core:
         return run_oracle_1core(args)
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

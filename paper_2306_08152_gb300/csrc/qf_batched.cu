@@ -93,7 +93,13 @@ struct W {
     __syncwarp();
   }
 
-  // T <- (L on (a,b)) T (R on (a,b)); operators in shared memory.
+  // T <- (L on (a,b)) T (R on (a,b)); operators in shared memory.  The
+  // tensor lives in the warp's shared memory, so the two products run as
+  // two in-place stages: R on every block row (item = (row x, block); a
+  // lane reads the row's 4 entries and writes 4), then L on every block
+  // column.  A lane holds one row or column at a time (a whole 4x4 block in
+  // registers set the kernel's register count, and with it the warps per
+  // SM), and 4 items per block give small circuits 4 times the active lanes.
   template <bool HL, bool HR>
   static __device__ void pass(C* T, int n, int pa, int pb, const C* Lm, const C* Rm) {
     const int lane = threadIdx.x & 31;
@@ -101,85 +107,66 @@ struct W {
     const int lnc = n - 2;
     const unsigned N = 1u << n, cmask = (1u << lnc) - 1u, nblk = 1u << (2 * lnc);
     const unsigned o1 = 1u << pb, o2 = 1u << pa;
-    const unsigned off[4] = {0u, o1, o2, o1 | o2};
-    for (unsigned blk = lane; blk < nblk; blk += 32) {
-      const unsigned r0 = dep2(blk >> lnc, plo, phi), c0 = dep2(blk & cmask, plo, phi);
-      C bm[4][4];
+    const unsigned items = 4u * nblk;
+    auto offv = [&](unsigned v) { return ((v & 2u) ? o2 : 0u) | ((v & 1u) ? o1 : 0u); };
+    if (HR) {  // row (r0 | off[x]) of block (r0, c0) <- row R
+      for (unsigned it = lane; it < items; it += 32) {
+        const unsigned blk = it & (nblk - 1u), x = it >> (2 * lnc);
+        const unsigned r0 = dep2(blk >> lnc, plo, phi), c0 = dep2(blk & cmask, plo, phi);
+        C* row = T + (size_t)(r0 | offv(x)) * N + c0;
+        C v[4];
 #pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) bm[x][y] = T[(r0 | off[x]) * N + (c0 | off[y])];
-      if (HR) {
-#pragma unroll
-        for (int x = 0; x < 4; ++x) {
-          C t[4];
-#pragma unroll
-          for (int y = 0; y < 4; ++y) {
-            C acc = czero<C>();
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc = cfma(bm[x][k], Rm[k * 4 + y], acc);
-            t[y] = acc;
-          }
-#pragma unroll
-          for (int y = 0; y < 4; ++y) bm[x][y] = t[y];
-        }
-      }
-      if (HL) {
+        for (int y = 0; y < 4; ++y) v[y] = row[offv(y)];
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
-          C t[4];
+          C acc = czero<C>();
 #pragma unroll
-          for (int x = 0; x < 4; ++x) {
-            C acc = czero<C>();
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc = cfma(Lm[x * 4 + k], bm[k][y], acc);
-            t[x] = acc;
-          }
-#pragma unroll
-          for (int x = 0; x < 4; ++x) bm[x][y] = t[x];
+          for (int k = 0; k < 4; ++k) acc = cfma(v[k], Rm[k * 4 + y], acc);
+          row[offv(y)] = acc;
         }
       }
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) T[(r0 | off[x]) * N + (c0 | off[y])] = bm[x][y];
+      __syncwarp();
     }
-    __syncwarp();
+    if (HL) {  // column (c0 | off[y]) of block (r0, c0) <- L column
+      for (unsigned it = lane; it < items; it += 32) {
+        const unsigned blk = it & (nblk - 1u), y = it >> (2 * lnc);
+        const unsigned r0 = dep2(blk >> lnc, plo, phi), c0 = dep2(blk & cmask, plo, phi);
+        C* col = T + (size_t)r0 * N + (c0 | offv(y));
+        C v[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) v[x] = col[(size_t)offv(x) * N];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          C acc = czero<C>();
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc = cfma(Lm[x * 4 + k], v[k], acc);
+          col[(size_t)offv(x) * N] = acc;
+        }
+      }
+      __syncwarp();
+    }
   }
 
-  // Band partial trace on (a, b): returns P[i][j] on lane (i, j).
+  // Band partial trace on (a, b): P[x][y] = sum over the rests r of
+  // T[(r, x), (r, y)].  Lane 16 h + 4 x + y sums entry (x, y) over the rests
+  // r = h, h + 2, ... in the tensor's precision; the two half-warps are
+  // added in FP64 with one shuffle (the same sum on both halves).  Returns
+  // P[i][j] on lane (i, j).
   static __device__ double2 band(const C* T, int n, int pa, int pb, const Lane& L) {
     const int plo = pa < pb ? pa : pb, phi = pa < pb ? pb : pa;
     const unsigned N = 1u << n, nr = 1u << (n - 2);
     const unsigned o1 = 1u << pb, o2 = 1u << pa;
-    const unsigned off[4] = {0u, o1, o2, o1 | o2};
-    R v[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = R(0);
-    for (unsigned r = L.l; r < nr; r += 32) {
+    const unsigned ox = ((L.i & 2) ? o2 : 0u) | ((L.i & 1) ? o1 : 0u);
+    const unsigned oy = ((L.j & 2) ? o2 : 0u) | ((L.j & 1) ? o1 : 0u);
+    R vx = R(0), vy = R(0);
+    for (unsigned r = (unsigned)L.l >> 4; r < nr; r += 2) {
       const unsigned d = dep2(r, plo, phi);
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) {
-          const C e = T[(d | off[x]) * N + (d | off[y])];
-          v[2 * (x * 4 + y)] += e.x;
-          v[2 * (x * 4 + y) + 1] += e.y;
-        }
+      const C e = T[(d | ox) * N + (d | oy)];
+      vx += e.x;
+      vy += e.y;
     }
-#pragma unroll
-    for (int h = 16; h >= 1; h >>= 1) {
-      const bool up = (L.l & h) != 0;
-#pragma unroll
-      for (int i = 0; i < h; ++i) {
-        const R keep = up ? v[i + h] : v[i];
-        const R send = up ? v[i] : v[i + h];
-        v[i] = keep + __shfl_xor_sync(kFull, send, h);
-      }
-    }
-    const double acc = (double)v[0];
-    const int e = L.l & 15;
-    return make_double2(__shfl_sync(kFull, acc, 2 * e), __shfl_sync(kFull, acc, 2 * e + 1));
+    const double px = (double)vx, py = (double)vy;
+    return make_double2(px + __shfl_xor_sync(kFull, px, 16), py + __shfl_xor_sync(kFull, py, 16));
   }
 
   // 1 - |Tr T| / N (FP64 sum)

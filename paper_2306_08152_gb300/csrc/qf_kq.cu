@@ -616,17 +616,31 @@ constexpr int kPass8aThreads = 128;
 constexpr int kPass8aCtasPerSm = 4;
 constexpr int kBlkA = 65;
 
+// Operators as pairs of adjacent entries for 16-byte shared loads (each
+// load serves two output columns or rows): R2[k][c/2] = (R[k][c], R[k][c+1]),
+// LT2[k][r/2] = (L[r][k], L[r+1][k]).  Threads 0..31 fill entry t of each.
+__device__ __forceinline__ void load_op_pairs8(float4* R2, float4* LT2, const double2* L,
+                                               const double2* Rm, bool hr) {
+  const int t = threadIdx.x;
+  if (t < 32) {
+    const int k = t >> 2, c2 = (t & 3) * 2;
+    const double2 l0 = L[c2 * 8 + k], l1 = L[(c2 + 1) * 8 + k];
+    LT2[t] = make_float4((float)l0.x, (float)l0.y, (float)l1.x, (float)l1.y);
+    if (hr) {
+      const double2 r0 = Rm[k * 8 + c2], r1 = Rm[k * 8 + c2 + 1];
+      R2[t] = make_float4((float)r0.x, (float)r0.y, (float)r1.x, (float)r1.y);
+    }
+  }
+}
+
 template <bool HR>
 __global__ void __launch_bounds__(kPass8aThreads, kPass8aCtasPerSm)
 pass8a_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const double2* __restrict__ L,
               long long Ls, const double2* __restrict__ Rm, long long Rs) {
-  __shared__ float2 sL[64], sR[64];
+  __shared__ float4 sR2[32], sLT2[32];
   __shared__ float2 buf[kPass8aThreads / 32][16 * kBlkA];
   const int s = blockIdx.y;
-  if (threadIdx.x < 64) {
-    sL[threadIdx.x] = cmake(L[s * Ls + threadIdx.x], 0.f);
-    if (HR) sR[threadIdx.x] = cmake(Rm[s * Rs + threadIdx.x], 0.f);
-  }
+  load_op_pairs8(sR2, sLT2, L + s * Ls, HR ? Rm + s * Rs : nullptr, HR);
   __syncthreads();
   const unsigned N = 1u << n;
   int q[3] = {p0, p1, p2};  // ascending for the deposit
@@ -652,20 +666,27 @@ pass8a_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const doubl
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int y = 0; y < 8; ++y) v[i][y] = Ts[(size_t)(r0 | ox | off(2 * i)) * N + (c0 | off(y))];
-    if (HR) {  // rolled by two: the fully unrolled group body overflows the instruction cache
-#pragma unroll 2
-      for (int c = 0; c < 8; ++c) {
-        float2 a[4];
+    if (HR) {  // kept rolled: the fully unrolled group body overflows the instruction cache
+#pragma unroll 1
+      for (int c = 0; c < 8; c += 2) {
+        float2 a[4], b2[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = make_float2(0.f, 0.f);
+        for (int i = 0; i < 4; ++i) a[i] = b2[i] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const float2 r = sR[k * 8 + c];
+          const float4 r = sR2[k * 4 + c / 2];
+          const float2 r0 = make_float2(r.x, r.y), r1 = make_float2(r.z, r.w);
 #pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = cfma(v[i][k], r, a[i]);
+          for (int i = 0; i < 4; ++i) {
+            a[i] = cfma(v[i][k], r0, a[i]);
+            b2[i] = cfma(v[i][k], r1, b2[i]);
+          }
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) wb[(xh + 2 * i) * 8 + c] = a[i];
+        for (int i = 0; i < 4; ++i) {
+          wb[(xh + 2 * i) * 8 + c] = a[i];
+          wb[(xh + 2 * i) * 8 + c + 1] = b2[i];
+        }
       }
     } else {
 #pragma unroll
@@ -681,19 +702,26 @@ pass8a_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const doubl
 #pragma unroll
         for (int k = 0; k < 8; ++k) col[j][k] = wb[k * 8 + xh + 2 * j];
       __syncwarp();  // the buffer is rewritten by the next group
-#pragma unroll 2
-      for (int r = 0; r < 8; ++r) {
-        float2 a[4];
+#pragma unroll 1
+      for (int r = 0; r < 8; r += 2) {
+        float2 a[4], b2[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) a[j] = make_float2(0.f, 0.f);
+        for (int j = 0; j < 4; ++j) a[j] = b2[j] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const float2 l = sL[r * 8 + k];
+          const float4 l = sLT2[k * 4 + r / 2];
+          const float2 l0 = make_float2(l.x, l.y), l1 = make_float2(l.z, l.w);
 #pragma unroll
-          for (int j = 0; j < 4; ++j) a[j] = cfma(l, col[j][k], a[j]);
+          for (int j = 0; j < 4; ++j) {
+            a[j] = cfma(l0, col[j][k], a[j]);
+            b2[j] = cfma(l1, col[j][k], b2[j]);
+          }
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) Ts[(size_t)(r0 | off(r)) * N + (c0 | ox | off(2 * j))] = a[j];
+        for (int j = 0; j < 4; ++j) {
+          Ts[(size_t)(r0 | off(r)) * N + (c0 | ox | off(2 * j))] = a[j];
+          Ts[(size_t)(r0 | off(r + 1)) * N + (c0 | ox | off(2 * j))] = b2[j];
+        }
       }
     }
   }
@@ -723,13 +751,10 @@ template <bool HR>
 __global__ void __launch_bounds__(kPass8cThreads, kPass8cCtasPerSm)
 pass8c_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const double2* __restrict__ L,
               long long Ls, const double2* __restrict__ Rm, long long Rs, unsigned phx, unsigned phh) {
-  __shared__ float2 sL[64], sR[64];
+  __shared__ float4 sR2[32], sLT2[32];
   __shared__ float2 buf[kPass8cThreads / 32][512];
   const int s = blockIdx.y;
-  if (threadIdx.x < 64) {
-    sL[threadIdx.x] = cmake(L[s * Ls + threadIdx.x], 0.f);
-    if (HR) sR[threadIdx.x] = cmake(Rm[s * Rs + threadIdx.x], 0.f);
-  }
+  load_op_pairs8(sR2, sLT2, L + s * Ls, HR ? Rm + s * Rs : nullptr, HR);
   __syncthreads();
   const unsigned N = 1u << n;
   int q[3] = {p0, p1, p2};  // ascending for the deposit
@@ -773,18 +798,23 @@ pass8c_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const doubl
         ia[y] = tb[slot(xa, c)];
         ib[y] = tb[slot(xa + 4, c)];
       }
-#pragma unroll 2
-      for (int c = 0; c < 8; ++c) {
-        float2 a = make_float2(0.f, 0.f), b = a;
+#pragma unroll 1
+      for (int c = 0; c < 8; c += 2) {
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
 #pragma unroll
         for (int y = 0; y < 8; ++y) {
-          const float2 r = sR[y * 8 + c];
-          a = cfma(ia[y], r, a);
-          b = cfma(ib[y], r, b);
+          const float4 r = sR2[y * 4 + c / 2];
+          const float2 r0 = make_float2(r.x, r.y), r1 = make_float2(r.z, r.w);
+          a0 = cfma(ia[y], r0, a0);
+          a1 = cfma(ia[y], r1, a1);
+          b0 = cfma(ib[y], r0, b0);
+          b1 = cfma(ib[y], r1, b1);
         }
-        const unsigned cc = cj | off(c);
-        tb[slot(xa, cc)] = a;
-        tb[slot(xa + 4, cc)] = b;
+        const unsigned cc0 = cj | off(c), cc1 = cj | off(c + 1);
+        tb[slot(xa, cc0)] = a0;
+        tb[slot(xa, cc1)] = a1;
+        tb[slot(xa + 4, cc0)] = b0;
+        tb[slot(xa + 4, cc1)] = b1;
       }
       __syncwarp();
     }
@@ -795,16 +825,20 @@ pass8c_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, const doubl
       co[k] = tb[slot(k, 2u * lane + 1u)];
     }
     __syncwarp();  // the buffer is rewritten by the next tile
-#pragma unroll 2
-    for (int r = 0; r < 8; ++r) {
-      float2 a = make_float2(0.f, 0.f), b = a;
+#pragma unroll 1
+    for (int r = 0; r < 8; r += 2) {
+      float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const float2 l = sL[r * 8 + k];
-        a = cfma(l, ce[k], a);
-        b = cfma(l, co[k], b);
+        const float4 l = sLT2[k * 4 + r / 2];
+        const float2 l0 = make_float2(l.x, l.y), l1 = make_float2(l.z, l.w);
+        a0 = cfma(l0, ce[k], a0);
+        b0 = cfma(l0, co[k], b0);
+        a1 = cfma(l1, ce[k], a1);
+        b1 = cfma(l1, co[k], b1);
       }
-      *reinterpret_cast<float4*>(Ts + (size_t)(r0 | off(r)) * N + cb) = make_float4(a.x, a.y, b.x, b.y);
+      *reinterpret_cast<float4*>(Ts + (size_t)(r0 | off(r)) * N + cb) = make_float4(a0.x, a0.y, b0.x, b0.y);
+      *reinterpret_cast<float4*>(Ts + (size_t)(r0 | off(r + 1)) * N + cb) = make_float4(a1.x, a1.y, b1.x, b1.y);
     }
   }
 }

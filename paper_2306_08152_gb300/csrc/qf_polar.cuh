@@ -121,63 +121,67 @@ __device__ __forceinline__ void polish4(const Lane& L, double2& w, double2& y, d
   }
 }
 
+// a[k] for a warp-uniform k without a dynamically indexed (local) array
+__device__ __forceinline__ double pick4(const double* a, int k) {
+  return k == 0 ? a[0] : k == 1 ? a[1] : k == 2 ? a[2] : a[3];
+}
+
 // X for the rare path: the columns of W whose norm s[k] is above 1e-13 of
 // the largest, normalised, in order of decreasing s, each orthogonalised
 // (twice, Kahan) against those before it; the others completed to an
-// orthonormal basis with the standard basis vectors.  FP64; every lane
-// computes the whole matrix (no shared memory) and returns its element.
+// orthonormal basis with the standard basis vectors.  FP64, on the lane
+// layout: the candidate column is held by every lane as its row's entry
+// v_i, column sums run over the rows with two shuffles, and the lanes of
+// column k keep the result.  Returns the lane's element of X.
 __device__ __forceinline__ double2 complete4(const Lane& L, double2 w, const double* s, double smax) {
-  double2 W[16];
-#pragma unroll
-  for (int e = 0; e < 16; ++e) W[e] = shfl(w, e);
   int ord[4] = {0, 1, 2, 3};
+#pragma unroll
   for (int a = 0; a < 4; ++a)
+#pragma unroll
     for (int b = 0; b < 3 - a; ++b)
-      if (s[ord[b]] < s[ord[b + 1]]) {
+      if (pick4(s, ord[b]) < pick4(s, ord[b + 1])) {
         const int t = ord[b];
         ord[b] = ord[b + 1];
         ord[b + 1] = t;
       }
-  double2 X[16];
-  bool done[4] = {false, false, false, false};
-  for (int e = 0; e < 16; ++e) X[e] = make_double2(0.0, 0.0);
+  double2 x = make_double2(0.0, 0.0);
+  unsigned done = 0u;
+#pragma unroll 1
   for (int oi = 0; oi < 4; ++oi) {
-    const int k = ord[oi];
+    const int k = oi == 0 ? ord[0] : oi == 1 ? ord[1] : oi == 2 ? ord[2] : ord[3];
+    const double sk = pick4(s, k);
+    const double2 wk = shfl(w, L.at(L.i, k));  // W[i][k]
+#pragma unroll 1
     for (int att = 0; att < 5; ++att) {
-      double2 v[4];
+      double2 v;
       if (att == 0) {
-        if (!(s[k] > 1e-13 * smax)) continue;  // numerically zero: complete instead
-        const double inv = 1.0 / s[k];
-        for (int i = 0; i < 4; ++i) v[i] = make_double2(W[i * 4 + k].x * inv, W[i * 4 + k].y * inv);
+        if (!(sk > 1e-13 * smax)) continue;  // numerically zero: complete instead
+        const double inv = 1.0 / sk;
+        v = make_double2(wk.x * inv, wk.y * inv);
       } else {
-        for (int i = 0; i < 4; ++i) v[i] = make_double2(i == att - 1 ? 1.0 : 0.0, 0.0);
+        v = make_double2(L.i == att - 1 ? 1.0 : 0.0, 0.0);
       }
+#pragma unroll 1
       for (int pass = 0; pass < 2; ++pass)
+#pragma unroll 1
         for (int jj = 0; jj < 4; ++jj) {
-          if (!done[jj]) continue;
-          double2 d = make_double2(0.0, 0.0);
-          for (int i = 0; i < 4; ++i) d = cfma_cj(X[i * 4 + jj], v[i], d);
-          for (int i = 0; i < 4; ++i) {
-            const double2 pr = cmul(d, X[i * 4 + jj]);
-            v[i].x -= pr.x;
-            v[i].y -= pr.y;
-          }
+          if (!(done & (1u << jj))) continue;
+          const double2 xj = shfl(x, L.at(L.i, jj));  // X[i][jj]
+          const double2 t = cfma_cj(xj, v, make_double2(0.0, 0.0));
+          const double2 d = make_double2(colsum4(t.x), colsum4(t.y));
+          const double2 pr = cmul(d, xj);
+          v.x -= pr.x;
+          v.y -= pr.y;
         }
-      double nv = 0.0;
-      for (int i = 0; i < 4; ++i) nv += v[i].x * v[i].x + v[i].y * v[i].y;
-      nv = sqrt(nv);
+      const double nv = sqrt(colsum4(v.x * v.x + v.y * v.y));
       if (nv > 0.4) {  // among e_0..e_3 one keeps a residual of at least 1/2
-        for (int i = 0; i < 4; ++i) X[i * 4 + k] = make_double2(v[i].x / nv, v[i].y / nv);
-        done[k] = true;
+        if (L.j == k) x = make_double2(v.x / nv, v.y / nv);
+        done |= 1u << k;
         break;
       }
     }
   }
-  double2 out = make_double2(0.0, 0.0);
-#pragma unroll
-  for (int e = 0; e < 16; ++e)
-    if (e == L.i * 4 + L.j) out = X[e];
-  return out;
+  return x;
 }
 
 // Stage 3 (rare): A (scaled, FP64) has a singular value below 1e-3 of the
