@@ -20,6 +20,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "qf_device.cuh"
 #include "qf_internal.h"
 
@@ -584,16 +586,186 @@ pass16_kernel(typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, int p2
   }
 }
 
+// complex64 version for the FP32 pipe.  In the kernel above every complex
+// multiply-add waits on one shared-memory operator load, which keeps the
+// FP32 pipe below a third busy.  Here a lane holds row x of two blocks of a
+// four-block group and each 16-byte operator load brings two adjacent
+// operator entries, so one load serves four complex multiply-adds (16
+// FMAs): R is read as (R[k][c], R[k][c+1]) pairs, L from a transposed copy
+// as (L[r][k], L[r+1][k]) pairs.  With kPair (no gate bit at 0, n >= 5) the
+// lane's two blocks are adjacent column rests 2m and 2m + 1, whose entries
+// sit side by side: every global load and store is one 16-byte access of
+// both blocks.  Otherwise the blocks are b and b + 2 and take 8-byte
+// accesses.  The output loops stay rolled: unrolled, the body overflows
+// the instruction cache.
+constexpr int kPass16cBlocks = 4;  // blocks per warp and group
+
+template <bool HL, bool HR, bool kPair>
+__global__ void __launch_bounds__(kPass16Threads)
+pass16c_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, int p3,
+               const double2* __restrict__ L, long long Ls, const double2* __restrict__ Rm,
+               long long Rs) {
+  __shared__ float4 sR2[16 * 8];   // [k][c/2]: (R[k][c], R[k][c+1])
+  __shared__ float4 sLT2[16 * 8];  // [k][r/2]: (L[r][k], L[r+1][k])
+  __shared__ float2 buf[kPass16Threads / 32][kPass16cBlocks * kBlk16];
+  const int s = blockIdx.y;
+  for (int e = threadIdx.x; e < 128; e += kPass16Threads) {
+    const int k = e >> 3, c2 = (e & 7) * 2;
+    if (HR) {
+      const double2 a = Rm[s * Rs + k * 16 + c2], b = Rm[s * Rs + k * 16 + c2 + 1];
+      sR2[e] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+    }
+    if (HL) {
+      const double2 a = L[s * Ls + c2 * 16 + k], b = L[s * Ls + (c2 + 1) * 16 + k];
+      sLT2[e] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+    }
+  }
+  __syncthreads();
+  const int p[4] = {p0, p1, p2, p3};
+  int qs[4];
+  sort4(p, qs);
+  unsigned off[16];  // constant indices only
+#pragma unroll
+  for (int v = 0; v < 16; ++v) off[v] = off16(v, p);
+  const unsigned N = 1u << n;
+  const int lnc = n - 4;
+  const unsigned cmask = (1u << lnc) - 1u;
+  const unsigned nblk = 1u << (2 * lnc);
+  float2* __restrict__ Ts = T + (size_t)s * N * N;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = lane >> 4, x = lane & 15;
+  const unsigned offx = off16(x, p);
+  // the lane's blocks within the group: (2b, 2b + 1) paired, else (b, b + 2)
+  const unsigned oa = kPair ? 2u * (unsigned)b : (unsigned)b, ob = kPair ? oa + 1u : oa + 2u;
+  float2* wa = buf[w] + oa * kBlk16;
+  float2* wbb = buf[w] + ob * kBlk16;
+  const unsigned warps = gridDim.x * (kPass16Threads / 32);
+  for (unsigned grp = blockIdx.x * (kPass16Threads / 32) + w; grp * kPass16cBlocks < nblk; grp += warps) {
+    const unsigned ba = grp * kPass16cBlocks + oa, bb2 = grp * kPass16cBlocks + ob;
+    const bool va = ba < nblk, vb = bb2 < nblk;  // both true with kPair (nblk >= 4)
+    const unsigned ra = dep4(ba >> lnc, qs), ca = dep4(ba & cmask, qs);
+    const unsigned rb = dep4(bb2 >> lnc, qs), cb = dep4(bb2 & cmask, qs);
+    // with kPair: rb = ra and cb = ca + 1 (block 2m + 1 differs in column bit 0)
+    float2 xa[16], xb[16];
+    if (kPair) {
+      const float2* sa = Ts + (size_t)(ra | offx) * N + ca;
+#pragma unroll
+      for (int y = 0; y < 16; ++y) {
+        const float4 v = *reinterpret_cast<const float4*>(sa + off[y]);
+        xa[y] = make_float2(v.x, v.y);
+        xb[y] = make_float2(v.z, v.w);
+      }
+    } else {
+      const float2* sa = Ts + (size_t)(ra | offx) * N + ca;
+      const float2* sb = Ts + (size_t)(rb | offx) * N + cb;
+#pragma unroll
+      for (int y = 0; y < 16; ++y) {
+        xa[y] = va ? sa[off[y]] : make_float2(0.f, 0.f);
+        xb[y] = vb ? sb[off[y]] : make_float2(0.f, 0.f);
+      }
+    }
+    if (HR) {  // rows <- rows R, two output columns per operator load
+#pragma unroll 1
+      for (int c = 0; c < 16; c += 2) {
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float4 r = sR2[k * 8 + c / 2];
+          const float2 r0 = make_float2(r.x, r.y), r1 = make_float2(r.z, r.w);
+          a0 = cfma(xa[k], r0, a0);
+          a1 = cfma(xa[k], r1, a1);
+          b0 = cfma(xb[k], r0, b0);
+          b1 = cfma(xb[k], r1, b1);
+        }
+        if (HL) {
+          wa[x * 17 + c] = a0;
+          wa[x * 17 + c + 1] = a1;
+          wbb[x * 17 + c] = b0;
+          wbb[x * 17 + c + 1] = b1;
+        } else if (kPair) {
+          const unsigned c0 = off16(c, p), c1 = off16(c + 1, p);
+          *reinterpret_cast<float4*>(Ts + (size_t)(ra | offx) * N + (ca | c0)) = make_float4(a0.x, a0.y, b0.x, b0.y);
+          *reinterpret_cast<float4*>(Ts + (size_t)(ra | offx) * N + (ca | c1)) = make_float4(a1.x, a1.y, b1.x, b1.y);
+        } else {
+          const unsigned c0 = off16(c, p), c1 = off16(c + 1, p);
+          if (va) {
+            Ts[(size_t)(ra | offx) * N + (ca | c0)] = a0;
+            Ts[(size_t)(ra | offx) * N + (ca | c1)] = a1;
+          }
+          if (vb) {
+            Ts[(size_t)(rb | offx) * N + (cb | c0)] = b0;
+            Ts[(size_t)(rb | offx) * N + (cb | c1)] = b1;
+          }
+        }
+      }
+    } else if (HL) {
+#pragma unroll
+      for (int y = 0; y < 16; ++y) {
+        wa[x * 17 + y] = xa[y];
+        wbb[x * 17 + y] = xb[y];
+      }
+    }
+    if (HL) {
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {  // column x of both blocks
+        xa[k] = wa[k * 17 + x];
+        xb[k] = wbb[k * 17 + x];
+      }
+      __syncwarp();  // the buffers are rewritten by the next group
+#pragma unroll 1
+      for (int r = 0; r < 16; r += 2) {
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float4 l = sLT2[k * 8 + r / 2];
+          const float2 l0 = make_float2(l.x, l.y), l1 = make_float2(l.z, l.w);
+          a0 = cfma(l0, xa[k], a0);
+          a1 = cfma(l1, xa[k], a1);
+          b0 = cfma(l0, xb[k], b0);
+          b1 = cfma(l1, xb[k], b1);
+        }
+        const unsigned r0o = off16(r, p), r1o = off16(r + 1, p);
+        if (kPair) {
+          *reinterpret_cast<float4*>(Ts + (size_t)(ra | r0o) * N + (ca | offx)) = make_float4(a0.x, a0.y, b0.x, b0.y);
+          *reinterpret_cast<float4*>(Ts + (size_t)(ra | r1o) * N + (ca | offx)) = make_float4(a1.x, a1.y, b1.x, b1.y);
+        } else {
+          if (va) {
+            Ts[(size_t)(ra | r0o) * N + (ca | offx)] = a0;
+            Ts[(size_t)(ra | r1o) * N + (ca | offx)] = a1;
+          }
+          if (vb) {
+            Ts[(size_t)(rb | r0o) * N + (cb | offx)] = b0;
+            Ts[(size_t)(rb | r1o) * N + (cb | offx)] = b1;
+          }
+        }
+      }
+    }
+  }
+}
+
 template <typename R, bool HL, bool HR>
 void pass16_launch(void* T, int n, int S, const int* p, const double2* L, long long Ls,
                    const double2* Rm, long long Rs, cudaStream_t st) {
   typedef typename Cplx<R>::T C;
-  const long long groups = ((1ll << (2 * (n - 4))) + 1) / 2;
+  const int per_group = std::is_same<R, float>::value ? kPass16cBlocks : 2;
+  const long long groups = ((1ll << (2 * (n - 4))) + per_group - 1) / per_group;
   const long long want = (groups + 3) / 4;
   long long cap = ((long long)sm_count() * 8 + S - 1) / S;
   if (cap < 1) cap = 1;
   dim3 grid((unsigned)(want < cap ? want : cap), S);
-  pass16_kernel<R, HL, HR><<<grid, kPass16Threads, 0, st>>>((C*)T, n, p[0], p[1], p[2], p[3], L, Ls, Rm, Rs);
+  if constexpr (std::is_same<R, float>::value) {
+    // adjacent block pairs when column bit 0 is a rest bit (and n >= 5)
+    const bool pair = n >= 5 && p[0] != 0 && p[1] != 0 && p[2] != 0 && p[3] != 0;
+    if (pair)
+      pass16c_kernel<HL, HR, true><<<grid, kPass16Threads, 0, st>>>((float2*)T, n, p[0], p[1], p[2], p[3], L, Ls,
+                                                                    Rm, Rs);
+    else
+      pass16c_kernel<HL, HR, false><<<grid, kPass16Threads, 0, st>>>((float2*)T, n, p[0], p[1], p[2], p[3], L,
+                                                                     Ls, Rm, Rs);
+  }
+  else
+    pass16_kernel<R, HL, HR><<<grid, kPass16Threads, 0, st>>>((C*)T, n, p[0], p[1], p[2], p[3], L, Ls, Rm, Rs);
 }
 
 template <typename R>
