@@ -219,6 +219,21 @@ def measured_alu_peaks(torch, dev):
     return _ALU_PEAKS
 
 
+def batched_pipes():
+    """Pipe fractions of the batched kernel from a committed ncu summary,
+    if it was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "batched_kernel_pipes.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    for src, h in d.get("kernel_sources", {}).items():
+        with open(os.path.join(ROOT, src), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != h:
+                return None
+    return d
+
+
 def kernel_traffic(precision, starts, n):
     """DRAM bytes per pass launch from a committed ncu summary, if it was
     taken on the current kernel source; else None."""
@@ -431,6 +446,7 @@ def run_batched(args, qf, torch, dev):
         "precision": "complex64 sweeps, FP64 4x4 updates, complex128 refinement",
         "workload": f"{len(probs)} reachable instances, 3/4/5 qubits 2:1:1, 5-40 U(4) gates on random "
                     "adjacent pairs, 4 Haar starts, tol 1e-10, <=500 sweeps",
+        "roofline": batched_roofline(),
         "success_c128": {"success": ok128, "value": ok128 / wall128, "wall_s": wall128,
                          "kernel_ms": res128["kernel_ms"], "sweeps": res128["total_sweeps"],
                          "success_in_both": both,
@@ -441,6 +457,23 @@ def run_batched(args, qf, torch, dev):
                                     "success": ok_plain, "sample": len(sample), "wall_s": wall_plain,
                                     "path": "qf_instantiate_ex per instance, complex128, 4 starts"},
     }
+
+
+def batched_roofline():
+    """The batched kernel runs whole small problems per warp with the
+    tensors in shared memory: no HBM bound; the FP64 pipe (the 4x4 updates'
+    refinement) is the busiest unit.  Fractions from the committed capture
+    of the same kernel source (null if the source changed since)."""
+    d = batched_pipes()
+    if d is None:
+        return None
+    return {"bound": "alu", "unit": "fraction of pipe cycles", "peak": 1.0,
+            "achieved": d["fp64_pipe_active_frac"], "frac": d["fp64_pipe_active_frac"],
+            "pipe": "FP64", "fp64_pipe_active_frac": d["fp64_pipe_active_frac"],
+            "fp64_pipe_elapsed_frac": d["fp64_pipe_elapsed_frac"],
+            "fp32_fma_pipe_active_frac": d["fma_pipe_active_frac"],
+            "sm_active_frac_of_elapsed": d["sm_active_frac_of_elapsed"],
+            "source": "ncu capture (profiles/batched_kernel_pipes.json): " + d["capture"]}
 
 
 def run_c128(args, qf, torch, dev, inst, V, starts):

@@ -277,7 +277,7 @@ __device__ bool plateau_test(const double* ring, int len, int it, const BatchPar
 // is the method's own plateau and the start stays in complex64.
 constexpr double kStallSwitchCost = 1e-5;
 
-__global__ void batched_kernel(BatchParams bp) {
+__global__ void __maxnreg__(168) batched_kernel(BatchParams bp) {
   extern __shared__ __align__(256) unsigned char smem[];
   const int wid = threadIdx.x >> 5;
   unsigned char* ws = smem + (size_t)wid * bp.warp_bytes;
