@@ -5,7 +5,8 @@ kernels and passes run on two internal streams, the plan's first sweep runs
 as live launches and the second as a replay of the captured CUDA graph.
 
 From 11 qubits the environment kernel splits each start's band over several
-CTAs (2 at 11 qubits, 4 at 12, 8 at 13): every CTA writes its partial sums,
+CTAs (2 at 11 qubits, 4 at 12, 8 at 13; a shorter 13-qubit circuit checks the
+last): every CTA writes its partial sums,
 the last CTA to finish (atomic ticket) adds them in a fixed order and runs
 the FP64 4x4 update in its epilogue.  Smaller circuits use one CTA per start,
 so only these sizes check that path inside a whole sweep.
@@ -201,3 +202,36 @@ def test_partial_trace_multi_cta_matches_oracle(qf, n, S, dtype):
             else:  # FP32 band sums within a CTA: 1e-6 of the sum of magnitudes
                 bound = 1e-6 * orc.calc_env_mat(np.abs(Ts).astype(np.complex128), a, b, n).real
                 assert np.all(np.abs(P[s] - ref) <= bound), (a, b, s)
+
+
+
+@pytest.fixture(scope="module")
+def p13():
+    # 13 qubits (8 CTAs per start in the environment kernel), brickwork of 2
+    # layers (12 gates), 2 starts; oracle on the second start (second group)
+    n = 13
+    locs = qi.brickwork_locations(n, 2)
+    inst = qi.make_problem(n, locs, 2, seed=1313)
+    V = orc.circuit_unitary(inst.target_gates, locs, n)
+    ref = _oracle_trajectory(V, inst.starts[1], locs, n, SWEEPS)
+    return n, locs, inst, V, ref
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_sweeps_13q_match_oracle(qf, p13, prec):
+    n, locs, inst, V, ref = p13
+    plan = qf.Plan(n, locs, 2, qf.QF_C128 if prec == "c128" else qf.QF_C64)
+    plan.load(torch.from_numpy(V).cuda(), torch.from_numpy(inst.starts).cuda())
+    for it in range(SWEEPS):
+        plan.sweep(1, reset_iter=0)  # sweep 1 live, sweep 2 a graph replay
+        costs, gates = plan.costs(), plan.gates().numpy()
+        c_ref, g_ref = ref[it]
+        dc = abs(costs[1] - c_ref)
+        dg = float(np.max(np.abs(gates[1] - g_ref)))
+        print(f"{prec} n=13 sweep {it + 1} start 1: |dcost| {dc:.2e} max|dgate| {dg:.2e}")
+        if prec == "c128":
+            assert dc <= 1e-10 and dg <= 1e-9, (it, dc, dg)
+        else:  # measured on a GB300: 1.2e-7 and 2.3e-7 after two sweeps
+            assert dc <= 1e-6 and dg <= C64_GATE_TOL, (it, dc, dg)
+    assert plan.status() == 0
+    plan.close()
