@@ -292,6 +292,20 @@ int qf_instantiate_k(const qf_c128* target, int n_qubits, int n_gates,
                      qf_c128* out_gates, double* out_costs,
                      qf_result* out_result, void* stream);
 
+/* qf_cost_and_env / qf_cost_grad for a circuit of 2-, 3- and 4-qubit gates
+ * (the same adjoint walk; Sec. III: Tr(V^dagger C) = Tr(E_k u_k) for a gate
+ * of any size, E_k its 2^k x 2^k environment).  gates, out_env and out_grad:
+ * host-or-device, n_sets x E entries in the concatenated layout above;
+ * out_cost, out_trace: host, n_sets each (may be NULL).  The gradient is
+ * -(t_s / (N |t_s|)) E_{s,k}^dagger for every gate, in the convention of
+ * PyTorch's complex autograd (d/dRe + i d/dIm).  Synchronises `stream`. */
+int qf_cost_and_env_k(const qf_c128* target, int n_qubits, int n_gates,
+                      const qf_gate_loc* locations, int n_sets, const qf_c128* gates,
+                      double* out_cost, qf_c128* out_env, qf_c128* out_trace, void* stream);
+int qf_cost_grad_k(const qf_c128* target, int n_qubits, int n_gates,
+                   const qf_gate_loc* locations, int n_sets, const qf_c128* gates,
+                   double* out_cost, qf_c128* out_grad, void* stream);
+
 /* Steps for one gate of size k (parity tests; enqueue only):
  *   qf_apply_gate_k     T_s <- (L_s on q) T_s (R_s on q); L, R device
  *                       n_starts x 4^k (either may be NULL for identity).

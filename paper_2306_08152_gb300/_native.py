@@ -103,6 +103,8 @@ SIGNATURES = {
                               ct.POINTER(qf_result), P]),
     "qf_cost_and_env": (I, [P, I, I, P, I, P, DP, P, P, P]),
     "qf_cost_grad": (I, [P, I, I, P, I, P, DP, P, P]),
+    "qf_cost_and_env_k": (I, [P, I, I, P, I, P, DP, P, P, P]),
+    "qf_cost_grad_k": (I, [P, I, I, P, I, P, DP, P, P]),
     "qf_instantiate_batched": (I, [I, P, P, P, P, I, P, ct.POINTER(qf_options), P, DP, P, P,
                                    ct.POINTER(qf_batch_stats), P]),
     "qf_plan_create": (I, [I, I, P, I, I, ct.POINTER(P)]),

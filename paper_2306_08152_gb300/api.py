@@ -22,7 +22,7 @@ __all__ = [
     "partial_trace", "partial_trace_noalloc", "apply_two_pairs", "partial_trace_after", "convert_tensor",
     "instantiate_k", "apply_gate_k", "partial_trace_k", "optimize_gates_k", "init_tensor_k",
     "circuit_unitary_k", "flatten_gates", "unflatten_gates", "gate_entries", "optimize_gates", "reunitarize_gates", "trace", "circuit_unitary",
-    "gate_specs", "spec_slots", "instantiate_spec",
+    "gate_specs", "spec_slots", "instantiate_spec", "cost_and_env_k", "cost_grad_k",
 ]
 
 QF_C128 = nat.QF_C128
@@ -331,6 +331,59 @@ def cost_grad(target, locations, gates, stream=None):
     costs = (ct.c_double * S)()
     check(_lib().qf_cost_grad(_ptr(target), n, p, _ptr(locs), S, _ptr(g), costs, _ptr(grads),
                               _stream_handle(stream)))
+    c = np.array(costs[:])
+    if single:
+        return c[0], grads[0]
+    return c, grads
+
+
+def _flat_sets(gates, locs):
+    """(S, E) complex128 gate sets from a tensor (S, E) / (E,) or S lists."""
+    if not isinstance(gates, torch.Tensor):
+        gates = flatten_gates(gates)
+    g = _c128(gates, "gates")
+    single = g.dim() == 1
+    if single:
+        g = g.unsqueeze(0)
+    if g.shape[1] != gate_entries(locs):
+        raise ValueError("gates do not match the locations' gate sizes")
+    return g.contiguous(), single
+
+
+def cost_and_env_k(target, locations, gates, stream=None):
+    """Costs, environments and traces of gate sets of 2-, 3- and 4-qubit
+    gates (qf_cost_and_env_k).  ``gates``: (S, E) concatenated layout, (E,),
+    or S lists of arrays.  Returns (costs (S,), envs like the (S, E) gates,
+    traces (S,) complex)."""
+    target = _c128(target, "target")
+    larr, locs = _gate_locs(locations)
+    g, single = _flat_sets(gates, locs)
+    n = _nqubits(target)
+    S = g.shape[0]
+    envs = torch.empty_like(g)
+    costs = (ct.c_double * S)()
+    trs = np.zeros(S, dtype=np.complex128)
+    check(_lib().qf_cost_and_env_k(_ptr(target), n, len(locs), larr, S, _ptr(g), costs, _ptr(envs),
+                                   ct.c_void_p(trs.ctypes.data), _stream_handle(stream)))
+    c = np.array(costs[:])
+    if single:
+        return c[0], envs[0], trs[0]
+    return c, envs, trs
+
+
+def cost_grad_k(target, locations, gates, stream=None):
+    """Costs and gradients for gate sets of 2-, 3- and 4-qubit gates
+    (qf_cost_grad_k), in PyTorch's complex-autograd convention; gates and
+    gradients in the concatenated layout (S, E) (or (E,))."""
+    target = _c128(target, "target")
+    larr, locs = _gate_locs(locations)
+    g, single = _flat_sets(gates, locs)
+    n = _nqubits(target)
+    S = g.shape[0]
+    grads = torch.empty_like(g)
+    costs = (ct.c_double * S)()
+    check(_lib().qf_cost_grad_k(_ptr(target), n, len(locs), larr, S, _ptr(g), costs, _ptr(grads),
+                                _stream_handle(stream)))
     c = np.array(costs[:])
     if single:
         return c[0], grads[0]

@@ -16,16 +16,27 @@ from . import api
 
 
 class QFactorCost(torch.autograd.Function):
+    """``locations`` of qubit pairs take gates (S, p, 4, 4) or (p, 4, 4);
+    locations with 3- or 4-qubit gates take the concatenated layout (S, E)
+    or (E,) (qf_cost_grad_k)."""
+
     @staticmethod
     def forward(ctx, gates, target, locations):
-        single = gates.dim() == 3
+        pairs = api._is_pairs(locations)
+        single = gates.dim() == (3 if pairs else 1)
         if ctx.needs_input_grad[0]:
-            c, g = api.cost_grad(target, locations, gates.detach())
+            if pairs:
+                c, g = api.cost_grad(target, locations, gates.detach())
+            else:
+                c, g = api.cost_grad_k(target, locations, gates.detach())
             ctx.save_for_backward(g)
         else:
-            c = api.costs(target, locations, gates.detach())
-            if single:
-                c = c[0]
+            if pairs:
+                c = api.costs(target, locations, gates.detach())
+                if single:
+                    c = c[0]
+            else:
+                c = api.cost_and_env_k(target, locations, gates.detach())[0]
         ctx.single = single
         return torch.as_tensor(c, dtype=torch.float64, device=gates.device)
 
@@ -35,7 +46,7 @@ class QFactorCost(torch.autograd.Function):
         scale = grad_out.to(g.device, torch.float64)
         if ctx.single:
             return g * scale, None, None
-        return g * scale.reshape(-1, 1, 1, 1), None, None
+        return g * scale.reshape((-1,) + (1,) * (g.dim() - 1)), None, None
 
 
 def qfactor_cost(gates, target, locations):

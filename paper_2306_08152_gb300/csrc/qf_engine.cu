@@ -1354,16 +1354,20 @@ namespace {
 // tensor, take its trace, then move each gate from the tensor's right to its
 // left (one pass, L = u, R = u^dagger), reading its environment on the way.
 // With `grad`, the environments are turned into cost gradients on the device.
-int adjoint_walk(const qf_c128* target, int n_qubits, int n_gates, const qf_loc* locations,
-                 int n_sets, const qf_c128* gates, double* out_cost, qf_c128* out_env,
-                 qf_c128* out_trace, bool grad, void* stream) {
-  QF_TRY(check_sizes(n_qubits, n_gates));
+// The adjoint walk: build T = V^dagger C once, then for k = p-1 .. 0 read the
+// environment of gate k (still on T's right: E_k = P u^dagger, kEnvOnly) and
+// move the gate to T's left with one pass (L = u, R = u^dagger), so that
+// T = G_k..G_{p-1} V^dagger G_0..G_{k-1} when gate k-1 is read.
+int adjoint_walk_desc(const qf_c128* target, int n_qubits, const std::vector<GateDesc>& gd,
+                      long long gsz, int n_sets, const qf_c128* gates, double* out_cost,
+                      qf_c128* out_env, qf_c128* out_trace, bool grad, void* stream) {
+  QF_TRY(check_sizes(n_qubits, (int)gd.size()));
   if (n_sets < 1) return set_error(QF_EINVAL, "n_sets=%d must be >= 1", n_sets);
   if (!out_env) return set_error(QF_EINVAL, "output array is NULL");
   cudaStream_t st = as_stream(stream);
-  const int S = n_sets, p = n_gates;
+  const int S = n_sets, p = (int)gd.size();
   PlanGuard g;
-  QF_TRY(plan_create_impl(n_qubits, p, locations, S, QF_C128, &g.p));
+  QF_TRY(plan_create_desc(n_qubits, gd, gsz, S, QF_C128, &g.p));
   qf_plan* P = g.p;
   QF_TRY(plan_load_impl(P, target, gates, st));
   std::vector<double> c(S);
@@ -1372,7 +1376,7 @@ int adjoint_walk(const qf_c128* target, int n_qubits, int n_gates, const qf_loc*
   // environments land in a device buffer laid out like out_env
   DevBuf envb;
   double2* env_dev = nullptr;
-  const size_t ecount = (size_t)S * p * 16;
+  const size_t ecount = (size_t)S * gsz;
   const bool out_on_device = is_device_ptr(out_env);
   if (out_on_device) {
     env_dev = reinterpret_cast<double2*>(out_env);
@@ -1380,15 +1384,17 @@ int adjoint_walk(const qf_c128* target, int n_qubits, int n_gates, const qf_loc*
     QF_TRY(envb.alloc(ecount * sizeof(double2)));
     env_dev = envb.as<double2>();
   }
-  const double2* LR = P->LR.as<double2>();
   for (int k = p - 1; k >= 0; --k) {
-    QF_TRY(plan_update(P, all_starts(P), k, qf::kEnvOnly, 0.0, env_dev + (size_t)k * 16,
-                       (long long)p * 16));
-    if (k > 0)
-      QF_TRY(plan_pass(P, all_starts(P), P->locs[k].a, P->locs[k].b, LR, 32, LR + 16, 32));
+    QF_TRY(plan_update(P, all_starts(P), k, qf::kEnvOnly, 0.0, env_dev + gd[k].off, gsz));
+    if (k > 0) QF_TRY(plan_gate_pass(P, all_starts(P), k));
   }
-  if (grad)
-    QF_CUDA(qf::launch_grad_from_env(env_dev, P->tr.as<double2>(), n_qubits, S, p, st));
+  if (grad) {
+    if (P->mixed)
+      QF_CUDA(qf::launch_grad_from_env_k(env_dev, P->tr.as<double2>(), n_qubits, S, gsz,
+                                         P->gdesc.as<int2>(), p, st));
+    else
+      QF_CUDA(qf::launch_grad_from_env(env_dev, P->tr.as<double2>(), n_qubits, S, p, st));
+  }
   if (!out_on_device)
     QF_CUDA(cudaMemcpyAsync(out_env, env_dev, ecount * sizeof(double2), cudaMemcpyDeviceToHost,
                             st));
@@ -1398,6 +1404,30 @@ int adjoint_walk(const qf_c128* target, int n_qubits, int n_gates, const qf_loc*
   if (out_trace)
     for (int s = 0; s < S; ++s) out_trace[s] = tr[s];
   return QF_OK;
+}
+
+int adjoint_walk(const qf_c128* target, int n_qubits, int n_gates, const qf_loc* locations,
+                 int n_sets, const qf_c128* gates, double* out_cost, qf_c128* out_env,
+                 qf_c128* out_trace, bool grad, void* stream) {
+  QF_TRY(check_sizes(n_qubits, n_gates));
+  std::vector<qf_loc> l;
+  QF_TRY(fetch_locations(locations, n_qubits, n_gates, &l));
+  std::vector<GateDesc> gd;
+  long long gsz = 0;
+  QF_TRY(descs_from_pairs(l, &gd, &gsz));
+  return adjoint_walk_desc(target, n_qubits, gd, gsz, n_sets, gates, out_cost, out_env, out_trace,
+                           grad, stream);
+}
+
+int adjoint_walk_k(const qf_c128* target, int n_qubits, int n_gates, const qf_gate_loc* locations,
+                   int n_sets, const qf_c128* gates, double* out_cost, qf_c128* out_env,
+                   qf_c128* out_trace, bool grad, void* stream) {
+  QF_TRY(check_sizes(n_qubits, n_gates));
+  std::vector<GateDesc> gd;
+  long long gsz = 0;
+  QF_TRY(fetch_gate_locs(locations, n_qubits, n_gates, &gd, &gsz));
+  return adjoint_walk_desc(target, n_qubits, gd, gsz, n_sets, gates, out_cost, out_env, out_trace,
+                           grad, stream);
 }
 
 }  // namespace
@@ -1414,6 +1444,20 @@ int qf_cost_grad(const qf_c128* target, int n_qubits, int n_gates, const qf_loc*
                  void* stream) {
   return adjoint_walk(target, n_qubits, n_gates, locations, n_sets, gates, out_cost, out_grad,
                       nullptr, true, stream);
+}
+
+int qf_cost_and_env_k(const qf_c128* target, int n_qubits, int n_gates,
+                      const qf_gate_loc* locations, int n_sets, const qf_c128* gates,
+                      double* out_cost, qf_c128* out_env, qf_c128* out_trace, void* stream) {
+  return adjoint_walk_k(target, n_qubits, n_gates, locations, n_sets, gates, out_cost, out_env,
+                        out_trace, false, stream);
+}
+
+int qf_cost_grad_k(const qf_c128* target, int n_qubits, int n_gates, const qf_gate_loc* locations,
+                   int n_sets, const qf_c128* gates, double* out_cost, qf_c128* out_grad,
+                   void* stream) {
+  return adjoint_walk_k(target, n_qubits, n_gates, locations, n_sets, gates, out_cost, out_grad,
+                        nullptr, true, stream);
 }
 
 // ------------------------------------------------------------ single steps

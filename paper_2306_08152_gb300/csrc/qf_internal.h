@@ -138,6 +138,10 @@ cudaError_t launch_optimize(const double2* E, const double2* u_old, double beta,
 // env[s][k] <- -(t_s / (N |t_s|)) env[s][k]^dagger in place (t = tr[s]).
 cudaError_t launch_grad_from_env(double2* env, const double2* tr, int n, int S, int p,
                                  cudaStream_t st);
+// The same for a circuit of 2-, 3- and 4-qubit gates: desc[k] = (qubits,
+// entry offset) of gate k; set s's environments begin at env + s * gsz.
+cudaError_t launch_grad_from_env_k(double2* env, const double2* tr, int n, int S, long long gsz,
+                                   const int2* desc, int p, cudaStream_t st);
 
 // Two FP64 Newton-Schulz steps on each of `count` gates, in place.
 cudaError_t launch_reunitarize(double2* gates, int count, cudaStream_t st);

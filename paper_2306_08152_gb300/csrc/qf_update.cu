@@ -340,6 +340,29 @@ __global__ void grad_from_env_kernel(double2* __restrict__ env, const double2* _
     for (int j = 0; j < 4; ++j) E[i * 4 + j] = cmul(f, cconj(e[j * 4 + i]));
 }
 
+// The same for a circuit of 2-, 3- and 4-qubit gates: CTA (k, s) turns the
+// d x d environment of gate k of set s (desc[k] = (qubits, entry offset),
+// d = 2^qubits, set stride gsz) into -(t/(N|t|)) E^dagger in place; thread
+// e owns the unordered pair of entries (i, j), (j, i) with i <= j.
+__global__ void grad_from_env_k_kernel(double2* __restrict__ env, const double2* __restrict__ tr,
+                                       double inv_n, long long gsz, const int2* __restrict__ desc) {
+  const int k = blockIdx.x, s = blockIdx.y;
+  const int2 dk = desc[k];
+  const int d = 1 << dk.x;
+  const double2 t = tr[s];
+  const double at = sqrt(t.x * t.x + t.y * t.y);
+  const double2 f = at > 0.0 ? make_double2(-t.x * inv_n / at, -t.y * inv_n / at)
+                             : make_double2(0.0, 0.0);
+  double2* E = env + (size_t)s * gsz + dk.y;
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
+    const int i = e / d, j = e % d;
+    if (i > j) continue;
+    const double2 a = E[i * d + j], b = E[j * d + i];
+    E[i * d + j] = cmul(f, cconj(b));
+    E[j * d + i] = cmul(f, cconj(a));
+  }
+}
+
 // Periodic re-unitarisation of gates in FP64 (reset_iter, Sec. III-A2): three
 // Newton-Schulz steps u <- u (3I - u^dagger u) / 2 per gate, one warp per gate.
 // Each step squares the deviation from unitarity; on gates that are already
@@ -372,6 +395,13 @@ cudaError_t launch_grad_from_env(double2* env, const double2* tr, int n, int S, 
                                  cudaStream_t st) {
   const int count = S * p;
   grad_from_env_kernel<<<(count + 127) / 128, 128, 0, st>>>(env, tr, 1.0 / (double)(1 << n), S, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_from_env_k(double2* env, const double2* tr, int n, int S, long long gsz,
+                                   const int2* desc, int p, cudaStream_t st) {
+  if (S * p <= 0) return cudaSuccess;
+  grad_from_env_k_kernel<<<dim3(p, S), 128, 0, st>>>(env, tr, 1.0 / (double)(1 << n), gsz, desc);
   return cudaGetLastError();
 }
 

@@ -80,3 +80,50 @@ def test_cost_without_grad_is_the_plain_cost(qf):
     for s in range(2):
         c_ref, _, _ = orc.cost_and_env(V, gates[s], locs, n)
         assert abs(c[s].item() - c_ref) <= 1e-10
+
+
+def _mixed_locs(n, g):
+    locs = [(0, 1, 2, 3), (n - 1, 1), (2, n - 1, 0), (1, 3), (n - 4, n - 3, n - 2, n - 1), (0, 2, 4)]
+    return [tuple(int(x) for x in q) for q in locs if max(q) < n and len(set(q)) == len(q)]
+
+
+@pytest.mark.parametrize("n,sets", [(5, 3), (7, 2)])
+def test_k_qubit_gradient_matches_oracle(qf, n, sets):
+    """Circuits of 2-, 3- and 4-qubit gates (qf_cost_grad_k, QFactorCost on
+    the concatenated gate layout): costs, environments and gradients against
+    the k-qubit oracle's environments (pinned by finite differences)."""
+    import oracle.kqubit as ok
+
+    g = qi.rng(930 + n)
+    locs = _mixed_locs(n, g)
+    V = qi.haar_unitary(2**n, g)
+    sets_l = [[qi.haar_unitary(2 ** len(q), g) for q in locs] for _ in range(sets)]
+    flat = qf.flatten_gates(sets_l)
+    Vt = torch.from_numpy(V).cuda()
+    costs, envs, trs = qf.cost_and_env_k(Vt, locs, flat.cuda())
+    envs = qf.unflatten_gates(envs, locs)
+    x = flat.cuda().requires_grad_(True)
+    c = qf.QFactorCost.apply(x, Vt, locs)
+    c.sum().backward()
+    grads = qf.unflatten_gates(x.grad, locs)
+    for s in range(sets):
+        c_ref, e_ref, t_ref = ok.cost_and_env_k(V, sets_l[s], locs, n)
+        assert abs(costs[s] - c_ref) <= 1e-10 and abs(c[s].item() - c_ref) <= 1e-10
+        assert abs(trs[s] - t_ref) <= 1e-10 * 2**n
+        f = -(t_ref / (2**n * abs(t_ref)))
+        for k in range(len(locs)):
+            scale = np.max(np.abs(e_ref[k]))
+            assert np.max(np.abs(envs[s][k] - e_ref[k])) <= 1e-9 * scale, (s, k)
+            want = f * e_ref[k].conj().T
+            assert np.max(np.abs(grads[s][k] - want)) <= 1e-9 * np.max(np.abs(want)), (s, k)
+
+
+def test_k_qubit_gradcheck(qf):
+    n = 4
+    locs = [(0, 1, 2, 3), (1, 2), (3, 0, 2)]
+    g = qi.rng(940)
+    V = torch.from_numpy(qi.haar_unitary(16, g)).cuda()
+    flat = qf.flatten_gates([[qi.haar_unitary(2 ** len(q), g) for q in locs]]).cuda()[0]
+    x = flat.clone().requires_grad_(True)
+    f = lambda y: qf.QFactorCost.apply(y, V, locs)
+    assert torch.autograd.gradcheck(f, (x,), eps=1e-6, atol=1e-8, rtol=1e-6)
