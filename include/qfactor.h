@@ -58,6 +58,8 @@ typedef struct { int32_t a, b; } qf_loc;     /* gate location: qubits a != b  */
 #define QF_ENOMEM       -2   /* device allocation failed                     */
 #define QF_ECUDA        -3   /* a CUDA runtime call failed                   */
 #define QF_ENONFINITE   -4   /* NaN/Inf in an input or in an environment     */
+#define QF_ETIMEOUT     -5   /* a bounded tensor-core completion wait ran out;
+                                the tensor entries it left are NaN          */
 
 /* Circuit-tensor precision. */
 #define QF_C128          0   /* complex128 tensor, FP64 arithmetic throughout */
@@ -335,6 +337,16 @@ int qf_circuit_unitary_k(int n_qubits, int n_gates,
                          const qf_gate_loc* locations, const qf_c128* gates,
                          qf_c128* C_out, void* stream);
 
+/* Four-qubit passes in complex64 with both operators at n_qubits >= 7 run
+ * on the tensor cores (tcgen05, 3xTF32: FP32-level results).  Each of
+ * their completion waits polls at most `polls` times (default 4194304,
+ * well above any real wait); when one runs out, the pass writes NaN over
+ * the tensor entries it has not finished and a plan returns QF_ETIMEOUT at
+ * its next status check.  qf_set_tc_wait_limit sets the limit for later
+ * launches (0 makes every wait run out at once, which tests that path) and
+ * returns the previous limit; polls < 0 only returns it. */
+int qf_set_tc_wait_limit(int polls);
+
 /* ------------------------------------------------------------------------
  * Resident plan: device-resident tensors, target and gates for repeated
  * sweeps (the form the benchmark times).
@@ -404,8 +416,9 @@ int qf_plan_lookahead_windows(qf_plan* plan, int* pairs_per_sweep);
 int qf_plan_pass_stats(qf_plan* plan, double* pass_ms, int64_t* pass_launches,
                        int64_t* all_launches, double* pass_bytes);
 
-/* Current device status word of the plan (0 = clean; QF_ENONFINITE if an
- * update met a non-finite environment).  Synchronises. */
+/* Current device status word of the plan: 0 = clean, else the first error
+ * recorded (QF_ENONFINITE: an update met a non-finite environment;
+ * QF_ETIMEOUT: a tensor-core pass's completion wait ran out).  Synchronises. */
 int qf_plan_status(qf_plan* plan);
 
 /* A resident plan for a circuit of 2- and 3-qubit gates (as qf_plan_create;

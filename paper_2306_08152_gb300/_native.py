@@ -15,6 +15,7 @@ QF_EINVAL = -1
 QF_ENOMEM = -2
 QF_ECUDA = -3
 QF_ENONFINITE = -4
+QF_ETIMEOUT = -5
 
 QF_C128 = 0
 QF_C64 = 1
@@ -144,6 +145,7 @@ SIGNATURES = {
     "qf_optimize_gates_k": (I, [P, I, P, D, I, P, P, P]),
     "qf_init_tensor_k": (I, [P, I, I, P, I, P, P, I, P]),
     "qf_circuit_unitary_k": (I, [I, I, P, P, P, P]),
+    "qf_set_tc_wait_limit": (I, [I]),
 }
 
 _lib = None

@@ -22,7 +22,7 @@ __all__ = [
     "partial_trace", "partial_trace_noalloc", "apply_two_pairs", "partial_trace_after", "convert_tensor",
     "instantiate_k", "apply_gate_k", "partial_trace_k", "optimize_gates_k", "init_tensor_k",
     "circuit_unitary_k", "flatten_gates", "unflatten_gates", "gate_entries", "optimize_gates", "reunitarize_gates", "trace", "circuit_unitary",
-    "gate_specs", "spec_slots", "instantiate_spec", "cost_and_env_k", "cost_grad_k",
+    "gate_specs", "spec_slots", "instantiate_spec", "cost_and_env_k", "cost_grad_k", "set_tc_wait_limit",
 ]
 
 QF_C128 = nat.QF_C128
@@ -712,6 +712,12 @@ def apply_gate_k(T, qubits, L=None, R=None, stream=None):
     Rp = _ptr(_dev(_c128(R, "R"), "R")) if R is not None else None
     check(_lib().qf_apply_gate_k(_ptr(T), n, S, larr, Lp, Rp, _tensor_prec(T), _stream_handle(stream)))
     return T
+
+
+def set_tc_wait_limit(polls):
+    """Polls of each tensor-core completion wait for later launches (0: every
+    wait runs out at once); returns the previous limit.  polls < 0 only queries."""
+    return int(_lib().qf_set_tc_wait_limit(int(polls)))
 
 
 def partial_trace_k(T, qubits, stream=None):

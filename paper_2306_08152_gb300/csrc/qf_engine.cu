@@ -383,7 +383,8 @@ int plan_pass16(qf_plan* P, const Slice& sl, const int* q, const double2* L, lon
                 const double2* R, long long Rs) {
   return timed_pass(P, sl, [&](void* T) {
     return qf::launch_pass16(T, P->n, sl.Sg, q, L ? L + sl.s0 * Ls : nullptr, Ls,
-                             R ? R + sl.s0 * Rs : nullptr, Rs, kprec(P->prec), sl.st);
+                             R ? R + sl.s0 * Rs : nullptr, Rs, kprec(P->prec), sl.st,
+                             P->status.as<int>());
   });
 }
 
@@ -921,6 +922,7 @@ int plan_status_impl(qf_plan* P) {
   int st = 0;
   QF_CUDA(cudaMemcpyAsync(&st, P->status.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
   QF_CUDA(cudaStreamSynchronize(P->stream));
+  if (st == QF_ETIMEOUT) return set_error(st, "a tensor-core completion wait ran out in a 16x16 pass");
   if (st != 0) return set_error(st, "an environment or update was not finite");
   return QF_OK;
 }

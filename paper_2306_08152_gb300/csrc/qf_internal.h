@@ -112,8 +112,11 @@ cudaError_t launch_reunitarize8(double2* gates, int count, cudaStream_t st);
 // start); LR has start stride 512 (L, then R); part needs
 // S * env_ctas(n) * 512 doubles.  Modes as for launch_update; the update
 // runs on one CTA of 256 threads per start.
+// Complex64 passes with both operators at n >= 7 run on the tensor cores;
+// their bounded waits record QF_ETIMEOUT in *status (may be NULL).
 cudaError_t launch_pass16(void* T, int n, int S, const int* q, const double2* L, long long Ls,
-                          const double2* R, long long Rs, int prec, cudaStream_t st);
+                          const double2* R, long long Rs, int prec, cudaStream_t st,
+                          int* status = nullptr);
 cudaError_t launch_update16(const void* T, int n, int S, const int* q, double2* gates_k,
                             long long gstride, int mode, double beta, double2* LR, double2* out,
                             long long out_stride, double* sigma_out, int* status, double* part,
@@ -147,7 +150,7 @@ cudaError_t launch_grad_from_env_k(double2* env, const double2* tr, int n, int S
 cudaError_t launch_reunitarize(double2* gates, int count, cudaStream_t st);
 
 // *status <- -4 (QF_ENONFINITE) if any of the `count` doubles at x is not
-// finite; otherwise *status is left alone.
+// finite and *status holds no earlier error; otherwise it is left alone.
 cudaError_t launch_check_finite(const double* x, size_t count, int* status, cudaStream_t st);
 
 // One-pass InitCircuitTensor after the conjugate transpose: every row of

@@ -24,6 +24,8 @@
 
 #include "qf_device.cuh"
 #include "qf_internal.h"
+#include "qf_tc.cuh"
+#include "qfactor.h"
 
 namespace qf {
 namespace {
@@ -447,7 +449,7 @@ env16_kernel(const typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, i
   if (cta_polar16(S, &sg)) {
     un = S.x[t];
   } else {
-    if (t == 0) atomicExch(status, -4);
+    if (t == 0) atomicCAS(status, 0, -4);
     un = u;  // keep the old gate: the tensor stays consistent
     sg = 0.0;
   }
@@ -744,10 +746,344 @@ pass16c_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, int p3,
   }
 }
 
+// ------------------------------------------- tensor-core 16x16 pass (tcgen05)
+// Complex64 with both operators, n >= 7.  The block products of the pass
+// are dense contractions (128 FP32 FMAs per entry, above what the FP32 pipe
+// delivers at HBM speed), so they run on the fifth-generation tensor cores
+// as real GEMMs in 3xTF32 form: each FP32 value x is split into TF32 parts
+// hi + lo, and A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32
+// accumulation in tensor memory (the dropped lo*lo term and the rounding of
+// the parts stay near 2^-21 of |A B|).
+//
+// A tile is the 16 x 128 slab of one row rest's 16 row variants and the 128
+// columns of the 8 column-rest blocks whose rests differ only in the 3
+// lowest non-gate column bits: the tile's columns are all values of the 7
+// column bits S = {gate bits} + {3 lowest non-gate bits} (tile column u:
+// bit k of u is the k-th lowest position of S).  Inside the kernel a local
+// gate index is in ascending-bit order (bit k <-> gate position qs[k]); the
+// operators are permuted to that order when they are embedded.  Per tile:
+//  0. (during the previous tile) the tile streams into a staging buffer as
+//     16-byte copies of adjacent column pairs (column bit 0 is always in S);
+//  1. thread m (tensor-memory lane m) takes tile column u = m from the
+//     staging buffer, 16 entries, one per row variant, and stores it as
+//     A[m][2 i + c] (row variant i, c = re / im) in TF32 hi (columns 0-31)
+//     and lo (32-63);
+//  2. one thread issues D = A Emb(L)^T (4 K steps of 8, three products:
+//     12 MMAs of M = 128, N = 32; A from tensor memory, the embedded
+//     operator from shared memory, K-major with the 128-byte swizzle) and
+//     commits to an mbarrier; meanwhile the next tile starts streaming in;
+//  3. thread m moves D (column u of L B) into the tile buffer;
+//  4. thread m' = 16 b + i takes row i of block b from the buffer and the
+//     same sequence applies Emb(R^T) (R on the column index);
+//  5. thread m' puts its output row into the buffer, and the tile goes to
+//     HBM as 16-byte column pairs.
+// The tile buffer holds entry (i, u) at i * 128 + (u ^ i): every access
+// pattern above hits each bank pair exactly twice per warp (a 16-byte
+// access of a pair takes the pair swapped for odd i).  Emb(O) is the real
+// 32 x 32 matrix with Emb[2 a + c'][2 b + c] = Re O[a][b] for c' = c, -Im
+// for (0, 1) and +Im for (1, 0), so that out[a] = sum_b O[a][b] x[b].
+// Tensor memory: 128 columns per CTA (A hi, A lo, D at 64-95); 52 KB of
+// shared memory per CTA keep at most 4 CTAs (512 columns) on an SM.
+// Every wait is bounded (wait_limit polls).  When one runs out, the CTA
+// records QF_ETIMEOUT in *status (if given), writes NaN over the rest of its
+// tiles, waits (bounded by the default limit) for its MMAs in flight, frees
+// its tensor memory and ends.
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTcCols = 128;
+constexpr int kTcSmem = 52 * 1024;
+constexpr int kTcWaitLimit = 1 << 22;  // polls of one completion wait
+int g_tc_wait_limit = kTcWaitLimit;     // qf_set_tc_wait_limit
+
+// Byte offset of element (row nn, column k) in a K-major, 128-byte-swizzled
+// 32 x 32 TF32 tile (1024-byte aligned).
+__device__ __forceinline__ uint32_t sw128_off(int nn, int k) {
+  return (uint32_t)(nn * 128 + (((k >> 2) ^ (nn & 7)) << 4) + ((k & 3) << 2));
+}
+
+// D (tensor-memory columns 64-95) = A (hi 0-31, lo 32-63) Emb^T; one thread.
+__device__ __forceinline__ void tc_issue_stage(uint32_t tb, uint32_t op_hi, uint32_t op_lo, uint32_t bar) {
+  constexpr uint32_t idesc = tc::idesc_tf32(128, 32);
+  tc::fence_after_sync();
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    const uint64_t bh = tc::desc_kmajor_sw128(op_hi + 32u * kk), bl = tc::desc_kmajor_sw128(op_lo + 32u * kk);
+    tc::mma_tf32_ts(tb + 64u, tb + 8u * kk, bh, idesc, kk > 0 ? 1u : 0u);
+    tc::mma_tf32_ts(tb + 64u, tb + 8u * kk, bl, idesc, 1u);
+    tc::mma_tf32_ts(tb + 64u, tb + 32u + 8u * kk, bh, idesc, 1u);
+  }
+  tc::commit(bar);
+}
+
+// 16 complex values get(0..15) -> TF32 hi parts at columns 0-31 and lo
+// parts at 32-63 of this thread's lane, eight values at a time.  The lo
+// part x - hi goes in as FP32: the tensor core takes its leading TF32 bits,
+// which keeps it to about 2^-10 of itself (2^-21 of x).
+template <typename Get>
+__device__ __forceinline__ void tc_store_a(uint32_t ta, Get get) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float2 z[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) z[e] = get(8 * h + e);
+    uint32_t v[16];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      v[2 * e] = tc::tf32(z[e].x);
+      v[2 * e + 1] = tc::tf32(z[e].y);
+    }
+    tc::st16(ta + 16u * h, v);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      v[2 * e] = __float_as_uint(z[e].x - __uint_as_float(v[2 * e]));
+      v[2 * e + 1] = __float_as_uint(z[e].y - __uint_as_float(v[2 * e + 1]));
+    }
+    tc::st16(ta + 32u + 16u * h, v);
+  }
+}
+
+// Rows 8 h .. 8 h + 7 of tile columns 2 pp and 2 pp + 1 (adjacent entries:
+// column bit 0 is always in S) -> the staging buffer, as asynchronous
+// 16-byte copies; `off` is the pair's entry offset in row variant 0.
+__device__ __forceinline__ void tc_prefetch(float2* stage, const float2* Tp, unsigned off, const unsigned* rowoff,
+                                            int pp, int h) {
+#pragma unroll 4
+  for (int e = 0; e < 8; ++e) {
+    const int i = 8 * h + e;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_addr(stage + i * 128 + 2 * pp)),
+                 "l"(Tp + off + rowoff[i])
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void tc_prefetch_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__global__ void __launch_bounds__(kTcThreads, 4)
+pass16tc_kernel(float2* __restrict__ T, int n, int S, int p0, int p1, int p2, int p3,
+                const double2* __restrict__ L, long long Ls, const double2* __restrict__ Rm, long long Rs,
+                int* status, int wait_limit) {
+  extern __shared__ unsigned char dsm[];
+  const uint32_t dsm_s = tc::smem_addr(dsm);
+  const uint32_t ops_s = (dsm_s + 1023u) & ~1023u;  // L hi, L lo, R hi, R lo: 4 KB each
+  unsigned char* ops = dsm + (ops_s - dsm_s);
+  float2* buf = reinterpret_cast<float2*>(ops + 4 * 4096);  // [16][128] complex, the tile
+  float2* stage = buf + 16 * 128;  // [16][128]: the next tile, in flight
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stage + 16 * 128);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  unsigned* s_rowoff = tslot + 1;  // [16] row offset (entries) of ascending row variant i
+  unsigned* s_uj = s_rowoff + 16;  // [16] tile-column bits of ascending gate index j
+  const uint32_t bar_s = tc::smem_addr(bar);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int pp = tid & 63, ph = tid >> 6;  // copy role: column pair pp, rows 8 ph ..
+  const unsigned N = 1u << n;
+
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), kTcCols);
+  if (tid == 0) tc::mbar_init(bar_s, 1);
+
+  const int p[4] = {p0, p1, p2, p3};
+  int qs[4];
+  sort4(p, qs);
+  int pidx[4];  // which of p[] is the k-th lowest gate position
+#pragma unroll
+  for (int k = 0; k < 4; ++k) pidx[k] = (p[0] == qs[k]) ? 0 : (p[1] == qs[k]) ? 1 : (p[2] == qs[k]) ? 2 : 3;
+  // S, ascending: tile-column bit k <-> the k-th selected position (bit 0
+  // is always selected: a gate bit or the lowest non-gate bit)
+  unsigned gbits_u = 0;  // tile-column bits that are gate bits
+  unsigned colm = 0;     // column offset of tile column u = tid
+  unsigned colp = 0;     // column offset of tile column u = 2 pp
+  {
+    int cnt = 0, ng = 0;
+    for (int pos = 0; cnt < 7; ++pos) {
+      const bool g = pos == qs[0] || pos == qs[1] || pos == qs[2] || pos == qs[3];
+      if (g || ng < 3) {
+        if (g)
+          gbits_u |= 1u << cnt;
+        else
+          ++ng;
+        colm |= (((unsigned)tid >> cnt) & 1u) << pos;
+        colp |= (((unsigned)(2 * pp) >> cnt) & 1u) << pos;
+        ++cnt;
+      }
+    }
+  }
+  if (tid < 16) {
+    const unsigned i = (unsigned)tid;
+    s_rowoff[tid] = ((i & 1u) << qs[0] | ((i >> 1) & 1u) << qs[1] | ((i >> 2) & 1u) << qs[2] |
+                     ((i >> 3) & 1u) << qs[3]) * N;
+    unsigned v = 0;
+    int gk = 0;
+    for (int k = 0; k < 7; ++k)
+      if ((gbits_u >> k) & 1u) v |= ((i >> gk++) & 1u) << k;
+    s_uj[tid] = v;
+  }
+  // row role: thread m' = 16 b + i holds row i of block b (tile-column bits ub)
+  const unsigned rb_i = (unsigned)tid & 15u;
+  unsigned ub = 0;
+  {
+    int bk = 0;
+    for (int k = 0; k < 7; ++k)
+      if (!((gbits_u >> k) & 1u)) ub |= (((unsigned)tid >> (4 + bk++)) & 1u) << k;
+  }
+
+  const int lnc = n - 4;
+  const unsigned cgbits = (unsigned)lnc - 3u;
+  const unsigned tps = 1u << (2 * lnc - 3);  // tiles per start
+  const unsigned total = tps * (unsigned)S;
+  const unsigned chunk = (total + gridDim.x - 1) / gridDim.x;
+  const unsigned t0 = blockIdx.x * chunk;
+  const unsigned t1 = t0 + chunk < total ? t0 + chunk : total;
+  const size_t NN = (size_t)N * N;
+
+  // tile -> start, and the entry offset of the tile's row rest and column
+  // base in row variant 0 of the start's tensor (below 2^30 for n <= 15)
+  const auto geom = [&](unsigned tile, unsigned& s, unsigned& base) {
+    s = tile / tps;
+    const unsigned t = tile - s * tps;
+    base = dep4(t >> cgbits, qs) * N + dep4((t & ((1u << cgbits) - 1u)) << 3, qs);
+  };
+
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tb = *tslot;
+  const uint32_t ta = tb + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
+
+  unsigned tile = t0, cur_s = 0xffffffffu, s_cur = 0, b_cur = 0;
+  uint32_t phase = 0;
+  bool failed = false;
+  if (tile < t1) {
+    geom(tile, s_cur, b_cur);
+    tc_prefetch(stage, T + s_cur * NN, b_cur + colp, s_rowoff, pp, ph);
+  }
+  tc_prefetch_wait();
+  __syncthreads();  // the first tile has landed
+  for (; tile < t1; ++tile) {
+    const unsigned s = s_cur, base = b_cur;
+    float2* Tp = T + s * NN;
+    const bool more = tile + 1 < t1;
+    if (more) geom(tile + 1, s_cur, b_cur);
+    if (s != cur_s) {  // embed this start's operators (no MMA is in flight)
+      cur_s = s;
+#pragma unroll 1
+      for (int e = tid; e < 2 * 32 * 32; e += kTcThreads) {
+        const int which = e >> 10, nn = (e >> 5) & 31, k = e & 31;
+        const int a = nn >> 1, cp = nn & 1, b = k >> 1, c = k & 1;
+        int ga = 0, gb = 0;  // the gate's own local indices of a and b
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ga |= ((a >> q) & 1) << (3 - pidx[q]);
+          gb |= ((b >> q) & 1) << (3 - pidx[q]);
+        }
+        // O = L (a: output row) or R^T (a: output column)
+        const double2 o = which == 0 ? L[s * Ls + ga * 16 + gb] : Rm[s * Rs + gb * 16 + ga];
+        const float ore = (float)o.x, oim = (float)o.y;  // FP32 operators, as the FMA kernels
+        const float val = (cp == c) ? ore : (cp == 0 ? -oim : oim);
+        const uint32_t hi = tc::tf32(val);
+        const uint32_t lo = tc::tf32(val - __uint_as_float(hi));
+        unsigned char* obase = ops + which * 8192;
+        *reinterpret_cast<uint32_t*>(obase + sw128_off(nn, k)) = hi;
+        *reinterpret_cast<uint32_t*>(obase + 4096 + sw128_off(nn, k)) = lo;
+      }
+      tc::fence_async_smem();
+    }
+    // 1. tile column tid -> A
+    tc_store_a(ta, [&](int i) { return stage[i * 128 + tid]; });
+    tc::fence_before_sync();
+    __syncthreads();
+    // 2. L stage; the next tile streams into the staging buffer meanwhile
+    if (tid == 0) tc_issue_stage(tb, ops_s, ops_s + 4096u, bar_s);
+    if (more) tc_prefetch(stage, T + s_cur * NN, b_cur + colp, s_rowoff, pp, ph);
+    bool ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_s, phase, wait_limit));
+    phase ^= 1u;
+    tc::fence_after_sync();
+    // 3. column tid of L B -> buffer
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint32_t d[16];
+      if (ok) tc::ld16(ta + 64u + 16u * h, d);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int i = 8 * h + e;
+        buf[i * 128 + (tid ^ i)] = make_float2(__uint_as_float(d[2 * e]), __uint_as_float(d[2 * e + 1]));
+      }
+    }
+    tc::fence_before_sync();
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    // 4. R stage on rows (b, i)
+    tc_store_a(ta, [&](int j) { return buf[rb_i * 128 + ((ub | s_uj[j]) ^ rb_i)]; });
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) tc_issue_stage(tb, ops_s + 8192u, ops_s + 12288u, bar_s);
+    ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_s, phase, wait_limit));
+    phase ^= 1u;
+    tc::fence_after_sync();
+    // 5. output rows -> buffer
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint32_t d[16];
+      if (ok) tc::ld16(ta + 64u + 16u * h, d);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int j = 8 * h + e;
+        buf[rb_i * 128 + ((ub | s_uj[j]) ^ rb_i)] =
+            make_float2(__uint_as_float(d[2 * e]), __uint_as_float(d[2 * e + 1]));
+      }
+    }
+    tc_prefetch_wait();  // the next tile is visible to every thread after the barrier
+    tc::fence_before_sync();
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    // 6. buffer -> HBM as 16-byte pairs (entries (i, u ^ i): odd i swaps a pair)
+#pragma unroll 4
+    for (int e = 0; e < 8; ++e) {
+      const int i = 8 * ph + e;
+      const float4 v = *reinterpret_cast<const float4*>(buf + i * 128 + ((2 * pp) ^ (i & 14)));
+      *reinterpret_cast<float4*>(Tp + base + colp + s_rowoff[i]) =
+          (i & 1) ? make_float4(v.z, v.w, v.x, v.y) : v;
+    }
+  }
+  if (failed) {
+    if (tid == 0 && status) atomicCAS(status, 0, QF_ETIMEOUT);
+    const float nan = __int_as_float(0x7fc00000);
+    for (; tile < t1; ++tile) {
+      unsigned s, base;
+      geom(tile, s, base);
+      float2* Tp = T + s * NN;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) Tp[base + colm + s_rowoff[i]] = make_float2(nan, nan);
+    }
+    tc::mbar_wait(bar_s, phase ^ 1u, kTcWaitLimit);  // the stage that ran out, should it still end
+  }
+  tc_prefetch_wait();
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tb, kTcCols);
+}
+
 template <typename R, bool HL, bool HR>
 void pass16_launch(void* T, int n, int S, const int* p, const double2* L, long long Ls,
-                   const double2* Rm, long long Rs, cudaStream_t st) {
+                   const double2* Rm, long long Rs, cudaStream_t st, int* status) {
   typedef typename Cplx<R>::T C;
+  if constexpr (std::is_same<R, float>::value && HL && HR) {
+    if (n >= 7) {
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(pass16tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+        cudaFuncSetAttribute(pass16tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        attr = true;
+      }
+      const long long tiles = (long long)S << (2 * (n - 4) - 3);
+      const long long cap = (long long)sm_count() * 4;
+      pass16tc_kernel<<<(unsigned)(tiles < cap ? tiles : cap), kTcThreads, kTcSmem, st>>>(
+          (float2*)T, n, S, p[0], p[1], p[2], p[3], L, Ls, Rm, Rs, status, g_tc_wait_limit);
+      return;
+    }
+  }
   const int per_group = std::is_same<R, float>::value ? kPass16cBlocks : 2;
   const long long groups = ((1ll << (2 * (n - 4))) + per_group - 1) / per_group;
   const long long want = (groups + 3) / 4;
@@ -770,13 +1106,13 @@ void pass16_launch(void* T, int n, int S, const int* p, const double2* L, long l
 
 template <typename R>
 void pass16_ops(void* T, int n, int S, const int* p, const double2* L, long long Ls,
-                const double2* Rm, long long Rs, cudaStream_t st) {
+                const double2* Rm, long long Rs, cudaStream_t st, int* status) {
   if (L && Rm)
-    pass16_launch<R, true, true>(T, n, S, p, L, Ls, Rm, Rs, st);
+    pass16_launch<R, true, true>(T, n, S, p, L, Ls, Rm, Rs, st, status);
   else if (L)
-    pass16_launch<R, true, false>(T, n, S, p, L, Ls, Rm, Rs, st);
+    pass16_launch<R, true, false>(T, n, S, p, L, Ls, Rm, Rs, st, status);
   else if (Rm)
-    pass16_launch<R, false, true>(T, n, S, p, L, Ls, Rm, Rs, st);
+    pass16_launch<R, false, true>(T, n, S, p, L, Ls, Rm, Rs, st, status);
 }
 
 }  // namespace
@@ -784,15 +1120,15 @@ void pass16_ops(void* T, int n, int S, const int* p, const double2* L, long long
 // ================================================================ launchers
 
 cudaError_t launch_pass16(void* T, int n, int S, const int* q, const double2* L, long long Ls,
-                          const double2* R, long long Rs, int prec, cudaStream_t st) {
+                          const double2* R, long long Rs, int prec, cudaStream_t st, int* status) {
   if (!L && !R) return cudaSuccess;
   const int p[4] = {qubit_bit(n, q[0]), qubit_bit(n, q[1]), qubit_bit(n, q[2]), qubit_bit(n, q[3])};
   if (prec == 0)
-    pass16_ops<double>(T, n, S, p, L, Ls, R, Rs, st);
+    pass16_ops<double>(T, n, S, p, L, Ls, R, Rs, st, status);
   else if (prec == 2)
-    pass16_ops<DF>(T, n, S, p, L, Ls, R, Rs, st);
+    pass16_ops<DF>(T, n, S, p, L, Ls, R, Rs, st, status);
   else
-    pass16_ops<float>(T, n, S, p, L, Ls, R, Rs, st);
+    pass16_ops<float>(T, n, S, p, L, Ls, R, Rs, st, status);
   return cudaGetLastError();
 }
 
@@ -833,3 +1169,9 @@ cudaError_t launch_reunitarize16(double2* gates, long long gsz, const int2* desc
 }
 
 }  // namespace qf
+
+int qf_set_tc_wait_limit(int polls) {
+  const int old = qf::g_tc_wait_limit;
+  if (polls >= 0) qf::g_tc_wait_limit = polls;
+  return old;
+}

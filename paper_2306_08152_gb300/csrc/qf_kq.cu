@@ -1025,7 +1025,7 @@ env8_kernel(const typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, in
   double2 n0, n1;
   double sg = 0.0;
   if (!warp_polar8(A0, A1, sm, &n0, &n1, &sg)) {
-    if (L.l == 0) atomicExch(status, -4);
+    if (L.l == 0) atomicCAS(status, 0, -4);
     n0 = u0;  // keep the old gate: the tensor stays consistent
     n1 = u1;
     sg = 0.0;

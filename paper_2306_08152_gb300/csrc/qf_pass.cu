@@ -961,14 +961,15 @@ build_rows_kernel(float2* __restrict__ T, const __grid_constant__ BuildParams bp
   }
 }
 
-// status <- QF_ENONFINITE (-4) if any of the `count` doubles is NaN or Inf.
+// status <- QF_ENONFINITE (-4) if any of the `count` doubles is NaN or Inf
+// and no earlier error is recorded there.
 __global__ void __launch_bounds__(256) check_finite_kernel(const double* __restrict__ x, size_t count,
                                                            int* __restrict__ status) {
   bool bad = false;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (size_t)gridDim.x * blockDim.x)
     bad |= !isfinite(x[i]);
-  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicExch(status, -4);
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicCAS(status, 0, -4);
 }
 
 // Entry-wise conversion between tensor precisions through FP64 (exact from

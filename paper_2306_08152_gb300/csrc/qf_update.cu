@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kEnvThreads) env_kernel(
   const bool ok = kind == kGateGeneral ? warp_polar(L, A, scratch, &un, &sg)
                                        : param_update(kind, A, prm + s * prm_stride, &un, &sg);
   if (!ok) {
-    if (L.l == 0) atomicExch(status, -4);
+    if (L.l == 0) atomicCAS(status, 0, -4);
     un = u;  // keep the old gate: the tensor stays consistent
     sg = 0.0;
   }
