@@ -791,6 +791,7 @@ pass16c_kernel(float2* __restrict__ T, int n, int p0, int p1, int p2, int p3,
 constexpr int kTcThreads = 128;
 constexpr uint32_t kTcCols = 128;
 constexpr int kTcSmem = 52 * 1024;
+constexpr int kTcChunk = 16;           // tiles per CTA at most
 constexpr int kTcWaitLimit = 1 << 22;  // polls of one completion wait
 int g_tc_wait_limit = kTcWaitLimit;     // qf_set_tc_wait_limit
 
@@ -800,18 +801,32 @@ __device__ __forceinline__ uint32_t sw128_off(int nn, int k) {
   return (uint32_t)(nn * 128 + (((k >> 2) ^ (nn & 7)) << 4) + ((k & 3) << 2));
 }
 
-// D (tensor-memory columns 64-95) = A (hi 0-31, lo 32-63) Emb^T; one thread.
-__device__ __forceinline__ void tc_issue_stage(uint32_t tb, uint32_t op_hi, uint32_t op_lo, uint32_t bar) {
-  constexpr uint32_t idesc = tc::idesc_tf32(128, 32);
+// D = A Emb^T in two halves, issued by one thread: with the operator tile
+// [Emb_hi; Emb_lo] (64 rows: the lo tile follows the hi tile) one N = 64 MMA
+// per K step gives A_hi Emb_hi^T (columns 64-95) and A_hi Emb_lo^T (96-127),
+// and an N = 32 MMA adds A_lo Emb_hi^T to the first half: 8 MMAs, the sum
+// of the halves is the 3xTF32 product.
+__device__ __forceinline__ void tc_issue_stage(uint32_t tb, uint32_t op_hi, uint32_t bar) {
+  constexpr uint32_t id64 = tc::idesc_tf32(128, 64), id32 = tc::idesc_tf32(128, 32);
   tc::fence_after_sync();
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
-    const uint64_t bh = tc::desc_kmajor_sw128(op_hi + 32u * kk), bl = tc::desc_kmajor_sw128(op_lo + 32u * kk);
-    tc::mma_tf32_ts(tb + 64u, tb + 8u * kk, bh, idesc, kk > 0 ? 1u : 0u);
-    tc::mma_tf32_ts(tb + 64u, tb + 8u * kk, bl, idesc, 1u);
-    tc::mma_tf32_ts(tb + 64u, tb + 32u + 8u * kk, bh, idesc, 1u);
+    const uint64_t bh = tc::desc_kmajor_sw128(op_hi + 32u * kk);
+    tc::mma_tf32_ts(tb + 64u, tb + 8u * kk, bh, id64, kk > 0 ? 1u : 0u);
+    tc::mma_tf32_ts(tb + 64u, tb + 32u + 8u * kk, bh, id32, 1u);
   }
   tc::commit(bar);
+}
+
+// Entries 8 h .. 8 h + 7 of this lane's D (the two halves summed).
+__device__ __forceinline__ void tc_load_d(uint32_t ta, int h, float2 (&out)[8]) {
+  uint32_t a[16], b[16];
+  tc::ld16(ta + 64u + 16u * h, a);
+  tc::ld16(ta + 96u + 16u * h, b);
+#pragma unroll
+  for (int e = 0; e < 8; ++e)
+    out[e] = make_float2(__uint_as_float(a[2 * e]) + __uint_as_float(b[2 * e]),
+                         __uint_as_float(a[2 * e + 1]) + __uint_as_float(b[2 * e + 1]));
 }
 
 // 16 complex values get(0..15) -> TF32 hi parts at columns 0-31 and lo
@@ -936,8 +951,8 @@ pass16tc_kernel(float2* __restrict__ T, int n, int S, int p0, int p1, int p2, in
   // tile -> start, and the entry offset of the tile's row rest and column
   // base in row variant 0 of the start's tensor (below 2^30 for n <= 15)
   const auto geom = [&](unsigned tile, unsigned& s, unsigned& base) {
-    s = tile / tps;
-    const unsigned t = tile - s * tps;
+    s = tile >> (2 * lnc - 3);
+    const unsigned t = tile & (tps - 1u);
     base = dep4(t >> cgbits, qs) * N + dep4((t & ((1u << cgbits) - 1u)) << 3, qs);
   };
 
@@ -947,7 +962,20 @@ pass16tc_kernel(float2* __restrict__ T, int n, int S, int p0, int p1, int p2, in
   const uint32_t tb = *tslot;
   const uint32_t ta = tb + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
 
+  // tile output (buffer) -> HBM as 16-byte column pairs; entry (i, u) sits
+  // at u ^ i, so odd i find the pair swapped
+  const auto store_tile = [&](float2* Tq, unsigned bq) {
+#pragma unroll 4
+    for (int e = 0; e < 8; ++e) {
+      const int i = 8 * ph + e;
+      const float4 v = *reinterpret_cast<const float4*>(buf + i * 128 + ((2 * pp) ^ (i & 14)));
+      *reinterpret_cast<float4*>(Tq + bq + colp + s_rowoff[i]) = (i & 1) ? make_float4(v.z, v.w, v.x, v.y) : v;
+    }
+  };
+
   unsigned tile = t0, cur_s = 0xffffffffu, s_cur = 0, b_cur = 0;
+  float2* prev_T = nullptr;  // the previous tile, its output still in the buffer
+  unsigned prev_b = 0;
   uint32_t phase = 0;
   bool failed = false;
   if (tile < t1) {
@@ -989,47 +1017,43 @@ pass16tc_kernel(float2* __restrict__ T, int n, int S, int p0, int p1, int p2, in
     tc_store_a(ta, [&](int i) { return stage[i * 128 + tid]; });
     tc::fence_before_sync();
     __syncthreads();
-    // 2. L stage; the next tile streams into the staging buffer meanwhile
-    if (tid == 0) tc_issue_stage(tb, ops_s, ops_s + 4096u, bar_s);
+    // 2. L stage; meanwhile the next tile streams into the staging buffer and
+    //    the previous tile's output goes to HBM
+    if (tid == 0) tc_issue_stage(tb, ops_s, bar_s);
     if (more) tc_prefetch(stage, T + s_cur * NN, b_cur + colp, s_rowoff, pp, ph);
-    bool ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_s, phase, wait_limit));
+    if (prev_T) store_tile(prev_T, prev_b);
+    const bool ok1 = tc::mbar_wait(bar_s, phase, wait_limit);
     phase ^= 1u;
+    if (__syncthreads_or(!ok1)) {  // also frees the buffer
+      failed = true;
+      break;
+    }
     tc::fence_after_sync();
     // 3. column tid of L B -> buffer
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      uint32_t d[16];
-      if (ok) tc::ld16(ta + 64u + 16u * h, d);
+      float2 d[8];
+      tc_load_d(ta, h, d);
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int i = 8 * h + e;
-        buf[i * 128 + (tid ^ i)] = make_float2(__uint_as_float(d[2 * e]), __uint_as_float(d[2 * e + 1]));
-      }
+      for (int e = 0; e < 8; ++e) buf[(8 * h + e) * 128 + (tid ^ (8 * h + e))] = d[e];
     }
     tc::fence_before_sync();
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
+    __syncthreads();
     // 4. R stage on rows (b, i)
     tc_store_a(ta, [&](int j) { return buf[rb_i * 128 + ((ub | s_uj[j]) ^ rb_i)]; });
     tc::fence_before_sync();
     __syncthreads();
-    if (tid == 0) tc_issue_stage(tb, ops_s + 8192u, ops_s + 12288u, bar_s);
-    ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_s, phase, wait_limit));
+    if (tid == 0) tc_issue_stage(tb, ops_s + 8192u, bar_s);
+    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_s, phase, wait_limit));
     phase ^= 1u;
     tc::fence_after_sync();
     // 5. output rows -> buffer
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      uint32_t d[16];
-      if (ok) tc::ld16(ta + 64u + 16u * h, d);
+      float2 d[8];
+      if (ok) tc_load_d(ta, h, d);
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int j = 8 * h + e;
-        buf[rb_i * 128 + ((ub | s_uj[j]) ^ rb_i)] =
-            make_float2(__uint_as_float(d[2 * e]), __uint_as_float(d[2 * e + 1]));
-      }
+      for (int e = 0; e < 8; ++e) buf[rb_i * 128 + ((ub | s_uj[8 * h + e]) ^ rb_i)] = d[e];
     }
     tc_prefetch_wait();  // the next tile is visible to every thread after the barrier
     tc::fence_before_sync();
@@ -1037,15 +1061,10 @@ pass16tc_kernel(float2* __restrict__ T, int n, int S, int p0, int p1, int p2, in
       failed = true;
       break;
     }
-    // 6. buffer -> HBM as 16-byte pairs (entries (i, u ^ i): odd i swaps a pair)
-#pragma unroll 4
-    for (int e = 0; e < 8; ++e) {
-      const int i = 8 * ph + e;
-      const float4 v = *reinterpret_cast<const float4*>(buf + i * 128 + ((2 * pp) ^ (i & 14)));
-      *reinterpret_cast<float4*>(Tp + base + colp + s_rowoff[i]) =
-          (i & 1) ? make_float4(v.z, v.w, v.x, v.y) : v;
-    }
+    prev_T = Tp;  // 6. stored during the next tile's L stage
+    prev_b = base;
   }
+  if (!failed && prev_T) store_tile(prev_T, prev_b);
   if (failed) {
     if (tid == 0 && status) atomicCAS(status, 0, QF_ETIMEOUT);
     const float nan = __int_as_float(0x7fc00000);
@@ -1077,9 +1096,13 @@ void pass16_launch(void* T, int n, int S, const int* p, const double2* L, long l
                              cudaSharedmemCarveoutMaxShared);
         attr = true;
       }
+      // chunks of at most kTcChunk tiles per CTA, over several waves: CTAs
+      // that find their SM shared with other kernels then delay few tiles
       const long long tiles = (long long)S << (2 * (n - 4) - 3);
-      const long long cap = (long long)sm_count() * 4;
-      pass16tc_kernel<<<(unsigned)(tiles < cap ? tiles : cap), kTcThreads, kTcSmem, st>>>(
+      const long long slots = (long long)sm_count() * 4;
+      long long chunk = (tiles + slots - 1) / slots;
+      if (chunk > kTcChunk) chunk = kTcChunk;
+      pass16tc_kernel<<<(unsigned)((tiles + chunk - 1) / chunk), kTcThreads, kTcSmem, st>>>(
           (float2*)T, n, S, p[0], p[1], p[2], p[3], L, Ls, Rm, Rs, status, g_tc_wait_limit);
       return;
     }
