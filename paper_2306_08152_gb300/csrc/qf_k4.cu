@@ -62,6 +62,13 @@ __device__ __forceinline__ void sort4(const int* p, int* qs) {
 // (t = 16 i + j); C must not alias A or B.  Ends with a barrier.
 enum MmOp { kMmNN = 0, kMmND = 1, kMmDN = 2 };  // A B, A B^dagger, A^dagger B
 
+// Every shared 16x16 matrix of the update keeps entry (r, c) at
+// 16 r + (c ^ r): a row and a column each hit 16 distinct positions mod 16,
+// so the column accesses of the Jacobi rounds and of A B^dagger are free of
+// bank conflicts.  swt(t) is the position of entry (t / 16, t % 16).
+__device__ __forceinline__ int sw16(int r, int c) { return r * 16 + (c ^ r); }
+__device__ __forceinline__ int swt(int t) { return t ^ (t >> 4); }
+
 template <int OP>
 __device__ __forceinline__ void cta_mm(const double2* A, const double2* B, double2* C) {
   const int t = threadIdx.x, i = t >> 4, j = t & 15;
@@ -69,14 +76,14 @@ __device__ __forceinline__ void cta_mm(const double2* A, const double2* B, doubl
 #pragma unroll 4
   for (int k = 0; k < 16; ++k) {
     if (OP == kMmNN) {
-      acc = cfma(A[i * 16 + k], B[k * 16 + j], acc);
+      acc = cfma(A[sw16(i, k)], B[sw16(k, j)], acc);
     } else if (OP == kMmND) {  // A[i][k] conj(B[j][k])
-      acc = cfma_cj(B[j * 16 + k], A[i * 16 + k], acc);
+      acc = cfma_cj(B[sw16(j, k)], A[sw16(i, k)], acc);
     } else {  // conj(A[k][i]) B[k][j]
-      acc = cfma_cj(A[k * 16 + i], B[k * 16 + j], acc);
+      acc = cfma_cj(A[sw16(k, i)], B[sw16(k, j)], acc);
     }
   }
-  C[t] = acc;
+  C[swt(t)] = acc;
   __syncthreads();
 }
 
@@ -86,10 +93,10 @@ __device__ __forceinline__ void cta_newton_schulz(double2* M, double2* tmp, doub
   const int t = threadIdx.x, i = t >> 4, j = t & 15;
   for (int s = 0; s < steps; ++s) {
     cta_mm<kMmDN>(M, M, tmp);
-    tmp[t] = make_double2((i == j ? 1.5 : 0.0) - 0.5 * tmp[t].x, -0.5 * tmp[t].y);
+    tmp[swt(t)] = make_double2((i == j ? 1.5 : 0.0) - 0.5 * tmp[swt(t)].x, -0.5 * tmp[swt(t)].y);
     __syncthreads();
     cta_mm<kMmNN>(M, tmp, tmp2);
-    M[t] = tmp2[t];
+    M[swt(t)] = tmp2[swt(t)];
     __syncthreads();
   }
 }
@@ -124,7 +131,7 @@ __device__ __forceinline__ unsigned cta_max_exponent(Polar16Smem& S) {
   const int t = threadIdx.x;
   if (t == 0) S.emax = 0u;
   __syncthreads();
-  const double2 v = S.a[t];
+  const double2 v = S.a[swt(t)];
   const unsigned e = __reduce_max_sync(kFull, max(expo_field(v.x), expo_field(v.y)));
   if ((t & 31) == 0) atomicMax(&S.emax, e);
   __syncthreads();
@@ -139,7 +146,7 @@ __device__ __forceinline__ float jacobi16_round_f(Polar16Smem& S, int r) {
   const int p = pair_col(r, w), q = p ^ r, row = lane & 15;
   const bool isW = lane < 16;
   float2* M = isW ? S.fw : S.fy;
-  const float2 xp = M[row * 16 + p], xq = M[row * 16 + q];
+  const float2 xp = M[sw16(row, p)], xq = M[sw16(row, q)];
   float al = isW ? xp.x * xp.x + xp.y * xp.y : 0.f;
   float be = isW ? xq.x * xq.x + xq.y * xq.y : 0.f;
   float gx = isW ? xp.x * xq.x + xp.y * xq.y : 0.f;  // conj(W[i][p]) W[i][q]
@@ -172,26 +179,28 @@ __device__ __forceinline__ float jacobi16_round_f(Polar16Smem& S, int r) {
     const float c = rsqrtf(1.f + tt * tt), sn = c * tt;
     const float2 e = make_float2(gxs * rr, -gys * rr);  // conj(g) / |g|
     const float2 ex = cmul(e, xq);
-    M[row * 16 + p] = make_float2(c * xp.x - sn * ex.x, c * xp.y - sn * ex.y);
-    M[row * 16 + q] = make_float2(sn * xp.x + c * ex.x, sn * xp.y + c * ex.y);
+    M[sw16(row, p)] = make_float2(c * xp.x - sn * ex.x, c * xp.y - sn * ex.y);
+    M[sw16(row, q)] = make_float2(sn * xp.x + c * ex.x, sn * xp.y + c * ex.y);
   }
   return off;
 }
 
-// The same round in FP64 (after the FP32 stage): FP64 inner products, an
-// FP32 rotation angle, a rotation unitary to FP64 rounding (rsqrt_d, no
-// FP64 division or square root).  Returns whether the pair is still above
-// |g| <= tol |W_p| |W_q|.
-__device__ __forceinline__ bool jacobi16_round_d(Polar16Smem& S, int r, double tol2) {
+// The same round in FP64 (after the FP32 stage), two column pairs per warp
+// so that the FP64 pipe (1/64 of the FP32 rate) does no work for zeros:
+// warp w < 4 takes pairs 2 w (lanes 0-15) and 2 w + 1 (lanes 16-31), lane
+// l holding row l % 16 of W and of Y.  FP64 inner products over the
+// half-warp, an FP32 rotation angle and a rotation unitary to FP64 rounding
+// (rsqrt_d, no FP64 division or square root); pairs with
+// |g| <= 1e-2 tol |W_p| |W_q| are left alone.
+__device__ __forceinline__ void jacobi16_round_d(Polar16Smem& S, int r, double tol2) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int p = pair_col(r, w), q = p ^ r, row = lane & 15;
-  const bool isW = lane < 16;
-  double2* M = isW ? S.w : S.y;
-  const double2 xp = M[row * 16 + p], xq = M[row * 16 + q];
-  double al = isW ? xp.x * xp.x + xp.y * xp.y : 0.0;
-  double be = isW ? xq.x * xq.x + xq.y * xq.y : 0.0;
-  double gx = isW ? xp.x * xq.x + xp.y * xq.y : 0.0;
-  double gy = isW ? xp.x * xq.y - xp.y * xq.x : 0.0;
+  if (w >= 4) return;
+  const int p = pair_col(r, 2 * w + (lane >> 4)), q = p ^ r, row = lane & 15;
+  const double2 xp = S.w[sw16(row, p)], xq = S.w[sw16(row, q)];
+  double al = xp.x * xp.x + xp.y * xp.y;
+  double be = xq.x * xq.x + xq.y * xq.y;
+  double gx = xp.x * xq.x + xp.y * xq.y;  // conj(W[i][p]) W[i][q]
+  double gy = xp.x * xq.y - xp.y * xq.x;
 #pragma unroll
   for (int h = 1; h < 16; h <<= 1) {
     al += __shfl_xor_sync(kFull, al, h);
@@ -199,12 +208,7 @@ __device__ __forceinline__ bool jacobi16_round_d(Polar16Smem& S, int r, double t
     gx += __shfl_xor_sync(kFull, gx, h);
     gy += __shfl_xor_sync(kFull, gy, h);
   }
-  al = __shfl_sync(kFull, al, 0);
-  be = __shfl_sync(kFull, be, 0);
-  gx = __shfl_sync(kFull, gx, 0);
-  gy = __shfl_sync(kFull, gy, 0);
   const double g2 = gx * gx + gy * gy, ab = al * be;
-  // rotate where |g| is above FP64 rounding of |W_p| |W_q| (and normal)
   if (g2 > 1e-4 * tol2 * ab && g2 > 1e-300) {
     const double rg = rsqrt_d(g2);
     const float z = (float)(0.5 * (be - al) * rg), az = fabsf(z);
@@ -213,10 +217,24 @@ __device__ __forceinline__ bool jacobi16_round_d(Polar16Smem& S, int r, double t
     const double c = rsqrt_d(1.0 + tt * tt), sn = c * tt;
     const double2 e = make_double2(gx * rg, -gy * rg);  // conj(g) / |g|
     const double2 ex = cmul(e, xq);
-    M[row * 16 + p] = make_double2(c * xp.x - sn * ex.x, c * xp.y - sn * ex.y);
-    M[row * 16 + q] = make_double2(sn * xp.x + c * ex.x, sn * xp.y + c * ex.y);
+    S.w[sw16(row, p)] = make_double2(c * xp.x - sn * ex.x, c * xp.y - sn * ex.y);
+    S.w[sw16(row, q)] = make_double2(sn * xp.x + c * ex.x, sn * xp.y + c * ex.y);
+    const double2 yp = S.y[sw16(row, p)], yq = S.y[sw16(row, q)];
+    const double2 ey = cmul(e, yq);
+    S.y[sw16(row, p)] = make_double2(c * yp.x - sn * ey.x, c * yp.y - sn * ey.y);
+    S.y[sw16(row, q)] = make_double2(sn * yp.x + c * ey.x, sn * yp.y + c * ey.y);
   }
-  return g2 > tol2 * ab;
+}
+
+// Whether every column pair of W is orthogonal to |g| <= tol |W_p| |W_q|
+// (the Gram matrix W^dagger W in FP64; t1 is scratch).
+__device__ __forceinline__ bool cta_w_orthogonal(Polar16Smem& S, double tol2) {
+  const int t = threadIdx.x, i = t >> 4, j = t & 15;
+  cta_mm<kMmDN>(S.w, S.w, S.t1);
+  const double2 g = S.t1[swt(t)];
+  const double gii = S.t1[16 * i].x, gjj = S.t1[16 * j].x;
+  const bool open = i != j && g.x * g.x + g.y * g.y > tol2 * gii * gjj;
+  return !__syncthreads_or(open);
 }
 
 // X for a nearly singular A (warp 0; lane i < 16 holds row i): the columns
@@ -243,7 +261,7 @@ __device__ void gram_schmidt16(Polar16Smem& S, double smax) {
         if (!(S.s[k] > 1e-13 * smax)) continue;
         if (lane < 16) {
           const double inv = 1.0 / S.s[k];
-          v = make_double2(S.w[lane * 16 + k].x * inv, S.w[lane * 16 + k].y * inv);
+          v = make_double2(S.w[sw16(lane, k)].x * inv, S.w[sw16(lane, k)].y * inv);
         }
       } else if (lane == att - 1) {
         v = make_double2(1.0, 0.0);
@@ -251,7 +269,7 @@ __device__ void gram_schmidt16(Polar16Smem& S, double smax) {
       for (int pass = 0; pass < 2; ++pass)
         for (int jj = 0; jj < 16; ++jj) {
           if (!(done & (1u << jj))) continue;
-          const double2 xj = lane < 16 ? S.x[lane * 16 + jj] : make_double2(0.0, 0.0);
+          const double2 xj = lane < 16 ? S.x[sw16(lane, jj)] : make_double2(0.0, 0.0);
           double2 d = cfma_cj(xj, v, make_double2(0.0, 0.0));
 #pragma unroll
           for (int h = 16; h >= 1; h >>= 1) {
@@ -268,7 +286,7 @@ __device__ void gram_schmidt16(Polar16Smem& S, double smax) {
       nv = sqrt(nv);
       // among e_0..e_15 one keeps a residual of at least 1/4
       if (nv > 0.24) {
-        if (lane < 16) S.x[lane * 16 + k] = make_double2(v.x / nv, v.y / nv);
+        if (lane < 16) S.x[sw16(lane, k)] = make_double2(v.x / nv, v.y / nv);
         done |= 1u << k;
         break;
       }
@@ -283,22 +301,22 @@ __device__ void gram_schmidt16(Polar16Smem& S, double smax) {
 __device__ bool cta_polar16(Polar16Smem& S, double* sig) {
   const int t = threadIdx.x, i = t >> 4, j = t & 15;
   {
-    const double2 a = S.a[t];
+    const double2 a = S.a[swt(t)];
     if (__syncthreads_or(!(isfinite(a.x) && isfinite(a.y)))) return false;
   }
   // exact power-of-two scaling: the largest entry in [1, 4)
   unsigned em = cta_max_exponent(S);
   double pre = 1.0;
   if (em == 0u) {
-    const double2 a = S.a[t];
+    const double2 a = S.a[swt(t)];
     if (__syncthreads_and(a.x == 0.0 && a.y == 0.0)) {  // A = 0: every unitary is optimal
-      S.x[t] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      S.x[swt(t)] = make_double2(i == j ? 1.0 : 0.0, 0.0);
       *sig = 0.0;
       __syncthreads();
       return true;
     }
     pre = __hiloint2double((1023 + 600) << 20, 0);  // 2^600: subnormal entries only
-    S.a[t] = make_double2(a.x * pre, a.y * pre);
+    S.a[swt(t)] = make_double2(a.x * pre, a.y * pre);
     em = cta_max_exponent(S);
   }
   if (em > 2045u) em = 2045u;
@@ -306,10 +324,10 @@ __device__ bool cta_polar16(Polar16Smem& S, double* sig) {
   const double unscale =
       __hiloint2double((int)em << 20, 0) * (pre == 1.0 ? 1.0 : __hiloint2double((1023 - 600) << 20, 0));
   {
-    const double2 a = S.a[t];
-    S.a[t] = make_double2(a.x * sc, a.y * sc);
-    S.fw[t] = make_float2((float)(a.x * sc), (float)(a.y * sc));
-    S.fy[t] = make_float2(i == j ? 1.f : 0.f, 0.f);
+    const double2 a = S.a[swt(t)];
+    S.a[swt(t)] = make_double2(a.x * sc, a.y * sc);
+    S.fw[swt(t)] = make_float2((float)(a.x * sc), (float)(a.y * sc));
+    S.fy[swt(t)] = make_float2(i == j ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
   // stage 1: FP32 one-sided Jacobi to an off-diagonal measure of 1e-6
@@ -326,22 +344,21 @@ __device__ bool cta_polar16(Polar16Smem& S, double* sig) {
     if (S.off[sweep & 1] < 1e-6f) break;
   }
   // stage 2: Y unitary in FP64, W = A Y, FP64 sweeps to 1e-15
-  S.y[t] = to_d2(S.fy[t]);
+  S.y[swt(t)] = to_d2(S.fy[swt(t)]);
   __syncthreads();
   cta_newton_schulz(S.y, S.t1, S.t2, 2);
   cta_mm<kMmNN>(S.a, S.y, S.w);
   const double tol2 = 1e-30;
   for (int sweep = 0; sweep < 8; ++sweep) {
-    bool open = false;
     for (int r = 1; r <= 15; ++r) {
-      open |= jacobi16_round_d(S, r, tol2);
+      jacobi16_round_d(S, r, tol2);
       __syncthreads();
     }
-    if (!__syncthreads_or(open)) break;
+    if (cta_w_orthogonal(S, tol2)) break;
   }
   if (t < 16) {
     double s2 = 0.0;
-    for (int r = 0; r < 16; ++r) s2 += S.w[r * 16 + t].x * S.w[r * 16 + t].x + S.w[r * 16 + t].y * S.w[r * 16 + t].y;
+    for (int r = 0; r < 16; ++r) s2 += S.w[sw16(r, t)].x * S.w[sw16(r, t)].x + S.w[sw16(r, t)].y * S.w[sw16(r, t)].y;
     S.s[t] = sqrt(s2);
   }
   __syncthreads();
@@ -353,14 +370,14 @@ __device__ bool cta_polar16(Polar16Smem& S, double* sig) {
   }
   if (smin > 1e-3 * smax) {
     const double inv = 1.0 / S.s[j];
-    S.x[t] = make_double2(S.w[t].x * inv, S.w[t].y * inv);
+    S.x[swt(t)] = make_double2(S.w[swt(t)].x * inv, S.w[swt(t)].y * inv);
   } else if (t < 32) {  // rare: re-orthonormalise, complete the null space
     gram_schmidt16(S, smax);
   }
   __syncthreads();
   cta_mm<kMmND>(S.y, S.x, S.t1);  // u = Y X^dagger
-  const double2 u = S.t1[t];
-  S.x[t] = u;
+  const double2 u = S.t1[swt(t)];
+  S.x[swt(t)] = u;
   *sig = ssum * unscale;
   return __syncthreads_and(isfinite(u.x) && isfinite(u.y));
 }
@@ -425,16 +442,16 @@ env16_kernel(const typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, i
     out[s * out_stride + t] = P;
     return;
   }
-  S.t1[t] = P;
+  S.t1[swt(t)] = P;
   const double2 u = gates_k[s * gstride + t];
-  S.t2[t] = u;
+  S.t2[swt(t)] = u;
   __syncthreads();
-  const double2 ud = cconj(S.t2[j * 16 + i]);  // u^dagger[i][j]
+  const double2 ud = cconj(S.t2[sw16(j, i)]);  // u^dagger[i][j]
   if (mode == kForward)
     cta_mm<kMmDN>(S.t2, S.t1, S.a);  // u^dagger P
   else
     cta_mm<kMmND>(S.t1, S.t2, S.a);  // P u^dagger
-  const double2 E = S.a[t];
+  const double2 E = S.a[swt(t)];
   if (out) out[s * out_stride + t] = E;
   double2* lr = LR + (size_t)s * 512;
   if (mode == kEnvOnly) {
@@ -442,12 +459,12 @@ env16_kernel(const typename Cplx<R>::T* __restrict__ T, int n, int p0, int p1, i
     lr[256 + t] = ud;
     return;
   }
-  if (beta != 0.0) S.a[t] = make_double2((1.0 - beta) * E.x + beta * ud.x, (1.0 - beta) * E.y + beta * ud.y);
+  if (beta != 0.0) S.a[swt(t)] = make_double2((1.0 - beta) * E.x + beta * ud.x, (1.0 - beta) * E.y + beta * ud.y);
   __syncthreads();
   double sg = 0.0;
   double2 un;
   if (cta_polar16(S, &sg)) {
-    un = S.x[t];
+    un = S.x[swt(t)];
   } else {
     if (t == 0) atomicCAS(status, 0, -4);
     un = u;  // keep the old gate: the tensor stays consistent
@@ -472,11 +489,11 @@ __global__ void __launch_bounds__(kCta16) optimize16_kernel(const double2* __res
     const double2 d = cconj(u_old[(size_t)m * 256 + j * 16 + i]);
     a = make_double2((1.0 - beta) * a.x + beta * d.x, (1.0 - beta) * a.y + beta * d.y);
   }
-  S.a[t] = a;
+  S.a[swt(t)] = a;
   __syncthreads();
   double sg = 0.0;
   const bool ok = cta_polar16(S, &sg);
-  u_out[(size_t)m * 256 + t] = ok ? S.x[t] : make_double2(NAN, NAN);
+  u_out[(size_t)m * 256 + t] = ok ? S.x[swt(t)] : make_double2(NAN, NAN);
   if (sigma_out && t == 0) sigma_out[m] = ok ? sg : NAN;
 }
 
@@ -490,10 +507,10 @@ __global__ void __launch_bounds__(kCta16) reunitarize16_kernel(double2* __restri
   const int2 d = desc[k];
   if (d.x != 4) return;  // the whole CTA leaves together
   double2* gp = gates + (size_t)s * gsz + d.y;
-  M[threadIdx.x] = gp[threadIdx.x];
+  M[swt(threadIdx.x)] = gp[threadIdx.x];
   __syncthreads();
   cta_newton_schulz(M, t1, t2, 3);
-  gp[threadIdx.x] = M[threadIdx.x];
+  gp[threadIdx.x] = M[swt(threadIdx.x)];
 }
 
 // ------------------------------------------------------------------ pass
