@@ -184,6 +184,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_tf32_peak():
+    """Dense TF32 tensor rate: the measured sustained BF16 GEMM rate (the
+    pass is timed inside long sweeps) times the nominal TF32 / BF16 ratio;
+    the fallback's sustained BF16 figure without the file."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("bf16_tflops_sustained"):
+            return float(d["bf16_tflops_sustained"]) * TF32_PER_BF16, \
+                "measured bf16_tflops_sustained x nominal TF32/BF16 (1.1/2.25)"
+    return 1700.0 * TF32_PER_BF16, "fallback sustained BF16 1.7 PFLOP/s x nominal TF32/BF16 (1.1/2.25)"
+
+
 _ALU_PEAKS = {}
 
 
@@ -688,16 +702,21 @@ def run_kqubit(args, qf, torch, dev):
             "final_costs": [float(c) for c in costs]}
 
 
-# FP32 FMA operations per tensor entry of a complex64 16x16 pass (both
-# operators): 2 x 16 complex multiply-adds of 4 FMAs.
-K4_FMA_PER_ENTRY = 2 * 16 * 4
+# Tensor-core flops per tensor entry of the complex64 16x16 pass (both
+# operators, tcgen05 in 3xTF32 form): two stages of a real K = 32 dot
+# product per real output value (2 per entry), three TF32 products each.
+K4_TC_FLOPS_PER_ENTRY = 2 * 2 * 32 * 2 * 3
+# nominal dense TF32 / BF16 tensor rate on GB300 (1.1 / 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
 
 
 def run_k4(args, qf, torch, dev):
     """Four-qubit gates: 12 qubits, layers of gates on consecutive quadruples
     (offsets 0 and 2 in turn, 15 gates), 8 starts, complex64 tensors, one
-    sweep per step; the 16x16 pass reads and writes the tensor once per
-    update but does 128 FP32 FMAs per entry, so the FP32 pipe bounds it."""
+    sweep per step.  The 16x16 pass reads and writes the tensor once per
+    update and runs its 128 complex-FMA-equivalents per entry on the tensor
+    cores (768 TF32 flops per entry in 3xTF32 form), so HBM is its
+    roofline (48 flop/byte, below the TF32 ridge of about 120)."""
     n, S = 12, 8
     locs = []
     for layer in range(6):
@@ -734,23 +753,25 @@ def run_k4(args, qf, torch, dev):
         raise RuntimeError("device status reports a non-finite update")
     plan.close()
     peak, peak_kind = measured_peaks()
-    peaks = measured_alu_peaks(torch, dev)
     avg_s = (pass_ms / 1e3) / max(launches, 1)
     alg = pbytes / max(launches, 1)
     entries = alg / 16  # 8-byte entries, read + write
-    fma_ops = entries * K4_FMA_PER_ENTRY / avg_s / 1e9
-    fma_peak = peaks["fp32_gflops"] / 2  # measured SGEMM flops, an FMA counted twice
+    tc_tflops = entries * K4_TC_FLOPS_PER_ENTRY / avg_s / 1e12
+    tf32_peak, tf32_kind = measured_tf32_peak()
     updates = S * 2 * len(locs) * steps
     return {"metric": "gate-updates/s at 12 qubits, four-qubit gates, complex64",
             "unit": "gate-updates/s", "value": updates / (ms_graph / 1e3),
             "ms_per_sweep": ms_graph / steps, "ms_per_sweep_live": ms / steps,
             "workload": f"12 qubits, {len(locs)} four-qubit gates on consecutive quadruples (6 layers, "
                         "offsets 0/2), 8 starts, reachable Haar target, complex64 tensor, FP64 16x16 update",
-            "roofline": {"bound": "alu", "achieved": fma_ops, "peak": fma_peak, "unit": "G FMA/s",
-                         "frac": fma_ops / fma_peak,
-                         "kernel": "pass16_kernel (B <- L B R on 16x16 blocks, 128 FP32 FMAs per entry)",
-                         "peak_source": "measured FP32: " + peaks["how"] + "; FMAs = flops / 2",
+            "roofline": {"bound": "hbm", "achieved": alg / avg_s / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / avg_s / 1e9 / peak,
+                         "kernel": "pass16tc_kernel (B <- L B R on 16x16 blocks, tcgen05 3xTF32)",
+                         "peak_source": peak_kind,
                          "hbm_gbs": alg / avg_s / 1e9, "hbm_frac": alg / avg_s / 1e9 / peak,
+                         "tensor": {"achieved_tflops": tc_tflops, "peak_tflops": tf32_peak,
+                                    "frac": tc_tflops / tf32_peak if tf32_peak else None,
+                                    "peak_source": tf32_kind},
                          "alg_bytes_per_launch": alg, "avg_launch_ms": avg_s * 1e3,
                          "pass_share_of_step": pass_ms / ms if ms > 0 else None},
             "final_costs": [float(c) for c in costs]}
