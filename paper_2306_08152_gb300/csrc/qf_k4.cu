@@ -1008,25 +1008,33 @@ pass16tc_kernel(float2* __restrict__ T, int n, int S, int p0, int p1, int p2, in
     if (more) geom(tile + 1, s_cur, b_cur);
     if (s != cur_s) {  // embed this start's operators (no MMA is in flight)
       cur_s = s;
+      // one complex entry O[a][b] per thread and step -> the four real
+      // entries (2 a + c', 2 b + c), hi and lo
 #pragma unroll 1
-      for (int e = tid; e < 2 * 32 * 32; e += kTcThreads) {
-        const int which = e >> 10, nn = (e >> 5) & 31, k = e & 31;
-        const int a = nn >> 1, cp = nn & 1, b = k >> 1, c = k & 1;
+      for (int e = tid; e < 512; e += kTcThreads) {
+        const int which = e >> 8, a = (e >> 4) & 15, b = e & 15;
         int ga = 0, gb = 0;  // the gate's own local indices of a and b
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           ga |= ((a >> q) & 1) << (3 - pidx[q]);
           gb |= ((b >> q) & 1) << (3 - pidx[q]);
         }
-        // O = L (a: output row) or R^T (a: output column)
+        // O = L (a: output row) or R^T (a: output column); FP32 operators,
+        // as the FMA kernels
         const double2 o = which == 0 ? L[s * Ls + ga * 16 + gb] : Rm[s * Rs + gb * 16 + ga];
-        const float ore = (float)o.x, oim = (float)o.y;  // FP32 operators, as the FMA kernels
-        const float val = (cp == c) ? ore : (cp == 0 ? -oim : oim);
-        const uint32_t hi = tc::tf32(val);
-        const uint32_t lo = tc::tf32(val - __uint_as_float(hi));
+        const float ore = (float)o.x, oim = (float)o.y;
         unsigned char* obase = ops + which * 8192;
-        *reinterpret_cast<uint32_t*>(obase + sw128_off(nn, k)) = hi;
-        *reinterpret_cast<uint32_t*>(obase + 4096 + sw128_off(nn, k)) = lo;
+#pragma unroll
+        for (int cp = 0; cp < 2; ++cp)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const float val = (cp == c) ? ore : (cp == 0 ? -oim : oim);
+            const uint32_t hi = tc::tf32(val);
+            const uint32_t lo = tc::tf32(val - __uint_as_float(hi));
+            const uint32_t off = sw128_off(2 * a + cp, 2 * b + c);
+            *reinterpret_cast<uint32_t*>(obase + off) = hi;
+            *reinterpret_cast<uint32_t*>(obase + 4096 + off) = lo;
+          }
       }
       tc::fence_async_smem();
     }
