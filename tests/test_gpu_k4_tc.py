@@ -9,7 +9,7 @@ ApplyRight / ApplyLeft (Alg. 1) element by element:
   starts per launch, so CTAs whose tiles cross into the next start re-embed
   the operators;
 - the benchmark's launch (12 qubits, 4 starts per launch) at every
-  consecutive quadruple;
+  consecutive quadruple, and every set of four qubits at 8 qubits;
 - a whole 12-qubit sweep of 15 four-qubit gates through the plan (two start
   groups, the second sweep a CUDA-graph replay) against the oracle's
   TwoSidedSweep;
@@ -155,3 +155,29 @@ def test_tc_wait_limit_reports_timeout(qf):
         ref = ok.apply_left_k(ok.apply_right_k(T0[s].astype(np.complex128), R[s].cpu().numpy(), q, n),
                               L[s].cpu().numpy(), q, n)
         assert _relerr(out[s], ref) <= TOL
+
+
+def test_tc_pass_every_gate_position_8q(qf):
+    """Every set of four qubits at 8 qubits (70 sets, each in a shuffled
+    local order): the tile's column set, the operator permutation to
+    ascending-bit order and the bank layout all depend on where the gate
+    bits fall."""
+    import itertools
+
+    n, S = 8, 2
+    g = qi.rng(15500)
+    worst = 0.0
+    for subset in itertools.combinations(range(n), 4):
+        q = tuple(int(x) for x in g.permutation(np.array(subset)))
+        T0 = _rand_T(S, n, g).astype(np.complex64)
+        L = np.stack([qi.haar_unitary(16, g) for _ in range(S)])
+        R = np.stack([qi.haar_unitary(16, g) for _ in range(S)])
+        T = torch.from_numpy(T0).cuda()
+        qf.apply_gate_k(T, q, torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda())
+        out = T.cpu().numpy().astype(np.complex128)
+        for s in range(S):
+            ref = ok.apply_left_k(ok.apply_right_k(T0[s].astype(np.complex128), R[s], q, n), L[s], q, n)
+            err = _relerr(out[s], ref)
+            worst = max(worst, err)
+            assert err <= TOL, (q, s, err)
+    print(f"tensor-core 16x16 pass, all 70 four-qubit sets at n=8: max rel err {worst:.2e}")
