@@ -311,6 +311,10 @@ int qf_cost_grad_k(const qf_c128* target, int n_qubits, int n_gates,
 /* Steps for one gate of size k (parity tests; enqueue only):
  *   qf_apply_gate_k     T_s <- (L_s on q) T_s (R_s on q); L, R device
  *                       n_starts x 4^k (either may be NULL for identity).
+ *                       Four-qubit complex64 calls with both operators at
+ *                       n_qubits >= 7 run on the tensor cores (see
+ *                       qf_set_tc_wait_limit); a wait that runs out leaves
+ *                       NaN in the entries it did not finish.
  *   qf_partial_trace_k  P_s = partial trace of T_s over every qubit not in
  *                       q (CalcEnvMat, Alg. 1); P device n_starts x 4^k.
  *                       k = 3 and 4 allocate their scratch stream-ordered.
