@@ -286,13 +286,31 @@ typedef struct {
  * updates use the 8x8 FP64 polar (one-sided Jacobi on one warp), the
  * four-qubit updates the 16x16 FP64 polar (one-sided Jacobi on one CTA of
  * 256 threads); the look-ahead and the one-pass InitCircuitTensor apply to
- * two-qubit-only circuits.  Errors as qf_instantiate_ex, QF_EINVAL for k
+ * two-qubit-only circuits, qf_instantiate_batched_k takes 2- and 3-qubit
+ * gates.  Errors as qf_instantiate_ex, QF_EINVAL for k
  * outside {2, 3, 4}, k > n_qubits, repeated or out-of-range qubits. */
 int qf_instantiate_k(const qf_c128* target, int n_qubits, int n_gates,
                      const qf_gate_loc* locations, int n_starts,
                      const qf_c128* initial_gates, const qf_options* opts,
                      qf_c128* out_gates, double* out_costs,
                      qf_result* out_result, void* stream);
+
+/* qf_instantiate_batched for circuits of 2- and 3-qubit gates: the same
+ * per-warp Qfactor (multistart rule, stopping rules, precisions, autotuner,
+ * cost history), with the three-qubit updates as the band sum over 8x8
+ * blocks, the warp 8x8 FP64 polar and the fused pass on 8x8 blocks in the
+ * warp's shared memory.  locations: host-or-device, concatenated over
+ * instances (n_gates[i] each); initial_gates and out_gates: host-or-device,
+ * [instance][start][E_i entries] in the concatenated gate layout above.
+ * Errors as qf_instantiate_batched, QF_EINVAL for k outside {2, 3}, k above
+ * an instance's qubit count, repeated or out-of-range qubits. */
+int qf_instantiate_batched_k(int n_instances, const int32_t* n_qubits,
+                             const int32_t* n_gates, const qf_gate_loc* locations,
+                             const qf_c128* targets, int n_starts,
+                             const qf_c128* initial_gates, const qf_options* opts,
+                             qf_c128* out_gates, double* out_costs,
+                             int32_t* out_sweeps, int32_t* out_best,
+                             qf_batch_stats* stats, void* stream);
 
 /* qf_cost_and_env / qf_cost_grad for a circuit of 2-, 3- and 4-qubit gates
  * (the same adjoint walk; Sec. III: Tr(V^dagger C) = Tr(E_k u_k) for a gate

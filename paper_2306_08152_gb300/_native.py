@@ -108,6 +108,8 @@ SIGNATURES = {
     "qf_cost_grad_k": (I, [P, I, I, P, I, P, DP, P, P]),
     "qf_instantiate_batched": (I, [I, P, P, P, P, I, P, ct.POINTER(qf_options), P, DP, P, P,
                                    ct.POINTER(qf_batch_stats), P]),
+    "qf_instantiate_batched_k": (I, [I, P, P, P, P, I, P, ct.POINTER(qf_options), P, DP, P, P,
+                                     ct.POINTER(qf_batch_stats), P]),
     "qf_plan_create": (I, [I, I, P, I, I, ct.POINTER(P)]),
     "qf_plan_destroy": (I, [P]),
     "qf_plan_load": (I, [P, P, P, P]),

@@ -23,6 +23,7 @@ __all__ = [
     "instantiate_k", "apply_gate_k", "partial_trace_k", "optimize_gates_k", "init_tensor_k",
     "circuit_unitary_k", "flatten_gates", "unflatten_gates", "gate_entries", "optimize_gates", "reunitarize_gates", "trace", "circuit_unitary",
     "gate_specs", "spec_slots", "instantiate_spec", "cost_and_env_k", "cost_grad_k", "set_tc_wait_limit",
+    "instantiate_batched_k",
 ]
 
 QF_C128 = nat.QF_C128
@@ -305,6 +306,63 @@ def instantiate_batched(instances, options=None, stream=None, history=False, **k
     for i in range(I):
         k = S * ng[i] * 16
         gates.append(out[off:off + k].reshape(S, ng[i], 4, 4))
+        off += k
+    r = {"costs": costs.reshape(I, S), "sweeps": sweeps.reshape(I, S), "best": best,
+         "gates": gates, "warps_per_cta": stats.warps_per_cta, "ctas": stats.ctas,
+         "kernel_ms": stats.kernel_ms, "total_sweeps": stats.total_sweeps,
+         "total_c64_sweeps": stats.total_c64_sweeps}
+    if history:
+        r["history"] = hist.reshape(I, S, -1)
+    return r
+
+
+def instantiate_batched_k(instances, options=None, stream=None, history=False, **kw):
+    """instantiate_batched for circuits of 2- and 3-qubit gates
+    (qf_instantiate_batched_k).  ``instances`` is a sequence of (target
+    (N,N), locations (sequence of qubit tuples of 2 or 3), starts: S lists
+    of 2^k x 2^k gates or an (S, E) concatenated array) with the same S.
+    Returns the dict of instantiate_batched with "gates" as S lists of
+    gate arrays per instance."""
+    targets, locs, starts, nq, ng, lists = [], [], [], [], [], []
+    S = None
+    for V, L, G in instances:
+        V = np.ascontiguousarray(np.asarray(V, dtype=np.complex128))
+        arr, lq = _gate_locs(L)
+        flat = G if isinstance(G, (np.ndarray, torch.Tensor)) and np.ndim(G) == 2 else flatten_gates(G)
+        flat = np.ascontiguousarray(np.asarray(flat, dtype=np.complex128))
+        if S is None:
+            S = flat.shape[0]
+        if flat.shape != (S, gate_entries(lq)):
+            raise ValueError("every instance needs the same number of starts and its gate entries per start")
+        nq.append(int(V.shape[0]).bit_length() - 1)
+        ng.append(len(lq))
+        targets.append(V.reshape(-1))
+        locs.extend(arr)
+        lists.append(lq)
+        starts.append(flat.reshape(-1))
+    I = len(nq)
+    nq = np.asarray(nq, dtype=np.int32)
+    ng = np.asarray(ng, dtype=np.int32)
+    tg = np.concatenate(targets)
+    larr = (nat.qf_gate_loc * len(locs))(*locs)
+    st = np.concatenate(starts)
+    out = np.empty_like(st)
+    costs = np.empty(I * S, dtype=np.float64)
+    sweeps = np.empty(I * S, dtype=np.int32)
+    best = np.empty(I, dtype=np.int32)
+    stats = nat.qf_batch_stats()
+    opts = options if options is not None else Options(**kw)
+    oc, hist = _history_buffer(opts, I * S) if history else (opts.c, None)
+    check(_lib().qf_instantiate_batched_k(
+        I, ct.c_void_p(nq.ctypes.data), ct.c_void_p(ng.ctypes.data), larr,
+        ct.c_void_p(tg.ctypes.data), S, ct.c_void_p(st.ctypes.data), ct.byref(oc),
+        ct.c_void_p(out.ctypes.data), costs.ctypes.data_as(ct.POINTER(ct.c_double)),
+        ct.c_void_p(sweeps.ctypes.data), ct.c_void_p(best.ctypes.data), ct.byref(stats),
+        _stream_handle(stream)))
+    gates, off = [], 0
+    for i in range(I):
+        k = S * gate_entries(lists[i])
+        gates.append(unflatten_gates(out[off:off + k].reshape(S, -1), lists[i]))
         off += k
     r = {"costs": costs.reshape(I, S), "sweeps": sweeps.reshape(I, S), "best": best,
          "gates": gates, "warps_per_cta": stats.warps_per_cta, "ctas": stats.ctas,

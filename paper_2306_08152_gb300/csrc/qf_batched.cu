@@ -29,6 +29,7 @@
 #include "qf_device.cuh"
 #include "qf_internal.h"
 #include "qf_polar.cuh"
+#include "qf_warp8.cuh"
 #include "qfactor.h"
 
 namespace qf {
@@ -409,6 +410,354 @@ __global__ void __maxnreg__(168) batched_kernel(BatchParams bp) {
   }
 }
 
+
+// ------------------------------------------------------ circuits of 2- and 3-qubit gates
+//
+// The same per-warp Qfactor for circuits that mix two- and three-qubit
+// gates (Sec. III: a k-qubit unitary is one variable with a 2^k x 2^k
+// environment).  Gate k of an instance is gk[k] = (size, q0, q1, q2) and
+// starts at entry goff[k] of the start's gate block (4^size entries each,
+// row-major in the gate's local index 4 bit(q0) + 2 bit(q1) + bit(q2)).  A
+// three-qubit update is the band sum over 8x8 blocks, E = P u^dagger
+// (backward) or u^dagger P (forward), the warp 8x8 polar of qf_warp8.cuh
+// (lane 8 g + j holds entries (g, j) and (g + 4, j)) and the fused pass on
+// 8x8 blocks; two-qubit gates take the routines above.
+
+struct BatchParamsK {
+  BatchParams b;
+  const int4* gk;       // per gate: (size, q0, q1, q2)
+  const int* goff;      // per gate: entry offset in the start's gate block
+  const int* inst_ge;   // per instance: gate entries per start
+};
+
+template <typename R>
+struct WK {
+  typedef typename Cplx<R>::T C;
+
+  // offset of local index v of a three-qubit gate on bit positions (p0, p1, p2)
+  static __device__ __forceinline__ unsigned off8(unsigned v, int p0, int p1, int p2) {
+    return ((v & 4u) ? 1u << p0 : 0u) | ((v & 2u) ? 1u << p1 : 0u) | ((v & 1u) ? 1u << p2 : 0u);
+  }
+  // zero bits inserted at three ascending positions
+  static __device__ __forceinline__ unsigned dep3(unsigned x, int a, int b, int c) {
+    return dep1(dep1(dep1(x, a), b), c);
+  }
+  static __device__ __forceinline__ void sort3(int p0, int p1, int p2, int& a, int& b, int& c) {
+    a = p0, b = p1, c = p2;
+    if (a > b) { const int t = a; a = b; b = t; }
+    if (b > c) { const int t = b; b = c; c = t; }
+    if (a > b) { const int t = a; a = b; b = t; }
+  }
+
+  // T <- (L on the gate) T (R on the gate) on every 8x8 block, as two
+  // in-place stages (R along each block row, then L along each block column)
+  template <bool HL, bool HR>
+  static __device__ void pass8(C* T, int n, int p0, int p1, int p2, const C* Lm, const C* Rm) {
+    const int lane = threadIdx.x & 31;
+    int a, b, c;
+    sort3(p0, p1, p2, a, b, c);
+    const int lnc = n - 3;
+    const unsigned N = 1u << n, cmask = (1u << lnc) - 1u, nblk = 1u << (2 * lnc);
+    const unsigned items = 8u * nblk;
+    if (HR) {
+      for (unsigned it = lane; it < items; it += 32) {
+        const unsigned blk = it & (nblk - 1u), x = it >> (2 * lnc);
+        const unsigned r0 = dep3(blk >> lnc, a, b, c), c0 = dep3(blk & cmask, a, b, c);
+        C* row = T + (size_t)(r0 | off8(x, p0, p1, p2)) * N + c0;
+        C v[8];
+#pragma unroll
+        for (int y = 0; y < 8; ++y) v[y] = row[off8(y, p0, p1, p2)];
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          C acc = czero<C>();
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc = cfma(v[k], Rm[k * 8 + y], acc);
+          row[off8(y, p0, p1, p2)] = acc;
+        }
+      }
+      __syncwarp();
+    }
+    if (HL) {
+      for (unsigned it = lane; it < items; it += 32) {
+        const unsigned blk = it & (nblk - 1u), y = it >> (2 * lnc);
+        const unsigned r0 = dep3(blk >> lnc, a, b, c), c0 = dep3(blk & cmask, a, b, c);
+        C* col = T + (size_t)r0 * N + (c0 | off8(y, p0, p1, p2));
+        C v[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) v[x] = col[(size_t)off8(x, p0, p1, p2) * N];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+          C acc = czero<C>();
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc = cfma(Lm[x * 8 + k], v[k], acc);
+          col[(size_t)off8(x, p0, p1, p2) * N] = acc;
+        }
+      }
+      __syncwarp();
+    }
+  }
+
+  // P[x][y] = sum over the rests r of T[(r, x), (r, y)] for a three-qubit
+  // gate; lane (g, j) gets P[g][j] and P[g + 4][j] (FP64 from the tensor's
+  // precision)
+  static __device__ void band8(const C* T, int n, int p0, int p1, int p2, const w8::L8& L, double2& P0,
+                               double2& P1) {
+    int a, b, c;
+    sort3(p0, p1, p2, a, b, c);
+    const unsigned N = 1u << n, nr = 1u << (n - 3);
+    const unsigned ox0 = off8((unsigned)L.g, p0, p1, p2), ox1 = off8((unsigned)L.g + 4u, p0, p1, p2);
+    const unsigned oy = off8((unsigned)L.j, p0, p1, p2);
+    R v0x = R(0), v0y = R(0), v1x = R(0), v1y = R(0);
+    for (unsigned r = 0; r < nr; ++r) {
+      const unsigned d = dep3(r, a, b, c);
+      const C e0 = T[(size_t)(d | ox0) * N + (d | oy)], e1 = T[(size_t)(d | ox1) * N + (d | oy)];
+      v0x += e0.x;
+      v0y += e0.y;
+      v1x += e1.x;
+      v1y += e1.y;
+    }
+    P0 = make_double2((double)v0x, (double)v0y);
+    P1 = make_double2((double)v1x, (double)v1y);
+  }
+
+  // InitCircuitTensor: T <- V^dagger, then every gate on the right in order.
+  static __device__ __noinline__ void build(C* T, C* LRs, const double2* V, const double2* g,
+                                            const int4* gk, const int* goff, int n, int p, const Lane& L) {
+    W<R>::conj_transpose(T, V, n);
+    for (int k = 0; k < p; ++k) {
+      const int4 d = gk[k];
+      const double2* gp = g + goff[k];
+      if (d.x == 3) {
+        for (int e = L.l; e < 64; e += 32) LRs[64 + e] = cmake(gp[e], R());
+        __syncwarp();
+        pass8<false, true>(T, n, n - 1 - d.y, n - 1 - d.z, n - 1 - d.w, LRs, LRs + 64);
+      } else {
+        if (L.l < 16) LRs[64 + L.l] = cmake(gp[L.l], R());
+        __syncwarp();
+        W<R>::template pass<false, true>(T, n, n - 1 - d.y, n - 1 - d.z, LRs, LRs + 64);
+      }
+    }
+  }
+
+  // One three-qubit update: band, E, the warp 8x8 polar, the operators, the
+  // fused pass.
+  static __device__ __noinline__ void update8(C* T, C* LRs, double2* sm8, double2* g, int4 d, int n,
+                                              bool forward, double beta, int* bad) {
+    const w8::L8 L;
+    const int p0 = n - 1 - d.y, p1 = n - 1 - d.z, p2 = n - 1 - d.w;
+    double2 P0, P1;
+    band8(T, n, p0, p1, p2, L, P0, P1);
+    const double2 u0 = g[L.g * 8 + L.j], u1 = g[(L.g + 4) * 8 + L.j];
+    double2 E0, E1;
+    if (forward)
+      w8::mm8_dn(L, u0, u1, P0, P1, E0, E1);  // u^dagger P
+    else
+      w8::mm8_nd(L, P0, P1, u0, u1, E0, E1);  // P u^dagger
+    double2 ud0 = u0, ud1 = u1;
+    w8::dag8(L, ud0, ud1);
+    double2 A0 = E0, A1 = E1;
+    if (beta != 0.0) {
+      A0 = make_double2((1.0 - beta) * E0.x + beta * ud0.x, (1.0 - beta) * E0.y + beta * ud0.y);
+      A1 = make_double2((1.0 - beta) * E1.x + beta * ud1.x, (1.0 - beta) * E1.y + beta * ud1.y);
+    }
+    double2 n0, n1;
+    double sg = 0.0;
+    if (!w8::warp_polar8(A0, A1, sm8, &n0, &n1, &sg)) {
+      *bad = 1;
+      n0 = u0;  // keep the old gate: the tensor stays consistent
+      n1 = u1;
+    }
+    __syncwarp();
+    g[L.g * 8 + L.j] = n0;
+    g[(L.g + 4) * 8 + L.j] = n1;
+    LRs[L.g * 8 + L.j] = cmake(forward ? ud0 : n0, R());
+    LRs[(L.g + 4) * 8 + L.j] = cmake(forward ? ud1 : n1, R());
+    LRs[64 + L.g * 8 + L.j] = cmake(forward ? n0 : ud0, R());
+    LRs[64 + (L.g + 4) * 8 + L.j] = cmake(forward ? n1 : ud1, R());
+    __syncwarp();
+    pass8<true, true>(T, n, p0, p1, p2, LRs, LRs + 64);
+  }
+
+  // TwoSidedSweep (Alg. 1) over the mixed circuit.
+  static __device__ __noinline__ void sweep(C* T, C* LRs, float2* scratch, double2* sm8, double2* g,
+                                            float2* yp, const int4* gk, const int* goff, int n, int p,
+                                            double beta, const Lane& L, int* bad) {
+    for (int h = 0; h < 2; ++h)
+      for (int i = 0; i < p; ++i) {
+        const int k = h == 0 ? p - 1 - i : i;
+        const int4 d = gk[k];
+        if (d.x == 3)
+          update8(T, LRs, sm8, g + goff[k], d, n, h == 1, beta, bad);
+        else
+          W<R>::update(T, LRs, scratch, g + goff[k], yp + goff[k], make_int2(d.y, d.z), n, h == 1, beta, L,
+                       bad);
+      }
+  }
+};
+
+// Re-unitarisation of a mixed circuit: three FP64 Newton-Schulz steps per gate.
+__device__ void reunitarize_k(double2* g, const int4* gk, const int* goff, int p, const Lane& L) {
+  for (int k = 0; k < p; ++k) {
+    double2* gp = g + goff[k];
+    if (gk[k].x == 3) {
+      const w8::L8 L8;
+      double2 u0 = gp[L8.g * 8 + L8.j], u1 = gp[(L8.g + 4) * 8 + L8.j];
+      for (int step = 0; step < 3; ++step) {
+        double2 P0, P1;
+        w8::mm8_dn(L8, u0, u1, u0, u1, P0, P1);
+        const double2 Q0 = make_double2((L8.g == L8.j ? 1.5 : 0.0) - 0.5 * P0.x, -0.5 * P0.y);
+        const double2 Q1 = make_double2((L8.g + 4 == L8.j ? 1.5 : 0.0) - 0.5 * P1.x, -0.5 * P1.y);
+        w8::mm8(L8, u0, u1, Q0, Q1, u0, u1);
+      }
+      __syncwarp();
+      gp[L8.g * 8 + L8.j] = u0;
+      gp[(L8.g + 4) * 8 + L8.j] = u1;
+      __syncwarp();
+    } else {
+      const int e = L.l & 15;
+      double2 u = gp[e];
+      for (int step = 0; step < 3; ++step) {
+        const double2 P = wmm_dn(L, u, u);
+        const double2 Q = make_double2((L.i == L.j ? 1.5 : 0.0) - 0.5 * P.x, -0.5 * P.y);
+        u = wmm(L, u, Q);
+      }
+      __syncwarp();
+      if (L.l < 16) gp[e] = u;
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void __maxnreg__(168) batched_k_kernel(BatchParamsK pk) {
+  extern __shared__ __align__(256) unsigned char smem[];
+  const BatchParams& bp = pk.b;
+  const int wid = threadIdx.x >> 5;
+  unsigned char* ws = smem + (size_t)wid * bp.warp_bytes;
+  void* Tbuf = ws;
+  unsigned char* after = ws + bp.tmax_bytes;
+  double2* LRd = reinterpret_cast<double2*>(after);             // 128 x 16 B
+  double2* sm8 = reinterpret_cast<double2*>(after + 2048);      // 128 x 16 B
+  float2* scratch = reinterpret_cast<float2*>(after + 4096);    // 32 x 8 B
+  double* ring = reinterpret_cast<double*>(after + 4352);       // kRing x 8 B
+  const Lane L;
+  const unsigned total = (unsigned)bp.n_inst * (unsigned)bp.S;
+  for (;;) {
+    unsigned prob = 0;
+    if (L.l == 0) prob = atomicAdd(bp.work, 1u);
+    prob = __shfl_sync(kFull, prob, 0);
+    if (prob >= total) break;
+    const int i = bp.order[prob / bp.S], s = (int)(prob % bp.S);
+    const BatchInst in = bp.inst[i];
+    const int n = in.n, p = in.p, ge = pk.inst_ge[i];
+    double2* g = bp.gates + in.gate_off + (long long)s * ge;
+    float2* yp = bp.yprev + in.gate_off + (long long)s * ge;
+    const int4* gk = pk.gk + in.loc_off;
+    const int* goff = pk.goff + in.loc_off;
+    if (L.l < 16)
+      for (int k = 0; k < p; ++k)
+        if (gk[k].x == 2) yp[goff[k] + L.l] = make_float2(L.i == L.j ? 1.f : 0.f, 0.f);
+    __syncwarp();
+    const double2* V = bp.targets + in.tgt_off;
+    volatile int* conv = bp.conv_flag + i;
+    volatile int* plat = bp.plat_count + i;
+    bool c64 = bp.precision != QF_C128;
+    const bool refine = bp.precision == QF_C64_REFINE64;
+    int bad = 0;
+    float2* LRf = reinterpret_cast<float2*>(LRd);
+    if (c64)
+      WK<float>::build((float2*)Tbuf, LRf, V, g, gk, goff, n, p, L);
+    else
+      WK<double>::build((double2*)Tbuf, LRd, V, g, gk, goff, n, p, L);
+    double c = c64 ? W<float>::cost((float2*)Tbuf, n) : W<double>::cost((double2*)Tbuf, n);
+    double* hist = bp.hist ? bp.hist + ((long long)i * bp.S + s) * bp.hist_row : nullptr;
+    int len = 0;
+    if (L.l == 0) ring[0] = c;
+    if (hist && L.l == 0) hist[0] = c;
+    len = 1;
+    __syncwarp();
+    int it = 0, c64_sw = 0, reason = QF_STOP_MAX_SWEEPS;
+    bool plateaued = false;
+    for (it = 1; it <= bp.max_sweeps; ++it) {
+      if (*conv) {  // another start of this instance reached dist_tol
+        reason = QF_STOP_CONVERGED;
+        --it;
+        break;
+      }
+      if (c64)
+        WK<float>::sweep((float2*)Tbuf, LRf, scratch, sm8, g, yp, gk, goff, n, p, bp.beta, L, &bad);
+      else
+        WK<double>::sweep((double2*)Tbuf, LRd, scratch, sm8, g, yp, gk, goff, n, p, bp.beta, L, &bad);
+      if (bp.reset_iter > 0 && it % bp.reset_iter == 0) {
+        reunitarize_k(g, gk, goff, p, L);
+        if (c64)
+          WK<float>::build((float2*)Tbuf, LRf, V, g, gk, goff, n, p, L);
+        else
+          WK<double>::build((double2*)Tbuf, LRd, V, g, gk, goff, n, p, L);
+      }
+      c = c64 ? W<float>::cost((float2*)Tbuf, n) : W<double>::cost((double2*)Tbuf, n);
+      if (c64 && refine) {
+        ++c64_sw;
+        // the switch rule of the two-qubit kernel
+        const bool stalled = len > 10 && ring[(len - 10) % kRing] - c < 1e-7;
+        if (c <= bp.switch_tol || (stalled && c <= kStallSwitchCost) || c64_sw >= bp.max_c64) {
+          WK<double>::build((double2*)Tbuf, LRd, V, g, gk, goff, n, p, L);
+          c = W<double>::cost((double2*)Tbuf, n);
+          c64 = false;
+        } else {
+          if (L.l == 0) ring[len % kRing] = c;
+          if (hist && L.l == 0) hist[it] = c;
+          ++len;
+          __syncwarp();
+          if (it >= bp.min_sweeps && !plateaued && plateau_test(ring, len, it, bp)) {
+            plateaued = true;
+            if (L.l == 0) atomicAdd(bp.plat_count + i, 1);
+          }
+          __syncwarp();
+          if (*plat >= bp.S) {
+            reason = QF_STOP_PLATEAU;
+            break;
+          }
+          continue;
+        }
+      }
+      if (L.l == 0) ring[len % kRing] = c;
+      if (hist && L.l == 0) hist[it] = c;
+      ++len;
+      __syncwarp();
+      if (it >= bp.min_sweeps) {
+        if (c <= bp.dist_tol) {
+          if (L.l == 0) atomicExch(bp.conv_flag + i, 1);
+          reason = QF_STOP_CONVERGED;
+          break;
+        }
+        if (!plateaued && plateau_test(ring, len, it, bp)) {
+          plateaued = true;
+          if (L.l == 0) atomicAdd(bp.plat_count + i, 1);
+        }
+        __syncwarp();
+        if (*plat >= bp.S) {
+          reason = QF_STOP_PLATEAU;
+          break;
+        }
+      }
+    }
+    if (it > bp.max_sweeps) it = bp.max_sweeps;
+    if (c64) {  // report an FP64 cost: rebuild the tensor in complex128 once
+      WK<double>::build((double2*)Tbuf, LRd, V, g, gk, goff, n, p, L);
+      c = W<double>::cost((double2*)Tbuf, n);
+    }
+    if (L.l == 0) {
+      const long long q = (long long)i * bp.S + s;
+      bp.cost_out[q] = c;
+      bp.sweeps_out[q] = it;
+      bp.c64_out[q] = c64_sw;
+      bp.reason_out[q] = reason;
+      if (bad) atomicExch(bp.status, QF_ENONFINITE);
+    }
+    __syncwarp();
+  }
+}
+
 // ------------------------------------------------------------------ host
 
 struct DevMem {
@@ -455,23 +804,47 @@ cudaError_t launch_batch(const BatchParams& bp, int wpc, int smem_limit, cudaStr
   return cudaGetLastError();
 }
 
+cudaError_t launch_batch_k(const BatchParamsK& pk, int wpc, int smem_limit, cudaStream_t st,
+                           int* ctas_out) {
+  const int smem = wpc * pk.b.warp_bytes;
+  cudaError_t e = cudaFuncSetAttribute(batched_k_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_limit);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_k_kernel, 32 * wpc, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long problems = (long long)pk.b.n_inst * pk.b.S;
+  long long ctas = (long long)sm_count() * per_sm;
+  const long long need = (problems + wpc - 1) / wpc;
+  if (ctas > need) ctas = need;
+  if (ctas < 1) ctas = 1;
+  if (ctas_out) *ctas_out = (int)ctas;
+  batched_k_kernel<<<(unsigned)ctas, 32 * wpc, smem, st>>>(pk);
+  return cudaGetLastError();
+}
+
 }  // namespace
 }  // namespace qf
 
 using namespace qf;
 
-extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
-                                      const int32_t* n_gates, const qf_loc* locations,
-                                      const qf_c128* targets, int n_starts,
-                                      const qf_c128* initial_gates, const qf_options* opts,
-                                      qf_c128* out_gates, double* out_costs, int32_t* out_sweeps,
-                                      int32_t* out_best, qf_batch_stats* stats, void* stream) {
+namespace {
+
+// The batched call for circuits of two-qubit gates (`locations`) or of two-
+// and three-qubit gates (`klocations`, the mixed kernel); exactly one is set.
+int batched_impl(int n_instances, const int32_t* n_qubits, const int32_t* n_gates,
+                 const qf_loc* locations, const qf_gate_loc* klocations, const qf_c128* targets,
+                 int n_starts, const qf_c128* initial_gates, const qf_options* opts, qf_c128* out_gates,
+                 double* out_costs, int32_t* out_sweeps, int32_t* out_best, qf_batch_stats* stats,
+                 void* stream) {
+  const bool kmode = klocations != nullptr;
   qf_options o;
   qf_options_default(&o);
   if (opts) o = *opts;
   if (n_instances < 1 || n_starts < 1)
     return qf_internal_set_error(QF_EINVAL, "n_instances and n_starts must be >= 1", "");
-  if (!n_qubits || !n_gates || !locations || !targets || !initial_gates || !out_gates ||
+  if (!n_qubits || !n_gates || !(locations || klocations) || !targets || !initial_gates || !out_gates ||
       !out_costs)
     return qf_internal_set_error(QF_EINVAL, "NULL argument", "");
   if (o.max_sweeps < 1) return qf_internal_set_error(QF_EINVAL, "max_sweeps must be >= 1", "");
@@ -485,34 +858,65 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
     return qf_internal_set_error(QF_EINVAL, "long_diff_count must be in [0, 127] here", "");
   // sizes and offsets (host arrays)
   std::vector<BatchInst> inst(n_instances);
-  long long loc_total = 0, tgt_total = 0, gate_total = 0;
-  int nmax = 0;
+  long long loc_total = 0;
   for (int i = 0; i < n_instances; ++i) {
     const int n = n_qubits[i], p = n_gates[i];
     if (n < QF_MIN_QUBITS || n > QF_BATCH_MAX_QUBITS)
       return qf_internal_set_error(QF_EINVAL, "an instance's qubit count is outside [2, QF_BATCH_MAX_QUBITS]", "");
     if (p < 1) return qf_internal_set_error(QF_EINVAL, "an instance has no gates", "");
-    inst[i] = BatchInst{n, p, loc_total, tgt_total, gate_total};
     loc_total += p;
-    tgt_total += 1ll << (2 * n);
-    gate_total += (long long)n_starts * p * 16;
-    if (n > nmax) nmax = n;
   }
   // locations to the host for validation
-  std::vector<qf_loc> hl(loc_total);
-  if (is_dev(locations)) {
-    if (cudaMemcpy(hl.data(), locations, sizeof(qf_loc) * loc_total, cudaMemcpyDeviceToHost) !=
-        cudaSuccess)
-      return qf_internal_set_error(QF_ECUDA, "copying locations failed", "");
-  } else {
-    memcpy(hl.data(), locations, sizeof(qf_loc) * loc_total);
-  }
-  for (int i = 0; i < n_instances; ++i)
-    for (int k = 0; k < inst[i].p; ++k) {
-      const qf_loc l = hl[inst[i].loc_off + k];
-      if (l.a < 0 || l.a >= inst[i].n || l.b < 0 || l.b >= inst[i].n || l.a == l.b)
-        return qf_internal_set_error(QF_EINVAL, "an instance has an invalid location", "");
+  std::vector<qf_loc> hl(kmode ? 0 : loc_total);
+  std::vector<qf_gate_loc> hk(kmode ? loc_total : 0);
+  {
+    void* dst = kmode ? (void*)hk.data() : (void*)hl.data();
+    const void* src = kmode ? (const void*)klocations : (const void*)locations;
+    const size_t bytes = (kmode ? sizeof(qf_gate_loc) : sizeof(qf_loc)) * loc_total;
+    if (is_dev(src)) {
+      if (cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return qf_internal_set_error(QF_ECUDA, "copying locations failed", "");
+    } else {
+      memcpy(dst, src, bytes);
     }
+  }
+  std::vector<int4> hgk(kmode ? loc_total : 0);
+  std::vector<int> hgoff(kmode ? loc_total : 0), hge(n_instances);
+  long long tgt_total = 0, gate_total = 0, lo = 0;
+  int nmax = 0;
+  for (int i = 0; i < n_instances; ++i) {
+    const int n = n_qubits[i], p = n_gates[i];
+    int ge = 0;
+    for (int k = 0; k < p; ++k) {
+      if (kmode) {
+        const qf_gate_loc l = hk[lo + k];
+        if (l.k != 2 && l.k != 3)
+          return qf_internal_set_error(QF_EINVAL, "the batched call takes gates of 2 or 3 qubits", "");
+        for (int a = 0; a < l.k; ++a) {
+          if (l.q[a] < 0 || l.q[a] >= n)
+            return qf_internal_set_error(QF_EINVAL, "an instance has an invalid location", "");
+          for (int b = 0; b < a; ++b)
+            if (l.q[a] == l.q[b])
+              return qf_internal_set_error(QF_EINVAL, "an instance has a repeated qubit", "");
+        }
+        if (l.k > n) return qf_internal_set_error(QF_EINVAL, "a gate has more qubits than its instance", "");
+        hgk[lo + k] = make_int4(l.k, l.q[0], l.q[1], l.k == 3 ? l.q[2] : 0);
+        hgoff[lo + k] = ge;
+        ge += 1 << (2 * l.k);
+      } else {
+        const qf_loc l = hl[lo + k];
+        if (l.a < 0 || l.a >= n || l.b < 0 || l.b >= n || l.a == l.b)
+          return qf_internal_set_error(QF_EINVAL, "an instance has an invalid location", "");
+        ge += 16;
+      }
+    }
+    hge[i] = ge;
+    inst[i] = BatchInst{n, p, lo, tgt_total, gate_total};
+    lo += p;
+    tgt_total += 1ll << (2 * n);
+    gate_total += (long long)n_starts * ge;
+    if (n > nmax) nmax = n;
+  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const long long problems = (long long)n_instances * n_starts;
   // device buffers
@@ -521,10 +925,10 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
   std::vector<int> order(n_instances);
   for (int i = 0; i < n_instances; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    return ((long long)inst[x].p << (2 * inst[x].n)) > ((long long)inst[y].p << (2 * inst[y].n));
+    return ((long long)hge[x] << (2 * inst[x].n)) > ((long long)hge[y] << (2 * inst[y].n));
   });
   DevMem d_inst, d_order, d_locs, d_tgt, d_gates, d_yprev, d_cost, d_sw, d_c64, d_reason, d_flags,
-      d_hist;
+      d_hist, d_gk, d_goff, d_ge;
   const size_t hist_row = (size_t)o.max_sweeps + 1;
   const size_t hist_bytes = sizeof(double) * (size_t)problems * hist_row;
   double* hist_dev = nullptr;  // where the kernel writes the cost history
@@ -541,7 +945,10 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
   }
   if (d_inst.alloc(sizeof(BatchInst) * n_instances) != cudaSuccess ||
       d_order.alloc(sizeof(int) * n_instances) != cudaSuccess ||
-      d_locs.alloc(sizeof(qf_loc) * loc_total) != cudaSuccess ||
+      d_locs.alloc(kmode ? 16 : sizeof(qf_loc) * loc_total) != cudaSuccess ||
+      d_gk.alloc(kmode ? sizeof(int4) * loc_total : 16) != cudaSuccess ||
+      d_goff.alloc(kmode ? sizeof(int) * loc_total : 16) != cudaSuccess ||
+      d_ge.alloc(kmode ? sizeof(int) * n_instances : 16) != cudaSuccess ||
       d_tgt.alloc(sizeof(double2) * tgt_total) != cudaSuccess ||
       d_gates.alloc(sizeof(double2) * gate_total) != cudaSuccess ||
       d_yprev.alloc(sizeof(float2) * gate_total) != cudaSuccess ||
@@ -557,8 +964,14 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_order.p, order.data(), sizeof(int) * n_instances, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && !kmode)
     e = cudaMemcpyAsync(d_locs.p, hl.data(), sizeof(qf_loc) * loc_total, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && kmode)
+    e = cudaMemcpyAsync(d_gk.p, hgk.data(), sizeof(int4) * loc_total, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && kmode)
+    e = cudaMemcpyAsync(d_goff.p, hgoff.data(), sizeof(int) * loc_total, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && kmode)
+    e = cudaMemcpyAsync(d_ge.p, hge.data(), sizeof(int) * n_instances, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_tgt.p, targets, sizeof(double2) * tgt_total, cudaMemcpyDefault, st);
   if (e != cudaSuccess)
@@ -597,7 +1010,13 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
   bp.hist = hist_dev;
   bp.hist_row = (int)hist_row;
   bp.tmax_bytes = (1 << (2 * nmax)) * 16;
-  bp.warp_bytes = ((bp.tmax_bytes + 768 + kRing * 8) + 255) & ~255;
+  // after the tensor: operators, scratch and the cost ring (the mixed kernel
+  // also keeps 8x8 operators and the 8x8 polar's scratch)
+  bp.warp_bytes = ((bp.tmax_bytes + (kmode ? 4352 : 768) + kRing * 8) + 255) & ~255;
+  BatchParamsK pk;
+  pk.gk = (const int4*)d_gk.p;
+  pk.goff = (const int*)d_goff.p;
+  pk.inst_ge = (const int*)d_ge.p;
   const size_t flag_bytes = sizeof(int) * (2 * (size_t)n_instances + 2);
 
   int dev = 0, smem_optin = 0;
@@ -606,10 +1025,15 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
   const int max_wpc = smem_optin / bp.warp_bytes;
   if (max_wpc < 1)
     return qf_internal_set_error(QF_EINVAL, "the largest instance does not fit in shared memory", "");
+  const auto launch = [&](const BatchParams& b, int wpc_, cudaStream_t s_, int* ctas_) {
+    if (!kmode) return launch_batch(b, wpc_, smem_optin, s_, ctas_);
+    pk.b = b;
+    return launch_batch_k(pk, wpc_, smem_optin, s_, ctas_);
+  };
 
   // choose warps per CTA
   int wpc = 0;
-  const auto key = std::make_tuple(nmax, o.precision, dev);
+  const auto key = std::make_tuple(nmax | (kmode ? 256 : 0), o.precision, dev);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tuned.find(key);
@@ -629,7 +1053,7 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
       e = cudaMemcpyAsync(d_gates.p, initial_gates, sizeof(double2) * gate_total, cudaMemcpyDefault, st);
       if (e == cudaSuccess) e = cudaMemsetAsync(d_flags.p, 0, flag_bytes, st);
       if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-      if (e == cudaSuccess) e = launch_batch(tp, cand, smem_optin, st, nullptr);
+      if (e == cudaSuccess) e = launch(tp, cand, st, nullptr);
       if (e == cudaSuccess) e = cudaEventRecord(e1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -667,7 +1091,7 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
     cudaError_t e1 = cudaMemsetAsync(d_flags.p, 0, flag_bytes, cap);
     // all-ones bytes are a NaN: entries after a start's last sweep
     if (e1 == cudaSuccess && hist_dev) e1 = cudaMemsetAsync(hist_dev, 0xff, hist_bytes, cap);
-    cudaError_t e2 = e1 == cudaSuccess ? launch_batch(bp, wpc, smem_optin, cap, &ctas) : e1;
+    cudaError_t e2 = e1 == cudaSuccess ? launch(bp, wpc, cap, &ctas) : e1;
     e = cudaStreamEndCapture(cap, &graph);
     if (e == cudaSuccess) e = e2;
   }
@@ -729,4 +1153,28 @@ extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
   if (hstatus != 0)
     return qf_internal_set_error(QF_ENONFINITE, "an environment or update was not finite", "");
   return QF_OK;
+}
+
+}  // namespace
+
+extern "C" int qf_instantiate_batched(int n_instances, const int32_t* n_qubits,
+                                      const int32_t* n_gates, const qf_loc* locations,
+                                      const qf_c128* targets, int n_starts,
+                                      const qf_c128* initial_gates, const qf_options* opts,
+                                      qf_c128* out_gates, double* out_costs, int32_t* out_sweeps,
+                                      int32_t* out_best, qf_batch_stats* stats, void* stream) {
+  if (!locations) return qf_internal_set_error(QF_EINVAL, "NULL argument", "");
+  return batched_impl(n_instances, n_qubits, n_gates, locations, nullptr, targets, n_starts,
+                      initial_gates, opts, out_gates, out_costs, out_sweeps, out_best, stats, stream);
+}
+
+extern "C" int qf_instantiate_batched_k(int n_instances, const int32_t* n_qubits,
+                                        const int32_t* n_gates, const qf_gate_loc* locations,
+                                        const qf_c128* targets, int n_starts,
+                                        const qf_c128* initial_gates, const qf_options* opts,
+                                        qf_c128* out_gates, double* out_costs, int32_t* out_sweeps,
+                                        int32_t* out_best, qf_batch_stats* stats, void* stream) {
+  if (!locations) return qf_internal_set_error(QF_EINVAL, "NULL argument", "");
+  return batched_impl(n_instances, n_qubits, n_gates, nullptr, locations, targets, n_starts,
+                      initial_gates, opts, out_gates, out_costs, out_sweeps, out_best, stats, stream);
 }

@@ -20,6 +20,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "qf_device.cuh"
@@ -810,7 +811,7 @@ constexpr uint32_t kTcCols = 128;
 constexpr int kTcSmem = 52 * 1024;
 constexpr int kTcChunk = 16;           // tiles per CTA at most
 constexpr int kTcWaitLimit = 1 << 22;  // polls of one completion wait
-int g_tc_wait_limit = kTcWaitLimit;     // qf_set_tc_wait_limit
+std::atomic<int> g_tc_wait_limit{kTcWaitLimit};  // qf_set_tc_wait_limit
 
 // Byte offset of element (row nn, column k) in a K-major, 128-byte-swizzled
 // 32 x 32 TF32 tile (1024-byte aligned).
@@ -1114,13 +1115,13 @@ void pass16_launch(void* T, int n, int S, const int* p, const double2* L, long l
   typedef typename Cplx<R>::T C;
   if constexpr (std::is_same<R, float>::value && HL && HR) {
     if (n >= 7) {
-      static bool attr = false;
-      if (!attr) {
+      static const bool attr = [] {  // once per process (thread-safe static)
         cudaFuncSetAttribute(pass16tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
         cudaFuncSetAttribute(pass16tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        attr = true;
-      }
+        return true;
+      }();
+      (void)attr;
       // chunks of at most kTcChunk tiles per CTA, over several waves: CTAs
       // that find their SM shared with other kernels then delay few tiles
       const long long tiles = (long long)S << (2 * (n - 4) - 3);
@@ -1128,7 +1129,7 @@ void pass16_launch(void* T, int n, int S, const int* p, const double2* L, long l
       long long chunk = (tiles + slots - 1) / slots;
       if (chunk > kTcChunk) chunk = kTcChunk;
       pass16tc_kernel<<<(unsigned)((tiles + chunk - 1) / chunk), kTcThreads, kTcSmem, st>>>(
-          (float2*)T, n, S, p[0], p[1], p[2], p[3], L, Ls, Rm, Rs, status, g_tc_wait_limit);
+          (float2*)T, n, S, p[0], p[1], p[2], p[3], L, Ls, Rm, Rs, status, g_tc_wait_limit.load());
       return;
     }
   }
@@ -1219,7 +1220,6 @@ cudaError_t launch_reunitarize16(double2* gates, long long gsz, const int2* desc
 }  // namespace qf
 
 int qf_set_tc_wait_limit(int polls) {
-  const int old = qf::g_tc_wait_limit;
-  if (polls >= 0) qf::g_tc_wait_limit = polls;
-  return old;
+  if (polls < 0) return qf::g_tc_wait_limit.load();
+  return qf::g_tc_wait_limit.exchange(polls);
 }
