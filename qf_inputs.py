@@ -136,3 +136,41 @@ def batched_instances(count: int, n_starts: int, seed: int,
         sub = int(gen.integers(0, 2**31 - 1))
         out.append(make_problem(int(nq), locs, n_starts, sub))
     return out
+
+
+class InstanceK:
+    """A reachable problem of 2- and 3-qubit gates: ``locs`` qubit tuples,
+    ``target_gates`` and ``starts[j]`` lists of 2^k x 2^k Haar unitaries."""
+
+    def __init__(self, n, locs, target_gates, starts):
+        self.n, self.locs, self.target_gates, self.starts = n, locs, target_gates, starts
+
+
+def batched_instances_k(count: int, n_starts: int, seed: int,
+                        qubit_mix=((3, 2), (4, 1), (5, 1)), p_range=(4, 16), frac3=0.5):
+    """Uneven batch of small reachable instances mixing 2- and 3-qubit
+    gates: qubit counts in the ratio ``qubit_mix``, gate counts uniform in
+    ``p_range``, each gate three-qubit with probability ``frac3`` on a random
+    set of distinct qubits in random order (two-qubit otherwise); target and
+    start gates Haar."""
+    gen = rng(seed)
+    sizes = []
+    total = sum(w for _, w in qubit_mix)
+    for nq, w in qubit_mix:
+        sizes += [nq] * (count * w // total)
+    while len(sizes) < count:
+        sizes.append(qubit_mix[0][0])
+    sizes = np.asarray(sizes[:count])
+    gen.shuffle(sizes)
+    out = []
+    for nq in sizes:
+        nq = int(nq)
+        p = int(gen.integers(p_range[0], p_range[1] + 1))
+        locs = []
+        for _ in range(p):
+            k = 3 if (nq >= 3 and gen.random() < frac3) else 2
+            locs.append(tuple(int(x) for x in gen.choice(nq, k, replace=False)))
+        tg = [haar_unitary(2 ** len(q), gen) for q in locs]
+        starts = [[haar_unitary(2 ** len(q), gen) for q in locs] for _ in range(n_starts)]
+        out.append(InstanceK(nq, locs, tg, starts))
+    return out
