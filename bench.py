@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-kqubit", action="store_true")
     ap.add_argument("--no-spec", action="store_true")
     ap.add_argument("--oracle-1core", default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--profile-case", choices=["k4", "k3", "pair", "pass", "batched"], default=None,
+    ap.add_argument("--profile-case", choices=["k4", "k3", "pair", "pass", "batched", "batched_k"], default=None,
                     help="run one small case of a kernel family for a profiler capture (12 qubits, "
                          "2 starts, complex64, one live sweep after one warm-up sweep) and exit")
     return ap.parse_args()
@@ -1210,6 +1210,21 @@ def run_profile_case(args):
         res = qf.instantiate_batched(probs, **opts)
         best = res["costs"].min(axis=1)
         print(json.dumps({"case": "batched", "instances": len(probs), "kernel_ms": res["kernel_ms"],
+                          "success": int((best <= 1e-10).sum()), "warps_per_cta": res["warps_per_cta"],
+                          "sweeps": res["total_sweeps"]}))
+        return 0
+    if args.profile_case == "batched_k":
+        # the first 256 instances of the benchmark's batch of 2- and 3-qubit
+        # circuits: a warm-up call (autotuning: 4 trial launches, then its
+        # run), then one run
+        insts = qi.batched_instances_k(1024, 4, seed=SEED + 9)[:256]
+        probs = [(qf.circuit_unitary_k(i.n, i.locs, i.target_gates, device=dev).cpu().numpy(), i.locs, i.starts)
+                 for i in insts]
+        opts = dict(dist_tol=1e-10, max_sweeps=500, precision=qf.QF_C64_REFINE64)
+        qf.instantiate_batched_k(probs, **opts)
+        res = qf.instantiate_batched_k(probs, **opts)
+        best = res["costs"].min(axis=1)
+        print(json.dumps({"case": "batched_k", "instances": len(probs), "kernel_ms": res["kernel_ms"],
                           "success": int((best <= 1e-10).sum()), "warps_per_cta": res["warps_per_cta"],
                           "sweeps": res["total_sweeps"]}))
         return 0

@@ -278,15 +278,17 @@ __device__ bool plateau_test(const double* ring, int len, int it, const BatchPar
 // is the method's own plateau and the start stays in complex64.
 constexpr double kStallSwitchCost = 1e-5;
 
-__global__ void __maxnreg__(168) batched_kernel(BatchParams bp) {
-  extern __shared__ __align__(256) unsigned char smem[];
-  const int wid = threadIdx.x >> 5;
-  unsigned char* ws = smem + (size_t)wid * bp.warp_bytes;
-  void* Tbuf = ws;
-  unsigned char* after = ws + bp.tmax_bytes;
-  double2* LRd = reinterpret_cast<double2*>(after);            // 32 x 16 B
-  float2* scratch = reinterpret_cast<float2*>(after + 512);    // 32 x 8 B
-  double* ring = reinterpret_cast<double*>(after + 768);       // kRing x 8 B
+// The per-warp problem loop of the batched kernels: each warp takes the next
+// (instance, start) from the work counter, runs Qfactor on it (Alg. 1) with
+// the stopping rules of Sec. III-A2 and the multistart rule of Sec. IV-A,
+// and writes its outputs.  Ops supplies the steps for its kind of circuit:
+//   load(in, s)            gate pointers of start s; warm-start rotations reset
+//   build<R>()             InitCircuitTensor into the warp's tensor
+//   sweep<R>(bad)          one TwoSidedSweep
+//   reunit()               the periodic re-unitarisation of the gates
+// with R = float for the complex64 tensor and double for complex128.
+template <typename Ops>
+__device__ __forceinline__ void run_problems(const BatchParams& bp, Ops ops, void* Tbuf, double* ring) {
   const Lane L;
   const unsigned total = (unsigned)bp.n_inst * (unsigned)bp.S;
   for (;;) {
@@ -296,24 +298,18 @@ __global__ void __maxnreg__(168) batched_kernel(BatchParams bp) {
     if (prob >= total) break;
     const int i = bp.order[prob / bp.S], s = (int)(prob % bp.S);
     const BatchInst in = bp.inst[i];
-    const int n = in.n, p = in.p;
-    double2* g = bp.gates + in.gate_off + (long long)s * p * 16;
-    float2* yp = bp.yprev + in.gate_off + (long long)s * p * 16;
-    if (L.l < 16)
-      for (int k = 0; k < p; ++k) yp[k * 16 + L.l] = make_float2(L.i == L.j ? 1.f : 0.f, 0.f);
+    const int n = in.n;
+    ops.load(in, i, s);
     __syncwarp();
-    const double2* V = bp.targets + in.tgt_off;
-    const int2* locs = bp.locs + in.loc_off;
     volatile int* conv = bp.conv_flag + i;
     volatile int* plat = bp.plat_count + i;
     bool c64 = bp.precision != QF_C128;
     const bool refine = bp.precision == QF_C64_REFINE64;
     int bad = 0;
-    float2* LRf = reinterpret_cast<float2*>(LRd);
     if (c64)
-      W<float>::build((float2*)Tbuf, LRf, V, g, locs, n, p, L);
+      ops.template build<float>();
     else
-      W<double>::build((double2*)Tbuf, LRd, V, g, locs, n, p, L);
+      ops.template build<double>();
     double c = c64 ? W<float>::cost((float2*)Tbuf, n) : W<double>::cost((double2*)Tbuf, n);
     double* hist = bp.hist ? bp.hist + ((long long)i * bp.S + s) * bp.hist_row : nullptr;
     int len = 0;
@@ -330,17 +326,16 @@ __global__ void __maxnreg__(168) batched_kernel(BatchParams bp) {
         break;
       }
       if (c64)
-        W<float>::sweep((float2*)Tbuf, LRf, scratch, g, yp, locs, n, p, bp.beta, L, &bad);
+        ops.template sweep<float>(&bad);
       else
-        W<double>::sweep((double2*)Tbuf, LRd, scratch, g, yp, locs, n, p, bp.beta, L, &bad);
+        ops.template sweep<double>(&bad);
       if (bp.reset_iter > 0 && it % bp.reset_iter == 0) {
-        reunitarize(g, p, L);
+        ops.reunit();
         if (c64)
-          W<float>::build((float2*)Tbuf, LRf, V, g, locs, n, p, L);
+          ops.template build<float>();
         else
-          W<double>::build((double2*)Tbuf, LRd, V, g, locs, n, p, L);
+          ops.template build<double>();
       }
-      const double prev = c;
       c = c64 ? W<float>::cost((float2*)Tbuf, n) : W<double>::cost((double2*)Tbuf, n);
       if (c64 && refine) {
         ++c64_sw;
@@ -352,7 +347,7 @@ __global__ void __maxnreg__(168) batched_kernel(BatchParams bp) {
         const bool stalled = len > 10 && ring[(len - 10) % kRing] - c < 1e-7;
         if (c <= bp.switch_tol || (stalled && c <= kStallSwitchCost) || c64_sw >= bp.max_c64) {
           // rebuild in complex128 from the target and the FP64 gates
-          W<double>::build((double2*)Tbuf, LRd, V, g, locs, n, p, L);
+          ops.template build<double>();
           c = W<double>::cost((double2*)Tbuf, n);
           c64 = false;
         } else {
@@ -395,7 +390,7 @@ __global__ void __maxnreg__(168) batched_kernel(BatchParams bp) {
     }
     if (it > bp.max_sweeps) it = bp.max_sweeps;
     if (c64) {  // report an FP64 cost: rebuild the tensor in complex128 once
-      W<double>::build((double2*)Tbuf, LRd, V, g, locs, n, p, L);
+      ops.template build<double>();
       c = W<double>::cost((double2*)Tbuf, n);
     }
     if (L.l == 0) {
@@ -408,6 +403,56 @@ __global__ void __maxnreg__(168) batched_kernel(BatchParams bp) {
     }
     __syncwarp();
   }
+}
+
+// Steps of a circuit of two-qubit gates (gate k: 16 entries at k * 16).
+struct Ops2 {
+  double2* gates;
+  float2* yprev;
+  const double2* targets;
+  const int2* all_locs;
+  double beta;
+  void* T;
+  double2* LR;      // 32 x 16 B: the pass operators (complex64 or complex128)
+  float2* scratch;  // 32 x 8 B
+  Lane L;
+  const double2* V;
+  double2* g;
+  float2* yp;
+  const int2* locs;
+  int n, p;
+  __device__ __forceinline__ Ops2(const BatchParams& b, void* t, double2* lr, float2* sc)
+      : gates(b.gates), yprev(b.yprev), targets(b.targets), all_locs(b.locs), beta(b.beta), T(t), LR(lr),
+        scratch(sc) {}
+  __device__ __forceinline__ void load(const BatchInst& in, int, int s) {
+    n = in.n;
+    p = in.p;
+    g = gates + in.gate_off + (long long)s * p * 16;
+    yp = yprev + in.gate_off + (long long)s * p * 16;
+    V = targets + in.tgt_off;
+    locs = all_locs + in.loc_off;
+    if (L.l < 16)
+      for (int k = 0; k < p; ++k) yp[k * 16 + L.l] = make_float2(L.i == L.j ? 1.f : 0.f, 0.f);
+  }
+  template <typename R>
+  __device__ __forceinline__ void build() {
+    typedef typename Cplx<R>::T C;
+    W<R>::build((C*)T, (C*)LR, V, g, locs, n, p, L);
+  }
+  template <typename R>
+  __device__ __forceinline__ void sweep(int* bad) {
+    typedef typename Cplx<R>::T C;
+    W<R>::sweep((C*)T, (C*)LR, scratch, g, yp, locs, n, p, beta, L, bad);
+  }
+  __device__ __forceinline__ void reunit() { reunitarize(g, p, L); }
+};
+
+__global__ void __maxnreg__(168) batched_kernel(BatchParams bp) {
+  extern __shared__ __align__(256) unsigned char smem[];
+  unsigned char* ws = smem + (size_t)(threadIdx.x >> 5) * bp.warp_bytes;
+  unsigned char* after = ws + bp.tmax_bytes;
+  Ops2 ops(bp, ws, reinterpret_cast<double2*>(after), reinterpret_cast<float2*>(after + 512));
+  run_problems(bp, ops, ws, reinterpret_cast<double*>(after + 768));  // ring: kRing x 8 B
 }
 
 
@@ -539,10 +584,10 @@ struct WK {
     }
   }
 
-  // One three-qubit update: band, E, the warp 8x8 polar, the operators, the
-  // fused pass.
-  static __device__ __noinline__ void update8(C* T, C* LRs, double2* sm8, double2* g, int4 d, int n,
-                                              bool forward, double beta, int* bad) {
+  // One three-qubit update: band, E, the warp 8x8 polar (warm-started from
+  // the gate's previous rotation yp), the operators, the fused pass.
+  static __device__ __noinline__ void update8(C* T, C* LRs, double2* sm8, double2* g, float2* yp, int4 d,
+                                              int n, bool forward, double beta, int* bad) {
     const w8::L8 L;
     const int p0 = n - 1 - d.y, p1 = n - 1 - d.z, p2 = n - 1 - d.w;
     double2 P0, P1;
@@ -562,7 +607,7 @@ struct WK {
     }
     double2 n0, n1;
     double sg = 0.0;
-    if (!w8::warp_polar8(A0, A1, sm8, &n0, &n1, &sg)) {
+    if (!w8::warp_polar8(A0, A1, sm8, &n0, &n1, &sg, yp)) {
       *bad = 1;
       n0 = u0;  // keep the old gate: the tensor stays consistent
       n1 = u1;
@@ -587,7 +632,7 @@ struct WK {
         const int k = h == 0 ? p - 1 - i : i;
         const int4 d = gk[k];
         if (d.x == 3)
-          update8(T, LRs, sm8, g + goff[k], d, n, h == 1, beta, bad);
+          update8(T, LRs, sm8, g + goff[k], yp + goff[k], d, n, h == 1, beta, bad);
         else
           W<R>::update(T, LRs, scratch, g + goff[k], yp + goff[k], make_int2(d.y, d.z), n, h == 1, beta, L,
                        bad);
@@ -628,134 +673,67 @@ __device__ void reunitarize_k(double2* g, const int4* gk, const int* goff, int p
   }
 }
 
+// Steps of a circuit of 2- and 3-qubit gates (gate k: gk[k], entries from goff[k]).
+struct OpsK {
+  double2* gates;
+  float2* yprev;
+  const double2* targets;
+  const int4* all_gk;
+  const int* all_goff;
+  const int* inst_ge;
+  double beta;
+  void* T;
+  double2* LR;      // 128 x 16 B: the pass operators
+  double2* sm8;     // 128 x 16 B: scratch of the 8x8 update
+  float2* scratch;  // 32 x 8 B
+  Lane L;
+  const double2* V;
+  double2* g;
+  float2* yp;
+  const int4* gk;
+  const int* goff;
+  int n, p;
+  __device__ __forceinline__ OpsK(const BatchParamsK& b, void* t, double2* lr, double2* s8, float2* sc)
+      : gates(b.b.gates), yprev(b.b.yprev), targets(b.b.targets), all_gk(b.gk), all_goff(b.goff),
+        inst_ge(b.inst_ge), beta(b.b.beta), T(t), LR(lr), sm8(s8), scratch(sc) {}
+  __device__ __forceinline__ void load(const BatchInst& in, int i, int s) {
+    const int ge = inst_ge[i];
+    n = in.n;
+    p = in.p;
+    g = gates + in.gate_off + (long long)s * ge;
+    yp = yprev + in.gate_off + (long long)s * ge;
+    V = targets + in.tgt_off;
+    gk = all_gk + in.loc_off;
+    goff = all_goff + in.loc_off;
+    for (int k = 0; k < p; ++k) {  // warm-start rotations: the identity
+      if (gk[k].x == 2) {
+        if (L.l < 16) yp[goff[k] + L.l] = make_float2(L.i == L.j ? 1.f : 0.f, 0.f);
+      } else {
+        yp[goff[k] + L.l] = make_float2((L.l >> 3) == (L.l & 7) ? 1.f : 0.f, 0.f);
+        yp[goff[k] + L.l + 32] = make_float2(((L.l + 32) >> 3) == (L.l & 7) ? 1.f : 0.f, 0.f);
+      }
+    }
+  }
+  template <typename R>
+  __device__ __forceinline__ void build() {
+    typedef typename Cplx<R>::T C;
+    WK<R>::build((C*)T, (C*)LR, V, g, gk, goff, n, p, L);
+  }
+  template <typename R>
+  __device__ __forceinline__ void sweep(int* bad) {
+    typedef typename Cplx<R>::T C;
+    WK<R>::sweep((C*)T, (C*)LR, scratch, sm8, g, yp, gk, goff, n, p, beta, L, bad);
+  }
+  __device__ __forceinline__ void reunit() { reunitarize_k(g, gk, goff, p, L); }
+};
+
 __global__ void __maxnreg__(168) batched_k_kernel(BatchParamsK pk) {
   extern __shared__ __align__(256) unsigned char smem[];
-  const BatchParams& bp = pk.b;
-  const int wid = threadIdx.x >> 5;
-  unsigned char* ws = smem + (size_t)wid * bp.warp_bytes;
-  void* Tbuf = ws;
-  unsigned char* after = ws + bp.tmax_bytes;
-  double2* LRd = reinterpret_cast<double2*>(after);             // 128 x 16 B
-  double2* sm8 = reinterpret_cast<double2*>(after + 2048);      // 128 x 16 B
-  float2* scratch = reinterpret_cast<float2*>(after + 4096);    // 32 x 8 B
-  double* ring = reinterpret_cast<double*>(after + 4352);       // kRing x 8 B
-  const Lane L;
-  const unsigned total = (unsigned)bp.n_inst * (unsigned)bp.S;
-  for (;;) {
-    unsigned prob = 0;
-    if (L.l == 0) prob = atomicAdd(bp.work, 1u);
-    prob = __shfl_sync(kFull, prob, 0);
-    if (prob >= total) break;
-    const int i = bp.order[prob / bp.S], s = (int)(prob % bp.S);
-    const BatchInst in = bp.inst[i];
-    const int n = in.n, p = in.p, ge = pk.inst_ge[i];
-    double2* g = bp.gates + in.gate_off + (long long)s * ge;
-    float2* yp = bp.yprev + in.gate_off + (long long)s * ge;
-    const int4* gk = pk.gk + in.loc_off;
-    const int* goff = pk.goff + in.loc_off;
-    if (L.l < 16)
-      for (int k = 0; k < p; ++k)
-        if (gk[k].x == 2) yp[goff[k] + L.l] = make_float2(L.i == L.j ? 1.f : 0.f, 0.f);
-    __syncwarp();
-    const double2* V = bp.targets + in.tgt_off;
-    volatile int* conv = bp.conv_flag + i;
-    volatile int* plat = bp.plat_count + i;
-    bool c64 = bp.precision != QF_C128;
-    const bool refine = bp.precision == QF_C64_REFINE64;
-    int bad = 0;
-    float2* LRf = reinterpret_cast<float2*>(LRd);
-    if (c64)
-      WK<float>::build((float2*)Tbuf, LRf, V, g, gk, goff, n, p, L);
-    else
-      WK<double>::build((double2*)Tbuf, LRd, V, g, gk, goff, n, p, L);
-    double c = c64 ? W<float>::cost((float2*)Tbuf, n) : W<double>::cost((double2*)Tbuf, n);
-    double* hist = bp.hist ? bp.hist + ((long long)i * bp.S + s) * bp.hist_row : nullptr;
-    int len = 0;
-    if (L.l == 0) ring[0] = c;
-    if (hist && L.l == 0) hist[0] = c;
-    len = 1;
-    __syncwarp();
-    int it = 0, c64_sw = 0, reason = QF_STOP_MAX_SWEEPS;
-    bool plateaued = false;
-    for (it = 1; it <= bp.max_sweeps; ++it) {
-      if (*conv) {  // another start of this instance reached dist_tol
-        reason = QF_STOP_CONVERGED;
-        --it;
-        break;
-      }
-      if (c64)
-        WK<float>::sweep((float2*)Tbuf, LRf, scratch, sm8, g, yp, gk, goff, n, p, bp.beta, L, &bad);
-      else
-        WK<double>::sweep((double2*)Tbuf, LRd, scratch, sm8, g, yp, gk, goff, n, p, bp.beta, L, &bad);
-      if (bp.reset_iter > 0 && it % bp.reset_iter == 0) {
-        reunitarize_k(g, gk, goff, p, L);
-        if (c64)
-          WK<float>::build((float2*)Tbuf, LRf, V, g, gk, goff, n, p, L);
-        else
-          WK<double>::build((double2*)Tbuf, LRd, V, g, gk, goff, n, p, L);
-      }
-      c = c64 ? W<float>::cost((float2*)Tbuf, n) : W<double>::cost((double2*)Tbuf, n);
-      if (c64 && refine) {
-        ++c64_sw;
-        // the switch rule of the two-qubit kernel
-        const bool stalled = len > 10 && ring[(len - 10) % kRing] - c < 1e-7;
-        if (c <= bp.switch_tol || (stalled && c <= kStallSwitchCost) || c64_sw >= bp.max_c64) {
-          WK<double>::build((double2*)Tbuf, LRd, V, g, gk, goff, n, p, L);
-          c = W<double>::cost((double2*)Tbuf, n);
-          c64 = false;
-        } else {
-          if (L.l == 0) ring[len % kRing] = c;
-          if (hist && L.l == 0) hist[it] = c;
-          ++len;
-          __syncwarp();
-          if (it >= bp.min_sweeps && !plateaued && plateau_test(ring, len, it, bp)) {
-            plateaued = true;
-            if (L.l == 0) atomicAdd(bp.plat_count + i, 1);
-          }
-          __syncwarp();
-          if (*plat >= bp.S) {
-            reason = QF_STOP_PLATEAU;
-            break;
-          }
-          continue;
-        }
-      }
-      if (L.l == 0) ring[len % kRing] = c;
-      if (hist && L.l == 0) hist[it] = c;
-      ++len;
-      __syncwarp();
-      if (it >= bp.min_sweeps) {
-        if (c <= bp.dist_tol) {
-          if (L.l == 0) atomicExch(bp.conv_flag + i, 1);
-          reason = QF_STOP_CONVERGED;
-          break;
-        }
-        if (!plateaued && plateau_test(ring, len, it, bp)) {
-          plateaued = true;
-          if (L.l == 0) atomicAdd(bp.plat_count + i, 1);
-        }
-        __syncwarp();
-        if (*plat >= bp.S) {
-          reason = QF_STOP_PLATEAU;
-          break;
-        }
-      }
-    }
-    if (it > bp.max_sweeps) it = bp.max_sweeps;
-    if (c64) {  // report an FP64 cost: rebuild the tensor in complex128 once
-      WK<double>::build((double2*)Tbuf, LRd, V, g, gk, goff, n, p, L);
-      c = W<double>::cost((double2*)Tbuf, n);
-    }
-    if (L.l == 0) {
-      const long long q = (long long)i * bp.S + s;
-      bp.cost_out[q] = c;
-      bp.sweeps_out[q] = it;
-      bp.c64_out[q] = c64_sw;
-      bp.reason_out[q] = reason;
-      if (bad) atomicExch(bp.status, QF_ENONFINITE);
-    }
-    __syncwarp();
-  }
+  unsigned char* ws = smem + (size_t)(threadIdx.x >> 5) * pk.b.warp_bytes;
+  unsigned char* after = ws + pk.b.tmax_bytes;
+  OpsK ops(pk, ws, reinterpret_cast<double2*>(after), reinterpret_cast<double2*>(after + 2048),
+           reinterpret_cast<float2*>(after + 4096));
+  run_problems(pk.b, ops, ws, reinterpret_cast<double*>(after + 4352));  // ring: kRing x 8 B
 }
 
 // ------------------------------------------------------------------ host

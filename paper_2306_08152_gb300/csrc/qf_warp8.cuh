@@ -30,10 +30,11 @@ struct L8 {
 __device__ __forceinline__ int src8(int row, int col) { return ((row & 3) << 3) | col; }
 
 // element (row, col) of the matrix (v0, v1) for every lane; `row` may differ
-// between lanes
-__device__ __forceinline__ double2 get8(double2 v0, double2 v1, int row, int col) {
-  const double2 a = shfl(v0, src8(row, col));
-  const double2 b = shfl(v1, src8(row, col));
+// between lanes.  C2 is float2 or double2 here and in the products below.
+template <typename C2>
+__device__ __forceinline__ C2 get8(C2 v0, C2 v1, int row, int col) {
+  const C2 a = shfl(v0, src8(row, col));
+  const C2 b = shfl(v1, src8(row, col));
   return row < 4 ? a : b;
 }
 
@@ -41,14 +42,20 @@ __device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+template <typename C2>
+__device__ __forceinline__ C2 conj8(C2 v) {
+  v.y = -v.y;
+  return v;
+}
+
 // C = A B
-__device__ __forceinline__ void mm8(const L8& L, double2 a0, double2 a1, double2 b0, double2 b1,
-                                    double2& c0, double2& c1) {
-  double2 s0 = make_double2(0.0, 0.0), s1 = s0;
+template <typename C2>
+__device__ __forceinline__ void mm8(const L8& L, C2 a0, C2 a1, C2 b0, C2 b1, C2& c0, C2& c1) {
+  C2 s0 = czero<C2>(), s1 = s0;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
-    const double2 x0 = shfl(a0, src8(L.g, m)), x1 = shfl(a1, src8(L.g, m));  // A[g][m], A[g+4][m]
-    const double2 bm = m < 4 ? shfl(b0, src8(m, L.j)) : shfl(b1, src8(m, L.j));  // B[m][j]
+    const C2 x0 = shfl(a0, src8(L.g, m)), x1 = shfl(a1, src8(L.g, m));  // A[g][m], A[g+4][m]
+    const C2 bm = m < 4 ? shfl(b0, src8(m, L.j)) : shfl(b1, src8(m, L.j));  // B[m][j]
     s0 = cfma(x0, bm, s0);
     s1 = cfma(x1, bm, s1);
   }
@@ -57,14 +64,13 @@ __device__ __forceinline__ void mm8(const L8& L, double2 a0, double2 a1, double2
 }
 
 // C = A B^dagger
-__device__ __forceinline__ void mm8_nd(const L8& L, double2 a0, double2 a1, double2 b0, double2 b1,
-                                       double2& c0, double2& c1) {
-  double2 s0 = make_double2(0.0, 0.0), s1 = s0;
+template <typename C2>
+__device__ __forceinline__ void mm8_nd(const L8& L, C2 a0, C2 a1, C2 b0, C2 b1, C2& c0, C2& c1) {
+  C2 s0 = czero<C2>(), s1 = s0;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
-    const double2 x0 = shfl(a0, src8(L.g, m)), x1 = shfl(a1, src8(L.g, m));
-    const double2 bjm = get8(b0, b1, L.j, m);  // B[j][m]
-    const double2 cb = make_double2(bjm.x, -bjm.y);
+    const C2 x0 = shfl(a0, src8(L.g, m)), x1 = shfl(a1, src8(L.g, m));
+    const C2 cb = conj8(get8(b0, b1, L.j, m));  // conj(B[j][m])
     s0 = cfma(x0, cb, s0);
     s1 = cfma(x1, cb, s1);
   }
@@ -73,27 +79,28 @@ __device__ __forceinline__ void mm8_nd(const L8& L, double2 a0, double2 a1, doub
 }
 
 // C = A^dagger B
-__device__ __forceinline__ void mm8_dn(const L8& L, double2 a0, double2 a1, double2 b0, double2 b1,
-                                       double2& c0, double2& c1) {
-  double2 s0 = make_double2(0.0, 0.0), s1 = s0;
+template <typename C2>
+__device__ __forceinline__ void mm8_dn(const L8& L, C2 a0, C2 a1, C2 b0, C2 b1, C2& c0, C2& c1) {
+  C2 s0 = czero<C2>(), s1 = s0;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     // A^dagger[i][m] = conj(A[m][i]) for i = g and g + 4
-    const double2 ami0 = m < 4 ? shfl(a0, src8(m, L.g)) : shfl(a1, src8(m, L.g));
-    const double2 ami1 = m < 4 ? shfl(a0, src8(m, L.g + 4)) : shfl(a1, src8(m, L.g + 4));
-    const double2 bm = m < 4 ? shfl(b0, src8(m, L.j)) : shfl(b1, src8(m, L.j));
-    s0 = cfma(make_double2(ami0.x, -ami0.y), bm, s0);
-    s1 = cfma(make_double2(ami1.x, -ami1.y), bm, s1);
+    const C2 ami0 = m < 4 ? shfl(a0, src8(m, L.g)) : shfl(a1, src8(m, L.g));
+    const C2 ami1 = m < 4 ? shfl(a0, src8(m, L.g + 4)) : shfl(a1, src8(m, L.g + 4));
+    const C2 bm = m < 4 ? shfl(b0, src8(m, L.j)) : shfl(b1, src8(m, L.j));
+    s0 = cfma(conj8(ami0), bm, s0);
+    s1 = cfma(conj8(ami1), bm, s1);
   }
   c0 = s0;
   c1 = s1;
 }
 
 // (v0, v1) <- its conjugate transpose
-__device__ __forceinline__ void dag8(const L8& L, double2& v0, double2& v1) {
-  const double2 t0 = get8(v0, v1, L.j, L.g), t1 = get8(v0, v1, L.j, L.g + 4);
-  v0 = make_double2(t0.x, -t0.y);
-  v1 = make_double2(t1.x, -t1.y);
+template <typename C2>
+__device__ __forceinline__ void dag8(const L8& L, C2& v0, C2& v1) {
+  const C2 t0 = get8(v0, v1, L.j, L.g), t1 = get8(v0, v1, L.j, L.g + 4);
+  v0 = conj8(t0);
+  v1 = conj8(t1);
 }
 
 __device__ __forceinline__ double wmaxd(double v) {
@@ -101,7 +108,8 @@ __device__ __forceinline__ double wmaxd(double v) {
   for (int h = 16; h >= 1; h >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, h));
   return v;
 }
-__device__ __forceinline__ double colsum(double v) {  // over the 4 row groups
+template <typename T>
+__device__ __forceinline__ T colsum(T v) {  // over the 4 row groups
   v += __shfl_xor_sync(kFull, v, 8);
   v += __shfl_xor_sync(kFull, v, 16);
   return v;
@@ -294,38 +302,18 @@ __device__ __forceinline__ void polish8(const L8& L, double2& w0, double2& w1, d
   }
 }
 
-// Warp 8x8 polar update (OptimizeGate, Sec. III-A1, Eq. opt_u): with
-// A = X D Y^dagger, u = Y X^dagger maximises Re Tr(A u).  One-sided Jacobi
-// (rotations J with A J = W having orthogonal columns: Y = J, X = W's
-// normalised columns, D = their norms), first in FP32 from A to an
-// off-diagonal measure of 1e-6, then in FP64 from W = A Y32 (Y32 made
-// unitary to FP64 rounding first), where a couple of polishing sweeps
-// (angles from FP32, exactly unitary FP64 rotations) reach 1e-14:
-// the FP32 stage carries most of the rotations at 1/64 of the FP64 cost on
-// GB300.  *sig = sum(D).
-// Returns false for a non-finite A.
-__device__ __noinline__ bool warp_polar8(double2 a0, double2 a1, double2* sm, double2* u0,
-                                                double2* u1, double* sig) {
+// Rare path of the 8x8 update (some FP32 singular value is below 1e-3 of
+// the largest): from the FP32 rotation (fy0, fy1), Y made unitary in FP64
+// (two Newton-Schulz steps), W = A Y, FP64 polishing sweeps to 1e-15, X =
+// W's normalised columns (or, with a singular value still below 1e-3 of the
+// largest, complete8), u = Y X^dagger.  The polar factor of a nearly
+// singular A is ill-conditioned (a perturbation dA moves it by up to about
+// 2 ||dA|| / s_min, R.-C. Li's bound), so this path keeps the FP64 rounding
+// of A as the only source of error.  Returns the sum of the singular values
+// of the scaled A; y_io (if not null) receives the final rotation.
+__device__ __noinline__ double polar8_rare(double2 as0, double2 as1, float2 fy0, float2 fy1, double2* sm,
+                                           double2* u0, double2* u1, float2* y_io) {
   const L8 L;
-  const bool fin = __all_sync(kFull, isfinite(a0.x) && isfinite(a0.y) && isfinite(a1.x) && isfinite(a1.y));
-  if (!fin) return false;
-  const double amax = wmaxd(fmax(fmax(fabs(a0.x), fabs(a0.y)), fmax(fabs(a1.x), fabs(a1.y))));
-  if (amax == 0.0) {  // A = 0: every unitary is optimal
-    *u0 = make_double2(L.g == L.j ? 1.0 : 0.0, 0.0);
-    *u1 = make_double2(L.g + 4 == L.j ? 1.0 : 0.0, 0.0);
-    *sig = 0.0;
-    return true;
-  }
-  const double sc = 1.0 / amax;
-  const double2 as0 = make_double2(a0.x * sc, a0.y * sc), as1 = make_double2(a1.x * sc, a1.y * sc);
-  // stage 1: FP32
-  float2 fw0 = make_float2((float)as0.x, (float)as0.y), fw1 = make_float2((float)as1.x, (float)as1.y);
-  float2 fy0 = make_float2(L.g == L.j ? 1.f : 0.f, 0.f), fy1 = make_float2(L.g + 4 == L.j ? 1.f : 0.f, 0.f);
-  jacobi8<float>(L, fw0, fw1, fy0, fy1, 1e-6f, 15);
-  // stage 2: FP64.  Y32 is unitary only to FP32 rounding: two Newton-Schulz
-  // steps Y <- Y (3I - Y^dagger Y) / 2 in FP64 make it unitary to FP64
-  // rounding (the error squares each step), so W = A Y has A's singular
-  // values; then FP64 sweeps from W
   double2 y0 = to_d2(fy0), y1 = to_d2(fy1);
   for (int step = 0; step < 2; ++step) {
     double2 P0, P1;
@@ -353,15 +341,160 @@ __device__ __noinline__ bool warp_polar8(double2 a0, double2 a1, double2* sm, do
     x0 = make_double2(w0.x / sj, w0.y / sj);
     x1 = make_double2(w1.x / sj, w1.y / sj);
   } else {
-    // A close to singular (rare): a column of small norm s has its direction
-    // only to ~eps s_max / s, so X is re-orthonormalised (Gram-Schmidt, in
-    // order of decreasing s) rather than normalised, keeping u unitary to
-    // FP64 rounding; columns below 1e-13 s_max are completed
+    // a column of small norm s has its direction only to ~eps s_max / s, so
+    // X is re-orthonormalised (Gram-Schmidt, in order of decreasing s)
+    // rather than normalised, keeping u unitary to FP64 rounding
     complete8(L, w0, w1, s8, smax, sm, x0, x1);
   }
   mm8_nd(L, y0, y1, x0, x1, *u0, *u1);  // Y X^dagger
-  *sig = ssum * amax;
-  return __all_sync(kFull, isfinite(u0->x) && isfinite(u0->y) && isfinite(u1->x) && isfinite(u1->y));
+  if (y_io) {
+    y_io[L.g * 8 + L.j] = to_f2(y0);
+    y_io[L.g * 8 + L.j + 32] = to_f2(y1);
+  }
+  return ssum;
+}
+
+// Warp 8x8 polar update (OptimizeGate, Sec. III-A1, Eq. opt_u): with
+// A = X D Y^dagger, u = Y X^dagger maximises Re Tr(A u); *sig = sum(D).
+// The stages follow the 4x4 update, because GB300's FP64 rate is 1/64 of
+// its FP32 rate and the warps of an SM share one FP64 pipe:
+//   0. A is scaled by a power of two (exact) to a largest entry in [1, 2);
+//   1. one-sided Jacobi in FP32 to an off-diagonal measure of 1e-6
+//      (no FP64 work), from A, or from A Y0 with Y0 the rotation of the
+//      previous update of the same gate (y_io, a warm start);
+//   2. with every FP32 singular value above 1e-3 of the largest (the
+//      common case), FP64 refinement rounds: Newton-Schulz
+//      re-unitarisation of u (the small correction product in FP32),
+//      M = A u (Hermitian positive definite at the optimum), and
+//      u <- u (I - W + W^2 / 2) with W the solution of H W + W H = M - M^dagger
+//      in X's eigenbasis (W'_ij = K'_ij / (d_i + d_j), FP32): each round
+//      squares the error, two FP64 8x8 products a round;
+//   3. otherwise polar8_rare.
+// y_io: nullptr, or the 64-entry row-major FP32 rotation of the previous
+// update (read, then rewritten with this update's; lane (g, j) touches
+// entries (g, j) and (g + 4, j) only).  Returns false for a non-finite A.
+__device__ __noinline__ bool warp_polar8(double2 a0, double2 a1, double2* sm, double2* u0, double2* u1,
+                                         double* sig, float2* y_io = nullptr) {
+  const L8 L;
+  const bool fin = __all_sync(kFull, isfinite(a0.x) && isfinite(a0.y) && isfinite(a1.x) && isfinite(a1.y));
+  if (!fin) return false;
+  const double amax = wmaxd(fmax(fmax(fabs(a0.x), fabs(a0.y)), fmax(fabs(a1.x), fabs(a1.y))));
+  if (amax == 0.0) {  // A = 0: every unitary is optimal
+    *u0 = make_double2(L.g == L.j ? 1.0 : 0.0, 0.0);
+    *u1 = make_double2(L.g + 4 == L.j ? 1.0 : 0.0, 0.0);
+    *sig = 0.0;
+    return true;
+  }
+  int ex;
+  frexp(amax, &ex);  // amax = m 2^ex, m in [0.5, 1)
+  const double sc = ldexp(1.0, 1 - ex), unscale = ldexp(1.0, ex - 1);
+  const double2 as0 = make_double2(a0.x * sc, a0.y * sc), as1 = make_double2(a1.x * sc, a1.y * sc);
+  const float2 fa0 = to_f2(as0), fa1 = to_f2(as1);
+
+  // ---- stage 1: FP32 Jacobi
+  const int e0 = L.g * 8 + L.j, e1 = e0 + 32;
+  float2 fw0, fw1, fy0, fy1;
+  if (y_io) {
+    fy0 = y_io[e0];
+    fy1 = y_io[e1];
+    mm8(L, fa0, fa1, fy0, fy1, fw0, fw1);  // W = A Y0
+  } else {
+    fw0 = fa0;
+    fw1 = fa1;
+    fy0 = make_float2(L.g == L.j ? 1.f : 0.f, 0.f);
+    fy1 = make_float2(L.g + 4 == L.j ? 1.f : 0.f, 0.f);
+  }
+  jacobi8<float>(L, fw0, fw1, fy0, fy1, 1e-6f, 15);
+  const float sj = sqrtf(colsum(fw0.x * fw0.x + fw0.y * fw0.y + fw1.x * fw1.x + fw1.y * fw1.y));
+  float smax = 0.f, smin = 3.4e38f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float sk = __shfl_sync(kFull, sj, k);  // lane k holds column k
+    smax = fmaxf(smax, sk);
+    smin = fminf(smin, sk);
+  }
+  if (!(smin > 1e-3f * smax)) {  // ---- stage 3 (rare): A close to singular
+    *sig = polar8_rare(as0, as1, fy0, fy1, sm, u0, u1, y_io) * unscale;
+    return __all_sync(kFull, isfinite(u0->x) && isfinite(u0->y) && isfinite(u1->x) && isfinite(u1->y));
+  }
+  const float2 x0 = make_float2(fw0.x / sj, fw0.y / sj), x1 = make_float2(fw1.x / sj, fw1.y / sj);
+  // d_i + d_j for rows g and g + 4 of this lane's column j (>= 2e-3 smax)
+  const float den0 = __shfl_sync(kFull, sj, L.g) + sj, den1 = __shfl_sync(kFull, sj, L.g + 4) + sj;
+  float2 v0, v1;
+  mm8_nd(L, fy0, fy1, x0, x1, v0, v1);  // Y X^dagger
+  double2 w0 = to_d2(v0), w1 = to_d2(v1);
+
+  // ---- stage 2: FP64 refinement
+  double2 M0 = make_double2(0.0, 0.0), M1 = M0;
+  float2 D0 = make_float2(0.f, 0.f), D1 = D0;
+  // the correction's first-order error is about 1e-7 smax / (d_i + d_j) of
+  // its size: stop once that is below FP64 rounding of the result
+  const float wtol = 3e-6f * fminf(1.f, 10.f * smin / smax);
+  for (int round = 0; round < 5; ++round) {
+    // Newton-Schulz: u <- u - u (u^dagger u - I) / 2
+    double2 P0, P1;
+    mm8_dn(L, w0, w1, w0, w1, P0, P1);
+    const float2 Pm0 = make_float2((float)(P0.x - (L.g == L.j ? 1.0 : 0.0)), (float)P0.y);
+    const float2 Pm1 = make_float2((float)(P1.x - (L.g + 4 == L.j ? 1.0 : 0.0)), (float)P1.y);
+    float2 c0, c1;
+    mm8(L, to_f2(w0), to_f2(w1), Pm0, Pm1, c0, c1);
+    w0 = make_double2(w0.x - 0.5 * (double)c0.x, w0.y - 0.5 * (double)c0.y);
+    w1 = make_double2(w1.x - 0.5 * (double)c1.x, w1.y - 0.5 * (double)c1.y);
+    // M = A u, K = M - M^dagger
+    mm8(L, as0, as1, w0, w1, M0, M1);
+    double2 Md0 = M0, Md1 = M1;
+    dag8(L, Md0, Md1);
+    const float2 K0 = make_float2((float)(M0.x - Md0.x), (float)(M0.y - Md0.y));
+    const float2 K1 = make_float2((float)(M1.x - Md1.x), (float)(M1.y - Md1.y));
+    // H W + W H = K in the eigenbasis X of H: W = X (X^dagger K X ./ (d_i + d_j)) X^dagger
+    float2 t0, t1, k0, k1;
+    mm8(L, K0, K1, x0, x1, t0, t1);
+    mm8_dn(L, x0, x1, t0, t1, k0, k1);
+    k0 = make_float2(k0.x / den0, k0.y / den0);
+    k1 = make_float2(k1.x / den1, k1.y / den1);
+    mm8_nd(L, k0, k1, x0, x1, t0, t1);
+    float2 W0, W1;
+    mm8(L, x0, x1, t0, t1, W0, W1);
+    float om = fmaxf(fmaxf(fabsf(W0.x), fabsf(W0.y)), fmaxf(fabsf(W1.x), fabsf(W1.y)));
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) om = fmaxf(om, __shfl_xor_sync(kFull, om, h));
+    // u <- u (I - W + W^2 / 2)
+    mm8(L, W0, W1, W0, W1, t0, t1);
+    const float2 Z0 = make_float2(-W0.x + 0.5f * t0.x, -W0.y + 0.5f * t0.y);
+    const float2 Z1 = make_float2(-W1.x + 0.5f * t1.x, -W1.y + 0.5f * t1.y);
+    mm8(L, to_f2(w0), to_f2(w1), Z0, Z1, D0, D1);
+    w0 = make_double2(w0.x + (double)D0.x, w0.y + (double)D0.y);
+    w1 = make_double2(w1.x + (double)D1.x, w1.y + (double)D1.y);
+    if (om < wtol) break;
+  }
+  // sum of singular values = Re Tr(A u) = Re Tr(M) + Re Tr(A D) (M from the
+  // last round, before D was added; Tr(A D) is small, FP32 suffices)
+  const float2 dt0 = get8(D0, D1, L.j, L.g), dt1 = get8(D0, D1, L.j, L.g + 4);  // D[j][g], D[j][g+4]
+  float trd = fa0.x * dt0.x - fa0.y * dt0.y + fa1.x * dt1.x - fa1.y * dt1.y;
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) trd += __shfl_xor_sync(kFull, trd, h);
+  double trm = 0.0;
+#pragma unroll
+  for (int g = 0; g < 4; ++g)  // M[g][g] at lane 9 g, M[g+4][g+4] at lane 9 g + 4
+    trm += __shfl_sync(kFull, M0.x, 9 * g) + __shfl_sync(kFull, M1.x, 9 * g + 4);
+  *sig = (trm + (double)trd) * unscale;
+  {  // final Newton-Schulz step: unitary to FP64 rounding whatever the last D
+    double2 P0, P1;
+    mm8_dn(L, w0, w1, w0, w1, P0, P1);
+    const float2 Pm0 = make_float2((float)(P0.x - (L.g == L.j ? 1.0 : 0.0)), (float)P0.y);
+    const float2 Pm1 = make_float2((float)(P1.x - (L.g + 4 == L.j ? 1.0 : 0.0)), (float)P1.y);
+    float2 c0, c1;
+    mm8(L, to_f2(w0), to_f2(w1), Pm0, Pm1, c0, c1);
+    w0 = make_double2(w0.x - 0.5 * (double)c0.x, w0.y - 0.5 * (double)c0.y);
+    w1 = make_double2(w1.x - 0.5 * (double)c1.x, w1.y - 0.5 * (double)c1.y);
+  }
+  *u0 = w0;
+  *u1 = w1;
+  if (y_io) {
+    y_io[e0] = fy0;
+    y_io[e1] = fy1;
+  }
+  return __all_sync(kFull, isfinite(w0.x) && isfinite(w0.y) && isfinite(w1.x) && isfinite(w1.y));
 }
 
 }  // namespace w8
