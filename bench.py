@@ -233,10 +233,11 @@ def measured_alu_peaks(torch, dev):
     return _ALU_PEAKS
 
 
-def batched_pipes():
-    """Pipe fractions of the batched kernel from a committed ncu summary,
-    if it was taken on the current kernel sources; else None."""
-    path = os.path.join(ROOT, "profiles", "batched_kernel_pipes.json")
+def batched_pipes(name="batched_kernel_pipes.json"):
+    """Pipe fractions of a batched kernel from a committed ncu summary
+    (profiles/<name>), if it was taken on the current kernel sources; else
+    None."""
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     with open(path) as f:
@@ -500,18 +501,18 @@ def run_batched_k(args, qf, torch, dev):
         "unit": "instantiations/s", "value": ok / wall, "success": ok, "instances": len(probs),
         "starts": 4, "wall_s": wall, "kernel_ms": res["kernel_ms"], "warps_per_cta": res["warps_per_cta"],
         "ctas": res["ctas"], "sweeps": res["total_sweeps"], "c64_sweeps": res["total_c64_sweeps"],
-        "three_qubit_gates": n3, "gates": ng,
+        "three_qubit_gates": n3, "gates": ng, "roofline": batched_roofline("batched_k_kernel_pipes.json"),
         "precision": "complex64 sweeps, FP64 4x4 and 8x8 updates, complex128 refinement",
         "workload": f"{len(probs)} reachable instances, 3/4/5 qubits 2:1:1, 4-16 gates on random qubit "
                     "sets (three-qubit with probability 1/2), 4 Haar starts, tol 1e-10, <=500 sweeps"}
 
 
-def batched_roofline():
-    """The batched kernel runs whole small problems per warp with the
-    tensors in shared memory: no HBM bound; the FP64 pipe (the 4x4 updates'
+def batched_roofline(name="batched_kernel_pipes.json"):
+    """The batched kernels run whole small problems per warp with the
+    tensors in shared memory: no HBM bound; the FP64 pipe (the updates'
     refinement) is the busiest unit.  Fractions from the committed capture
     of the same kernel source (null if the source changed since)."""
-    d = batched_pipes()
+    d = batched_pipes(name)
     if d is None:
         return None
     return {"bound": "alu", "unit": "fraction of pipe cycles", "peak": 1.0,
@@ -520,7 +521,7 @@ def batched_roofline():
             "fp64_pipe_elapsed_frac": d["fp64_pipe_elapsed_frac"],
             "fp32_fma_pipe_active_frac": d["fma_pipe_active_frac"],
             "sm_active_frac_of_elapsed": d["sm_active_frac_of_elapsed"],
-            "source": "ncu capture (profiles/batched_kernel_pipes.json): " + d["capture"]}
+            "source": f"ncu capture (profiles/{name}): " + d["capture"]}
 
 
 def run_c128(args, qf, torch, dev, inst, V, starts):

@@ -110,28 +110,36 @@ struct W {
     const unsigned o1 = 1u << pb, o2 = 1u << pa;
     const unsigned items = 4u * nblk;
     auto offv = [&](unsigned v) { return ((v & 2u) ? o2 : 0u) | ((v & 1u) ? o1 : 0u); };
+    // N is a multiple of 16 entries, so an entry's bank is set by its column.
+    // Row stage: lanes with the same c0 take the row's entries in the order
+    // y ^ s, s = (it >> lnc) & 3 (off is GF(2)-linear: off(y ^ s) =
+    // off(y) ^ off(s), and R's entry (k ^ s, y ^ s) is index (4k + y) ^ 5s),
+    // so the lanes of a step touch distinct columns.
     if (HR) {  // row (r0 | off[x]) of block (r0, c0) <- row R
       for (unsigned it = lane; it < items; it += 32) {
         const unsigned blk = it & (nblk - 1u), x = it >> (2 * lnc);
         const unsigned r0 = dep2(blk >> lnc, plo, phi), c0 = dep2(blk & cmask, plo, phi);
+        const unsigned sk = (it >> lnc) & 3u, os = offv(sk), s5 = 5u * sk;
         C* row = T + (size_t)(r0 | offv(x)) * N + c0;
         C v[4];
 #pragma unroll
-        for (int y = 0; y < 4; ++y) v[y] = row[offv(y)];
+        for (int y = 0; y < 4; ++y) v[y] = row[offv(y) ^ os];
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
           C acc = czero<C>();
 #pragma unroll
-          for (int k = 0; k < 4; ++k) acc = cfma(v[k], Rm[k * 4 + y], acc);
-          row[offv(y)] = acc;
+          for (int k = 0; k < 4; ++k) acc = cfma(v[k], Rm[(k * 4 + y) ^ s5], acc);
+          row[offv(y) ^ os] = acc;
         }
       }
       __syncwarp();
     }
+    // Column stage: the gate column y varies fastest over the lanes, then
+    // the block column, so a step's lanes cover distinct columns.
     if (HL) {  // column (c0 | off[y]) of block (r0, c0) <- L column
       for (unsigned it = lane; it < items; it += 32) {
-        const unsigned blk = it & (nblk - 1u), y = it >> (2 * lnc);
-        const unsigned r0 = dep2(blk >> lnc, plo, phi), c0 = dep2(blk & cmask, plo, phi);
+        const unsigned y = it & 3u, cb = (it >> 2) & cmask, rb = it >> (2 + lnc);
+        const unsigned r0 = dep2(rb, plo, phi), c0 = dep2(cb, plo, phi);
         C* col = T + (size_t)r0 * N + (c0 | offv(y));
         C v[4];
 #pragma unroll
@@ -504,28 +512,33 @@ struct WK {
     const int lnc = n - 3;
     const unsigned N = 1u << n, cmask = (1u << lnc) - 1u, nblk = 1u << (2 * lnc);
     const unsigned items = 8u * nblk;
+    // Bank-conflict-free order, as in the 4x4 pass: the row stage takes a
+    // row's entries in the order y ^ s, s = (it >> lnc) & 7 (R's entry
+    // (k ^ s, y ^ s) is index (8k + y) ^ 9s); the column stage maps the
+    // gate column y to the lowest lane bits.
     if (HR) {
       for (unsigned it = lane; it < items; it += 32) {
         const unsigned blk = it & (nblk - 1u), x = it >> (2 * lnc);
         const unsigned r0 = dep3(blk >> lnc, a, b, c), c0 = dep3(blk & cmask, a, b, c);
+        const unsigned sk = (it >> lnc) & 7u, os = off8(sk, p0, p1, p2), s9 = 9u * sk;
         C* row = T + (size_t)(r0 | off8(x, p0, p1, p2)) * N + c0;
         C v[8];
 #pragma unroll
-        for (int y = 0; y < 8; ++y) v[y] = row[off8(y, p0, p1, p2)];
+        for (int y = 0; y < 8; ++y) v[y] = row[off8(y, p0, p1, p2) ^ os];
 #pragma unroll
         for (int y = 0; y < 8; ++y) {
           C acc = czero<C>();
 #pragma unroll
-          for (int k = 0; k < 8; ++k) acc = cfma(v[k], Rm[k * 8 + y], acc);
-          row[off8(y, p0, p1, p2)] = acc;
+          for (int k = 0; k < 8; ++k) acc = cfma(v[k], Rm[(k * 8 + y) ^ s9], acc);
+          row[off8(y, p0, p1, p2) ^ os] = acc;
         }
       }
       __syncwarp();
     }
     if (HL) {
       for (unsigned it = lane; it < items; it += 32) {
-        const unsigned blk = it & (nblk - 1u), y = it >> (2 * lnc);
-        const unsigned r0 = dep3(blk >> lnc, a, b, c), c0 = dep3(blk & cmask, a, b, c);
+        const unsigned y = it & 7u, cb = (it >> 3) & cmask, rb = it >> (3 + lnc);
+        const unsigned r0 = dep3(rb, a, b, c), c0 = dep3(cb, a, b, c);
         C* col = T + (size_t)r0 * N + (c0 | off8(y, p0, p1, p2));
         C v[8];
 #pragma unroll
