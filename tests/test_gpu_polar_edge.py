@@ -17,7 +17,7 @@ well-conditioned E.  Independently of that bound, every result must attain
 the optimum: Re Tr(E u) = sum of singular values to 1e-12 relative, the
 returned sum likewise, and u must be unitary to 1e-13.
 
-Spectra: graded (s_min / s_max = 1e-3 .. 1e-12, geometric and with a single
+Spectra: graded (s_min / s_max = 1e-1 .. 1e-12, geometric and with a single
 small value), near-degenerate and exactly degenerate singular values, global
 complex phases and scales far from 1.  The same environments are also fed
 through whole sweeps of the resident plan and of the batched kernel (whose
@@ -56,7 +56,10 @@ def _bound(sig):
 
 def _spectra(d):
     out = []
-    for r in (1e-3, 1e-6, 1e-9, 1e-12):
+    # 1e-1 .. 2e-3: the FP32 stage's singular values stay above 1e-3 of the
+    # largest, so the FP64 refinement rounds take them, with a round
+    # tolerance that tightens with s_min / s_max; from 1e-3 on the rare path
+    for r in (1e-1, 1e-2, 2e-3, 1e-3, 1e-6, 1e-9, 1e-12):
         out.append(r ** (np.arange(d) / (d - 1)))             # geometric grading
         out.append(np.r_[np.linspace(1.0, 0.5, d - 1), r])   # one small value
     out.append(np.r_[1.0, 1.0 + 1e-9, np.full(d - 2, 0.3) * (1 + 1e-12 * np.arange(d - 2))])
@@ -168,3 +171,48 @@ def test_ill_conditioned_environments_in_batched_kernel(qf):
             assert abs(res["costs"][i, s] - (1.0 - s_ref / 8.0)) <= 1e-13, (sv, s)
             err = np.max(np.abs(res["gates"][i][s, 0] - u_ref))
             assert err <= _bound(sv), (sv, s, err)
+
+
+SWEEP_SPECTRA_8 = [(2.0, 1.8, 1.5, 1.2, 1.0, 0.5, 0.2, 0.1), (2.0, 2.0, 1.0, 1.0, 0.1, 0.05, 0.02, 0.01),
+                   (2.0, 1.5, 1.0, 1e-2, 1e-2, 3e-3, 3e-3, 2.5e-3), (2.0, 1.0, 1e-3, 1e-6, 1e-6, 1e-9, 1e-9, 1e-12),
+                   (2.0, 2.0, 2.0, 2.0, 2.0, 2.0, 2.0, 1e-10)]
+
+
+def _controlled_problem_8(sig, g):
+    """n = 4, one three-qubit gate on (0, 1, 2); E = U1 + U2 (8x8) has
+    singular values sig."""
+    U1 = qi.haar_unitary(8, g)
+    Z = qi.haar_unitary(8, g)
+    theta = np.pi - 2.0 * np.arcsin(np.asarray(sig) / 2.0)
+    U2 = U1 @ ((Z * np.exp(1j * theta)[None, :]) @ Z.conj().T)
+    W = np.kron(U1, np.diag([1.0, 0.0])) + np.kron(U2, np.diag([0.0, 1.0]))
+    V = W.conj().T
+    E = U1 + U2
+    sv = np.linalg.svd(E, compute_uv=False)
+    assert np.allclose(np.sort(sv), np.sort(sig), rtol=0, atol=1e-14)
+    assert np.allclose(ok.calc_env_mat_k(V.conj().T, (0, 1, 2), 4), E, atol=1e-14)
+    return V, E, sv
+
+
+def test_ill_conditioned_8x8_environments_in_sweeps(qf):
+    """Three-qubit updates on the same ill-conditioned 8x8 environment: three
+    sweeps through the sweep engine (cold-started update in the environment
+    kernel) and through the batched kernel (warm-started from the previous
+    rotation), complex128 tensors."""
+    g = qi.rng(12300)
+    insts, refs = [], []
+    for sig in SWEEP_SPECTRA_8:
+        V, E, sv = _controlled_problem_8(sig, g)
+        starts = [[qi.haar_unitary(8, g)] for _ in range(2)]
+        insts.append((V, [(0, 1, 2)], starts))
+        refs.append((ok.optimize_gate_k(E), sv))
+    res_b = qf.instantiate_batched_k(insts, dist_tol=0.0, max_sweeps=3, reset_iter=0, precision=qf.QF_C128)
+    for i, (((u_ref, s_ref), sv), (V, locs, starts)) in enumerate(zip(refs, insts)):
+        res_e = qf.instantiate_k(torch.from_numpy(V).cuda(), locs, starts, dist_tol=0.0, max_sweeps=3, reset_iter=0,
+                                 precision=qf.QF_C128)
+        for s in range(2):
+            for label, cost, gate in (("batched", res_b["costs"][i, s], res_b["gates"][i][s][0]),
+                                      ("engine", res_e["costs"][s], res_e["gates"][s][0])):
+                assert abs(cost - (1.0 - s_ref / 16.0)) <= 1e-13, (label, sv, s, cost)
+                err = np.max(np.abs(gate - u_ref))
+                assert err <= _bound(sv), (label, sv, s, err, _bound(sv))
