@@ -59,8 +59,9 @@ __device__ __forceinline__ void sort4(const int* p, int* qs) {
 }
 
 // ------------------------------------------------------ CTA 16x16 products
-// C = op(A) op(B) on shared 16x16 FP64 matrices, one element per thread
-// (t = 16 i + j); C must not alias A or B.  Ends with a barrier.
+// C = op(A) op(B) on shared 16x16 matrices (FP64, or FP32 for the small
+// corrections of the update), one element per thread (t = 16 i + j); C
+// must not alias A or B.  Ends with a barrier.
 enum MmOp { kMmNN = 0, kMmND = 1, kMmDN = 2 };  // A B, A B^dagger, A^dagger B
 
 // Every shared 16x16 matrix of the update keeps entry (r, c) at
@@ -70,10 +71,10 @@ enum MmOp { kMmNN = 0, kMmND = 1, kMmDN = 2 };  // A B, A B^dagger, A^dagger B
 __device__ __forceinline__ int sw16(int r, int c) { return r * 16 + (c ^ r); }
 __device__ __forceinline__ int swt(int t) { return t ^ (t >> 4); }
 
-template <int OP>
-__device__ __forceinline__ void cta_mm(const double2* A, const double2* B, double2* C) {
+template <int OP, typename C2>
+__device__ __forceinline__ void cta_mm(const C2* A, const C2* B, C2* C) {
   const int t = threadIdx.x, i = t >> 4, j = t & 15;
-  double2 acc = make_double2(0.0, 0.0);
+  C2 acc = czero<C2>();
 #pragma unroll 4
   for (int k = 0; k < 16; ++k) {
     if (OP == kMmNN) {
@@ -121,6 +122,7 @@ struct Polar16Smem {
   double s[16];             // column norms (singular values)
   unsigned emax;
   float off[2];
+  double red[kCta16 / 32];  // per-warp partial sums
 };
 
 __device__ __forceinline__ unsigned expo_field(double v) {
@@ -296,6 +298,48 @@ __device__ void gram_schmidt16(Polar16Smem& S, double smax) {
   __syncwarp();
 }
 
+// Largest of a non-negative value over the CTA (every thread gets it).
+__device__ __forceinline__ float cta_max_nonneg(Polar16Smem& S, float v) {
+  __syncthreads();
+  if (threadIdx.x == 0) S.emax = 0u;
+  __syncthreads();
+  const unsigned m = __reduce_max_sync(kFull, __float_as_uint(v));
+  if ((threadIdx.x & 31) == 0) atomicMax(&S.emax, m);
+  __syncthreads();
+  return __uint_as_float(S.emax);
+}
+
+// Sum over the CTA in a fixed order (warps, then the warps' partials in
+// order); every thread gets it.
+__device__ __forceinline__ double cta_sum(Polar16Smem& S, double v) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) v += __shfl_xor_sync(kFull, v, h);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+#pragma unroll
+  for (int w = 0; w < kCta16 / 32; ++w) r += S.red[w];
+  return r;
+}
+
+// One Newton-Schulz step on the FP64 u in S.x: u <- u - u (u^dagger u - I) / 2,
+// u^dagger u in FP64 and the small correction product in FP32 (F0-F2: FP32
+// scratch matrices).
+__device__ __forceinline__ void cta_ns_step(Polar16Smem& S, float2* F0, float2* F1, float2* F2) {
+  const int t = threadIdx.x, i = t >> 4, j = t & 15;
+  cta_mm<kMmDN>(S.x, S.x, S.t1);
+  const double2 pq = S.t1[swt(t)];
+  F1[swt(t)] = make_float2((float)(pq.x - (i == j ? 1.0 : 0.0)), (float)pq.y);
+  F0[swt(t)] = to_f2(S.x[swt(t)]);
+  __syncthreads();
+  cta_mm<kMmNN>(F0, F1, F2);
+  const float2 c = F2[swt(t)];
+  const double2 u = S.x[swt(t)];
+  S.x[swt(t)] = make_double2(u.x - 0.5 * (double)c.x, u.y - 0.5 * (double)c.y);
+  __syncthreads();
+}
+
 // OptimizeGate on a CTA of kCta16 threads: A in S.a (FP64, destroyed) ->
 // u = Y X^dagger in S.x with A = X D Y^dagger, *sig = sum(D).  Returns false
 // for a non-finite A.  Every thread must call it.
@@ -344,7 +388,93 @@ __device__ bool cta_polar16(Polar16Smem& S, double* sig) {
     __syncthreads();
     if (S.off[sweep & 1] < 1e-6f) break;
   }
-  // stage 2: Y unitary in FP64, W = A Y, FP64 sweeps to 1e-15
+  // FP32 singular values: the column norms of W
+  if (t < 16) {
+    float s2 = 0.f;
+    for (int r = 0; r < 16; ++r) {
+      const float2 v = S.fw[sw16(r, t)];
+      s2 += v.x * v.x + v.y * v.y;
+    }
+    S.s[t] = (double)sqrtf(s2);
+  }
+  __syncthreads();
+  float fsmax = 0.f, fsmin = 3.4e38f;
+  for (int k = 0; k < 16; ++k) {
+    fsmax = fmaxf(fsmax, (float)S.s[k]);
+    fsmin = fminf(fsmin, (float)S.s[k]);
+  }
+  if (fsmin > 1e-3f * fsmax) {
+    // stage 2 (common): FP64 refinement rounds from u = Y X^dagger, as in
+    // the 4x4 and 8x8 updates: a Newton-Schulz step, M = A u, and
+    // u <- u (I - W + W^2 / 2) with H W + W H = M - M^dagger solved in X's
+    // eigenbasis (W'_ij = K'_ij / (d_i + d_j), FP32); each round squares the
+    // error.  FP32 scratch: t2 and y (unused on this path).
+    float2* F0 = reinterpret_cast<float2*>(S.t2);
+    float2* F1 = F0 + 256;
+    float2* F2 = reinterpret_cast<float2*>(S.y);
+    float2* F3 = F2 + 256;
+    const float si = (float)S.s[i], sj = (float)S.s[j];
+    {  // X = W's normalised columns, in place
+      const float2 v = S.fw[swt(t)];
+      S.fw[swt(t)] = make_float2(v.x / sj, v.y / sj);
+    }
+    __syncthreads();
+    cta_mm<kMmND>(S.fy, S.fw, F0);  // Y X^dagger
+    S.x[swt(t)] = to_d2(F0[swt(t)]);
+    F3[swt(t)] = make_float2(0.f, 0.f);  // D
+    __syncthreads();
+    const float den = si + sj;  // >= 2e-3 of the largest singular value
+    // the correction's first-order error is about 1e-7 smax / (d_i + d_j)
+    // of its size: stop once that is below FP64 rounding of the result
+    const float wtol = 3e-6f * fminf(1.f, 10.f * fsmin / fsmax);
+    for (int round = 0; round < 5; ++round) {
+      cta_ns_step(S, F0, F1, F2);
+      cta_mm<kMmNN>(S.a, S.x, S.w);  // M = A u
+      {
+        const double2 m = S.w[swt(t)], mt = S.w[sw16(j, i)];
+        F0[swt(t)] = make_float2((float)(m.x - mt.x), (float)(m.y + mt.y));  // K = M - M^dagger
+      }
+      __syncthreads();
+      cta_mm<kMmNN>(F0, S.fw, F1);  // K X
+      cta_mm<kMmDN>(S.fw, F1, F2);  // K' = X^dagger K X
+      {
+        const float2 v = F2[swt(t)];
+        F2[swt(t)] = make_float2(v.x / den, v.y / den);  // W'
+      }
+      __syncthreads();
+      cta_mm<kMmND>(F2, S.fw, F0);  // W' X^dagger
+      cta_mm<kMmNN>(S.fw, F0, F1);  // W = X W' X^dagger
+      const float2 wv = F1[swt(t)];
+      const float om = cta_max_nonneg(S, fmaxf(fabsf(wv.x), fabsf(wv.y)));
+      cta_mm<kMmNN>(F1, F1, F2);  // W^2
+      {
+        const float2 w2 = F2[swt(t)];
+        F2[swt(t)] = make_float2(-wv.x + 0.5f * w2.x, -wv.y + 0.5f * w2.y);  // Z = -W + W^2 / 2
+      }
+      F0[swt(t)] = to_f2(S.x[swt(t)]);
+      __syncthreads();
+      cta_mm<kMmNN>(F0, F2, F3);  // D = u Z
+      {
+        const float2 d = F3[swt(t)];
+        const double2 u = S.x[swt(t)];
+        S.x[swt(t)] = make_double2(u.x + (double)d.x, u.y + (double)d.y);
+      }
+      __syncthreads();
+      if (om < wtol) break;
+    }
+    cta_ns_step(S, F0, F1, F2);  // unitary to FP64 rounding whatever the last D
+    // sum of singular values = Re Tr(A u), from the final u: the last
+    // Newton-Schulz step moves Re Tr(A u) to first order in u's distance
+    // from unitarity (FP32 rounding of D leaves ~1e-12 at 16x16), so the
+    // trace is taken after it, in FP64 (one product per thread, summed in
+    // a fixed order)
+    const double2 u = S.x[swt(t)], ut = S.x[sw16(j, i)];  // u[i][j], u[j][i]
+    const double2 av = S.a[swt(t)];                       // A[i][j]
+    *sig = cta_sum(S, av.x * ut.x - av.y * ut.y) * unscale;
+    return __syncthreads_and(isfinite(u.x) && isfinite(u.y));
+  }
+  // stage 2 (rare: a singular value below 1e-3 of the largest): Y unitary in
+  // FP64, W = A Y, FP64 sweeps to 1e-15
   S.y[swt(t)] = to_d2(S.fy[swt(t)]);
   __syncthreads();
   cta_newton_schulz(S.y, S.t1, S.t2, 2);

@@ -11,7 +11,7 @@ times ||E||, so the two may differ by
 
     bound = C * eps * s_max / s_min,     eps = 2^-52,
 
-with C = 100 for 4x4 and 8x8 matrices (a few rounding errors per entry,
+with C = 100 for 4x4, 8x8 and 16x16 matrices (a few rounding errors per entry,
 two sides, Frobenius norms), and never by more than 1e-11 for a
 well-conditioned E.  Independently of that bound, every result must attain
 the optimum: Re Tr(E u) = sum of singular values to 1e-12 relative, the
@@ -110,6 +110,12 @@ def test_optimize_gates_8x8_ill_conditioned(qf):
     Es, sigs = _cases(8, 12001)
     U, S = qf.optimize_gates_k(torch.from_numpy(Es).cuda())
     _check(U.cpu().numpy(), S.cpu().numpy(), Es, sigs, "8x8")
+
+
+def test_optimize_gates_16x16_ill_conditioned(qf):
+    Es, sigs = _cases(16, 12002)
+    U, S = qf.optimize_gates_k(torch.from_numpy(Es).cuda())
+    _check(U.cpu().numpy(), S.cpu().numpy(), Es, sigs, "16x16")
 
 
 # ---------------------------------------------------------------- in sweeps
