@@ -283,9 +283,11 @@ typedef struct {
 /* qf_instantiate_ex for a circuit of 2-, 3- and 4-qubit gates.  locations:
  * host-or-device, n_gates entries; initial_gates and out_gates:
  * host-or-device, n_starts x E entries (see above).  The three-qubit
- * updates use the 8x8 FP64 polar (one-sided Jacobi on one warp), the
- * four-qubit updates the 16x16 FP64 polar (one-sided Jacobi on one CTA of
- * 256 threads); the look-ahead and the one-pass InitCircuitTensor apply to
+ * updates use the 8x8 polar on one warp, the four-qubit updates the 16x16
+ * polar on one CTA of 256 threads: an FP32 one-sided Jacobi SVD, then FP64
+ * refinement rounds (FP64 Jacobi sweeps when a singular value is below
+ * 1e-3 of the largest), accurate to FP64 rounding within the polar
+ * factor's conditioning; the look-ahead and the one-pass InitCircuitTensor apply to
  * two-qubit-only circuits, qf_instantiate_batched_k takes 2- and 3-qubit
  * gates.  Errors as qf_instantiate_ex, QF_EINVAL for k
  * outside {2, 3, 4}, k > n_qubits, repeated or out-of-range qubits. */
