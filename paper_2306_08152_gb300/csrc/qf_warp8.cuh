@@ -213,16 +213,16 @@ __device__ __forceinline__ void jacobi8(const L8& L, C2& w0, C2& w1, C2& y0, C2&
       const R nrm = sqrt(al) * sqrt(be);
       const R tiny = sizeof(R) == 4 ? R(1e-12) : R(1e-200);
       if (gm0 > tol * R(0.01) * nrm && fmax(al, be) > tiny && gm0 > R(0)) {
-        const R gxs = gx / gm0, gys = gy / gm0;
-        const R hs = sqrt(gxs * gxs + gys * gys);
-        const R gm = gm0 * hs;
-        off = fmax(off, gm / nrm);
-        const R zeta = R(0.5) * (be - al) / gm;
-        const R t = copysign(R(1) / (fabs(zeta) + sqrt(R(1) + zeta * zeta)), zeta);
-        const R c = R(1) / sqrt(R(1) + t * t), sn = c * t;
+        const float gxs = __fdividef(gx, gm0), gys = __fdividef(gy, gm0);
+        const float rr = rsqrtf(gxs * gxs + gys * gys);
+        const float gm = gm0 * (gxs * gxs + gys * gys) * rr;
+        off = fmaxf(off, __fdividef(gm, nrm));
+        const float zeta = 0.5f * __fdividef(be - al, gm), az = fabsf(zeta);
+        const float t = az > 1e18f ? __fdividef(0.5f, zeta) : copysignf(__fdividef(1.f, az + sqrtf(1.f + az * az)), zeta);
+        const float c = rsqrtf(1.f + t * t), sn = c * t;
         C2 e;  // conj(g) / |g|
-        e.x = gxs / hs;
-        e.y = -gys / hs;
+        e.x = gxs * rr;
+        e.y = -gys * rr;
         if (isP) {  // W[:,p] <- c W[:,p] - s e W[:,q]
           const C2 e0 = cmul(e, wq0), e1 = cmul(e, wq1), f0 = cmul(e, yq0), f1 = cmul(e, yq1);
           w0.x = c * w0.x - sn * e0.x; w0.y = c * w0.y - sn * e0.y;
@@ -368,7 +368,8 @@ __device__ __noinline__ double polar8_rare(double2 as0, double2 as1, float2 fy0,
 //      M = A u (Hermitian positive definite at the optimum), and
 //      u <- u (I - W + W^2 / 2) with W the solution of H W + W H = M - M^dagger
 //      in X's eigenbasis (W'_ij = K'_ij / (d_i + d_j), FP32): each round
-//      squares the error, two FP64 8x8 products a round;
+//      squares the error, two FP64 8x8 products a round; *sig = Re Tr(A u)
+//      of the final u;
 //   3. otherwise polar8_rare.
 // y_io: nullptr, or the 64-entry row-major FP32 rotation of the previous
 // update (read, then rewritten with this update's; lane (g, j) touches
@@ -467,17 +468,6 @@ __device__ __noinline__ bool warp_polar8(double2 a0, double2 a1, double2* sm, do
     w1 = make_double2(w1.x + (double)D1.x, w1.y + (double)D1.y);
     if (om < wtol) break;
   }
-  // sum of singular values = Re Tr(A u) = Re Tr(M) + Re Tr(A D) (M from the
-  // last round, before D was added; Tr(A D) is small, FP32 suffices)
-  const float2 dt0 = get8(D0, D1, L.j, L.g), dt1 = get8(D0, D1, L.j, L.g + 4);  // D[j][g], D[j][g+4]
-  float trd = fa0.x * dt0.x - fa0.y * dt0.y + fa1.x * dt1.x - fa1.y * dt1.y;
-#pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) trd += __shfl_xor_sync(kFull, trd, h);
-  double trm = 0.0;
-#pragma unroll
-  for (int g = 0; g < 4; ++g)  // M[g][g] at lane 9 g, M[g+4][g+4] at lane 9 g + 4
-    trm += __shfl_sync(kFull, M0.x, 9 * g) + __shfl_sync(kFull, M1.x, 9 * g + 4);
-  *sig = (trm + (double)trd) * unscale;
   {  // final Newton-Schulz step: unitary to FP64 rounding whatever the last D
     double2 P0, P1;
     mm8_dn(L, w0, w1, w0, w1, P0, P1);
@@ -487,6 +477,16 @@ __device__ __noinline__ bool warp_polar8(double2 a0, double2 a1, double2* sm, do
     mm8(L, to_f2(w0), to_f2(w1), Pm0, Pm1, c0, c1);
     w0 = make_double2(w0.x - 0.5 * (double)c0.x, w0.y - 0.5 * (double)c0.y);
     w1 = make_double2(w1.x - 0.5 * (double)c1.x, w1.y - 0.5 * (double)c1.y);
+  }
+  // sum of singular values = Re Tr(A u) of the final u, in FP64: the last
+  // Newton-Schulz step moves Re Tr(A u) to first order in u's distance from
+  // unitarity, which the FP32 correction leaves near FP64 rounding only
+  {
+    const double2 ut0 = get8(w0, w1, L.j, L.g), ut1 = get8(w0, w1, L.j, L.g + 4);  // u[j][g], u[j][g+4]
+    double tr = as0.x * ut0.x - as0.y * ut0.y + as1.x * ut1.x - as1.y * ut1.y;
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) tr += __shfl_xor_sync(kFull, tr, h);
+    *sig = tr * unscale;
   }
   *u0 = w0;
   *u1 = w1;
