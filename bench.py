@@ -62,8 +62,10 @@ def parse():
     ap.add_argument("--no-spec", action="store_true")
     ap.add_argument("--oracle-1core", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--profile-case", choices=["k4", "k3", "pair", "pass", "batched", "batched_k"], default=None,
-                    help="run one small case of a kernel family for a profiler capture (12 qubits, "
-                         "2 starts, complex64, one live sweep after one warm-up sweep) and exit")
+                    help="run one small case of a kernel family for a profiler capture and exit: "
+                         "k4/k3/pair/pass: 12 qubits, 2 starts, complex64, one live sweep after one "
+                         "warm-up sweep; batched/batched_k: the first 512/256 instances of the "
+                         "benchmark's batches, an autotuning call then one run")
     return ap.parse_args()
 
 
