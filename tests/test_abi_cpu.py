@@ -199,3 +199,69 @@ def test_spec_helpers_match_the_slot_rule():
     assert qf.spec_slots(specs, 3) == [(2, 1), (0, 3), (1, 2), (0, 1), (0, 1, 2), (1, 2)]
     with pytest.raises(ValueError):
         qf.gate_specs([("cx", 0, 1)])
+
+
+def _call_batched_k(lib, n, gates, S=1, precision=None, n_instances=1):
+    """qf_instantiate_batched_k on one instance of n qubits with the given
+    (k, qubits) gates; host arrays, default options."""
+    from paper_2306_08152_gb300 import _native as nat
+
+    p = len(gates)
+    locs = (nat.qf_gate_loc * max(p, 1))()
+    for i, (k, qs) in enumerate(gates):
+        locs[i].k = k
+        for j, q in enumerate(qs):
+            locs[i].q[j] = q
+    nq = np.full(max(n_instances, 1), n, dtype=np.int32)
+    ng = np.full(max(n_instances, 1), p, dtype=np.int32)
+    V = np.eye(2**n, dtype=np.complex128)
+    g = np.zeros(S * max(p, 1) * 256, dtype=np.complex128)
+    out = np.zeros_like(g)
+    costs = np.zeros(S * max(n_instances, 1))
+    sweeps = np.zeros(S * max(n_instances, 1), dtype=np.int32)
+    best = np.zeros(max(n_instances, 1), dtype=np.int32)
+    stats = nat.qf_batch_stats()
+    opts = None
+    if precision is not None:
+        opts = nat.qf_options()
+        lib.qf_options_default(ct.byref(opts))
+        opts.precision = precision
+    return lib.qf_instantiate_batched_k(n_instances, nq.ctypes.data, ng.ctypes.data, locs, V.ctypes.data, S,
+                                        g.ctypes.data, ct.byref(opts) if opts is not None else None,
+                                        out.ctypes.data, costs.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                        sweeps.ctypes.data, best.ctypes.data, ct.byref(stats), None)
+
+
+@pytest.mark.parametrize("n,gates,msg", [
+    (4, [(4, (0, 1, 2, 3))], b"2 or 3 qubits"),
+    (3, [(1, (0,))], b"2 or 3 qubits"),
+    (3, [(3, (0, 1, 1))], b"repeated qubit"),
+    (3, [(2, (2, 2))], b"repeated qubit"),
+    (3, [(3, (0, 1, 3))], b"invalid location"),
+    (3, [(2, (-1, 0))], b"invalid location"),
+    (2, [(3, (0, 1, 2))], b"invalid location"),
+    (3, [(2, (0, 1)), (3, (2, 1, 5))], b"invalid location"),
+])
+def test_batched_k_rejects_invalid_gates_before_any_cuda_call(lib, n, gates, msg):
+    from paper_2306_08152_gb300 import _native as nat
+
+    assert _call_batched_k(lib, n, gates) == nat.QF_EINVAL
+    assert msg in lib.qf_last_error(), lib.qf_last_error()
+
+
+def test_batched_k_rejects_invalid_sizes_and_precisions(lib):
+    from paper_2306_08152_gb300 import _native as nat
+
+    ok_gates = [(3, (0, 1, 2))]
+    assert _call_batched_k(lib, 3, ok_gates, n_instances=0) == nat.QF_EINVAL
+    assert b"n_instances" in lib.qf_last_error()
+    assert _call_batched_k(lib, 3, ok_gates, S=0) == nat.QF_EINVAL
+    assert _call_batched_k(lib, 1, [(2, (0, 1))]) == nat.QF_EINVAL
+    assert b"qubit count" in lib.qf_last_error()
+    assert _call_batched_k(lib, 3, []) == nat.QF_EINVAL
+    assert b"no gates" in lib.qf_last_error()
+    for prec in (nat.QF_DF64, nat.QF_C64_REFINE_DF):
+        assert _call_batched_k(lib, 3, ok_gates, precision=prec) == nat.QF_EINVAL
+        assert b"batched kernel takes" in lib.qf_last_error()
+    assert _call_batched_k(lib, 3, ok_gates, precision=9) == nat.QF_EINVAL
+    assert b"unknown precision" in lib.qf_last_error()
