@@ -265,3 +265,53 @@ def test_batched_k_rejects_invalid_sizes_and_precisions(lib):
         assert b"batched kernel takes" in lib.qf_last_error()
     assert _call_batched_k(lib, 3, ok_gates, precision=9) == nat.QF_EINVAL
     assert b"unknown precision" in lib.qf_last_error()
+
+
+def _call_instantiate_k(lib, n, gates, S=1):
+    from paper_2306_08152_gb300 import _native as nat
+
+    p = len(gates)
+    locs = (nat.qf_gate_loc * max(p, 1))()
+    for i, (k, qs) in enumerate(gates):
+        locs[i].k = k
+        for j, q in enumerate(qs):
+            locs[i].q[j] = q
+    V = np.eye(2**n, dtype=np.complex128)
+    g = np.zeros(max(S, 1) * max(p, 1) * 256, dtype=np.complex128)
+    out = np.zeros_like(g)
+    costs = (ct.c_double * max(S, 1))()
+    res = nat.qf_result()
+    return lib.qf_instantiate_k(V.ctypes.data, n, p, locs, S, g.ctypes.data, None, out.ctypes.data, costs,
+                                ct.byref(res), None)
+
+
+@pytest.mark.parametrize("n,gates,S,msg", [
+    (4, [(5, (0, 1, 2, 3))], 1, b"must be 2, 3 or 4"),
+    (4, [(4, (0, 1, 2, 2))], 1, b"repeated qubit"),
+    (4, [(4, (0, 1, 2, 4))], 1, b"invalid for 4 qubits"),
+    (3, [(4, (0, 1, 2, 3))], 1, b"invalid for 3 qubits"),
+    (3, [(2, (0, 0))], 1, b"repeated qubit"),
+    (3, [], 1, b"n_gates"),
+    (1, [(2, (0, 1))], 1, b"n_qubits"),
+    (15, [(2, (0, 1))], 1, b"n_qubits"),
+    (3, [(2, (0, 1))], 0, b"n_starts"),
+])
+def test_instantiate_k_rejects_invalid_arguments_before_any_cuda_call(lib, n, gates, S, msg):
+    from paper_2306_08152_gb300 import _native as nat
+
+    assert _call_instantiate_k(lib, n, gates, S) == nat.QF_EINVAL
+    assert msg in lib.qf_last_error(), lib.qf_last_error()
+
+
+def test_valid_call_without_a_gpu_fails_loudly(lib):
+    """No CPU fallback: with no CUDA device a valid call returns a CUDA or
+    memory error and says why."""
+    import torch
+
+    from paper_2306_08152_gb300 import _native as nat
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    rc = _call_instantiate_k(lib, 3, [(3, (0, 1, 2))])
+    assert rc in (nat.QF_ENOMEM, nat.QF_ECUDA), rc
+    assert lib.qf_last_error()
