@@ -315,3 +315,35 @@ def test_valid_call_without_a_gpu_fails_loudly(lib):
     rc = _call_instantiate_k(lib, 3, [(3, (0, 1, 2))])
     assert rc in (nat.QF_ENOMEM, nat.QF_ECUDA), rc
     assert lib.qf_last_error()
+
+
+def test_every_entry_point_rejects_null_pointers(lib):
+    """Every call of the boundary, given NULL for each pointer argument and
+    small sizes, returns QF_EINVAL with a message (qf_plan_destroy(NULL) is
+    a no-op, like free(NULL)); none dereferences a NULL pointer."""
+    from paper_2306_08152_gb300 import _native as nat
+
+    skip = {"qf_last_error", "qf_version", "qf_set_tc_wait_limit", "qf_options_default"}
+    checked = 0
+    for name in declared_functions():
+        if name in skip:
+            continue
+        fn = getattr(lib, name)
+        args = []
+        for t in fn.argtypes:
+            if t in (ct.c_int, ct.c_int32):
+                args.append(3)
+            elif t is ct.c_double:
+                args.append(0.0)
+            elif t is ct.c_int64:
+                args.append(8)
+            else:
+                args.append(None)
+        rc = fn(*args)
+        if name == "qf_plan_destroy":
+            assert rc == 0
+            continue
+        assert rc == nat.QF_EINVAL, (name, rc, lib.qf_last_error())
+        assert lib.qf_last_error(), name
+        checked += 1
+    assert checked >= 40
